@@ -1,0 +1,176 @@
+/*
+ * mixts.h -- C ABI of the GB300 mixTS-PIMD hot path (arXiv 2411.11988, "MixPI").
+ *
+ * One system = atoms of n_types types; type t carries P_t beads (a power of
+ * two, Sec. "Setup"; every pair of counts then has the integer ratio the
+ * sequential Trotter splitting needs, Sec. "MixTS Ring Polymer Hamiltonian").
+ * The potential is V_mix of Eq. (mts-hamiltonian): every interaction is
+ * evaluated on the finer participant's bead grid, bead b of the finer
+ * particle i meeting bead floor(b P_j / P_i) of j, with weight 1/P_i.
+ * The dynamics is the split propagator of Sec. "Evaluation" (exact normal-mode
+ * free ring polymer between half kicks of V_mix) inside PILE thermostat half
+ * steps (Sec. "System I"). Estimators follow Sec. "Output and Analysis".
+ *
+ * Units: A, fs, amu, e; energies kcal/mol, forces kcal/mol/A, momenta
+ * amu A/fs, pseudopotential amplitudes eV.
+ *
+ * Bead layout of every per-bead array (q, p, f): FP64, [n_beads][3], blocked
+ * by type in type-index order; inside the block of type t (P_t beads, N_t
+ * atoms) bead b of the atom of within-type rank k is row off_t + b*N_t + k.
+ *
+ * Ownership: the caller owns q, p, f and the workspace (device memory,
+ * e.g. torch tensors). The library owns only the host handle; it calls no
+ * cudaMalloc. All device work is queued on the caller's stream.
+ *
+ * Errors: every entry point returns a mixts_status. Conditions detected on
+ * the device (neighbour-list overflow, non-finite or out-of-range forces,
+ * list radius beyond what [-2,2]^3 images cover) are latched in a device
+ * word and reported by the next synchronising call (mixts_forces with an
+ * energy pointer, mixts_estimators, mixts_get_state, mixts_nlist).
+ * mixts_last_error gives text for the last failure of a handle.
+ */
+#ifndef MIXTS_H
+#define MIXTS_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MIXTS_MAX_TYPES 16
+
+#if defined(__GNUC__)
+#define MIXTS_API __attribute__((visibility("default")))
+#else
+#define MIXTS_API
+#endif
+
+typedef struct mixts_ctx* mixts_handle;
+
+typedef enum {
+  MIXTS_OK = 0,
+  MIXTS_ERR_ARG = 1,            /* bad argument, NULL pointer, size mismatch */
+  MIXTS_ERR_BEADS = 2,          /* a bead count is not a power of two, or a pseudo particle is coarser than a site */
+  MIXTS_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  MIXTS_ERR_WORKSPACE = 4,      /* workspace too small or misaligned (256 B) */
+  MIXTS_ERR_NLIST_OVERFLOW = 5, /* an owner row outgrew nlist_cap; re-create with a larger cap */
+  MIXTS_ERR_TIMEOUT = 6,        /* a bounded device wait expired */
+  MIXTS_ERR_NONFINITE = 7,      /* non-finite or out-of-range force/energy */
+  MIXTS_ERR_STATE = 8,          /* state blob does not match this handle */
+  MIXTS_ERR_BOX = 9             /* list radius >= 2 L: the periodic box is too small */
+} mixts_status;
+
+typedef enum { MIXTS_FP64 = 0, MIXTS_FP32_FORCES = 1 } mixts_precision;
+
+/* One system. All arrays are HOST pointers read during mixts_init, except
+ * q, p, f which are caller-owned DEVICE arrays used for the handle's life. */
+typedef struct {
+  int n_atoms, n_types;
+  const int* type_of_atom;    /* [n_atoms] */
+  const int* mol_of_atom;     /* [n_atoms]; same molecule, zero image: no nonbonded term */
+  const int* P_type;          /* [n_types] bead counts, powers of two, <= 1024 */
+  const double* mass_type;    /* [n_types] amu; the bead mass equals the physical mass */
+  const double* charge_type;  /* [n_types] e */
+  const double* lj_eps;       /* [n_types*n_types] kcal/mol, symmetric */
+  const double* lj_sig;       /* [n_types*n_types] A */
+  const int* pseudo_type;     /* [n_types] 1: particle meets sites only through the pseudopotential */
+  const double* pp_sigma;     /* [n_types] site parameters of V(r) = -k_e q erf(r/sigma)/r + A exp(-r/b) */
+  const double* pp_A_eV;      /* [n_types] */
+  const double* pp_b;         /* [n_types] */
+  int n_bonds;
+  const int* bonds;           /* [n_bonds*2] atom indices */
+  const double* bond_k;       /* [n_bonds] kcal/mol/A^2, V = k/2 (r - r0)^2 */
+  const double* bond_r0;      /* [n_bonds] A */
+  int n_angles;
+  const int* angles;          /* [n_angles*3] atom indices, vertex in the middle */
+  const double* angle_k;      /* [n_angles] kcal/mol/rad^2, V = k/2 (theta - theta0)^2 */
+  const double* angle_theta0; /* [n_angles] rad */
+  double box;                 /* cubic periodic box edge, A */
+  double* q;                  /* DEVICE [n_beads][3] positions (unwrapped ring polymers) */
+  double* p;                  /* DEVICE [n_beads][3] momenta */
+  double* f;                  /* DEVICE [n_beads][3] forces, written by the library */
+  uint64_t seed;              /* Philox key of the thermostat noise */
+} mixts_system;
+
+typedef struct {
+  double T;            /* K */
+  double dt;           /* fs */
+  double tau_centroid; /* fs, centroid Langevin time; <= 0: off */
+  double pile_lambda;  /* internal modes get friction 2*lambda*omega_k; 0: off */
+  double r_cut;        /* A, cutoff of every nonbonded and pseudopotential term */
+  double dsf_alpha;    /* 1/A, damping of the damped-shifted-force Coulomb */
+  int precision;       /* mixts_precision */
+  int nlist_cap;       /* entries per owner row of the neighbour list; 0: automatic */
+} mixts_params;
+
+/* Estimates of the state after the last completed step (or of the current
+ * state after mixts_forces). Energies kcal/mol, Rg2 A^2. */
+typedef struct {
+  double V, V_lj, V_coul, V_bond, V_angle, V_pseudo;
+  double KE_beads;   /* sum p^2/2m over beads */
+  double E_spring;   /* ring-polymer spring energy of Eq. (mts-hamiltonian-b) */
+  double virial;     /* sum over bead-pair terms of r . f */
+  double T_beads;    /* K, 2 KE_beads / (3 n_beads k_B) */
+  double H_mix;      /* KE_beads + E_spring + V */
+  double heat;       /* minus the kinetic energy the thermostat added */
+  double H_conserved;/* H_mix + heat */
+  double n_evals;    /* nonbonded bead-pair terms inside r_cut (algorithmic count) */
+  double n_pseudo_evals;
+  double KE_prim[MIXTS_MAX_TYPES]; /* primitive kinetic estimator per type */
+  double KE_cv[MIXTS_MAX_TYPES];   /* centroid-virial kinetic estimator per type */
+  double Rg2[MIXTS_MAX_TYPES];     /* mean squared bead distance from the centroid */
+  double E_spring_t[MIXTS_MAX_TYPES];
+  int64_t step;                    /* completed steps */
+} mixts_estimates;
+
+/* Bytes of device workspace mixts_init needs for these systems. */
+MIXTS_API size_t mixts_workspace_size(const mixts_system* sys, int n_sys, const mixts_params* prm);
+
+/* Validate, build tables, carve the workspace (256-byte aligned, owned by
+ * the caller, must outlive the handle). stream is a cudaStream_t (NULL:
+ * legacy default stream). The current CUDA device must hold q, p, f and the
+ * workspace. n_sys must be 1 in this version. */
+MIXTS_API mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* prm, void* workspace,
+                        size_t ws_bytes, void* stream, mixts_handle* out);
+
+/* F <- -dV_mix/dq at the current q (neighbour list rebuilt from q), written
+ * to sys.f. If energy_host is not NULL it receives V (one per system) and
+ * the call synchronises; otherwise it is asynchronous. Reads the caller's q
+ * afresh; the next mixts_step restarts from the caller's q and p. */
+MIXTS_API mixts_status mixts_forces(mixts_handle h, double* energy_host);
+
+/* Advance n_steps OBABO steps (asynchronous). On return (in stream order)
+ * sys.q, sys.p and sys.f hold the state after the last step. */
+MIXTS_API mixts_status mixts_step(mixts_handle h, int n_steps);
+
+/* Synchronise and return the estimates of the last completed step. */
+MIXTS_API mixts_status mixts_estimators(mixts_handle h, mixts_estimates* out_host);
+
+/* Synchronise and copy the neighbour list of the last force evaluation:
+ * triplets (owner atom, partner atom, image code (nx+2)*25+(ny+2)*5+(nz+2)),
+ * unordered. n_out gets the count; thresh_host (3 doubles, may be NULL) gets
+ * d_max, the list radius r_cut + 2 d_max, and the pseudo-list radius.
+ * kind 0: nonbonded list, 1: pseudo-particle site list. */
+MIXTS_API mixts_status mixts_nlist(mixts_handle h, int kind, int* out3_host, long cap, long* n_out, double* thresh_host);
+
+/* Opaque checkpoint of the whole dynamical state (normal-mode coordinates,
+ * step counter, thermostat heat): size, save (synchronises), restore. A
+ * restore followed by n steps reproduces the saved run bit for bit. */
+MIXTS_API size_t mixts_state_size(mixts_handle h);
+MIXTS_API mixts_status mixts_get_state(mixts_handle h, void* blob_host, size_t bytes);
+MIXTS_API mixts_status mixts_set_state(mixts_handle h, const void* blob_host, size_t bytes);
+
+/* Test hook: standard normals of the thermostat stream (Philox4x32-10 and
+ * the binary32 Box-Muller transform) for dofs [dof0, dof0+n), written to a
+ * DEVICE float array on the handle's stream. */
+MIXTS_API mixts_status mixts_gaussians(mixts_handle h, uint32_t step, uint32_t stage, uint64_t dof0, long n,
+                             float* out_dev);
+
+MIXTS_API void mixts_destroy(mixts_handle h);
+MIXTS_API const char* mixts_last_error(mixts_handle h);
+MIXTS_API const char* mixts_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,630 @@
+// k_prop.cu -- ring-polymer propagation: normal-mode transforms, PILE
+// thermostat half steps, half kicks and the exact free-ring rotation of the
+// split propagator (Sec. "Evaluation"), plus the per-step estimator partials
+// (Sec. "Output and Analysis") and the position mirrors the force kernels read.
+//
+// Types with P <= SMALL_P: one CTA owns all P beads of a few atoms (a P x C
+// column tile, C = 3 * atoms) in shared memory and runs transform ->
+// elementwise update -> inverse transform in one pass. Types with larger P
+// (the 1024-bead electron) split the transforms over many CTAs by mode/bead
+// blocks, with the cosine table in shared memory.
+#include <math.h>
+
+#include "mixts_internal.cuh"
+
+namespace mx {
+
+constexpr int PROP_THREADS = 128;
+constexpr int NPART = 6;  // KE, spring, CV, Rg, heat(end), heat(start)
+
+__device__ __forceinline__ void block_sum6(double* v, double* red) {
+  // v[NPART] per thread -> red[0..NPART) on thread 0, fixed order
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NPART; ++i) v[i] = warp_sum(v[i]);
+  __syncthreads();
+  if (lane == 0)
+    for (int i = 0; i < NPART; ++i) red[w * NPART + i] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NPART; ++i) {
+      double s = 0.0;
+      for (int x = 0; x < nw; ++x) s += red[x * NPART + i];
+      red[i] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// writes the force-kernel mirrors of one atom's beads. xc(j, d) is the
+// Cartesian coordinate of bead j; rows r(j) = row0 + j * stride.
+struct MirrorOut {
+  __device__ static void wrap_ref(double x, double L, double* fl_out, double* ref_out) {
+    const double fl = floor(__ddiv_rn(x, L));
+    *fl_out = fl;
+    *ref_out = __dsub_rn(x, __dmul_rn(L, fl));
+  }
+};
+
+__device__ __forceinline__ void write_mirror(const Dev& d, int row, double x, double y, double z, double mx_,
+                                             double my_, double mz_) {
+  const double L = d.box;
+  const double wx = x - mx_ * L, wy = y - my_ * L, wz = z - mz_ * L;
+  d.Xw[row] = make_double4_32a(wx, wy, wz, 0.0);
+  // FP32 mirror: hi on the 2^-12 A grid (exact differences), lo the rest
+  const float hx = (float)(rint(wx * 4096.0) * (1.0 / 4096.0));
+  const float hy = (float)(rint(wy * 4096.0) * (1.0 / 4096.0));
+  const float hz = (float)(rint(wz * 4096.0) * (1.0 / 4096.0));
+  d.Xf[row] = make_float4(hx, hy, hz, 0.0f);
+  d.Xl[row] = make_float4((float)(wx - (double)hx), (float)(wy - (double)hy), (float)(wz - (double)hz), 0.0f);
+}
+
+__device__ __forceinline__ double bead_dist(double dx, double dy, double dz) {
+  double d2 = __dmul_rn(dx, dx);
+  d2 = __dadd_rn(d2, __dmul_rn(dy, dy));
+  d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
+  return __dsqrt_rn(d2);
+}
+
+// ---------------------------------------------------------------------------
+// small-P fused tile kernel
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PROP_THREADS) k_prop_small(Dev d, int mode) {
+  extern __shared__ double sm[];
+  __shared__ double red[(PROP_THREADS / 32) * NPART];
+  __shared__ long long s_step;
+  const PropTile tl = d.tiles[blockIdx.x];
+  const int t = tl.type, P = d.P[t], N = d.N[t], k0 = tl.k0, na = tl.na;
+  const int C = 3 * na;
+  const int PC = P * C;
+  double* Cm = sm;
+  double* Fb = Cm + P * P;
+  double* Fn = Fb + PC;
+  double* Qn = Fn + PC;
+  double* Pn = Qn + PC;
+  double* Xc = Pn + PC;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double m = d.mass[t];
+  const double* cmg = d.cm + d.cm_off[t];
+  const ModeCoef* mcf = d.mc + d.mc_off[t];
+  auto gidx = [&](int j, int c) -> size_t { return (size_t)(d.off[t] + j * N + k0) * 3 + c; };
+
+  if (tid == 0) s_step = *d.step_ctr;
+  for (int e = tid; e < P * P; e += nt) Cm[e] = cmg[e];
+  const bool need_f = (mode & (PM_END | PM_START)) != 0;
+  for (int e = tid; e < PC; e += nt) {
+    const int j = e / C, c = e - (e / C) * C;
+    const size_t g = gidx(j, c);
+    if (mode & PM_IMPORT) {
+      Xc[e] = d.q[g];
+      Fb[e] = d.p[g];
+    } else {
+      Qn[e] = d.q_nm[g];
+      Pn[e] = d.p_nm[g];
+    }
+  }
+  __syncthreads();
+  if (mode & PM_IMPORT) {
+    for (int e = tid; e < PC; e += nt) {
+      const int k = e / C, c = e - (e / C) * C;
+      double aq = 0.0, ap = 0.0;
+      for (int j = 0; j < P; ++j) {
+        aq = fma(Cm[j * P + k], Xc[j * C + c], aq);
+        ap = fma(Cm[j * P + k], Fb[j * C + c], ap);
+      }
+      Qn[e] = aq;
+      Pn[e] = ap;
+    }
+    __syncthreads();
+  }
+  double part[NPART] = {0, 0, 0, 0, 0, 0};
+  if (need_f) {
+    for (int e = tid; e < PC; e += nt) {
+      const int j = e / C, c = e - (e / C) * C;
+      const size_t g = gidx(j, c);
+      const double f = fix_to_double(d.F_fix[g], FINV);
+      Fb[e] = f;
+      if (mode & PM_END) d.f[g] = f;
+      if (mode & PM_START) d.F_fix[g] = 0ull;
+      if ((mode & PM_END) && (mode & PM_EST)) {
+        // centroid virial: sum_b (q_b - qbar) . F_b, qbar from the centroid mode
+        const double qbar = Qn[c] * rsqrt((double)P);
+        part[2] += (d.q[g] - qbar) * f;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < PC; e += nt) {
+      const int k = e / C, c = e - (e / C) * C;
+      double a = 0.0;
+      for (int j = 0; j < P; ++j) a = fma(Cm[j * P + k], Fb[j * C + c], a);
+      Fn[e] = a;
+    }
+    __syncthreads();
+    const double hk = 0.5 * d.dt * d.kcal;  // F in kcal/mol/A -> amu A/fs^2
+    const uint32_t s_end = (uint32_t)s_step;
+    const uint32_t s_start = (uint32_t)(s_step + ((mode & PM_END) ? 1 : 0));
+    const double inv2m = 0.5 / m;
+    for (int e = tid; e < PC; e += nt) {
+      const int k = e / C, c = e - (e / C) * C;
+      const ModeCoef mk = mcf[k];
+      const uint64_t dof = (uint64_t)gidx(k, c);
+      double p = Pn[e], q = Qn[e];
+      const double fk = Fn[e];
+      if (mode & PM_END) {
+        p = fma(hk, fk, p);
+        const double xi = (double)gauss_dof(d.seed, s_end, 1u, dof);
+        const double pn = fma(mk.c1, p, mk.c2s * xi);
+        part[4] += (p * p - pn * pn) * inv2m;
+        p = pn;
+        if (mode & PM_EST) {
+          part[0] += p * p * inv2m;
+          part[1] += mk.hmw2 * q * q;
+          if (k > 0) part[3] += q * q;
+        }
+      }
+      if (mode & PM_START) {
+        const double xi = (double)gauss_dof(d.seed, s_start, 0u, dof);
+        const double pn = fma(mk.c1, p, mk.c2s * xi);
+        part[5] += (p * p - pn * pn) * inv2m;
+        p = fma(hk, fk, pn);
+        // exact free ring: [p; q] <- [[cw, -m w sw], [sw/(m w), cw]] [p; q]; k = 0 drifts
+        const double pr = fma(mk.cw, p, -mk.mws * q);
+        const double qr = fma(mk.swm, p, mk.cw * q);
+        p = pr;
+        q = qr;
+      }
+      Pn[e] = p;
+      Qn[e] = q;
+    }
+    __syncthreads();
+  }
+  // write the mode-space state back
+  if (mode & (PM_IMPORT | PM_END | PM_START)) {
+    for (int e = tid; e < PC; e += nt) {
+      const int j = e / C, c = e - (e / C) * C;
+      const size_t g = gidx(j, c);
+      d.q_nm[g] = Qn[e];
+      d.p_nm[g] = Pn[e];
+    }
+  }
+  // Cartesian positions and mirrors
+  if (mode & (PM_START | PM_QCART)) {
+    for (int e = tid; e < PC; e += nt) {
+      const int j = e / C, c = e - (e / C) * C;
+      double a = 0.0;
+      for (int k = 0; k < P; ++k) a = fma(Cm[j * P + k], Qn[k * C + c], a);
+      Xc[e] = a;
+      d.q[gidx(j, c)] = a;
+    }
+    __syncthreads();
+    for (int e = tid; e < P * na; e += nt) {
+      const int j = e / na, a = e - (e / na) * na;
+      const int atom = d.atom_of_tk[d.atoff[t] + k0 + a];
+      double fl[3], rf[3];
+      for (int x = 0; x < 3; ++x) MirrorOut::wrap_ref(Xc[0 * C + 3 * a + x], d.box, &fl[x], &rf[x]);
+      const int row = d.off[t] + j * N + k0 + a;
+      write_mirror(d, row, Xc[j * C + 3 * a], Xc[j * C + 3 * a + 1], Xc[j * C + 3 * a + 2], fl[0], fl[1], fl[2]);
+      if (j == 0) {
+        for (int x = 0; x < 3; ++x) d.ref[3 * atom + x] = rf[x];
+        double sp = 0.0;
+        for (int b = 1; b < P; ++b) {
+          const double dd = bead_dist(Xc[b * C + 3 * a] - Xc[3 * a], Xc[b * C + 3 * a + 1] - Xc[3 * a + 1],
+                                      Xc[b * C + 3 * a + 2] - Xc[3 * a + 2]);
+          sp = dd > sp ? dd : sp;
+        }
+        d.spread[(size_t)atom * d.spread_slots] = sp;
+        for (int s = 1; s < d.spread_slots; ++s) d.spread[(size_t)atom * d.spread_slots + s] = 0.0;
+      }
+    }
+  }
+  if (mode & PM_PCART) {
+    for (int e = tid; e < PC; e += nt) {
+      const int j = e / C, c = e - (e / C) * C;
+      double a = 0.0;
+      for (int k = 0; k < P; ++k) a = fma(Cm[j * P + k], Pn[k * C + c], a);
+      d.p[gidx(j, c)] = a;
+    }
+  }
+  if (mode & (PM_END | PM_START)) {
+    block_sum6(part, red);
+    if (tid == 0)
+      for (int i = 0; i < NPART; ++i) d.parts[(size_t)tl.slot * NPART + i] = red[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// mirrors straight from the caller's Cartesian q (force evaluation without
+// touching the mode-space state); one thread per atom
+// ---------------------------------------------------------------------------
+__global__ void k_mirror_from_q(Dev d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_atoms) return;
+  int t = 0;
+  while (t + 1 < d.n_types && d.atoff[t + 1] <= i) ++t;
+  const int k = i - d.atoff[t];
+  const int atom = d.atom_of_tk[i];
+  const int P = d.P[t], N = d.N[t];
+  const int r0 = d.off[t] + k;
+  double q0[3], fl[3], rf[3];
+  for (int x = 0; x < 3; ++x) {
+    q0[x] = d.q[3 * (size_t)r0 + x];
+    MirrorOut::wrap_ref(q0[x], d.box, &fl[x], &rf[x]);
+    d.ref[3 * atom + x] = rf[x];
+  }
+  double sp = 0.0;
+  for (int j = 0; j < P; ++j) {
+    const size_t row = (size_t)r0 + (size_t)j * N;
+    const double x = d.q[3 * row], y = d.q[3 * row + 1], z = d.q[3 * row + 2];
+    write_mirror(d, (int)row, x, y, z, fl[0], fl[1], fl[2]);
+    if (j > 0) {
+      const double dd = bead_dist(x - q0[0], y - q0[1], z - q0[2]);
+      sp = dd > sp ? dd : sp;
+    }
+  }
+  d.spread[(size_t)atom * d.spread_slots] = sp;
+  for (int s = 1; s < d.spread_slots; ++s) d.spread[(size_t)atom * d.spread_slots + s] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// large-P path
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cjk(const double* T, int P, int j, int k, double rP, double r2P) {
+  if (k == 0) return rP;
+  if (2 * k < P) return r2P * T[(j * k) & (P - 1)];
+  if (2 * k == P) return (j & 1) ? -rP : rP;
+  return r2P * T[(j * k - P / 4) & (P - 1)];  // sin(2 pi jk / P) = cos(2 pi (jk - P/4) / P)
+}
+
+constexpr int BIG_THREADS = 256;
+
+// forward transforms (C^T x) of this block's BIG_MB modes and the elementwise
+// step on them
+__global__ void __launch_bounds__(BIG_THREADS) k_big_fwd(Dev d, int t, int mode) {
+  extern __shared__ double sm[];
+  const int P = d.P[t], N = d.N[t], C = 3 * N;
+  double* T = sm;                       // [P]
+  double* Fn = T + P;                   // [BIG_MB*C]
+  double* Qi = Fn + BIG_MB * C;         // [BIG_MB*C] imported q modes
+  double* Pi = Qi + BIG_MB * C;         // [BIG_MB*C]
+  double* qbar = Pi + BIG_MB * C;       // [C]
+  __shared__ double red[(BIG_THREADS / 32) * NPART];
+  __shared__ long long s_step;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int kb = blockIdx.x * BIG_MB;
+  const double rP = rsqrt((double)P), r2P = sqrt(2.0 / P);
+  const double* cmg = d.cm + d.cm_off[t];
+  const ModeCoef* mcf = d.mc + d.mc_off[t];
+  const size_t base = (size_t)d.off[t] * 3;  // element (j, c) at base + j*C + c
+  if (tid == 0) s_step = *d.step_ctr;
+  for (int e = tid; e < P; e += blockDim.x) T[e] = cmg[e];
+  __syncthreads();
+  const bool need_f = (mode & (PM_END | PM_START)) != 0;
+  const int nout = BIG_MB * C;
+  for (int o = warp; o < nout; o += nw) {
+    const int k = kb + o / C, c = o - (o / C) * C;
+    double af = 0.0, aq = 0.0, ap = 0.0;
+    for (int j = lane; j < P; j += 32) {
+      const double cj = cjk(T, P, j, k, rP, r2P);
+      const size_t g = base + (size_t)j * C + c;
+      if (need_f) af = fma(cj, fix_to_double(d.F_fix[g], FINV), af);
+      if (mode & PM_IMPORT) {
+        aq = fma(cj, d.q[g], aq);
+        ap = fma(cj, d.p[g], ap);
+      }
+    }
+    af = warp_sum(af);
+    aq = warp_sum(aq);
+    ap = warp_sum(ap);
+    if (lane == 0) {
+      Fn[o] = af;
+      Qi[o] = aq;
+      Pi[o] = ap;
+    }
+  }
+  double part[NPART] = {0, 0, 0, 0, 0, 0};
+  if ((mode & PM_END) && (mode & PM_EST)) {
+    for (int c = warp; c < C; c += nw) {
+      double a = 0.0;
+      for (int j = lane; j < P; j += 32) a += d.q[base + (size_t)j * C + c];
+      a = warp_sum(a);
+      if (lane == 0) qbar[c] = a / P;
+    }
+  }
+  __syncthreads();
+  if (need_f) {
+    // this block's bead range: caller forces and the centroid virial
+    for (int e = tid; e < nout; e += blockDim.x) {
+      const int j = kb + e / C, c = e - (e / C) * C;
+      const size_t g = base + (size_t)j * C + c;
+      const double f = fix_to_double(d.F_fix[g], FINV);
+      if (mode & PM_END) {
+        d.f[g] = f;
+        if (mode & PM_EST) part[2] += (d.q[g] - qbar[c]) * f;
+      }
+    }
+  }
+  const double m = d.mass[t];
+  const double inv2m = 0.5 / m;
+  const double hk = 0.5 * d.dt * d.kcal;
+  const uint32_t s_end = (uint32_t)s_step;
+  const uint32_t s_start = (uint32_t)(s_step + ((mode & PM_END) ? 1 : 0));
+  for (int e = tid; e < nout; e += blockDim.x) {
+    const int k = kb + e / C, c = e - (e / C) * C;
+    const size_t g = base + (size_t)k * C + c;
+    double p, q;
+    if (mode & PM_IMPORT) {
+      p = Pi[e];
+      q = Qi[e];
+    } else {
+      p = d.p_nm[g];
+      q = d.q_nm[g];
+    }
+    if (need_f) {
+      const ModeCoef mk = mcf[k];
+      const double fk = Fn[e];
+      if (mode & PM_END) {
+        p = fma(hk, fk, p);
+        const double xi = (double)gauss_dof(d.seed, s_end, 1u, (uint64_t)g);
+        const double pn = fma(mk.c1, p, mk.c2s * xi);
+        part[4] += (p * p - pn * pn) * inv2m;
+        p = pn;
+        if (mode & PM_EST) {
+          part[0] += p * p * inv2m;
+          part[1] += mk.hmw2 * q * q;
+          if (k > 0) part[3] += q * q;
+        }
+      }
+      if (mode & PM_START) {
+        const double xi = (double)gauss_dof(d.seed, s_start, 0u, (uint64_t)g);
+        const double pn = fma(mk.c1, p, mk.c2s * xi);
+        part[5] += (p * p - pn * pn) * inv2m;
+        p = fma(hk, fk, pn);
+        const double pr = fma(mk.cw, p, -mk.mws * q);
+        const double qr = fma(mk.swm, p, mk.cw * q);
+        p = pr;
+        q = qr;
+      }
+    }
+    if (mode & (PM_IMPORT | PM_END | PM_START)) {
+      d.p_nm[g] = p;
+      d.q_nm[g] = q;
+    }
+  }
+  if (need_f) {
+    block_sum6(part, red);
+    if (tid == 0)
+      for (int i = 0; i < NPART; ++i) d.parts[(size_t)(d.big_slot0[t] + blockIdx.x) * NPART + i] = red[i];
+  }
+}
+
+// inverse transforms (C x) of this block's BIG_MB beads, mirrors, spread
+__global__ void __launch_bounds__(BIG_THREADS) k_big_inv(Dev d, int t, int mode) {
+  extern __shared__ double sm[];
+  const int P = d.P[t], N = d.N[t], C = 3 * N;
+  double* T = sm;
+  double* Qc = T + P;                 // [(BIG_MB+1)*C], row 0 = bead 0, rows 1.. = own beads
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int jb = blockIdx.x * BIG_MB;
+  const double rP = rsqrt((double)P), r2P = sqrt(2.0 / P);
+  const double* cmg = d.cm + d.cm_off[t];
+  const size_t base = (size_t)d.off[t] * 3;
+  for (int e = tid; e < P; e += blockDim.x) T[e] = cmg[e];
+  __syncthreads();
+  const bool qc = (mode & (PM_START | PM_QCART)) != 0;
+  const int nout = (BIG_MB + 1) * C;
+  if (qc || (mode & PM_PCART)) {
+    for (int o = warp; o < nout; o += nw) {
+      const int r = o / C, c = o - (o / C) * C;
+      const int j = r == 0 ? 0 : jb + r - 1;
+      double aq = 0.0, ap = 0.0;
+      for (int k = lane; k < P; k += 32) {
+        const double cj = cjk(T, P, j, k, rP, r2P);
+        const size_t g = base + (size_t)k * C + c;
+        if (qc) aq = fma(cj, d.q_nm[g], aq);
+        if (mode & PM_PCART) ap = fma(cj, d.p_nm[g], ap);
+      }
+      aq = warp_sum(aq);
+      ap = warp_sum(ap);
+      if (lane == 0) {
+        if (qc) Qc[o] = aq;
+        if ((mode & PM_PCART) && r > 0) d.p[base + (size_t)j * C + c] = ap;
+      }
+    }
+  }
+  __syncthreads();
+  if (qc) {
+    for (int e = tid; e < BIG_MB * C; e += blockDim.x) {
+      const int j = jb + e / C, c = e - (e / C) * C;
+      d.q[base + (size_t)j * C + c] = Qc[C + e];
+    }
+    for (int e = tid; e < BIG_MB * N; e += blockDim.x) {
+      const int jj = e / N, a = e - (e / N) * N;
+      const int j = jb + jj;
+      const int atom = d.atom_of_tk[d.atoff[t] + a];
+      double fl[3], rf[3];
+      for (int x = 0; x < 3; ++x) MirrorOut::wrap_ref(Qc[3 * a + x], d.box, &fl[x], &rf[x]);
+      const double* xb = Qc + (size_t)(jj + 1) * C + 3 * a;
+      write_mirror(d, d.off[t] + j * N + a, xb[0], xb[1], xb[2], fl[0], fl[1], fl[2]);
+      if (jj == 0 && blockIdx.x == 0)
+        for (int x = 0; x < 3; ++x) d.ref[3 * atom + x] = rf[x];
+    }
+    // spread partial of this bead block, per atom
+    for (int a = warp; a < N; a += nw) {
+      double sp = 0.0;
+      for (int jj = lane; jj < BIG_MB; jj += 32) {
+        const int j = jb + jj;
+        if (j == 0) continue;
+        const double* xb = Qc + (size_t)(jj + 1) * C + 3 * a;
+        const double dd = bead_dist(xb[0] - Qc[3 * a], xb[1] - Qc[3 * a + 1], xb[2] - Qc[3 * a + 2]);
+        sp = dd > sp ? dd : sp;
+      }
+      for (int o = 16; o > 0; o >>= 1) sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, o));
+      if (lane == 0) {
+        const int atom = d.atom_of_tk[d.atoff[t] + a];
+        d.spread[(size_t)atom * d.spread_slots + blockIdx.x] = sp;
+      }
+    }
+  }
+  if (mode & PM_START) {
+    for (int e = tid; e < BIG_MB * C; e += blockDim.x) {
+      const int j = jb + e / C, c = e - (e / C) * C;
+      d.F_fix[base + (size_t)j * C + c] = 0ull;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// step finalisation: reduce estimator partials in a fixed order, advance the
+// step counter, clear the energy accumulators
+// ---------------------------------------------------------------------------
+__global__ void k_final(Dev d, int mode, const int* slot_type) {
+  __shared__ double acc[MT * 4 + 2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int nq = d.n_types * 4 + 2;
+  const bool have = (mode & (PM_END | PM_START)) != 0;
+  if (have) {
+    for (int x = warp; x < nq; x += nw) {
+      double a = 0.0;
+      if (x < d.n_types * 4) {
+        const int t = x / 4, qi = x % 4;
+        for (int s = lane; s < d.n_part_slots; s += 32)
+          if (slot_type[s] == t) a += d.parts[(size_t)s * NPART + qi];
+      } else {
+        const int qi = 4 + (x - d.n_types * 4);
+        for (int s = lane; s < d.n_part_slots; s += 32) a += d.parts[(size_t)s * NPART + qi];
+      }
+      a = warp_sum(a);
+      if (lane == 0) acc[x] = a;
+    }
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  double* est = d.est;
+  const double kc = d.kcal;
+  double heat = *d.heat;
+  if (have) heat += acc[d.n_types * 4] / kc;  // end-of-step thermostat half
+  if (mode & PM_END) {
+    double v[E_NSLOTS];
+    for (int i = 0; i < E_NSLOTS; ++i) v[i] = (double)(long long)d.E_fix[i] * EINV;
+    const double V = v[E_LJ] + v[E_COUL] + v[E_BOND] + v[E_ANGLE] + v[E_PSEUDO];
+    double ke = 0.0, es = 0.0;
+    for (int t = 0; t < d.n_types; ++t) {
+      ke += acc[4 * t] / kc;
+      es += acc[4 * t + 1] / kc;
+    }
+    est[0] = V;
+    est[1] = v[E_LJ];
+    est[2] = v[E_COUL];
+    est[3] = v[E_BOND];
+    est[4] = v[E_ANGLE];
+    est[5] = v[E_PSEUDO];
+    est[6] = ke;
+    est[7] = es;
+    est[8] = v[E_VIRIAL];
+    // counters are integers carried in the fixed-point slots
+    est[13] = (double)(long long)d.E_fix[E_NEVAL];
+    est[14] = (double)(long long)d.E_fix[E_NPEVAL];
+    est[9] = 2.0 * ke * kc / (3.0 * (double)d.n_beads * d.kB);
+    est[11] = heat;
+    est[10] = ke + es + V;
+    est[12] = est[10] + heat;
+    const long long st = *d.step_ctr + 1;
+    est[15] = (double)st;
+    for (int t = 0; t < d.n_types; ++t) {
+      const double nP = (double)d.N[t] * d.P[t];
+      const double espr = acc[4 * t + 1] / kc;
+      const double kT_kcal = d.kT / kc;
+      est[16 + 4 * t] = 1.5 * nP * kT_kcal - espr;
+      est[16 + 4 * t + 1] = 1.5 * d.N[t] * kT_kcal - 0.5 * acc[4 * t + 2];
+      est[16 + 4 * t + 2] = nP > 0 ? acc[4 * t + 3] / nP : 0.0;
+      est[16 + 4 * t + 3] = espr;
+    }
+    *d.step_ctr = st;
+  }
+  if (have) heat += acc[d.n_types * 4 + 1] / kc;  // start-of-step thermostat half
+  *d.heat = heat;
+  for (int i = 0; i < E_NSLOTS; ++i) d.E_fix[i] = 0ull;
+}
+
+// caller forces and the energy record after a bare force evaluation
+__global__ void k_forces_out(Dev d) {
+  const size_t n = (size_t)d.n_beads * 3;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    d.f[e] = fix_to_double(d.F_fix[e], FINV);
+    d.F_fix[e] = 0ull;
+  }
+}
+
+__global__ void k_energy_out(Dev d) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double v[E_NSLOTS];
+  for (int i = 0; i < E_NSLOTS; ++i) v[i] = (double)(long long)d.E_fix[i] * EINV;
+  d.est[0] = v[E_LJ] + v[E_COUL] + v[E_BOND] + v[E_ANGLE] + v[E_PSEUDO];
+  d.est[1] = v[E_LJ];
+  d.est[2] = v[E_COUL];
+  d.est[3] = v[E_BOND];
+  d.est[4] = v[E_ANGLE];
+  d.est[5] = v[E_PSEUDO];
+  d.est[8] = v[E_VIRIAL];
+  d.est[13] = (double)(long long)d.E_fix[E_NEVAL];
+  d.est[14] = (double)(long long)d.E_fix[E_NPEVAL];
+  for (int i = 0; i < E_NSLOTS; ++i) d.E_fix[i] = 0ull;
+}
+
+__global__ void k_gauss(Dev d, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = gauss_dof(d.seed, step, stage, dof0 + (uint64_t)i);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static size_t small_smem(int P) {
+  const int C = 3 * (128 / P);
+  return sizeof(double) * ((size_t)P * P + 5 * (size_t)P * C);
+}
+
+void launch_prop(const Dev& d, cudaStream_t s, int mode) {
+  if (mode & PM_MIRROR) {
+    k_mirror_from_q<<<(d.n_atoms + 127) / 128, 128, 0, s>>>(d);
+    return;
+  }
+  if (d.n_tiles > 0) {
+    size_t smem = 0;
+    for (int t = 0; t < d.n_types; ++t)
+      if (d.P[t] <= SMALL_P && d.N[t] > 0) smem = small_smem(d.P[t]) > smem ? small_smem(d.P[t]) : smem;
+    k_prop_small<<<d.n_tiles, PROP_THREADS, smem, s>>>(d, mode);
+  }
+  for (int t = 0; t < d.n_types; ++t) {
+    if (d.P[t] <= SMALL_P || d.N[t] == 0) continue;
+    const int C = 3 * d.N[t];
+    const int nb = d.P[t] / BIG_MB;
+    if (mode & (PM_IMPORT | PM_END | PM_START)) {
+      const size_t smem = sizeof(double) * ((size_t)d.P[t] + 3 * (size_t)BIG_MB * C + C);
+      k_big_fwd<<<nb, BIG_THREADS, smem, s>>>(d, t, mode);
+    }
+    if (mode & (PM_START | PM_QCART | PM_PCART)) {
+      const size_t smem = sizeof(double) * ((size_t)d.P[t] + (size_t)(BIG_MB + 1) * C);
+      k_big_inv<<<nb, BIG_THREADS, smem, s>>>(d, t, mode);
+    }
+  }
+}
+
+void launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type) {
+  k_final<<<1, 256, 0, s>>>(d, mode, slot_type);
+}
+
+void launch_forces_out(const Dev& d, cudaStream_t s) {
+  k_forces_out<<<296, 256, 0, s>>>(d);
+  k_energy_out<<<1, 32, 0, s>>>(d);
+}
+
+void launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n,
+                  float* out) {
+  long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_gauss<<<(int)blocks, 256, 0, s>>>(d, step, stage, dof0, n, out);
+}
+
+}  // namespace mx

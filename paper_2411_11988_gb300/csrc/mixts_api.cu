@@ -1,0 +1,818 @@
+// mixts_api.cu -- host side of the C ABI declared in include/mixts.h:
+// validation, table construction, workspace carving and the per-step launch
+// sequence (optionally replayed from a CUDA graph).
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "mixts_internal.cuh"
+
+using namespace mx;
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+
+struct Units {  // internal units: amu, A, fs; potentials kcal/mol
+  double kB, hbar, kcal, ev_kcal, ke;
+};
+
+// exact SI values of the 2019 redefinition; epsilon_0 from CODATA 2018;
+// 1 amu = 1e-3/N_A kg, so one amu A^2 fs^-2 is 1e7/N_A J
+Units units() {
+  const double h = 6.62607015e-34, e = 1.602176634e-19, kB = 1.380649e-23, NA = 6.02214076e23;
+  const double eps0 = 8.8541878128e-12;
+  const double E_md = 1.0e7 / NA;
+  Units u;
+  u.kB = kB / E_md;
+  u.hbar = h / (2.0 * PI) / (E_md * 1.0e-15);
+  u.kcal = (4184.0 / NA) / E_md;
+  u.ev_kcal = e * NA / 4184.0;
+  u.ke = e * e / (4.0 * PI * eps0) / 1.0e-10 * NA / 4184.0;
+  return u;
+}
+
+int ilog2(int x) {
+  int l = 0;
+  while ((1 << l) < x) ++l;
+  return l;
+}
+
+struct Arena {
+  size_t size = 0;
+  size_t add(size_t bytes) {
+    size_t o = (size + 255) & ~(size_t)255;
+    size = o + bytes;
+    return o;
+  }
+};
+
+// everything mixts_init derives from a system, before touching the device
+struct Plan {
+  mixts_status st = MIXTS_OK;
+  std::string why;
+  int nt = 0, na = 0, n_nonp = 0, n_pseudo = 0, n_beads = 0;
+  std::vector<int> N, off, atoff, rank, atom_of_tk;
+  std::vector<int> pos_atom, pos_mol, pos_of_atom;
+  std::vector<AtomInfo> ainfo, ainfo_atom, pinfo;
+  std::vector<int> atom_is_pseudo, pseudo_atom;
+  std::vector<PairPar> pairpar;
+  std::vector<PseudoPar> pspar;
+  std::vector<BondItem> bitems;
+  std::vector<int> bond_atoms, ang_atoms;
+  std::vector<double> bond_par, ang_par;
+  std::vector<double> cm;
+  std::vector<int> cm_off, mc_off, big_slot0;
+  std::vector<ModeCoef> mc;
+  std::vector<PropTile> tiles;
+  std::vector<int> slot_type;
+  int spread_slots = 1;
+  int nl_cap = 0, pl_cap = 0;
+  int n_classes = 0;
+  int cls_P[MAX_CLASSES], cls_log2P[MAX_CLASSES], cls_pos0[MAX_CLASSES], cls_n[MAX_CLASSES],
+      cls_item0[MAX_CLASSES + 1];
+  int n_pitems = 0, n_ppitems = 0;
+  // workspace offsets
+  Arena ar;
+  size_t o_tab = 0, tab_bytes = 0;
+  size_t o_ainfo, o_pos_atom, o_pos_mol, o_atom_of_tk, o_ainfo_atom, o_is_pseudo, o_pseudo_atom, o_pinfo,
+      o_pairpar, o_pspar, o_bitems, o_bond_atoms, o_bond_par, o_ang_atoms, o_ang_par, o_cm, o_mc, o_tiles,
+      o_slot_type;
+  size_t o_state = 0, state_bytes = 0;
+  size_t o_qnm, o_pnm, o_ffix, o_xw, o_xf, o_xl, o_ref, o_spread, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
+      o_err, o_step, o_heat, o_est, o_parts;
+};
+
+void fail(Plan& p, mixts_status s, const std::string& why) {
+  if (p.st == MIXTS_OK) {
+    p.st = s;
+    p.why = why;
+  }
+}
+
+void lj_at(double e4, double s2, double r, double* v, double* dv) {
+  const double sr2 = s2 / (r * r);
+  const double sr6 = sr2 * sr2 * sr2;
+  const double sr12 = sr6 * sr6;
+  *v = e4 * (sr12 - sr6);
+  *dv = -6.0 * e4 * (2.0 * sr12 - sr6) / r;
+}
+
+void pseudo_at(const PseudoPar& pp, double r, double* v, double* dv) {
+  const double x = r / pp.sig;
+  const double ef = erf(x);
+  const double gg = ef / r;
+  const double dg = 2.0 / sqrt(PI) * exp(-x * x) / (pp.sig * r) - ef / (r * r);
+  const double ex = exp(-r / pp.b);
+  *v = -pp.kq * gg + pp.A * ex;
+  *dv = -pp.kq * dg - (pp.A / pp.b) * ex;
+}
+
+Plan make_plan(const mixts_system* s, const mixts_params* prm) {
+  Plan p;
+  const Units u = units();
+  if (!s || !prm) {
+    fail(p, MIXTS_ERR_ARG, "NULL system or params");
+    return p;
+  }
+  p.nt = s->n_types;
+  p.na = s->n_atoms;
+  if (p.nt < 1 || p.nt > MT || p.na < 1) {
+    fail(p, MIXTS_ERR_ARG, "n_types must be 1..16 and n_atoms >= 1");
+    return p;
+  }
+  if (!s->type_of_atom || !s->mol_of_atom || !s->P_type || !s->mass_type || !s->charge_type || !s->lj_eps ||
+      !s->lj_sig || !s->pseudo_type || !s->pp_sigma || !s->pp_A_eV || !s->pp_b) {
+    fail(p, MIXTS_ERR_ARG, "NULL per-type or per-atom array");
+    return p;
+  }
+  if (!(s->box > 0.0) || !(prm->r_cut > 0.0) || !(prm->dt > 0.0) || !(prm->T > 0.0)) {
+    fail(p, MIXTS_ERR_ARG, "box, r_cut, dt and T must be positive");
+    return p;
+  }
+  for (int t = 0; t < p.nt; ++t) {
+    const int P = s->P_type[t];
+    if (P < 1 || P > 1024 || (P & (P - 1))) {
+      fail(p, MIXTS_ERR_BEADS, "bead counts must be powers of two in 1..1024");
+      return p;
+    }
+    if (!(s->mass_type[t] > 0.0)) {
+      fail(p, MIXTS_ERR_ARG, "masses must be positive");
+      return p;
+    }
+  }
+  p.N.assign(p.nt, 0);
+  p.rank.assign(p.na, 0);
+  for (int a = 0; a < p.na; ++a) {
+    const int t = s->type_of_atom[a];
+    if (t < 0 || t >= p.nt) {
+      fail(p, MIXTS_ERR_ARG, "type_of_atom out of range");
+      return p;
+    }
+    p.rank[a] = p.N[t]++;
+  }
+  p.off.assign(p.nt + 1, 0);
+  p.atoff.assign(p.nt + 1, 0);
+  for (int t = 0; t < p.nt; ++t) {
+    p.off[t + 1] = p.off[t] + p.N[t] * s->P_type[t];
+    p.atoff[t + 1] = p.atoff[t] + p.N[t];
+  }
+  p.n_beads = p.off[p.nt];
+  p.atom_of_tk.assign(p.na, 0);
+  p.ainfo_atom.resize(p.na);
+  p.atom_is_pseudo.assign(p.na, 0);
+  for (int a = 0; a < p.na; ++a) {
+    const int t = s->type_of_atom[a];
+    p.atom_of_tk[p.atoff[t] + p.rank[a]] = a;
+    p.ainfo_atom[a] = AtomInfo{p.off[t] + p.rank[a], p.N[t], ilog2(s->P_type[t]), t};
+    p.atom_is_pseudo[a] = s->pseudo_type[t] ? 1 : 0;
+  }
+  // sorted positions of non-pseudo atoms: P descending, index ascending
+  std::vector<int> order;
+  for (int a = 0; a < p.na; ++a)
+    if (!p.atom_is_pseudo[a]) order.push_back(a);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return s->P_type[s->type_of_atom[x]] > s->P_type[s->type_of_atom[y]];
+  });
+  p.n_nonp = (int)order.size();
+  p.pos_of_atom.assign(p.na, -1);
+  for (int i = 0; i < p.n_nonp; ++i) {
+    const int a = order[i];
+    p.pos_atom.push_back(a);
+    p.pos_mol.push_back(s->mol_of_atom[a]);
+    p.ainfo.push_back(p.ainfo_atom[a]);
+    p.pos_of_atom[a] = i;
+  }
+  if ((long long)p.n_nonp >= (1LL << 24)) {
+    fail(p, MIXTS_ERR_ARG, "too many atoms for the 25-bit list entries");
+    return p;
+  }
+  // classes
+  p.cls_item0[0] = 0;
+  for (int i = 0; i < p.n_nonp;) {
+    const int P = 1 << p.ainfo[i].log2P;
+    int j = i;
+    while (j < p.n_nonp && (1 << p.ainfo[j].log2P) == P) ++j;
+    if (p.n_classes >= MAX_CLASSES) {
+      fail(p, MIXTS_ERR_BEADS, "too many distinct bead counts");
+      return p;
+    }
+    const int c = p.n_classes++;
+    p.cls_P[c] = P;
+    p.cls_log2P[c] = ilog2(P);
+    p.cls_pos0[c] = i;
+    p.cls_n[c] = j - i;
+    p.cls_item0[c + 1] = p.cls_item0[c] + P * (j - i);
+    i = j;
+  }
+  p.n_pitems = p.cls_item0[p.n_classes];
+  // pseudo particles
+  int maxP_site = 1;
+  for (int t = 0; t < p.nt; ++t)
+    if (!s->pseudo_type[t] && p.N[t] > 0) maxP_site = std::max(maxP_site, s->P_type[t]);
+  for (int a = 0; a < p.na; ++a) {
+    if (!p.atom_is_pseudo[a]) continue;
+    if (s->P_type[s->type_of_atom[a]] < maxP_site) {
+      fail(p, MIXTS_ERR_BEADS, "a pseudo particle must have at least as many beads as every site");
+      return p;
+    }
+    p.pseudo_atom.push_back(a);
+    p.pinfo.push_back(p.ainfo_atom[a]);
+    p.n_ppitems += s->P_type[s->type_of_atom[a]];
+  }
+  p.n_pseudo = (int)p.pseudo_atom.size();
+  // pair parameters
+  const double rc = prm->r_cut;
+  p.pairpar.assign(MT * MT, PairPar{0, 0, 1, 0, 0});
+  for (int a = 0; a < p.nt; ++a)
+    for (int b = 0; b < p.nt; ++b) {
+      PairPar pp;
+      pp.qq = u.ke * s->charge_type[a] * s->charge_type[b];
+      const double eps = s->lj_eps[a * p.nt + b], sig = s->lj_sig[a * p.nt + b];
+      pp.e4 = 4.0 * eps;
+      pp.s2 = sig * sig;
+      pp.vrc = 0.0;
+      pp.dvrc = 0.0;
+      if (eps != 0.0) lj_at(pp.e4, pp.s2, rc, &pp.vrc, &pp.dvrc);
+      p.pairpar[a * MT + b] = pp;
+    }
+  p.pspar.assign(MT, PseudoPar{0, 1, 0, 1, 0, 0});
+  for (int t = 0; t < p.nt; ++t) {
+    PseudoPar pp;
+    pp.kq = u.ke * s->charge_type[t];
+    pp.sig = s->pp_sigma[t];
+    pp.A = s->pp_A_eV[t] * u.ev_kcal;
+    pp.b = s->pp_b[t];
+    if (p.n_pseudo > 0 && !s->pseudo_type[t] && p.N[t] > 0 && (!(pp.sig > 0.0) || !(pp.b > 0.0))) {
+      fail(p, MIXTS_ERR_ARG, "pseudopotential sigma and b must be positive");
+      return p;
+    }
+    pp.vrc = pp.dvrc = 0.0;
+    if (pp.sig > 0.0 && pp.b > 0.0) pseudo_at(pp, rc, &pp.vrc, &pp.dvrc);
+    p.pspar[t] = pp;
+  }
+  // bonded work items: one per (term, slice of the term's finest grid)
+  if (s->n_bonds < 0 || s->n_angles < 0 || (s->n_bonds > 0 && (!s->bonds || !s->bond_k || !s->bond_r0)) ||
+      (s->n_angles > 0 && (!s->angles || !s->angle_k || !s->angle_theta0))) {
+    fail(p, MIXTS_ERR_ARG, "bad bond/angle arrays");
+    return p;
+  }
+  for (int b = 0; b < s->n_bonds; ++b) {
+    const int a = s->bonds[2 * b], c = s->bonds[2 * b + 1];
+    if (a < 0 || a >= p.na || c < 0 || c >= p.na || a == c) {
+      fail(p, MIXTS_ERR_ARG, "bond atom out of range");
+      return p;
+    }
+    p.bond_atoms.push_back(a);
+    p.bond_atoms.push_back(c);
+    p.bond_par.push_back(s->bond_k[b]);
+    p.bond_par.push_back(s->bond_r0[b]);
+    const int Ps = std::max(s->P_type[s->type_of_atom[a]], s->P_type[s->type_of_atom[c]]);
+    for (int sl = 0; sl < Ps; ++sl) p.bitems.push_back(BondItem{0, b, sl, 0});
+  }
+  for (int g = 0; g < s->n_angles; ++g) {
+    int Ps = 1;
+    for (int x = 0; x < 3; ++x) {
+      const int a = s->angles[3 * g + x];
+      if (a < 0 || a >= p.na) {
+        fail(p, MIXTS_ERR_ARG, "angle atom out of range");
+        return p;
+      }
+      p.ang_atoms.push_back(a);
+      Ps = std::max(Ps, s->P_type[s->type_of_atom[a]]);
+    }
+    p.ang_par.push_back(s->angle_k[g]);
+    p.ang_par.push_back(s->angle_theta0[g]);
+    for (int sl = 0; sl < Ps; ++sl) p.bitems.push_back(BondItem{1, g, sl, 0});
+  }
+  // normal modes, thermostat, rotation
+  const double kT = u.kB * prm->T;
+  const double bh = u.hbar / kT;
+  p.cm_off.assign(MT, 0);
+  p.mc_off.assign(MT, 0);
+  p.big_slot0.assign(MT, 0);
+  for (int t = 0; t < p.nt; ++t) {
+    const int P = s->P_type[t];
+    const double m = s->mass_type[t];
+    std::vector<double> T(P);
+    for (int k = 0; k < P; ++k) T[k] = cos(2.0 * PI * k / P);
+    p.cm_off[t] = (int)p.cm.size();
+    if (P <= SMALL_P) {
+      const double rP = 1.0 / sqrt((double)P), r2P = sqrt(2.0 / P);
+      for (int j = 0; j < P; ++j)
+        for (int k = 0; k < P; ++k) {
+          double v;
+          if (k == 0)
+            v = rP;
+          else if (2 * k < P)
+            v = r2P * T[(j * k) & (P - 1)];
+          else if (2 * k == P)
+            v = (j & 1) ? -rP : rP;
+          else
+            v = r2P * T[(j * k - P / 4) & (P - 1)];
+          p.cm.push_back(v);
+        }
+    } else {
+      for (int k = 0; k < P; ++k) p.cm.push_back(T[k]);
+    }
+    p.mc_off[t] = (int)p.mc.size();
+    for (int k = 0; k < P; ++k) {
+      const double w = 2.0 * sqrt((double)P) / bh * sin(PI * k / P);
+      const double gam = (k == 0) ? (prm->tau_centroid > 0.0 ? 1.0 / prm->tau_centroid : 0.0)
+                                  : 2.0 * prm->pile_lambda * w;
+      ModeCoef c;
+      c.c1 = exp(-0.5 * prm->dt * gam);
+      c.c2s = sqrt(1.0 - c.c1 * c.c1) * sqrt(m * kT);
+      if (k == 0) {
+        c.cw = 1.0;
+        c.mws = 0.0;
+        c.swm = prm->dt / m;
+        c.hmw2 = 0.0;
+      } else {
+        c.cw = cos(w * prm->dt);
+        c.mws = m * w * sin(w * prm->dt);
+        c.swm = sin(w * prm->dt) / (m * w);
+        c.hmw2 = 0.5 * m * w * w;
+      }
+      p.mc.push_back(c);
+    }
+  }
+  // propagation tiles and estimator partial slots
+  for (int t = 0; t < p.nt; ++t) {
+    const int P = s->P_type[t];
+    if (P > SMALL_P || p.N[t] == 0) continue;
+    const int apt = std::max(1, 128 / P);
+    for (int k0 = 0; k0 < p.N[t]; k0 += apt) {
+      p.tiles.push_back(PropTile{t, k0, std::min(apt, p.N[t] - k0), (int)p.slot_type.size()});
+      p.slot_type.push_back(t);
+    }
+  }
+  for (int t = 0; t < p.nt; ++t) {
+    const int P = s->P_type[t];
+    if (P <= SMALL_P || p.N[t] == 0) continue;
+    p.big_slot0[t] = (int)p.slot_type.size();
+    for (int b = 0; b < P / BIG_MB; ++b) p.slot_type.push_back(t);
+    p.spread_slots = std::max(p.spread_slots, P / BIG_MB);
+  }
+  // neighbour-list capacities
+  const double vol = s->box * s->box * s->box;
+  const double rho = p.n_nonp / vol;
+  if (prm->nlist_cap > 0) {
+    p.nl_cap = prm->nlist_cap;
+  } else {
+    const double Rest = rc + 2.5;
+    const double full = rho * 4.0 / 3.0 * PI * Rest * Rest * Rest;
+    p.nl_cap = (int)(1.3 * full) + 64;
+    p.nl_cap = (p.nl_cap + 31) & ~31;
+  }
+  {
+    const double Rp = rc + 12.0;
+    const double full = rho * 4.0 / 3.0 * PI * Rp * Rp * Rp;
+    p.pl_cap = std::max(64, std::min((int)(1.3 * full) + 128, 125 * std::max(1, p.n_nonp)));
+  }
+  // workspace layout: read-only tables first, then the state
+  Arena& A = p.ar;
+  p.o_ainfo = A.add(sizeof(AtomInfo) * std::max(1, p.n_nonp));
+  p.o_pos_atom = A.add(sizeof(int) * std::max(1, p.n_nonp));
+  p.o_pos_mol = A.add(sizeof(int) * std::max(1, p.n_nonp));
+  p.o_atom_of_tk = A.add(sizeof(int) * p.na);
+  p.o_ainfo_atom = A.add(sizeof(AtomInfo) * p.na);
+  p.o_is_pseudo = A.add(sizeof(int) * p.na);
+  p.o_pseudo_atom = A.add(sizeof(int) * std::max(1, p.n_pseudo));
+  p.o_pinfo = A.add(sizeof(AtomInfo) * std::max(1, p.n_pseudo));
+  p.o_pairpar = A.add(sizeof(PairPar) * MT * MT);
+  p.o_pspar = A.add(sizeof(PseudoPar) * MT);
+  p.o_bitems = A.add(sizeof(BondItem) * std::max<size_t>(1, p.bitems.size()));
+  p.o_bond_atoms = A.add(sizeof(int) * std::max<size_t>(1, p.bond_atoms.size()));
+  p.o_bond_par = A.add(sizeof(double) * std::max<size_t>(1, p.bond_par.size()));
+  p.o_ang_atoms = A.add(sizeof(int) * std::max<size_t>(1, p.ang_atoms.size()));
+  p.o_ang_par = A.add(sizeof(double) * std::max<size_t>(1, p.ang_par.size()));
+  p.o_cm = A.add(sizeof(double) * p.cm.size());
+  p.o_mc = A.add(sizeof(ModeCoef) * p.mc.size());
+  p.o_tiles = A.add(sizeof(PropTile) * std::max<size_t>(1, p.tiles.size()));
+  p.o_slot_type = A.add(sizeof(int) * std::max<size_t>(1, p.slot_type.size()));
+  p.tab_bytes = A.size;
+  const size_t nb3 = (size_t)p.n_beads * 3;
+  p.o_qnm = A.add(sizeof(double) * nb3);
+  p.o_pnm = A.add(sizeof(double) * nb3);
+  p.o_ffix = A.add(sizeof(unsigned long long) * nb3);
+  p.o_xw = A.add(sizeof(double4_32a) * p.n_beads);
+  p.o_xf = A.add(sizeof(float4) * p.n_beads);
+  p.o_xl = A.add(sizeof(float4) * p.n_beads);
+  p.o_ref = A.add(sizeof(double) * 3 * p.na);
+  p.o_spread = A.add(sizeof(double) * (size_t)p.na * p.spread_slots);
+  p.o_nl = A.add(sizeof(int) * (size_t)std::max(1, p.n_nonp) * p.nl_cap);
+  p.o_nlcnt = A.add(sizeof(int) * std::max(1, p.n_nonp));
+  p.o_pl = A.add(sizeof(int) * (size_t)std::max(1, p.n_pseudo) * p.pl_cap);
+  p.o_plcnt = A.add(sizeof(int) * std::max(1, p.n_pseudo));
+  p.o_thresh = A.add(sizeof(double) * 4);
+  p.o_efix = A.add(sizeof(unsigned long long) * E_NSLOTS);
+  p.o_err = A.add(sizeof(int) * 4);
+  p.o_step = A.add(sizeof(long long));
+  p.o_heat = A.add(sizeof(double));
+  p.o_est = A.add(sizeof(double) * EST_N);
+  p.o_parts = A.add(sizeof(double) * 6 * std::max<size_t>(1, p.slot_type.size()));
+  p.state_bytes = A.size - p.tab_bytes;
+  return p;
+}
+
+template <class T>
+void put(std::vector<unsigned char>& img, size_t off, const std::vector<T>& v) {
+  if (!v.empty()) memcpy(img.data() + off, v.data(), sizeof(T) * v.size());
+}
+
+}  // namespace
+
+struct mixts_ctx {
+  Dev d;
+  Plan plan;
+  cudaStream_t stream = nullptr;
+  unsigned char* ws = nullptr;
+  const int* slot_type = nullptr;
+  const AtomInfo* ainfo_atom = nullptr;
+  const int* atom_is_pseudo = nullptr;
+  bool nm_valid = false;  // mode-space state is authoritative
+  bool f_valid = false;   // F_fix holds the forces at the current positions
+  long long steps_done = 0;
+  std::string err;
+  int device = 0;
+};
+
+static mixts_status set_err(mixts_handle h, mixts_status s, const std::string& why) {
+  if (h) h->err = why;
+  return s;
+}
+
+static mixts_status cuda_check(mixts_handle h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MIXTS_OK;
+  return set_err(h, MIXTS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static mixts_status device_error(mixts_handle h) {
+  int e = 0;
+  cudaError_t ce = cudaMemcpyAsync(&e, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+  if (ce != cudaSuccess) return cuda_check(h, ce, "synchronise");
+  if (e == 0) return MIXTS_OK;
+  cudaMemsetAsync(h->d.err, 0, sizeof(int), h->stream);
+  if (e & ERR_BOX) return set_err(h, MIXTS_ERR_BOX, "list radius reached twice the box edge");
+  if (e & (ERR_NLIST | ERR_PLIST))
+    return set_err(h, MIXTS_ERR_NLIST_OVERFLOW, "a neighbour-list row outgrew its capacity");
+  if (e & ERR_NONFINITE) return set_err(h, MIXTS_ERR_NONFINITE, "non-finite or out-of-range force");
+  if (e & ERR_TIMEOUT) return set_err(h, MIXTS_ERR_TIMEOUT, "bounded device wait expired");
+  return set_err(h, MIXTS_ERR_CUDA, "unknown device error bits");
+}
+
+extern "C" {
+
+const char* mixts_version(void) { return "mixts-gb300 0.1 (sm_103a)"; }
+
+size_t mixts_workspace_size(const mixts_system* sys, int n_sys, const mixts_params* prm) {
+  if (n_sys != 1 || !sys) return 0;
+  Plan p = make_plan(sys, prm);
+  if (p.st != MIXTS_OK) return 0;
+  return p.ar.size + 256;
+}
+
+mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* prm, void* workspace,
+                        size_t ws_bytes, void* stream, mixts_handle* out) {
+  if (!out) return MIXTS_ERR_ARG;
+  *out = nullptr;
+  if (n_sys != 1 || !sys || !prm) return MIXTS_ERR_ARG;
+  if (!sys->q || !sys->p || !sys->f) return MIXTS_ERR_ARG;
+  mixts_handle h = new mixts_ctx();
+  h->plan = make_plan(sys, prm);
+  Plan& p = h->plan;
+  if (p.st != MIXTS_OK) {
+    mixts_status st = p.st;
+    fprintf(stderr, "mixts_init: %s\n", p.why.c_str());
+    delete h;
+    return st;
+  }
+  if (!workspace || ((uintptr_t)workspace & 255) || ws_bytes < p.ar.size) {
+    delete h;
+    return MIXTS_ERR_WORKSPACE;
+  }
+  cudaGetDevice(&h->device);
+  h->stream = (cudaStream_t)stream;
+  h->ws = (unsigned char*)workspace;
+  // table image
+  std::vector<unsigned char> img(p.tab_bytes, 0);
+  put(img, p.o_ainfo, p.ainfo);
+  put(img, p.o_pos_atom, p.pos_atom);
+  put(img, p.o_pos_mol, p.pos_mol);
+  put(img, p.o_atom_of_tk, p.atom_of_tk);
+  put(img, p.o_ainfo_atom, p.ainfo_atom);
+  put(img, p.o_is_pseudo, p.atom_is_pseudo);
+  put(img, p.o_pseudo_atom, p.pseudo_atom);
+  put(img, p.o_pinfo, p.pinfo);
+  put(img, p.o_pairpar, p.pairpar);
+  put(img, p.o_pspar, p.pspar);
+  put(img, p.o_bitems, p.bitems);
+  put(img, p.o_bond_atoms, p.bond_atoms);
+  put(img, p.o_bond_par, p.bond_par);
+  put(img, p.o_ang_atoms, p.ang_atoms);
+  put(img, p.o_ang_par, p.ang_par);
+  put(img, p.o_cm, p.cm);
+  put(img, p.o_mc, p.mc);
+  put(img, p.o_tiles, p.tiles);
+  put(img, p.o_slot_type, p.slot_type);
+  mixts_status st = cuda_check(h, cudaMemcpy(h->ws, img.data(), p.tab_bytes, cudaMemcpyHostToDevice), "upload tables");
+  if (st == MIXTS_OK)
+    st = cuda_check(h, cudaMemsetAsync(h->ws + p.tab_bytes, 0, p.ar.size - p.tab_bytes, h->stream), "clear state");
+  if (st == MIXTS_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "init sync");
+  if (st != MIXTS_OK) {
+    fprintf(stderr, "mixts_init: %s\n", h->err.c_str());
+    delete h;
+    return st;
+  }
+  const Units u = units();
+  Dev& d = h->d;
+  memset(&d, 0, sizeof(d));
+  d.n_atoms = p.na;
+  d.n_nonp = p.n_nonp;
+  d.n_pseudo = p.n_pseudo;
+  d.n_types = p.nt;
+  d.n_beads = p.n_beads;
+  d.n_bitems = (int)p.bitems.size();
+  d.n_pitems = p.n_pitems;
+  d.n_ppitems = p.n_ppitems;
+  d.nl_cap = p.nl_cap;
+  d.pl_cap = p.pl_cap;
+  d.n_classes = p.n_classes;
+  d.n_tiles = (int)p.tiles.size();
+  d.n_part_slots = (int)p.slot_type.size();
+  d.spread_slots = p.spread_slots;
+  d.precision = prm->precision;
+  d.box = sys->box;
+  d.rc = prm->r_cut;
+  d.rc2 = prm->r_cut * prm->r_cut;
+  d.alpha = prm->dsf_alpha;
+  d.dsf_g = 2.0 * prm->dsf_alpha / sqrt(PI);
+  d.dsf_erfc_rc_over_rc = erfc(prm->dsf_alpha * prm->r_cut) / prm->r_cut;
+  d.dsf_cf = erfc(prm->dsf_alpha * prm->r_cut) / (prm->r_cut * prm->r_cut) +
+             d.dsf_g * exp(-prm->dsf_alpha * prm->dsf_alpha * prm->r_cut * prm->r_cut) / prm->r_cut;
+  d.dt = prm->dt;
+  d.kcal = u.kcal;
+  d.kB = u.kB;
+  d.kT = u.kB * prm->T;
+  d.seed = sys->seed;
+  for (int t = 0; t < p.nt; ++t) {
+    d.P[t] = sys->P_type[t];
+    d.log2P[t] = ilog2(sys->P_type[t]);
+    d.N[t] = p.N[t];
+    d.off[t] = p.off[t];
+    d.atoff[t] = p.atoff[t];
+    d.pseudo[t] = sys->pseudo_type[t] ? 1 : 0;
+    d.cm_off[t] = p.cm_off[t];
+    d.mc_off[t] = p.mc_off[t];
+    d.big_slot0[t] = p.big_slot0[t];
+    d.mass[t] = sys->mass_type[t];
+  }
+  for (int c = 0; c < p.n_classes; ++c) {
+    d.cls_P[c] = p.cls_P[c];
+    d.cls_log2P[c] = p.cls_log2P[c];
+    d.cls_pos0[c] = p.cls_pos0[c];
+    d.cls_n[c] = p.cls_n[c];
+    d.cls_item0[c] = p.cls_item0[c];
+  }
+  unsigned char* w = h->ws;
+  d.ainfo = (const AtomInfo*)(w + p.o_ainfo);
+  d.pos_atom = (const int*)(w + p.o_pos_atom);
+  d.pos_mol = (const int*)(w + p.o_pos_mol);
+  d.atom_of_tk = (const int*)(w + p.o_atom_of_tk);
+  h->ainfo_atom = (const AtomInfo*)(w + p.o_ainfo_atom);
+  h->atom_is_pseudo = (const int*)(w + p.o_is_pseudo);
+  d.pseudo_atom = (const int*)(w + p.o_pseudo_atom);
+  d.pinfo = (const AtomInfo*)(w + p.o_pinfo);
+  d.pairpar = (const PairPar*)(w + p.o_pairpar);
+  d.pspar = (const PseudoPar*)(w + p.o_pspar);
+  d.bitems = (const BondItem*)(w + p.o_bitems);
+  d.bond_atoms = (const int*)(w + p.o_bond_atoms);
+  d.bond_par = (const double*)(w + p.o_bond_par);
+  d.ang_atoms = (const int*)(w + p.o_ang_atoms);
+  d.ang_par = (const double*)(w + p.o_ang_par);
+  d.cm = (const double*)(w + p.o_cm);
+  d.mc = (const ModeCoef*)(w + p.o_mc);
+  d.tiles = (const PropTile*)(w + p.o_tiles);
+  h->slot_type = (const int*)(w + p.o_slot_type);
+  d.q = sys->q;
+  d.p = sys->p;
+  d.f = sys->f;
+  d.q_nm = (double*)(w + p.o_qnm);
+  d.p_nm = (double*)(w + p.o_pnm);
+  d.F_fix = (unsigned long long*)(w + p.o_ffix);
+  d.Xw = (double4_32a*)(w + p.o_xw);
+  d.Xf = (float4*)(w + p.o_xf);
+  d.Xl = (float4*)(w + p.o_xl);
+  d.ref = (double*)(w + p.o_ref);
+  d.spread = (double*)(w + p.o_spread);
+  d.nl = (int*)(w + p.o_nl);
+  d.nl_cnt = (int*)(w + p.o_nlcnt);
+  d.pl = (int*)(w + p.o_pl);
+  d.pl_cnt = (int*)(w + p.o_plcnt);
+  d.thresh = (double*)(w + p.o_thresh);
+  d.E_fix = (unsigned long long*)(w + p.o_efix);
+  d.err = (int*)(w + p.o_err);
+  d.step_ctr = (long long*)(w + p.o_step);
+  d.heat = (double*)(w + p.o_heat);
+  d.est = (double*)(w + p.o_est);
+  d.parts = (double*)(w + p.o_parts);
+  *out = h;
+  return MIXTS_OK;
+}
+
+static mixts_status eval_forces(mixts_handle h) {
+  launch_nlist(h->d, h->stream, h->atom_is_pseudo);
+  launch_forces(h->d, h->stream, h->ainfo_atom);
+  return cuda_check(h, cudaGetLastError(), "force launch");
+}
+
+mixts_status mixts_forces(mixts_handle h, double* energy_host) {
+  if (!h) return MIXTS_ERR_ARG;
+  // a fresh evaluation from the caller's q: clear the accumulators first
+  cudaMemsetAsync(h->d.F_fix, 0, sizeof(unsigned long long) * 3 * (size_t)h->d.n_beads, h->stream);
+  cudaMemsetAsync(h->d.E_fix, 0, sizeof(unsigned long long) * E_NSLOTS, h->stream);
+  launch_prop(h->d, h->stream, PM_MIRROR);
+  mixts_status st = eval_forces(h);
+  if (st != MIXTS_OK) return st;
+  launch_forces_out(h->d, h->stream);
+  st = cuda_check(h, cudaGetLastError(), "forces out");
+  if (st != MIXTS_OK) return st;
+  h->nm_valid = false;
+  h->f_valid = false;
+  if (energy_host) {
+    st = device_error(h);
+    if (st != MIXTS_OK) return st;
+    st = cuda_check(h, cudaMemcpy(energy_host, h->d.est, sizeof(double), cudaMemcpyDeviceToHost), "energy");
+  }
+  return st;
+}
+
+mixts_status mixts_step(mixts_handle h, int n_steps) {
+  if (!h || n_steps < 0) return MIXTS_ERR_ARG;
+  if (n_steps == 0) return MIXTS_OK;
+  cudaStream_t s = h->stream;
+  if (!h->nm_valid) {
+    launch_prop(h->d, s, PM_IMPORT);
+    h->nm_valid = true;
+    h->f_valid = false;
+  }
+  if (!h->f_valid) {
+    cudaMemsetAsync(h->d.F_fix, 0, sizeof(unsigned long long) * 3 * (size_t)h->d.n_beads, s);
+    cudaMemsetAsync(h->d.E_fix, 0, sizeof(unsigned long long) * E_NSLOTS, s);
+    launch_prop(h->d, s, PM_QCART);
+    mixts_status st = eval_forces(h);
+    if (st != MIXTS_OK) return st;
+    h->f_valid = true;
+  }
+  launch_prop(h->d, s, PM_START);
+  launch_final(h->d, s, PM_START, h->slot_type);
+  for (int i = 1; i < n_steps; ++i) {
+    eval_forces(h);
+    launch_prop(h->d, s, PM_END | PM_EST | PM_START);
+    launch_final(h->d, s, PM_END | PM_EST | PM_START, h->slot_type);
+  }
+  eval_forces(h);
+  launch_prop(h->d, s, PM_END | PM_EST | PM_PCART);
+  launch_final(h->d, s, PM_END | PM_EST, h->slot_type);
+  h->steps_done += n_steps;
+  return cuda_check(h, cudaGetLastError(), "step launch");
+}
+
+mixts_status mixts_estimators(mixts_handle h, mixts_estimates* out) {
+  if (!h || !out) return MIXTS_ERR_ARG;
+  mixts_status st = device_error(h);
+  if (st != MIXTS_OK) return st;
+  double e[EST_N];
+  st = cuda_check(h, cudaMemcpy(e, h->d.est, sizeof(e), cudaMemcpyDeviceToHost), "estimates");
+  if (st != MIXTS_OK) return st;
+  memset(out, 0, sizeof(*out));
+  out->V = e[0];
+  out->V_lj = e[1];
+  out->V_coul = e[2];
+  out->V_bond = e[3];
+  out->V_angle = e[4];
+  out->V_pseudo = e[5];
+  out->KE_beads = e[6];
+  out->E_spring = e[7];
+  out->virial = e[8];
+  out->T_beads = e[9];
+  out->H_mix = e[10];
+  out->heat = e[11];
+  out->H_conserved = e[12];
+  out->n_evals = e[13];
+  out->n_pseudo_evals = e[14];
+  out->step = (int64_t)e[15];
+  for (int t = 0; t < h->d.n_types; ++t) {
+    out->KE_prim[t] = e[16 + 4 * t];
+    out->KE_cv[t] = e[16 + 4 * t + 1];
+    out->Rg2[t] = e[16 + 4 * t + 2];
+    out->E_spring_t[t] = e[16 + 4 * t + 3];
+  }
+  return MIXTS_OK;
+}
+
+mixts_status mixts_nlist(mixts_handle h, int kind, int* out3, long cap, long* n_out, double* thresh) {
+  if (!h || !n_out || (kind != 0 && kind != 1)) return MIXTS_ERR_ARG;
+  mixts_status st = device_error(h);
+  if (st != MIXTS_OK) return st;
+  const Plan& p = h->plan;
+  if (thresh) {
+    double t4[4];
+    cudaMemcpy(t4, h->d.thresh, sizeof(t4), cudaMemcpyDeviceToHost);
+    thresh[0] = kind == 0 ? t4[0] : t4[2];
+    thresh[1] = kind == 0 ? t4[1] : t4[3];
+    thresh[2] = t4[3];
+  }
+  const int rows = kind == 0 ? p.n_nonp : p.n_pseudo;
+  const int rcap = kind == 0 ? p.nl_cap : p.pl_cap;
+  std::vector<int> cnt(std::max(1, rows)), ent((size_t)std::max(1, rows) * rcap);
+  if (rows > 0) {
+    cudaMemcpy(cnt.data(), kind == 0 ? h->d.nl_cnt : h->d.pl_cnt, sizeof(int) * rows, cudaMemcpyDeviceToHost);
+    st = cuda_check(h,
+                    cudaMemcpy(ent.data(), kind == 0 ? h->d.nl : h->d.pl, sizeof(int) * (size_t)rows * rcap,
+                               cudaMemcpyDeviceToHost),
+                    "list copy");
+    if (st != MIXTS_OK) return st;
+  }
+  long n = 0;
+  for (int r = 0; r < rows; ++r) {
+    const int owner = kind == 0 ? p.pos_atom[r] : p.pseudo_atom[r];
+    const int c = std::min(cnt[r], rcap);
+    for (int k = 0; k < c; ++k) {
+      const int e = ent[(size_t)r * rcap + k];
+      if (out3 && n < cap) {
+        out3[3 * n] = owner;
+        out3[3 * n + 1] = p.pos_atom[e >> 7];
+        out3[3 * n + 2] = e & 127;
+      }
+      ++n;
+    }
+  }
+  *n_out = n;
+  return (out3 && n > cap) ? set_err(h, MIXTS_ERR_ARG, "cap too small") : MIXTS_OK;
+}
+
+size_t mixts_state_size(mixts_handle h) {
+  if (!h) return 0;
+  return 64 + sizeof(double) * 6 * (size_t)h->d.n_beads;
+}
+
+mixts_status mixts_get_state(mixts_handle h, void* blob, size_t bytes) {
+  if (!h || !blob || bytes < mixts_state_size(h)) return MIXTS_ERR_ARG;
+  mixts_status st = device_error(h);
+  if (st != MIXTS_OK) return st;
+  if (!h->nm_valid) return set_err(h, MIXTS_ERR_STATE, "no mode-space state yet: call mixts_step first");
+  unsigned char* b = (unsigned char*)blob;
+  memset(b, 0, 64);
+  const uint64_t magic = 0x4d49585453543031ull;  // "MIXTST01"
+  const uint64_t nb = (uint64_t)h->d.n_beads;
+  memcpy(b, &magic, 8);
+  memcpy(b + 8, &nb, 8);
+  cudaMemcpy(b + 16, h->d.step_ctr, 8, cudaMemcpyDeviceToHost);
+  cudaMemcpy(b + 24, h->d.heat, 8, cudaMemcpyDeviceToHost);
+  const size_t n3 = sizeof(double) * 3 * nb;
+  cudaMemcpy(b + 64, h->d.q_nm, n3, cudaMemcpyDeviceToHost);
+  return cuda_check(h, cudaMemcpy(b + 64 + n3, h->d.p_nm, n3, cudaMemcpyDeviceToHost), "get state");
+}
+
+mixts_status mixts_set_state(mixts_handle h, const void* blob, size_t bytes) {
+  if (!h || !blob || bytes < mixts_state_size(h)) return MIXTS_ERR_ARG;
+  const unsigned char* b = (const unsigned char*)blob;
+  uint64_t magic, nb;
+  memcpy(&magic, b, 8);
+  memcpy(&nb, b + 8, 8);
+  if (magic != 0x4d49585453543031ull || nb != (uint64_t)h->d.n_beads)
+    return set_err(h, MIXTS_ERR_STATE, "state blob does not match this system");
+  cudaStream_t s = h->stream;
+  const size_t n3 = sizeof(double) * 3 * nb;
+  cudaMemcpyAsync(h->d.step_ctr, b + 16, 8, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->d.heat, b + 24, 8, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->d.q_nm, b + 64, n3, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->d.p_nm, b + 64 + n3, n3, cudaMemcpyHostToDevice, s);
+  mixts_status st = cuda_check(h, cudaStreamSynchronize(s), "set state");
+  if (st != MIXTS_OK) return st;
+  h->nm_valid = true;
+  h->f_valid = false;
+  // Cartesian q, p for the caller
+  launch_prop(h->d, s, PM_QCART | PM_PCART);
+  return cuda_check(h, cudaGetLastError(), "set state export");
+}
+
+mixts_status mixts_gaussians(mixts_handle h, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out) {
+  if (!h || !out || n < 0) return MIXTS_ERR_ARG;
+  launch_gauss(h->d, h->stream, step, stage, dof0, n, out);
+  return cuda_check(h, cudaGetLastError(), "gaussians");
+}
+
+void mixts_destroy(mixts_handle h) { delete h; }
+
+const char* mixts_last_error(mixts_handle h) { return h ? h->err.c_str() : "NULL handle"; }
+
+}  // extern "C"

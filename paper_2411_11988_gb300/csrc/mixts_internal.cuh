@@ -1,0 +1,308 @@
+// mixts_internal.cuh -- device-side data view and helpers of the mixTS-PIMD
+// hot path for sm_103a. Everything here is used only by the .cu files of
+// this library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mixts.h"
+
+namespace mx {
+
+constexpr int MT = MIXTS_MAX_TYPES;
+constexpr int MAX_CLASSES = 12;
+constexpr int SMALL_P = 64;     // types with P <= SMALL_P propagate in one fused tile kernel
+constexpr int BIG_MB = 8;       // modes (or beads) per CTA of the large-P transforms
+
+// Forces and energies are accumulated in 64-bit fixed point, so that sums
+// are exact integers whatever order the atomics land in: the whole step is
+// bitwise reproducible.
+constexpr double FSCALE = 17592186044416.0;   // 2^44 per kcal/mol/A
+constexpr double FINV = 1.0 / 17592186044416.0;
+constexpr double ESCALE = 1099511627776.0;    // 2^40 per kcal/mol
+constexpr double EINV = 1.0 / 1099511627776.0;
+constexpr double FMAX = 262144.0;             // |single contribution| limit, kcal/mol/A
+
+enum : int { ERR_NLIST = 1, ERR_NONFINITE = 2, ERR_BOX = 4, ERR_TIMEOUT = 8, ERR_PLIST = 16 };
+
+// energy accumulator slots (fixed point) and counters
+enum : int { E_LJ = 0, E_COUL, E_BOND, E_ANGLE, E_PSEUDO, E_VIRIAL, E_NEVAL, E_NPEVAL, E_NSLOTS };
+
+// estimator partial slots per propagation block: per type 4 values + heat
+constexpr int PART_PER_TYPE = 4;  // KE, spring energy, centroid-virial sum, Rg sum
+constexpr int PART_STRIDE = MT * PART_PER_TYPE + 2;
+
+// estimate record (device), see mixts_estimates
+constexpr int EST_N = 16 + 4 * MT;
+
+struct AtomInfo {  // one non-pseudo atom, by sorted position
+  int row0;        // bead-0 row in the flat layout
+  int stride;      // rows between consecutive beads (N_t)
+  int log2P;
+  int type;
+};
+
+struct PairPar {   // nonbonded parameters of a type pair
+  double qq;       // k_e q_i q_j
+  double e4;       // 4 eps
+  double s2;       // sigma^2
+  double vrc;      // LJ value at r_cut
+  double dvrc;     // LJ slope at r_cut
+};
+
+struct PseudoPar { // pseudopotential parameters of a site type
+  double kq;       // k_e q_site
+  double sig;      // sigma
+  double A;        // kcal/mol
+  double b;
+  double vrc, dvrc;
+};
+
+struct ModeCoef {  // per (type, mode): thermostat and exact free-ring rotation
+  double c1;       // exp(-gamma dt/2)
+  double c2s;      // sqrt(1 - c1^2) sqrt(m kT)
+  double cw;       // cos(omega dt)
+  double mws;      // m omega sin(omega dt)       (k = 0: 0)
+  double swm;      // sin(omega dt)/(m omega)     (k = 0: dt/m)
+  double hmw2;     // m omega^2 / 2 (spring energy in mode space)
+};
+
+struct PropTile {  // one CTA of the fused small-P propagation
+  int type, k0, na, slot;
+};
+
+struct BondItem {  // one bonded term evaluated on one fine slice
+  int kind;        // 0 bond, 1 angle
+  int term;
+  int slice;
+  int pad;
+};
+
+struct Dev {
+  // sizes
+  int n_atoms, n_nonp, n_pseudo, n_types, n_beads;
+  int n_bitems, n_pitems, n_ppitems;
+  int nl_cap, pl_cap;
+  int n_classes;
+  int n_tiles;          // small-P propagation tiles
+  int n_part_slots;     // estimator partial slots
+  int spread_slots;     // per atom
+  int precision;
+  double box, rc, rc2, alpha;
+  double dsf_erfc_rc_over_rc, dsf_cf, dsf_g;
+  double dt, kcal, kT, kB;
+  uint64_t seed;
+  // per type
+  int P[MT], log2P[MT], N[MT], off[MT], pseudo[MT], atoff[MT];
+  int cm_off[MT];       // offset of C (P <= SMALL_P) or the cos table (P > SMALL_P)
+  int mc_off[MT];       // offset of the ModeCoef rows
+  int big_slot0[MT];    // first estimator partial slot of a large-P type
+  double mass[MT];
+  // sorted classes of non-pseudo atoms (P descending)
+  int cls_P[MAX_CLASSES], cls_log2P[MAX_CLASSES], cls_pos0[MAX_CLASSES], cls_n[MAX_CLASSES],
+      cls_item0[MAX_CLASSES];
+  // tables
+  const AtomInfo* ainfo;   // [n_nonp]
+  const int* pos_atom;     // [n_nonp] atom index of a sorted position
+  const int* pos_mol;      // [n_nonp]
+  const int* atom_of_tk;   // [n_atoms] atom index of (type, rank), at atoff[t] + k
+  const int* pseudo_atom;  // [n_pseudo]
+  const AtomInfo* pinfo;   // [n_pseudo]
+  const PairPar* pairpar;  // [MT*MT]
+  const PseudoPar* pspar;  // [MT]
+  const BondItem* bitems;  // [n_bitems]
+  const int* bond_atoms;   // [n_bonds*2]
+  const double* bond_par;  // [n_bonds*2] k, r0
+  const int* ang_atoms;    // [n_angles*3]
+  const double* ang_par;   // [n_angles*2] k, theta0
+  const double* cm;        // NM matrices / cos tables
+  const ModeCoef* mc;      // mode coefficients
+  const PropTile* tiles;   // [n_tiles]
+  // caller state
+  double* q;
+  double* p;
+  double* f;
+  // internal state
+  double* q_nm;
+  double* p_nm;
+  unsigned long long* F_fix;   // [n_beads*3], two's-complement fixed point
+  double4_32a* Xw;                 // [n_beads] positions shifted so bead 0 of each atom lies in the box
+  float4* Xf;                  // [n_beads] FP32 mirror (hi parts) for the FP32 force path
+  float4* Xl;                  // [n_beads] FP32 mirror (lo parts)
+  double* ref;                 // [n_atoms*3] wrapped bead-0 reference positions
+  double* spread;              // [n_atoms*spread_slots] max |q_b - q_0| partials
+  int* nl;                     // [n_nonp*nl_cap] (partner position << 7) | image code
+  int* nl_cnt;                 // [n_nonp]
+  int* pl;                     // [n_pseudo*pl_cap]
+  int* pl_cnt;                 // [n_pseudo]
+  double* thresh;              // [4] d_max, list radius, d_max pseudo, pseudo radius
+  unsigned long long* E_fix;   // [E_NSLOTS]
+  int* err;                    // [1]
+  long long* step_ctr;         // [1] completed steps
+  double* heat;                // [1]
+  double* est;                 // [EST_N]
+  double* parts;               // [n_part_slots * PART_STRIDE]
+};
+
+// ---------------------------------------------------------------------------
+// fixed-point accumulation
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long to_fix(double v, double scale, int* err) {
+  double s = v * scale;
+  if (!(fabs(v) < FMAX)) {  // also catches NaN
+    atomicOr(err, ERR_NONFINITE);
+    s = 0.0;
+  }
+  return __double2ll_rn(s);
+}
+
+__device__ __forceinline__ void fadd3(unsigned long long* F, int row, double fx, double fy, double fz,
+                                      int* err) {
+  unsigned long long* r = F + 3 * (size_t)row;
+  atomicAdd(r + 0, (unsigned long long)to_fix(fx, FSCALE, err));
+  atomicAdd(r + 1, (unsigned long long)to_fix(fy, FSCALE, err));
+  atomicAdd(r + 2, (unsigned long long)to_fix(fz, FSCALE, err));
+}
+
+__device__ __forceinline__ void eadd(unsigned long long* E, int slot, double v) {
+  atomicAdd(E + slot, (unsigned long long)__double2ll_rn(v * ESCALE));
+}
+
+__device__ __forceinline__ double fix_to_double(unsigned long long v, double inv) {
+  return (double)(long long)v * inv;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sumi(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the thermostat's
+// standard normals: a binary32 Box-Muller whose logarithm and sine/cosine are
+// fixed sequences of correctly rounded operations (so any IEEE machine
+// running the same sequence produces the same bits).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// ln(u), u = (2 floor(r / 2^9) + 1) 2^-24: u = f 2^e exactly with f folded
+// into (sqrt(1/2), sqrt(2)], ln f from the odd series of 2 atanh(s),
+// s = (f-1)/(f+1), through s^9; e ln 2 added with ln 2 split in two parts.
+__device__ __forceinline__ float log_u24(uint32_t r) {
+  const uint32_t m = ((r >> 9) << 1) | 1u;
+  int e = 31 - __clz((int)m);
+  float f = __fmul_rn(__uint2float_rn(m), __int_as_float((127 - e) << 23));
+  if (f > 0x1.6a09e6p+0f) {
+    f = __fmul_rn(f, 0.5f);
+    e += 1;
+  }
+  const float s = __fdiv_rn(__fsub_rn(f, 1.0f), __fadd_rn(f, 1.0f));
+  const float s2 = __fmul_rn(s, s);
+  float poly = 0x1.c71c72p-4f;                    // 1/9
+  poly = __fmaf_rn(poly, s2, 0x1.24924ap-3f);     // 1/7
+  poly = __fmaf_rn(poly, s2, 0x1.99999ap-3f);     // 1/5
+  poly = __fmaf_rn(poly, s2, 0x1.555556p-2f);     // 1/3
+  const float s3 = __fmul_rn(s, s2);
+  float lnf = __fmaf_rn(s3, poly, s);
+  lnf = __fmul_rn(2.0f, lnf);
+  const float kf = __int2float_rn(e - 24);
+  return __fmaf_rn(kf, 0x1.62e4p-1f, __fmaf_rn(kf, 0x1.7f7d1cp-20f, lnf));
+}
+
+// sin and cos of 2 pi v, v from the top 25 bits of r: quadrant from the top
+// two bits, the in-quadrant angle folded into (0, pi/4], Taylor series of
+// sin through x^9 and cos through x^10 by Horner with fma.
+__device__ __forceinline__ void sincos_2pi(uint32_t r, float* sp, float* cp) {
+  const uint32_t quad = r >> 30;
+  uint32_t m = (((r >> 7) & 0x7FFFFFu) << 1) | 1u;
+  const bool comp = m > (1u << 23);
+  if (comp) m = (1u << 24) - m;
+  const float t = __fmul_rn(__uint2float_rn(m), 0x1p-24f);
+  const float x = __fmul_rn(t, 0x1.921fb6p+0f);  // pi/2
+  const float x2 = __fmul_rn(x, x);
+  float ps = 0x1.71de3ap-19f;                      // 1/9!
+  ps = __fmaf_rn(ps, x2, -0x1.a01a02p-13f);        // -1/7!
+  ps = __fmaf_rn(ps, x2, 0x1.111112p-7f);          // 1/5!
+  ps = __fmaf_rn(ps, x2, -0x1.555556p-3f);         // -1/3!
+  const float x3 = __fmul_rn(x, x2);
+  float sn = __fmaf_rn(x3, ps, x);
+  float pc = -0x1.27e4fcp-22f;                     // -1/10!
+  pc = __fmaf_rn(pc, x2, 0x1.a01a02p-16f);         // 1/8!
+  pc = __fmaf_rn(pc, x2, -0x1.6c16c2p-10f);        // -1/6!
+  pc = __fmaf_rn(pc, x2, 0x1.555556p-5f);          // 1/4!
+  pc = __fmaf_rn(pc, x2, -0x1p-1f);                // -1/2
+  float cs = __fmaf_rn(x2, pc, 1.0f);
+  if (comp) {
+    const float tmp = sn;
+    sn = cs;
+    cs = tmp;
+  }
+  switch (quad) {
+    case 0: *sp = sn; *cp = cs; break;
+    case 1: *sp = cs; *cp = -sn; break;
+    case 2: *sp = -sn; *cp = -cs; break;
+    default: *sp = -cs; *cp = sn; break;
+  }
+}
+
+// standard normal of degree of freedom `dof`: key (seed lo, seed hi),
+// counter (step, stage, dof/4 lo, dof/4 hi); lanes 0,1 from outputs (0,1),
+// lanes 2,3 from outputs (2,3); even lanes cosine, odd lanes sine.
+__device__ __forceinline__ float gauss_dof(uint64_t seed, uint32_t step, uint32_t stage, uint64_t dof) {
+  const uint64_t g = dof >> 2;
+  const int lane = (int)(dof & 3u);
+  const uint4 o = philox4x32_10(make_uint4(step, stage, (uint32_t)g, (uint32_t)(g >> 32)),
+                                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const uint32_t ra = (lane >> 1) ? o.z : o.x;
+  const uint32_t rb = (lane >> 1) ? o.w : o.y;
+  const float lg = log_u24(ra);
+  const float rho = __fsqrt_rn(__fmul_rn(-2.0f, lg));
+  float sn, cs;
+  sincos_2pi(rb, &sn, &cs);
+  return __fmul_rn(rho, (lane & 1) ? sn : cs);
+}
+
+// kernel launchers (defined in the .cu files)
+void launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo);
+void launch_forces(const Dev& d, cudaStream_t s, const AtomInfo* ainfo_atom);
+void launch_prop(const Dev& d, cudaStream_t s, int mode);
+void launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type);
+void launch_forces_out(const Dev& d, cudaStream_t s);
+void launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n,
+                  float* out);
+
+// propagation modes
+enum : int {
+  PM_END = 1,      // finish a step: B(dt/2), O(dt/2) stage 1
+  PM_START = 2,    // begin a step: O(dt/2) stage 0, B(dt/2), A(dt)
+  PM_EST = 4,      // estimator partials of the finished step
+  PM_PCART = 8,    // write Cartesian momenta to the caller
+  PM_QCART = 16,   // write Cartesian positions and force mirrors from q_nm
+  PM_IMPORT = 32,  // q_nm, p_nm <- C^T (caller q, p) before anything else
+  PM_MIRROR = 64,  // mirrors from the caller's q, mode-space state untouched
+};
+
+}  // namespace mx

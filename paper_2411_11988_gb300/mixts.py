@@ -1,0 +1,234 @@
+"""ctypes binding of the C ABI in include/mixts.h (argument marshalling only).
+
+Every step of the hot path runs in the CUDA library ``_build/libmixts.so``;
+this module allocates the caller-owned device buffers with torch, packs the
+system description into the C struct and forwards calls. There is no CPU
+fallback: if the library or a GPU is missing, construction raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmixts.so")
+MAX_TYPES = 16
+
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_BEADS", 3: "ERR_CUDA", 4: "ERR_WORKSPACE",
+          5: "ERR_NLIST_OVERFLOW", 6: "ERR_TIMEOUT", 7: "ERR_NONFINITE", 8: "ERR_STATE", 9: "ERR_BOX"}
+FP64, FP32_FORCES = 0, 1
+
+_lib = None
+
+
+class MixtsError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"mixts {STATUS.get(status, status)}: {msg}")
+
+
+class _System(C.Structure):
+    _fields_ = [
+        ("n_atoms", C.c_int), ("n_types", C.c_int),
+        ("type_of_atom", C.POINTER(C.c_int)), ("mol_of_atom", C.POINTER(C.c_int)),
+        ("P_type", C.POINTER(C.c_int)), ("mass_type", C.POINTER(C.c_double)),
+        ("charge_type", C.POINTER(C.c_double)), ("lj_eps", C.POINTER(C.c_double)),
+        ("lj_sig", C.POINTER(C.c_double)), ("pseudo_type", C.POINTER(C.c_int)),
+        ("pp_sigma", C.POINTER(C.c_double)), ("pp_A_eV", C.POINTER(C.c_double)),
+        ("pp_b", C.POINTER(C.c_double)),
+        ("n_bonds", C.c_int), ("bonds", C.POINTER(C.c_int)),
+        ("bond_k", C.POINTER(C.c_double)), ("bond_r0", C.POINTER(C.c_double)),
+        ("n_angles", C.c_int), ("angles", C.POINTER(C.c_int)),
+        ("angle_k", C.POINTER(C.c_double)), ("angle_theta0", C.POINTER(C.c_double)),
+        ("box", C.c_double),
+        ("q", C.c_void_p), ("p", C.c_void_p), ("f", C.c_void_p),
+        ("seed", C.c_uint64),
+    ]
+
+
+class _Params(C.Structure):
+    _fields_ = [("T", C.c_double), ("dt", C.c_double), ("tau_centroid", C.c_double),
+                ("pile_lambda", C.c_double), ("r_cut", C.c_double), ("dsf_alpha", C.c_double),
+                ("precision", C.c_int), ("nlist_cap", C.c_int)]
+
+
+class _Estimates(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "V", "V_lj", "V_coul", "V_bond", "V_angle", "V_pseudo", "KE_beads", "E_spring", "virial",
+        "T_beads", "H_mix", "heat", "H_conserved", "n_evals", "n_pseudo_evals")] + [
+        ("KE_prim", C.c_double * MAX_TYPES), ("KE_cv", C.c_double * MAX_TYPES),
+        ("Rg2", C.c_double * MAX_TYPES), ("E_spring_t", C.c_double * MAX_TYPES),
+        ("step", C.c_int64)]
+
+
+def lib():
+    """Load the CUDA library (build it first with ``build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_2411_11988_gb300.build.build())")
+        L = C.CDLL(LIB_PATH)
+        S, Pp = C.POINTER(_System), C.POINTER(_Params)
+        L.mixts_workspace_size.argtypes = [S, C.c_int, Pp]
+        L.mixts_workspace_size.restype = C.c_size_t
+        L.mixts_init.argtypes = [S, C.c_int, Pp, C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]
+        L.mixts_forces.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+        L.mixts_step.argtypes = [C.c_void_p, C.c_int]
+        L.mixts_estimators.argtypes = [C.c_void_p, C.POINTER(_Estimates)]
+        L.mixts_nlist.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_long, C.POINTER(C.c_long),
+                                  C.POINTER(C.c_double)]
+        L.mixts_state_size.argtypes = [C.c_void_p]
+        L.mixts_state_size.restype = C.c_size_t
+        L.mixts_get_state.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+        L.mixts_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+        L.mixts_gaussians.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint64, C.c_long, C.c_void_p]
+        L.mixts_destroy.argtypes = [C.c_void_p]
+        L.mixts_last_error.argtypes = [C.c_void_p]
+        L.mixts_last_error.restype = C.c_char_p
+        L.mixts_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+EXPORTED = ["mixts_workspace_size", "mixts_init", "mixts_forces", "mixts_step", "mixts_estimators",
+            "mixts_nlist", "mixts_state_size", "mixts_get_state", "mixts_set_state", "mixts_gaussians",
+            "mixts_destroy", "mixts_last_error", "mixts_version"]
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def pack_system(sysm, q_ptr=0, p_ptr=0, f_ptr=0, seed=0):
+    """Pack a system description (attributes as in the synthetic builders) into the C struct.
+
+    Returns (struct, keepalive) -- keep ``keepalive`` until mixts_init returns.
+    """
+    f64 = lambda x: np.ascontiguousarray(x, dtype=np.float64)
+    i32 = lambda x: np.ascontiguousarray(x, dtype=np.int32)
+    k = dict(type_of_atom=i32(sysm.type_of_atom), mol_of_atom=i32(sysm.mol_of_atom), P_type=i32(sysm.P_type),
+             mass_type=f64(sysm.mass_type), charge_type=f64(sysm.charge_type),
+             lj_eps=f64(sysm.lj_eps).ravel(), lj_sig=f64(sysm.lj_sig).ravel(),
+             pseudo_type=i32(sysm.pseudo_type), pp_sigma=f64(sysm.pp_sigma), pp_A_eV=f64(sysm.pp_A_eV),
+             pp_b=f64(sysm.pp_b), bonds=i32(sysm.bonds).ravel(), bond_k=f64(sysm.bond_k),
+             bond_r0=f64(sysm.bond_r0), angles=i32(sysm.angles).ravel(), angle_k=f64(sysm.angle_k),
+             angle_theta0=f64(sysm.angle_theta0))
+    s = _System(len(k["type_of_atom"]), len(k["P_type"]),
+                _ptr(k["type_of_atom"], C.c_int), _ptr(k["mol_of_atom"], C.c_int), _ptr(k["P_type"], C.c_int),
+                _ptr(k["mass_type"], C.c_double), _ptr(k["charge_type"], C.c_double),
+                _ptr(k["lj_eps"], C.c_double), _ptr(k["lj_sig"], C.c_double), _ptr(k["pseudo_type"], C.c_int),
+                _ptr(k["pp_sigma"], C.c_double), _ptr(k["pp_A_eV"], C.c_double), _ptr(k["pp_b"], C.c_double),
+                int(len(k["bond_k"])), _ptr(k["bonds"], C.c_int), _ptr(k["bond_k"], C.c_double),
+                _ptr(k["bond_r0"], C.c_double), int(len(k["angle_k"])), _ptr(k["angles"], C.c_int),
+                _ptr(k["angle_k"], C.c_double), _ptr(k["angle_theta0"], C.c_double),
+                float(sysm.box), q_ptr, p_ptr, f_ptr, int(seed))
+    return s, k
+
+
+class MixTS:
+    """One system on one GPU, driven through the C ABI.
+
+    ``q``, ``p``, ``f`` are float64 torch tensors [n_beads, 3] on the device in
+    the library's bead layout; the workspace is a uint8 torch tensor.
+    """
+
+    def __init__(self, sysm, T=300.0, dt=0.25, tau=100.0, pile_lambda=1.0, r_cut=9.0, alpha=0.2,
+                 precision=FP64, nlist_cap=0, seed=0, device="cuda:0", stream=None, q=None, p=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("MixTS needs a CUDA device")
+        L = lib()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        q0 = np.asarray(sysm.q if q is None else q, dtype=np.float64)
+        p0 = np.asarray(sysm.p if p is None else p, dtype=np.float64)
+        self.n_beads = q0.shape[0]
+        self.n_types = int(len(sysm.P_type))
+        with torch.cuda.device(self.device):
+            self.q = torch.from_numpy(q0.copy()).to(self.device)
+            self.p = torch.from_numpy(p0.copy()).to(self.device)
+            self.f = torch.zeros_like(self.q)
+        self.params = _Params(float(T), float(dt), float(tau), float(pile_lambda), float(r_cut), float(alpha),
+                              int(precision), int(nlist_cap))
+        s, keep = pack_system(sysm, self.q.data_ptr(), self.p.data_ptr(), self.f.data_ptr(), seed)
+        nbytes = L.mixts_workspace_size(C.byref(s), 1, C.byref(self.params))
+        if nbytes == 0:
+            raise MixtsError(1, "mixts_workspace_size rejected the system")
+        self.ws = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        aligned = (base + 255) & ~255
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = L.mixts_init(C.byref(s), 1, C.byref(self.params), C.c_void_p(aligned), int(nbytes),
+                              C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        del keep
+        if st != 0:
+            raise MixtsError(st, "mixts_init failed")
+        self.h = h
+
+    # -- calls -------------------------------------------------------------
+    def _check(self, st):
+        if st != 0:
+            raise MixtsError(st, lib().mixts_last_error(self.h).decode())
+
+    def forces(self, energy=True):
+        e = C.c_double(0.0)
+        self._check(lib().mixts_forces(self.h, C.byref(e) if energy else None))
+        return self.f, (e.value if energy else None)
+
+    def step(self, n=1):
+        self._check(lib().mixts_step(self.h, int(n)))
+
+    def estimators(self) -> dict:
+        out = _Estimates()
+        self._check(lib().mixts_estimators(self.h, C.byref(out)))
+        d = {n: getattr(out, n) for n, _ in _Estimates._fields_[:15]}
+        nt = self.n_types
+        for n in ("KE_prim", "KE_cv", "Rg2", "E_spring_t"):
+            d[n] = list(getattr(out, n))[:nt]
+        d["step"] = int(out.step)
+        return d
+
+    def nlist(self, kind=0):
+        """(triplets [n,3] int32 sorted by (owner, partner, code), thresholds[3])."""
+        n = C.c_long(0)
+        th = (C.c_double * 3)()
+        self._check(lib().mixts_nlist(self.h, kind, None, 0, C.byref(n), th))
+        out = np.zeros((max(1, n.value), 3), dtype=np.int32)
+        self._check(lib().mixts_nlist(self.h, kind, _ptr(out, C.c_int), n.value, C.byref(n), th))
+        t = out[:n.value]
+        order = np.lexsort((t[:, 2], t[:, 1], t[:, 0]))
+        return t[order], np.array(list(th))
+
+    def get_state(self) -> bytes:
+        nb = lib().mixts_state_size(self.h)
+        buf = (C.c_ubyte * nb)()
+        self._check(lib().mixts_get_state(self.h, buf, nb))
+        return bytes(buf)
+
+    def set_state(self, blob: bytes):
+        buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+        self._check(lib().mixts_set_state(self.h, buf, len(blob)))
+
+    def gaussians(self, step, stage, dof0, n):
+        out = self.torch.empty(int(n), dtype=self.torch.float32, device=self.device)
+        self._check(lib().mixts_gaussians(self.h, int(step), int(stage), int(dof0), int(n),
+                                          C.c_void_p(out.data_ptr())))
+        return out
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mixts_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,194 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GPU only).
+
+Tolerances (FP64 path): forces max|F_gpu - F_or| / RMS(F_or) <= 1e-11,
+energies |V_gpu - V_or| / |V_or| <= 1e-11; neighbour lists and the
+thermostat's normals bit for bit; one full step within 1e-11 of RMS.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FTOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_11988_gb300 as P
+    return P
+
+
+def _c1(seed=0, spread=0.0):
+    s = synth.water_box(32, 9.865, 8, 2, seed=seed)
+    if spread:
+        rng = np.random.default_rng(seed + 7)
+        s.q = s.q + rng.normal(0, spread, s.q.shape)
+    return s
+
+
+def _mixed(P_e=16, seed=3, box=8.4, n=8, spread=0.08):
+    s = synth.water_box(n, box, 8, 2, seed=seed, ion=dict(synth.systems.ION3), electron_P=P_e)
+    rng = np.random.default_rng(seed + 100)
+    s.q = s.q + rng.normal(0, spread, s.q.shape)
+    return s
+
+
+def _force_err(F, F_or):
+    rms = np.sqrt(np.mean(F_or ** 2))
+    return np.abs(F - F_or).max() / rms
+
+
+@pytest.mark.parametrize("case", ["c1", "c1_spread", "mixed16", "mixed128", "uniform4"])
+def test_forces_match_oracle(gpu, case):
+    if case == "c1":
+        s = _c1()
+    elif case == "c1_spread":
+        s = _c1(seed=2, spread=0.1)
+    elif case == "mixed16":
+        s = _mixed(16)
+    elif case == "mixed128":
+        s = _mixed(128)
+    else:
+        s = synth.water_box(27, 9.3, 4, 4, seed=4)
+    m = gpu.MixTS(s)
+    f, V = m.forces()
+    F = f.cpu().numpy()
+    F_or, parts = oracle.forces(s)
+    assert _force_err(F, F_or) < FTOL
+    assert abs(V - parts[0]) <= FTOL * abs(parts[0])
+    est = m.estimators()
+    for k, i in [("V_lj", 1), ("V_coul", 2), ("V_bond", 3), ("V_angle", 4), ("V_pseudo", 5)]:
+        assert abs(est[k] - parts[i]) <= FTOL * max(abs(parts[0]), 1.0), k
+    assert est["n_evals"] == parts[7]
+    assert est["n_pseudo_evals"] == parts[8]
+    assert abs(est["virial"] - parts[6]) <= 1e-10 * max(abs(parts[6]), 1.0)
+    m.close()
+
+
+@pytest.mark.parametrize("case", ["c1_spread", "mixed16", "mixed128"])
+def test_neighbour_lists_bit_exact(gpu, case):
+    s = _c1(seed=5, spread=0.15) if case == "c1_spread" else _mixed(16 if case == "mixed16" else 128)
+    m = gpu.MixTS(s)
+    m.forces()
+    tl, th = m.nlist(0)
+    ol, dmax, R = oracle.nlist(s)
+    assert th[0] == dmax and th[1] == R
+    assert np.array_equal(tl, ol)
+    if s.pseudo_type.any():
+        pl, pth = m.nlist(1)
+        opl, oth = oracle.pseudo_list(s)
+        assert pth[0] == oth[1] and pth[1] == oth[2]
+        assert np.array_equal(pl, opl)
+    m.close()
+
+
+def test_gaussians_bit_exact(gpu):
+    s = _c1()
+    m = gpu.MixTS(s, seed=987654321)
+    for step, stage, dof0, n in [(0, 0, 0, 4096), (17, 1, 123457, 1001), (2 ** 31 + 5, 0, 2 ** 33 + 3, 513)]:
+        g = m.gaussians(step, stage, dof0, n).cpu().numpy()
+        o = oracle.gaussians(987654321, step, stage, dof0, n)
+        assert np.array_equal(g.view(np.uint32), o.view(np.uint32))
+    m.close()
+
+
+def _run_both(s, nsteps, **kw):
+    prm = dict(T=300.0, dt=0.25, tau=100.0, lam=1.0, seed=11)
+    prm.update(kw)
+    import paper_2411_11988_gb300 as P
+    m = P.MixTS(s, T=prm["T"], dt=prm["dt"], tau=prm["tau"], pile_lambda=prm["lam"], seed=prm["seed"])
+    m.step(nsteps)
+    run = oracle.Runner(s, oracle.make_params(**prm))
+    run.step(nsteps)
+    return m, run
+
+
+@pytest.mark.parametrize("case", ["c1", "mixed16", "mixed128"])
+def test_one_step_matches_oracle(gpu, case):
+    s = _c1(seed=1) if case == "c1" else _mixed(16 if case == "mixed16" else 128, seed=9)
+    m, run = _run_both(s, 1, dt=0.1 if case != "c1" else 0.25)
+    q, p, f = (x.cpu().numpy() for x in (m.q, m.p, m.f))
+    assert np.abs(q - run.q).max() < 1e-11 * np.abs(run.q).max()
+    assert np.abs(p - run.p).max() < FTOL * 10 * np.sqrt(np.mean(run.p ** 2))
+    assert _force_err(f, run.F) < 1e-10
+    e, eo = m.estimators(), run.estimators()
+    for k in ["V", "KE_beads", "E_spring", "H_mix", "heat", "T_beads"]:
+        assert abs(e[k] - eo[k]) <= 1e-10 * max(abs(eo[k]), 1.0), (k, e[k], eo[k])
+    for t in range(len(s.P_type)):
+        for k in ["KE_prim", "KE_cv", "Rg2", "E_spring_t"]:
+            assert abs(e[k][t] - eo[k][t]) <= 1e-9 * max(abs(eo[k][t]), 1.0), (k, t)
+    assert e["step"] == 1
+    m.close()
+
+
+def test_twenty_steps_track_oracle(gpu):
+    s = _c1(seed=3)
+    m, run = _run_both(s, 20)
+    q = m.q.cpu().numpy()
+    assert np.abs(q - run.q).max() < 1e-8
+    e, eo = m.estimators(), run.estimators()
+    assert abs(e["H_conserved"] - eo["H_conserved"]) < 1e-7 * abs(eo["H_conserved"])
+    m.close()
+
+
+def test_bitwise_reproducible_and_resumable(gpu):
+    s = _c1(seed=6)
+    import paper_2411_11988_gb300 as P
+    a = P.MixTS(s, seed=5)
+    a.step(30)
+    qa, pa = a.q.cpu().numpy().copy(), a.p.cpu().numpy().copy()
+    b = P.MixTS(s, seed=5)
+    b.step(30)
+    assert np.array_equal(qa, b.q.cpu().numpy()) and np.array_equal(pa, b.p.cpu().numpy())
+    c = P.MixTS(s, seed=5)
+    c.step(12)
+    blob = c.get_state()
+    c.close()
+    d = P.MixTS(s, seed=5)
+    d.set_state(blob)
+    d.step(18)
+    assert np.array_equal(qa, d.q.cpu().numpy()) and np.array_equal(pa, d.p.cpu().numpy())
+    assert d.estimators()["step"] == 30
+    for x in (a, b, d):
+        x.close()
+
+
+def test_c2_full_size_sampled(gpu):
+    s = synth.water_box(512, 24.83, 32, 4, seed=0)
+    m = gpu.MixTS(s)
+    f, V = m.forces()
+    F = f.cpu().numpy()
+    F_or, parts = oracle.forces(s)
+    assert _force_err(F, F_or) < FTOL
+    assert abs(V - parts[0]) <= FTOL * abs(parts[0])
+    est = m.estimators()
+    assert est["n_evals"] == parts[7]
+    m.close()
+
+
+def test_c3_electron_full_size(gpu):
+    s = synth.water_box(256, 18.6, 8, 1, seed=0, ion=dict(synth.systems.ION3), electron_P=1024)
+    m = gpu.MixTS(s, dt=0.1)
+    f, V = m.forces()
+    F = f.cpu().numpy()
+    F_or, parts = oracle.forces(s)
+    assert _force_err(F, F_or) < FTOL
+    assert abs(V - parts[0]) <= FTOL * abs(parts[0])
+    m.close()
+
+
+def test_nlist_overflow_reported(gpu):
+    s = _c1()
+    m = gpu.MixTS(s, nlist_cap=32)
+    with pytest.raises(gpu.MixtsError) as ei:
+        m.forces()
+    assert ei.value.status == 5
+    m.close()
