@@ -1,0 +1,302 @@
+#!/usr/bin/env python3
+"""mixTS-PIMD step benchmark on one GB300 (or N independent replicas).
+
+Workload (the plain method at size): 512 flexible waters in a 24.83 A
+periodic box, mixTS bead counts H 32 / O 4, FP64 forces and integration,
+300 K, dt 0.25 fs, PILE-L tau 100 fs. One step = neighbour search + mixTS
+pair sweep + bonded terms + normal-mode propagation + thermostat +
+estimators. The uniform-bead form (all atoms P = 32) runs beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mixTS-PIMD ns/day and bead-pair force evals/s vs uniform-bead FP64, 1 GB300"
+WORKLOAD = dict(workload="512 flexible waters, 24.83 A box, mixTS H32/O4, FP64, 300 K, dt 0.25 fs",
+                n_waters=512, box_A=24.83, P_H=32, P_O=4, dt_fs=0.25, T_K=300.0, tau_fs=100.0,
+                r_cut_A=9.0, dsf_alpha=0.2)
+DT = 0.25
+# algorithmic FP64 flops per in-cutoff bead-pair term of the pair kernel,
+# counted from its source (add/mul 1, fma 2, rsqrt/erfc/exp 1 each):
+# displacement 6, r^2 5, r and 1/r^2 2, DSF energy+force 21, scaling and
+# accumulation 9 -> 43; terms with a Lennard-Jones part add 20.
+FLOPS_PAIR = 43
+FLOPS_LJ_EXTRA = 20
+# FP64 ALU peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def ns_per_day(ms_per_step, dt=DT):
+    return (1000.0 / ms_per_step) * dt * 86400.0 * 1e-6
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile(prefix="clocks_", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.close()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def build_system(P_H, P_O, seed):
+    import synth
+    return synth.water_box(WORKLOAD["n_waters"], WORKLOAD["box_A"], P_H, P_O, seed=seed)
+
+
+CHUNK = 10
+
+
+def timed_run(m, torch, stream, steps, warmup, flush, clocks_idx=None, chunk=CHUNK):
+    """Device time of exactly `steps` steps, run as chunks of `chunk` steps
+    (one mixts_step call each, the production loop); L2 is flushed before
+    every chunk, outside the timed events."""
+    for _ in range(warmup):
+        flush.zero_()
+        m.step(1)
+    stream.synchronize()
+    m.set_timing(True)
+    k0 = m.timing()[2]
+    sizes = [min(chunk, steps - i) for i in range(0, steps, chunk)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in sizes]
+    clk = Clocks(clocks_idx) if clocks_idx is not None else None
+    if clk:
+        clk.__enter__()
+    stream.synchronize()
+    with torch.cuda.stream(stream):
+        for (a, b), n in zip(ev, sizes):
+            flush.zero_()
+            a.record(stream)
+            m.step(n)
+            b.record(stream)
+    stream.synchronize()
+    if clk:
+        clk.__exit__()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ph_ms, ph_calls, k1 = m.timing()
+    m.set_timing(False)
+    return sum(ms) / steps, ph_ms, ph_calls, k1 - k0, (clk.summary() if clk else None)
+
+
+def single_call_ms(m, torch, stream, steps, flush):
+    """Mean device time of one mixts_step(1) call with L2 flushed before each."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stream.synchronize()
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            m.step(1)
+            b.record(stream)
+    stream.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+
+def e2e_run(m, torch, stream, steps):
+    """Host-resident state through the public API: per step upload q, p from
+    pinned host memory, step, download q, p and the estimates."""
+    hq = torch.empty(m.q.shape, dtype=torch.float64, pin_memory=True)
+    hp = torch.empty(m.p.shape, dtype=torch.float64, pin_memory=True)
+    hq.copy_(m.q)
+    hp.copy_(m.p)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            m.q.copy_(hq, non_blocking=True)
+            m.p.copy_(hp, non_blocking=True)
+            m.reload()
+            m.step(1)
+            hq.copy_(m.q, non_blocking=True)
+            hp.copy_(m.p, non_blocking=True)
+            m.estimators()  # synchronises and reads the estimate record
+    t1 = time.perf_counter()
+    nb = m.q.numel() * 8
+    return (t1 - t0) * 1000.0 / steps, 2 * nb, 2 * nb + 8 * 21
+
+
+def cpu_baseline(steps, warmup=0):
+    """The FP64 oracle, as it stands, on the host: `steps` full steps of the workload."""
+    import oracle
+    s = build_system(WORKLOAD["P_H"], WORKLOAD["P_O"], 0)
+    prm = oracle.make_params(T=300.0, dt=DT, tau=100.0, lam=1.0, seed=0)
+    run = oracle.Runner(s, prm)
+    run.step(warmup)
+    t0 = time.perf_counter()
+    run.step(steps)
+    t1 = time.perf_counter()
+    ms = (t1 - t0) * 1000.0 / steps
+    return ms, {"value": ns_per_day(ms), "unit": "ns/day", "cores": 1, "kind": "oracle",
+                "sample": f"{steps} full steps of the workload (single-threaded C oracle)",
+                "ms_per_step": ms}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-uniform", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # bounded sample: each step is one full oracle step of the workload
+        # (~2 s); warm-up steps untimed, at most 60 timed steps
+        k = max(1, min(args.steps, 60))
+        ms, cb = cpu_baseline(k, warmup=min(args.warmup, 3))
+        line = {"metric": METRIC, "value": cb["value"], "unit": "ns/day", "n_gpus": args.gpus,
+                "steps": k, "warmup": min(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": dict(WORKLOAD, l2="n/a (host)"), "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2411_11988_gb300 import MixTS
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    s = build_system(WORKLOAD["P_H"], WORKLOAD["P_O"], seed=rank)
+    m = MixTS(s, T=300.0, dt=DT, tau=100.0, seed=rank, device=str(dev), stream=stream)
+    step_ms, ph_ms, ph_calls, kernels, clk = timed_run(m, torch, stream, args.steps, args.warmup, flush,
+                                                       clocks_idx=local)
+    est = m.estimators()
+    single_ms = single_call_ms(m, torch, stream, max(3, args.steps // 2), flush)
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = ns_per_day(step_ms) * world
+    evals = est["n_evals"]
+    pair_ms = ph_ms["pair"] / max(1, ph_calls["pair"])
+    flops = (evals - est["n_lj_evals"]) * FLOPS_PAIR + est["n_lj_evals"] * (FLOPS_PAIR + FLOPS_LJ_EXTRA)
+    achieved = flops / (pair_ms * 1e-3) / 1e12
+    e2e_ms, h2d, d2h = e2e_run(m, torch, stream, max(3, args.steps // 2))
+
+    uni = None
+    if not args.no_uniform:
+        su = build_system(32, 32, seed=rank)
+        mu = MixTS(su, T=300.0, dt=DT, tau=100.0, seed=rank, device=str(dev), stream=stream)
+        ku = max(3, args.steps // 2)
+        su_ms, phu, callsu, _, _ = timed_run(mu, torch, stream, ku, 3, flush)
+        eu = mu.estimators()
+        uni = {"ns_per_day": ns_per_day(su_ms), "ms_per_step": su_ms, "bead_pair_evals_per_step": eu["n_evals"],
+               "bead_pair_evals_per_s": eu["n_evals"] * 1000.0 / su_ms, "steps": ku,
+               "pair_kernel_ms": phu["pair"] / max(1, callsu["pair"])}
+        mu.close()
+
+    cb = None
+    if rank == 0 and not args.no_cpu:
+        _, cb = cpu_baseline(args.cpu_steps)
+
+    if rank == 0:
+        per_phase = {k: ph_ms[k] / max(1, ph_calls[k]) for k in ph_ms if ph_calls[k]}
+        line = {
+            "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded lattice water, Maxwell-Boltzmann momenta)",
+            "config": dict(WORKLOAD, l2=f"flushed (256 MiB write, untimed) before every timed chunk of {CHUNK} "
+                                        "steps; steps in a chunk run back to back as in production",
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+            "bead_pair_evals_per_s": evals * 1000.0 / step_ms * world,
+            "bead_pair_evals_per_step": evals,
+            "ms_per_step_single_calls": single_ms,
+            "uniform_fp64": uni,
+            "mixts_speedup_vs_uniform": (uni["ms_per_step"] / step_ms) if uni else None,
+            "roofline": {"bound": "alu", "kernel": "k_pair64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                         "flops_per_launch": flops, "launch_ms": pair_ms},
+            "phase_ms_per_call": per_phase,
+            "cpu_baseline": cb,
+            "e2e": {"value": ns_per_day(e2e_ms) * world, "unit": "ns/day", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "note": "host-resident state: upload q,p, re-import and recompute forces, step, download"},
+            "gpu_launches": kernels,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    m.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

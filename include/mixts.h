@@ -116,6 +116,7 @@ typedef struct {
   double H_conserved;/* H_mix + heat */
   double n_evals;    /* nonbonded bead-pair terms inside r_cut (algorithmic count) */
   double n_pseudo_evals;
+  double n_lj_evals; /* nonbonded terms among them with a Lennard-Jones part */
   double KE_prim[MIXTS_MAX_TYPES]; /* primitive kinetic estimator per type */
   double KE_cv[MIXTS_MAX_TYPES];   /* centroid-virial kinetic estimator per type */
   double Rg2[MIXTS_MAX_TYPES];     /* mean squared bead distance from the centroid */
@@ -159,6 +160,22 @@ MIXTS_API mixts_status mixts_nlist(mixts_handle h, int kind, int* out3_host, lon
 MIXTS_API size_t mixts_state_size(mixts_handle h);
 MIXTS_API mixts_status mixts_get_state(mixts_handle h, void* blob_host, size_t bytes);
 MIXTS_API mixts_status mixts_set_state(mixts_handle h, const void* blob_host, size_t bytes);
+
+/* The caller rewrote q and/or p in place: the next mixts_step re-imports
+ * them into normal modes and recomputes the forces first. */
+MIXTS_API mixts_status mixts_reload(mixts_handle h);
+
+/* Per-phase device timing with CUDA events on the handle's stream.
+ * Phases: 0 neighbour lists, 1 nonbonded pair sweep, 2 bonded terms,
+ * 3 pseudopotential, 4 propagation (normal modes, thermostat, kicks),
+ * 5 step finalisation, 6 other. mixts_set_timing(h, 1) clears and starts
+ * collecting, 0 stops. mixts_get_timing synchronises and returns the summed
+ * milliseconds and launch counts per phase, plus the total number of kernels
+ * the library has launched since mixts_init (counted with timing on or off). */
+#define MIXTS_N_PHASES 7
+MIXTS_API mixts_status mixts_set_timing(mixts_handle h, int on);
+MIXTS_API mixts_status mixts_get_timing(mixts_handle h, double* ms_host, long long* calls_host,
+                                        long long* kernels_host);
 
 /* Test hook: standard normals of the thermostat stream (Philox4x32-10 and
  * the binary32 Box-Muller transform) for dofs [dof0, dof0+n), written to a

@@ -46,62 +46,100 @@ __device__ __forceinline__ float screen_margin(double L, double R) {
   return (float)(4.0 * e2 + 1e-9);
 }
 
-// max spread over atoms whose pseudo flag equals want
-__device__ double reduce_spread_kind(const Dev& d, const int* atom_is_pseudo, int want, double* red) {
-  double m = 0.0;
+// (float)(k - 2) for 0 <= k < 2^23 without a conversion instruction:
+// 2^23 + k has k in its mantissa bits.
+__device__ __forceinline__ float img_of(int k) { return __int_as_float(0x4B000000 | k) - 8388610.0f; }
+
+// bit k of the result is set when |d + (k - 2) L| < Rlin, k = 0..4
+__device__ __forceinline__ unsigned img_mask(float dd, float Lf, float Rlin) {
+  unsigned m = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) m |= (fabsf(dd + (float)(k - 2) * Lf) < Rlin ? 1u : 0u) << k;
+  return m;
+}
+
+// max spread over atoms whose pseudo flag equals want; spreads are
+// non-negative doubles, whose bit patterns order like the values, so the max
+// runs on integer instructions
+__device__ double reduce_spread_kind(const Dev& d, const int* atom_is_pseudo, int want, long long* red) {
+  long long m = 0;
   const int n = d.n_atoms * d.spread_slots;
   for (int a = threadIdx.x; a < n; a += blockDim.x) {
     const int atom = a / d.spread_slots;
-    if (atom_is_pseudo[atom] == want) m = fmax(m, d.spread[a]);
+    if (atom_is_pseudo[atom] == want) m = max(m, __double_as_longlong(d.spread[a]));
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
-  double r = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+  long long r = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, red[w]);
   __syncthreads();
-  return r;
+  return __longlong_as_double(r);
 }
 
 constexpr int NL_THREADS = 256;
+constexpr int NL_CPL = 4;  // candidates per lane of one list warp
 
-__global__ void __launch_bounds__(NL_THREADS) k_nlist(Dev d, const int* atom_is_pseudo) {
-  __shared__ double red[NL_THREADS / 32];
-  __shared__ int cnt[NL_THREADS / 32];
-  const double dmax = reduce_spread_kind(d, atom_is_pseudo, 0, red);
-  const double L = d.box;
-  const double R = __dadd_rn(d.rc, __dmul_rn(2.0, dmax));
-  const double R2 = __dmul_rn(R, R);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    d.thresh[0] = dmax;
+// Once per list build: d_max of sites and of pseudo particles, the two list
+// radii (binary64, in the order the definition states), and cleared row
+// counters. thresh: [0] d_max, [1] R, [2] d_max pseudo, [3] R pseudo.
+__global__ void k_list_prep(Dev d, const int* atom_is_pseudo) {
+  __shared__ long long red[32];
+  const double ds = reduce_spread_kind(d, atom_is_pseudo, 0, red);
+  const double dp = reduce_spread_kind(d, atom_is_pseudo, 1, red);
+  for (int i = threadIdx.x; i < d.n_nonp; i += blockDim.x) d.nl_cnt[i] = 0;
+  for (int i = threadIdx.x; i < d.n_pseudo; i += blockDim.x) d.pl_cnt[i] = 0;
+  if (threadIdx.x == 0) {
+    const double L = d.box;
+    const double R = __dadd_rn(d.rc, __dmul_rn(2.0, ds));
+    const double Rp = __dadd_rn(__dadd_rn(d.rc, ds), dp);
+    d.thresh[0] = ds;
     d.thresh[1] = R;
-  }
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int i = blockIdx.x * (NL_THREADS / 32) + wib;
-  if (lane == 0) cnt[wib] = 0;
-  __syncwarp();
-  if (i >= d.n_nonp) return;
-  if (!(R < 2.0 * L)) {
-    if (lane == 0) {
-      atomicOr(d.err, ERR_BOX);
-      d.nl_cnt[i] = 0;
+    d.thresh[2] = dp;
+    d.thresh[3] = Rp;
+    // binary32 screen constants of both lists: R^2 -/+ margin, linear radius
+    float* tf = (float*)(d.thresh + 4);
+    const double RR[2] = {R, Rp};
+    for (int k = 0; k < 2; ++k) {
+      const float m2 = screen_margin(L, RR[k]);
+      const float R2f = (float)__dmul_rn(RR[k], RR[k]);
+      tf[4 * k + 0] = R2f - m2;
+      tf[4 * k + 1] = R2f + m2;
+      tf[4 * k + 2] = sqrtf(R2f + m2);
+      tf[4 * k + 3] = (RR[k] < 2.0 * L) ? 1.0f : 0.0f;
     }
+    tf[8] = (float)L;
+  }
+}
+
+// One warp per (owner row, chunk of 32 * NL_CPL candidates); entries are
+// appended with a per-row counter, so the row order is arbitrary.
+__global__ void __launch_bounds__(NL_THREADS) k_nlist(Dev d, int nchunk) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int i = w / nchunk;
+  const int chunk = w - i * nchunk;
+  if (i >= d.n_nonp) return;
+  const float4 tf = ((const float4*)(d.thresh + 4))[0];
+  if (tf.w == 0.0f) {
+    if (lane == 0 && chunk == 0) atomicOr(d.err, ERR_BOX);
     return;
   }
-  const float m2 = screen_margin(L, R);
-  const float R2f = (float)R2;
-  const float R2lo = R2f - m2, R2hi = R2f + m2;
-  const float Lf = (float)L;
-  const AtomInfo ai = d.ainfo[i];
-  const int Pi = ai.log2P;
-  const int ai_atom = d.pos_atom[i];
+  const double L = d.box;
+  const double R2 = __dmul_rn(d.thresh[1], d.thresh[1]);
+  const float R2lo = tf.x, R2hi = tf.y, Rlin = tf.z;
+  const float Lf = ((const float*)(d.thresh + 4))[8];
+  const float4 ri = d.reff[i];
+  const int Pi = __float_as_int(ri.w);
   const int moli = d.pos_mol[i];
-  const double rix = d.ref[3 * ai_atom], riy = d.ref[3 * ai_atom + 1], riz = d.ref[3 * ai_atom + 2];
-  const float rfx = (float)rix, rfy = (float)riy, rfz = (float)riz;
   int* row = d.nl + (size_t)i * d.nl_cap;
-  for (int c = lane; c < d.n_nonp; c += 32) {
-    if (c == i) continue;
-    const int Pc = d.ainfo[c].log2P;
+  const int c0 = chunk * 32 * NL_CPL;
+#pragma unroll 1
+  for (int t = 0; t < NL_CPL; ++t) {
+    const int c = c0 + t * 32 + lane;
+    if (c >= d.n_nonp || c == i) continue;
+    const float4 rc4 = d.reff[c];
+    const int Pc = __float_as_int(rc4.w);
     bool own;
     if (Pi != Pc) {
       own = Pi > Pc;
@@ -110,22 +148,24 @@ __global__ void __launch_bounds__(NL_THREADS) k_nlist(Dev d, const int* atom_is_
       own = (((i + c) & 1) == 0) ? (i == lo) : (i != lo);
     }
     if (!own) continue;
-    const int ca = d.pos_atom[c];
-    const double rcx = d.ref[3 * ca], rcy = d.ref[3 * ca + 1], rcz = d.ref[3 * ca + 2];
-    const float dfx = (float)rcx - rfx, dfy = (float)rcy - rfy, dfz = (float)rcz - rfz;
+    const float dfx = rc4.x - ri.x, dfy = rc4.y - ri.y, dfz = rc4.z - ri.z;
+    const unsigned mx = img_mask(dfx, Lf, Rlin);
+    if (!mx) continue;
+    const unsigned my = img_mask(dfy, Lf, Rlin);
+    if (!my) continue;
+    const unsigned mz = img_mask(dfz, Lf, Rlin);
+    if (!mz) continue;
     const bool same = d.pos_mol[c] == moli;
-    // per-dimension candidate images
-    const float Rlin = sqrtf(R2hi);
-    for (int nx = -2; nx <= 2; ++nx) {
-      const float ex = dfx + (float)nx * Lf;
-      if (fabsf(ex) >= Rlin) continue;
-      for (int ny = -2; ny <= 2; ++ny) {
-        const float ey = dfy + (float)ny * Lf;
-        if (fabsf(ey) >= Rlin) continue;
-        for (int nz = -2; nz <= 2; ++nz) {
-          const float ez = dfz + (float)nz * Lf;
-          if (fabsf(ez) >= Rlin) continue;
-          if (same && nx == 0 && ny == 0 && nz == 0) continue;
+    for (unsigned bx = mx; bx; bx &= bx - 1) {
+      const int kx = __ffs(bx) - 1;
+      const float ex = dfx + img_of(kx) * Lf;
+      for (unsigned by = my; by; by &= by - 1) {
+        const int ky = __ffs(by) - 1;
+        const float ey = dfy + img_of(ky) * Lf;
+        for (unsigned bz = mz; bz; bz &= bz - 1) {
+          const int kz = __ffs(bz) - 1;
+          if (same && kx == 2 && ky == 2 && kz == 2) continue;
+          const float ez = dfz + img_of(kz) * Lf;
           const float d2f = ex * ex + ey * ey + ez * ez;
           bool keep;
           if (d2f < R2lo) {
@@ -133,54 +173,43 @@ __global__ void __launch_bounds__(NL_THREADS) k_nlist(Dev d, const int* atom_is_
           } else if (d2f > R2hi) {
             keep = false;
           } else {
-            const double dlx = __dsub_rn(rcx, rix), dly = __dsub_rn(rcy, riy), dlz = __dsub_rn(rcz, riz);
-            keep = exact_d2(dlx, dly, dlz, nx, ny, nz, L) < R2;
+            const double4_32a a = d.refd[i], bb = d.refd[c];
+            keep = exact_d2(__dsub_rn(bb.x, a.x), __dsub_rn(bb.y, a.y), __dsub_rn(bb.z, a.z), kx - 2, ky - 2,
+                            kz - 2, L) < R2;
           }
           if (keep) {
-            const int slot = atomicAdd(&cnt[wib], 1);
-            if (slot < d.nl_cap) row[slot] = (c << 7) | ((nx + 2) * 25 + (ny + 2) * 5 + (nz + 2));
+            const int slot = atomicAdd(&d.nl_cnt[i], 1);
+            if (slot < d.nl_cap)
+              row[slot] = (d.ainfo[c].row0 << 11) | (d.ainfo[c].type << 7) | (kx * 25 + ky * 5 + kz);
+            else
+              atomicOr(d.err, ERR_NLIST);
           }
         }
       }
     }
   }
-  __syncwarp();
-  if (lane == 0) {
-    const int n = cnt[wib];
-    if (n > d.nl_cap) atomicOr(d.err, ERR_NLIST);
-    d.nl_cnt[i] = n < d.nl_cap ? n : d.nl_cap;
-  }
 }
 
 // pseudo-particle site list: one thread per (pseudo atom, site position)
-__global__ void k_plist(Dev d, const int* atom_is_pseudo) {
-  __shared__ double red[8];
-  const double ds = reduce_spread_kind(d, atom_is_pseudo, 0, red);
-  const double dp = reduce_spread_kind(d, atom_is_pseudo, 1, red);
+__global__ void k_plist(Dev d) {
   const double L = d.box;
-  const double R = __dadd_rn(__dadd_rn(d.rc, ds), dp);
-  const double R2 = __dmul_rn(R, R);
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-    d.thresh[2] = dp;
-    d.thresh[3] = R;
-  }
+  const double R2 = __dmul_rn(d.thresh[3], d.thresh[3]);
   const int e = blockIdx.y;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.n_nonp) return;
-  if (!(R < 2.0 * L)) {
+  const float4 tf = ((const float4*)(d.thresh + 4))[1];
+  if (tf.w == 0.0f) {
     atomicOr(d.err, ERR_BOX);
     return;
   }
-  const float m2 = screen_margin(L, R);
-  const float R2f = (float)R2;
-  const float R2lo = R2f - m2, R2hi = R2f + m2;
+  const float R2lo = tf.x, R2hi = tf.y, Rlin = tf.z;
   const float Lf = (float)L;
-  const float Rlin = sqrtf(R2hi);
   const int ea = d.pseudo_atom[e];
   const double rex = d.ref[3 * ea], rey = d.ref[3 * ea + 1], rez = d.ref[3 * ea + 2];
-  const int ca = d.pos_atom[c];
-  const double rcx = d.ref[3 * ca], rcy = d.ref[3 * ca + 1], rcz = d.ref[3 * ca + 2];
-  const float dfx = (float)rcx - (float)rex, dfy = (float)rcy - (float)rey, dfz = (float)rcz - (float)rez;
+  const double4_32a rcd = d.refd[c];
+  const double rcx = rcd.x, rcy = rcd.y, rcz = rcd.z;
+  const float4 rcf = d.reff[c];
+  const float dfx = rcf.x - (float)rex, dfy = rcf.y - (float)rey, dfz = rcf.z - (float)rez;
   for (int nx = -2; nx <= 2; ++nx) {
     const float ex = dfx + (float)nx * Lf;
     if (fabsf(ex) >= Rlin) continue;
@@ -225,13 +254,60 @@ __device__ __forceinline__ void item_of_warp(const Dev& d, int w, int* pos, int*
   *pos = d.cls_pos0[c] + (local - *bead * d.cls_n[c]);
 }
 
+// Unit-charge DSF potential G(s), s = r^2, and -2 dG/ds from the interval
+// table: each is a quintic in x = s - s0 on each of 64 geometric
+// sub-intervals per octave of s; the interval and s0 come straight from the
+// exponent and top mantissa bits of s (integer instructions only).
+__device__ __forceinline__ void dsf_table(const double* tab, int hi, double s, double* g, double* fg) {
+  const double s0 = __hiloint2double((hi >> 14) << 14, 0);
+  const double x = s - s0;
+  const double* c = tab;
+  double p = fma(c[5], x, c[4]);
+  double q = fma(c[11], x, c[10]);
+  p = fma(p, x, c[3]);
+  q = fma(q, x, c[9]);
+  p = fma(p, x, c[2]);
+  q = fma(q, x, c[8]);
+  p = fma(p, x, c[1]);
+  q = fma(q, x, c[7]);
+  *g = fma(p, x, c[0]);
+  *fg = fma(q, x, c[6]);
+}
+
+// analytic G and -2 dG/ds (r below the table range)
+__device__ __forceinline__ void dsf_direct(const Dev& d, double s, double* g, double* fg) {
+  const double r = sqrt(s);
+  const double rinv = 1.0 / r;
+  const double ec = erfc(d.alpha * r);
+  const double ex = exp(-d.alpha * d.alpha * s);
+  *g = ec * rinv - d.dsf_erfc_rc_over_rc + d.dsf_cf * (r - d.rc);
+  // dG/dr = -erfc/r^2 - g exp/r + cf ; -2 dG/ds = -(dG/dr) / r
+  *fg = (ec * rinv * rinv + d.dsf_g * ex * rinv - d.dsf_cf) * rinv;
+}
+
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
+  extern __shared__ double dtab[];  // DSF interval table, 12 doubles per interval
   __shared__ PairPar tab[MT * MT];
-  __shared__ double3 sh[125];
+  __shared__ int flg[MT * MT];      // bit 0: Coulomb, bit 1: Lennard-Jones
+  __shared__ longlong4_32a shi[125];
+  __shared__ float4 shf[125];
+  __shared__ int tN[MT], tLg[MT];
   const int nt = d.n_types;
-  for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) tab[e] = d.pairpar[(e / nt) * MT + (e % nt)];
-  for (int e = threadIdx.x; e < 125; e += blockDim.x)
-    sh[e] = make_double3((e / 25 - 2) * d.box, ((e / 5) % 5 - 2) * d.box, (e % 5 - 2) * d.box);
+  for (int e = threadIdx.x; e < 12 * d.dsf_nint; e += blockDim.x) dtab[e] = d.dsf_tab[e];
+  for (int e = threadIdx.x; e < nt; e += blockDim.x) {
+    tN[e] = d.N[e];
+    tLg[e] = d.log2P[e];
+  }
+  for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
+    const PairPar pp = d.pairpar[(e / nt) * MT + (e % nt)];
+    tab[e] = pp;
+    flg[e] = (pp.qq != 0.0 ? 1 : 0) | (pp.e4 != 0.0 ? 2 : 0);
+  }
+  for (int e = threadIdx.x; e < 125; e += blockDim.x) {
+    const int nx = e / 25 - 2, ny = (e / 5) % 5 - 2, nz = e % 5 - 2;
+    shi[e] = make_longlong4_32a(nx * d.box_fix, ny * d.box_fix, nz * d.box_fix, 0);
+    shf[e] = make_float4(nx * d.box_hi, ny * d.box_hi, nz * d.box_hi, 0.0f);
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -240,77 +316,120 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   item_of_warp(d, w, &pos, &b);
   const AtomInfo ai = d.ainfo[pos];
   const int row_i = ai.row0 + b * ai.stride;
-  const double4_32a xi = d.Xw[row_i];
-  const double wgt = 1.0 / (double)(1 << ai.log2P);
-  const int cnt = d.nl_cnt[pos];
+  const longlong4_32a xi = d.Xi[row_i];
+  const float4 xif = d.Xf[row_i];
+  const int wsh = ai.log2P;  // weight 1/P_i = 2^-wsh
+  const int cnt = min(d.nl_cnt[pos], d.nl_cap);
   const int* lst = d.nl + (size_t)pos * d.nl_cap;
-  const double rc = d.rc, rc2 = d.rc2, al = d.alpha, al2 = d.alpha * d.alpha;
-  const double erc = d.dsf_erfc_rc_over_rc, cf = d.dsf_cf, g = d.dsf_g;
-  double fix = 0.0, fiy = 0.0, fiz = 0.0, elj = 0.0, ec = 0.0, vir = 0.0;
-  int nev = 0;
+  const double rc = d.rc;
+  const long long rc2_bits = __double_as_longlong(d.rc2);
+  const int slo_hi = __double2hiint(d.dsf_smin);
+  const float scr2 = d.screen_rc2;
+  const int base = d.dsf_base;
+  const int trow = ai.type * nt;
+  long long fix = 0, fiy = 0, fiz = 0;
+  double elj = 0.0, ec = 0.0, vir = 0.0;
+  int nev = 0, nlj = 0, bad = 0;
+  int ent_next = lane < cnt ? lst[lane] : 0;
   for (int e = lane; e < cnt; e += 32) {
-    const int ent = lst[e];
-    const int j = ent >> 7;
-    const AtomInfo aj = d.ainfo[j];
-    const int bj = b >> (ai.log2P - aj.log2P);
-    const int row_j = aj.row0 + bj * aj.stride;
-    const double4_32a xj = d.Xw[row_j];
-    const double3 s = sh[ent & 127];
-    const double dx = (xj.x - xi.x) + s.x;
-    const double dy = (xj.y - xi.y) + s.y;
-    const double dz = (xj.z - xi.z) + s.z;
-    const double r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 < rc2) {
-      const PairPar pp = tab[ai.type * nt + aj.type];
-      const double rinv = rsqrt(r2);
-      const double r = r2 * rinv;
-      const double rinv2 = rinv * rinv;
+    // entry: (bead-0 row of the partner << 11) | (partner type << 7) | image code
+    const int ent = ent_next;
+    ent_next = e + 32 < cnt ? lst[e + 32] : 0;
+    const int tj = (ent >> 7) & 15;
+    const int bj = b >> (ai.log2P - tLg[tj]);
+    const int row_j = (ent >> 11) + bj * tN[tj];
+    const float4 xjf = d.Xf[row_j];
+    const longlong4_32a xj = d.Xi[row_j];
+    // binary32 screen on the 2^-12 A grid: exact differences, error of the
+    // dropped low parts bounded; only candidates near or inside r_cut go on
+    const float4 sf = shf[ent & 127];
+    const float hx = (xjf.x - xif.x) + sf.x, hy = (xjf.y - xif.y) + sf.y, hz = (xjf.z - xif.z) + sf.z;
+    if (hx * hx + hy * hy + hz * hz > scr2) continue;
+    // exact displacement in 2^-48 A fixed point, converted without the FP64 pipe
+    const longlong4_32a sv = shi[ent & 127];
+    const double dx = fixpos_to_double((xj.x - xi.x) + sv.x);
+    const double dy = fixpos_to_double((xj.y - xi.y) + sv.y);
+    const double dz = fixpos_to_double((xj.z - xi.z) + sv.z);
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    if (__double_as_longlong(r2) < rc2_bits) {
+      const int fl = flg[trow + tj];
+      const PairPar pp = tab[trow + tj];
       double fr = 0.0;
-      if (pp.e4 != 0.0) {
+      if (fl & 1) {
+        double g, fg;
+        const int hi = __double2hiint(r2);
+        if (hi >= slo_hi)
+          dsf_table(dtab + 12 * ((hi >> 14) - base), hi, r2, &g, &fg);
+        else
+          dsf_direct(d, r2, &g, &fg);
+        ec = fma(pp.qq, g, ec);
+        fr = pp.qq * fg;
+      }
+      if (fl & 2) {
+        const double rinv = rsqrt(r2);
+        const double r = r2 * rinv;
+        const double rinv2 = rinv * rinv;
         const double sr2 = pp.s2 * rinv2;
         const double sr6 = sr2 * sr2 * sr2;
         const double sr12 = sr6 * sr6;
-        elj += wgt * (pp.e4 * (sr12 - sr6) - pp.vrc - (r - rc) * pp.dvrc);
+        elj += pp.e4 * (sr12 - sr6) - pp.vrc - (r - rc) * pp.dvrc;
         fr += (6.0 * pp.e4 * (2.0 * sr12 - sr6) * rinv + pp.dvrc) * rinv;
+        ++nlj;
       }
-      if (pp.qq != 0.0) {
-        const double erfc_r = erfc(al * r);
-        const double ex = exp(-al2 * r2);
-        ec += wgt * pp.qq * (erfc_r * rinv - erc + cf * (r - rc));
-        fr += pp.qq * ((erfc_r * rinv + g * ex) * rinv2 - cf * rinv);
-      }
-      fr *= wgt;
-      const double fx = fr * dx, fy = fr * dy, fz = fr * dz;  // force on j
-      fix -= fx;
-      fiy -= fy;
-      fiz -= fz;
-      vir += fr * r2;
+      const long long kx = fix44(fr * dx, wsh, &bad), ky = fix44(fr * dy, wsh, &bad),
+                      kz = fix44(fr * dz, wsh, &bad);
+      fix -= kx;
+      fiy -= ky;
+      fiz -= kz;
+      vir = fma(fr, r2, vir);
       ++nev;
-      fadd3(d.F_fix, row_j, fx, fy, fz, d.err);
+      unsigned long long* fj = d.F_fix + 3 * (size_t)row_j;
+      atomicAdd(fj + 0, (unsigned long long)kx);
+      atomicAdd(fj + 1, (unsigned long long)ky);
+      atomicAdd(fj + 2, (unsigned long long)kz);
     }
   }
-  fix = warp_sum(fix);
-  fiy = warp_sum(fiy);
-  fiz = warp_sum(fiz);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fix += __shfl_xor_sync(0xffffffffu, fix, o);
+    fiy += __shfl_xor_sync(0xffffffffu, fiy, o);
+    fiz += __shfl_xor_sync(0xffffffffu, fiz, o);
+  }
   elj = warp_sum(elj);
   ec = warp_sum(ec);
   vir = warp_sum(vir);
   nev = warp_sumi(nev);
+  nlj = warp_sumi(nlj);
+  bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
-    fadd3(d.F_fix, row_i, fix, fiy, fiz, d.err);
-    eadd(d.E_fix, E_LJ, elj);
-    eadd(d.E_fix, E_COUL, ec);
-    eadd(d.E_fix, E_VIRIAL, vir);
+    // energies carry the weight 1/P_i as an exponent offset of the fixed point
+    unsigned long long* fi = d.F_fix + 3 * (size_t)row_i;
+    atomicAdd(fi + 0, (unsigned long long)fix);
+    atomicAdd(fi + 1, (unsigned long long)fiy);
+    atomicAdd(fi + 2, (unsigned long long)fiz);
+    atomicAdd(d.E_fix + E_LJ, (unsigned long long)fixs(elj, 40 - wsh, &bad));
+    atomicAdd(d.E_fix + E_COUL, (unsigned long long)fixs(ec, 40 - wsh, &bad));
+    atomicAdd(d.E_fix + E_VIRIAL, (unsigned long long)fixs(vir, 40 - wsh, &bad));
+    atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nlj);
     atomicAdd(d.E_fix + E_NEVAL, (unsigned long long)nev);
+    if (bad) atomicOr(d.err, ERR_NONFINITE);
   }
 }
 
 // ---------------------------------------------------------------------------
 // bonded terms: one thread per (term, fine slice)
 // ---------------------------------------------------------------------------
-__global__ void k_bonded(Dev d, const AtomInfo* ainfo_atom) {
+__device__ __forceinline__ void fadd3w(unsigned long long* F, int row, double fx, double fy, double fz, int* bad) {
+  unsigned long long* r = F + 3 * (size_t)row;
+  atomicAdd(r + 0, (unsigned long long)fix44(fx, 0, bad));
+  atomicAdd(r + 1, (unsigned long long)fix44(fy, 0, bad));
+  atomicAdd(r + 2, (unsigned long long)fix44(fz, 0, bad));
+}
+
+__global__ void __launch_bounds__(64) k_bonded(Dev d, const AtomInfo* ainfo_atom) {
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
   double eb = 0.0, ea = 0.0, vir = 0.0;
+  int bad = 0;
   if (it < d.n_bitems) {
     const BondItem bi = d.bitems[it];
     const int s = bi.slice;
@@ -325,12 +444,15 @@ __global__ void k_bonded(Dev d, const AtomInfo* ainfo_atom) {
       const double dx = d.q[3 * (size_t)rcw] - d.q[3 * (size_t)ra];
       const double dy = d.q[3 * (size_t)rcw + 1] - d.q[3 * (size_t)ra + 1];
       const double dz = d.q[3 * (size_t)rcw + 2] - d.q[3 * (size_t)ra + 2];
-      const double r = sqrt(dx * dx + dy * dy + dz * dz);
-      eb = w * 0.5 * k * (r - r0) * (r - r0);
-      const double f = -w * k * (r - r0) / r;
-      vir = f * r * r;
-      fadd3(d.F_fix, rcw, f * dx, f * dy, f * dz, d.err);
-      fadd3(d.F_fix, ra, -f * dx, -f * dy, -f * dz, d.err);
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double rinv = rsqrt(r2);
+      const double r = r2 * rinv;
+      const double kd = w * k * (r - r0);
+      eb = 0.5 * kd * (r - r0);
+      const double f = -kd * rinv;
+      vir = f * r2;
+      fadd3w(d.F_fix, rcw, f * dx, f * dy, f * dz, &bad);
+      fadd3w(d.F_fix, ra, -f * dx, -f * dy, -f * dz, &bad);
     } else {
       const int a1 = d.ang_atoms[3 * bi.term], o = d.ang_atoms[3 * bi.term + 1], a2 = d.ang_atoms[3 * bi.term + 2];
       const AtomInfo A1 = ainfo_atom[a1], O = ainfo_atom[o], A2 = ainfo_atom[a2];
@@ -339,36 +461,41 @@ __global__ void k_bonded(Dev d, const AtomInfo* ainfo_atom) {
       const double w = 1.0 / (double)(1 << lmax);
       const int r1 = A1.row0 + (s >> (lmax - A1.log2P)) * A1.stride;
       const int ro = O.row0 + (s >> (lmax - O.log2P)) * O.stride;
-      const int r2 = A2.row0 + (s >> (lmax - A2.log2P)) * A2.stride;
+      const int r2i = A2.row0 + (s >> (lmax - A2.log2P)) * A2.stride;
       const double k = d.ang_par[2 * bi.term], th0 = d.ang_par[2 * bi.term + 1];
       double u[3], v[3];
       for (int x = 0; x < 3; ++x) {
         u[x] = d.q[3 * (size_t)r1 + x] - d.q[3 * (size_t)ro + x];
-        v[x] = d.q[3 * (size_t)r2 + x] - d.q[3 * (size_t)ro + x];
+        v[x] = d.q[3 * (size_t)r2i + x] - d.q[3 * (size_t)ro + x];
       }
-      const double uu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-      const double vv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-      double cs = (u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) / (uu * vv);
+      const double iu = rsqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      const double iv = rsqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      const double iuv = iu * iv;
+      double cs = (u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) * iuv;
       cs = fmin(1.0, fmax(-1.0, cs));
       const double th = acos(cs);
-      const double sn = sqrt(1.0 - cs * cs);
-      ea = w * 0.5 * k * (th - th0) * (th - th0);
-      const double pref = w * k * (th - th0) / sn;
+      const double isn = rsqrt(1.0 - cs * cs);
+      const double dth = th - th0;
+      ea = w * 0.5 * k * dth * dth;
+      const double pref = w * k * dth * isn;
+      const double au = pref * iuv, bu = pref * cs * iu * iu, bv = pref * cs * iv * iv;
       double f1[3], f2[3];
       for (int x = 0; x < 3; ++x) {
-        f1[x] = pref * (v[x] / (uu * vv) - cs * u[x] / (uu * uu));
-        f2[x] = pref * (u[x] / (uu * vv) - cs * v[x] / (vv * vv));
+        f1[x] = au * v[x] - bu * u[x];
+        f2[x] = au * u[x] - bv * v[x];
       }
       vir = f1[0] * u[0] + f1[1] * u[1] + f1[2] * u[2] + f2[0] * v[0] + f2[1] * v[1] + f2[2] * v[2];
-      fadd3(d.F_fix, r1, f1[0], f1[1], f1[2], d.err);
-      fadd3(d.F_fix, r2, f2[0], f2[1], f2[2], d.err);
-      fadd3(d.F_fix, ro, -f1[0] - f2[0], -f1[1] - f2[1], -f1[2] - f2[2], d.err);
+      fadd3w(d.F_fix, r1, f1[0], f1[1], f1[2], &bad);
+      fadd3w(d.F_fix, r2i, f2[0], f2[1], f2[2], &bad);
+      fadd3w(d.F_fix, ro, -f1[0] - f2[0], -f1[1] - f2[1], -f1[2] - f2[2], &bad);
     }
   }
   eb = warp_sum(eb);
   ea = warp_sum(ea);
   vir = warp_sum(vir);
+  bad = __any_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(d.err, ERR_NONFINITE);
     eadd(d.E_fix, E_BOND, eb);
     eadd(d.E_fix, E_ANGLE, ea);
     eadd(d.E_fix, E_VIRIAL, vir);
@@ -468,26 +595,48 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-void launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo) {
+int launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo) {
+  int n = 1;
+  k_list_prep<<<1, 1024, 0, s>>>(d, atom_is_pseudo);
   if (d.n_nonp > 0) {
+    const int nchunk = (d.n_nonp + 32 * NL_CPL - 1) / (32 * NL_CPL);
+    const long long warps = (long long)d.n_nonp * nchunk;
     const int wpb = NL_THREADS / 32;
-    k_nlist<<<(d.n_nonp + wpb - 1) / wpb, NL_THREADS, 0, s>>>(d, atom_is_pseudo);
+    k_nlist<<<(int)((warps + wpb - 1) / wpb), NL_THREADS, 0, s>>>(d, nchunk);
+    ++n;
   }
-  if (d.n_pseudo > 0) {
-    cudaMemsetAsync(d.pl_cnt, 0, sizeof(int) * d.n_pseudo, s);
-    if (d.n_nonp > 0) {
-      dim3 g((d.n_nonp + 127) / 128, d.n_pseudo);
-      k_plist<<<g, 128, 0, s>>>(d, atom_is_pseudo);
-    }
+  if (d.n_pseudo > 0 && d.n_nonp > 0) {
+    dim3 g((d.n_nonp + 127) / 128, d.n_pseudo);
+    k_plist<<<g, 128, 0, s>>>(d);
+    ++n;
   }
+  return n;
 }
 
-void launch_forces(const Dev& d, cudaStream_t s, const AtomInfo* ainfo_atom) {
+int launch_pair(const Dev& d, cudaStream_t s) {
   const int wpb = PAIR_THREADS / 32;
-  if (d.n_pitems > 0) k_pair64<<<(d.n_pitems + wpb - 1) / wpb, PAIR_THREADS, 0, s>>>(d);
-  if (d.n_bitems > 0) k_bonded<<<(d.n_bitems + 255) / 256, 256, 0, s>>>(d, ainfo_atom);
-  if (d.n_ppitems > 0 && d.n_nonp > 0)
-    k_pseudo64<<<(d.n_ppitems + wpb - 1) / wpb, PAIR_THREADS, 0, s>>>(d);
+  if (d.n_pitems == 0) return 0;
+  const size_t smem = sizeof(double) * 12 * (size_t)d.dsf_nint;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
+  k_pair64<<<(d.n_pitems + wpb - 1) / wpb, PAIR_THREADS, smem, s>>>(d);
+  return 1;
+}
+
+int launch_bonded(const Dev& d, cudaStream_t s, const AtomInfo* ainfo_atom) {
+  if (d.n_bitems == 0) return 0;
+  k_bonded<<<(d.n_bitems + 63) / 64, 64, 0, s>>>(d, ainfo_atom);
+  return 1;
+}
+
+int launch_pseudo(const Dev& d, cudaStream_t s) {
+  const int wpb = PAIR_THREADS / 32;
+  if (d.n_ppitems == 0 || d.n_nonp == 0) return 0;
+  k_pseudo64<<<(d.n_ppitems + wpb - 1) / wpb, PAIR_THREADS, 0, s>>>(d);
+  return 1;
 }
 
 }  // namespace mx

@@ -14,7 +14,7 @@
 
 namespace mx {
 
-constexpr int PROP_THREADS = 128;
+constexpr int PROP_THREADS = 384;  // one thread per element of a P x C tile (P C = 384)
 constexpr int NPART = 6;  // KE, spring, CV, Rg, heat(end), heat(start)
 
 __device__ __forceinline__ void block_sum6(double* v, double* red) {
@@ -49,22 +49,38 @@ struct MirrorOut {
 __device__ __forceinline__ void write_mirror(const Dev& d, int row, double x, double y, double z, double mx_,
                                              double my_, double mz_) {
   const double L = d.box;
-  const double wx = x - mx_ * L, wy = y - my_ * L, wz = z - mz_ * L;
+  const double wx = fma(-mx_, L, x), wy = fma(-my_, L, y), wz = fma(-mz_, L, z);
   d.Xw[row] = make_double4_32a(wx, wy, wz, 0.0);
-  // FP32 mirror: hi on the 2^-12 A grid (exact differences), lo the rest
-  const float hx = (float)(rint(wx * 4096.0) * (1.0 / 4096.0));
-  const float hy = (float)(rint(wy * 4096.0) * (1.0 / 4096.0));
-  const float hz = (float)(rint(wz * 4096.0) * (1.0 / 4096.0));
-  d.Xf[row] = make_float4(hx, hy, hz, 0.0f);
-  d.Xl[row] = make_float4((float)(wx - (double)hx), (float)(wy - (double)hy), (float)(wz - (double)hz), 0.0f);
+  // 2^-48 A fixed point, and the nearest 2^-12 A grid point as binary32
+  int bad = 0;
+  const long long ix = fixs(wx, 48, &bad), iy = fixs(wy, 48, &bad), iz = fixs(wz, 48, &bad);
+  d.Xi[row] = make_longlong4_32a(ix, iy, iz, 0);
+  const int gx = (int)((ix + (1LL << 35)) >> 36), gy = (int)((iy + (1LL << 35)) >> 36),
+            gz = (int)((iz + (1LL << 35)) >> 36);
+  d.Xf[row] = make_float4(small_int_float(gx) * 0x1p-12f, small_int_float(gy) * 0x1p-12f,
+                          small_int_float(gz) * 0x1p-12f, 0.0f);
+  if (bad) atomicOr(d.err, ERR_NONFINITE);
 }
 
-__device__ __forceinline__ double bead_dist(double dx, double dy, double dz) {
+// wrapped bead-0 reference of one atom, by atom index and (for non-pseudo
+// atoms) by sorted position for the neighbour search
+__device__ __forceinline__ void write_ref(const Dev& d, int atom, const double* rf) {
+  for (int x = 0; x < 3; ++x) d.ref[3 * atom + x] = rf[x];
+  const int pos = d.pos_of_atom[atom];
+  if (pos >= 0) {
+    d.refd[pos] = make_double4_32a(rf[0], rf[1], rf[2], 0.0);
+    d.reff[pos] = make_float4((float)rf[0], (float)rf[1], (float)rf[2], __int_as_float(d.ainfo[pos].log2P));
+  }
+}
+
+__device__ __forceinline__ double bead_d2(double dx, double dy, double dz) {
   double d2 = __dmul_rn(dx, dx);
   d2 = __dadd_rn(d2, __dmul_rn(dy, dy));
   d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
-  return __dsqrt_rn(d2);
+  return d2;
 }
+
+__device__ __forceinline__ double bead_dist(double dx, double dy, double dz) { return __dsqrt_rn(bead_d2(dx, dy, dz)); }
 
 // ---------------------------------------------------------------------------
 // small-P fused tile kernel
@@ -73,6 +89,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop_small(Dev d, int mode) {
   extern __shared__ double sm[];
   __shared__ double red[(PROP_THREADS / 32) * NPART];
   __shared__ long long s_step;
+  __shared__ long long s_d2[128];
   const PropTile tl = d.tiles[blockIdx.x];
   const int t = tl.type, P = d.P[t], N = d.N[t], k0 = tl.k0, na = tl.na;
   const int C = 3 * na;
@@ -152,7 +169,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop_small(Dev d, int mode) {
       const double fk = Fn[e];
       if (mode & PM_END) {
         p = fma(hk, fk, p);
-        const double xi = (double)gauss_dof(d.seed, s_end, 1u, dof);
+        const double xi = f2d_bits(gauss_dof(d.seed, s_end, 1u, dof));
         const double pn = fma(mk.c1, p, mk.c2s * xi);
         part[4] += (p * p - pn * pn) * inv2m;
         p = pn;
@@ -163,7 +180,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop_small(Dev d, int mode) {
         }
       }
       if (mode & PM_START) {
-        const double xi = (double)gauss_dof(d.seed, s_start, 0u, dof);
+        const double xi = f2d_bits(gauss_dof(d.seed, s_start, 0u, dof));
         const double pn = fma(mk.c1, p, mk.c2s * xi);
         part[5] += (p * p - pn * pn) * inv2m;
         p = fma(hk, fk, pn);
@@ -196,6 +213,10 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop_small(Dev d, int mode) {
       Xc[e] = a;
       d.q[gidx(j, c)] = a;
     }
+    // squared bead-0 distances, max over beads on the bit patterns, one
+    // square root per atom: sqrt is monotone, so this equals the max of
+    // the rounded distances
+    for (int e = tid; e < na; e += nt) s_d2[e] = 0;
     __syncthreads();
     for (int e = tid; e < P * na; e += nt) {
       const int j = e / na, a = e - (e / na) * na;
@@ -205,16 +226,18 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop_small(Dev d, int mode) {
       const int row = d.off[t] + j * N + k0 + a;
       write_mirror(d, row, Xc[j * C + 3 * a], Xc[j * C + 3 * a + 1], Xc[j * C + 3 * a + 2], fl[0], fl[1], fl[2]);
       if (j == 0) {
-        for (int x = 0; x < 3; ++x) d.ref[3 * atom + x] = rf[x];
-        double sp = 0.0;
-        for (int b = 1; b < P; ++b) {
-          const double dd = bead_dist(Xc[b * C + 3 * a] - Xc[3 * a], Xc[b * C + 3 * a + 1] - Xc[3 * a + 1],
-                                      Xc[b * C + 3 * a + 2] - Xc[3 * a + 2]);
-          sp = dd > sp ? dd : sp;
-        }
-        d.spread[(size_t)atom * d.spread_slots] = sp;
-        for (int s = 1; s < d.spread_slots; ++s) d.spread[(size_t)atom * d.spread_slots + s] = 0.0;
+        write_ref(d, atom, rf);
+      } else {
+        const double d2 = bead_d2(Xc[j * C + 3 * a] - Xc[3 * a], Xc[j * C + 3 * a + 1] - Xc[3 * a + 1],
+                                  Xc[j * C + 3 * a + 2] - Xc[3 * a + 2]);
+        atomicMax(&s_d2[a], __double_as_longlong(d2));
       }
+    }
+    __syncthreads();
+    for (int a = tid; a < na; a += nt) {
+      const int atom = d.atom_of_tk[d.atoff[t] + k0 + a];
+      d.spread[(size_t)atom * d.spread_slots] = __dsqrt_rn(__longlong_as_double(s_d2[a]));
+      for (int s2 = 1; s2 < d.spread_slots; ++s2) d.spread[(size_t)atom * d.spread_slots + s2] = 0.0;
     }
   }
   if (mode & PM_PCART) {
@@ -249,8 +272,8 @@ __global__ void k_mirror_from_q(Dev d) {
   for (int x = 0; x < 3; ++x) {
     q0[x] = d.q[3 * (size_t)r0 + x];
     MirrorOut::wrap_ref(q0[x], d.box, &fl[x], &rf[x]);
-    d.ref[3 * atom + x] = rf[x];
   }
+  write_ref(d, atom, rf);
   double sp = 0.0;
   for (int j = 0; j < P; ++j) {
     const size_t row = (size_t)r0 + (size_t)j * N;
@@ -364,7 +387,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_fwd(Dev d, int t, int mode)
       const double fk = Fn[e];
       if (mode & PM_END) {
         p = fma(hk, fk, p);
-        const double xi = (double)gauss_dof(d.seed, s_end, 1u, (uint64_t)g);
+        const double xi = f2d_bits(gauss_dof(d.seed, s_end, 1u, (uint64_t)g));
         const double pn = fma(mk.c1, p, mk.c2s * xi);
         part[4] += (p * p - pn * pn) * inv2m;
         p = pn;
@@ -375,7 +398,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_fwd(Dev d, int t, int mode)
         }
       }
       if (mode & PM_START) {
-        const double xi = (double)gauss_dof(d.seed, s_start, 0u, (uint64_t)g);
+        const double xi = f2d_bits(gauss_dof(d.seed, s_start, 0u, (uint64_t)g));
         const double pn = fma(mk.c1, p, mk.c2s * xi);
         part[5] += (p * p - pn * pn) * inv2m;
         p = fma(hk, fk, pn);
@@ -445,8 +468,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_inv(Dev d, int t, int mode)
       for (int x = 0; x < 3; ++x) MirrorOut::wrap_ref(Qc[3 * a + x], d.box, &fl[x], &rf[x]);
       const double* xb = Qc + (size_t)(jj + 1) * C + 3 * a;
       write_mirror(d, d.off[t] + j * N + a, xb[0], xb[1], xb[2], fl[0], fl[1], fl[2]);
-      if (jj == 0 && blockIdx.x == 0)
-        for (int x = 0; x < 3; ++x) d.ref[3 * atom + x] = rf[x];
+      if (jj == 0 && blockIdx.x == 0) write_ref(d, atom, rf);
     }
     // spread partial of this bead block, per atom
     for (int a = warp; a < N; a += nw) {
@@ -524,6 +546,7 @@ __global__ void k_final(Dev d, int mode, const int* slot_type) {
     // counters are integers carried in the fixed-point slots
     est[13] = (double)(long long)d.E_fix[E_NEVAL];
     est[14] = (double)(long long)d.E_fix[E_NPEVAL];
+    est[16 + 4 * MT] = (double)(long long)d.E_fix[E_NLJEVAL];
     est[9] = 2.0 * ke * kc / (3.0 * (double)d.n_beads * d.kB);
     est[11] = heat;
     est[10] = ke + es + V;
@@ -568,6 +591,7 @@ __global__ void k_energy_out(Dev d) {
   d.est[8] = v[E_VIRIAL];
   d.est[13] = (double)(long long)d.E_fix[E_NEVAL];
   d.est[14] = (double)(long long)d.E_fix[E_NPEVAL];
+  d.est[16 + 4 * MT] = (double)(long long)d.E_fix[E_NLJEVAL];
   for (int i = 0; i < E_NSLOTS; ++i) d.E_fix[i] = 0ull;
 }
 
@@ -584,16 +608,18 @@ static size_t small_smem(int P) {
   return sizeof(double) * ((size_t)P * P + 5 * (size_t)P * C);
 }
 
-void launch_prop(const Dev& d, cudaStream_t s, int mode) {
+int launch_prop(const Dev& d, cudaStream_t s, int mode) {
+  int n = 0;
   if (mode & PM_MIRROR) {
     k_mirror_from_q<<<(d.n_atoms + 127) / 128, 128, 0, s>>>(d);
-    return;
+    return 1;
   }
   if (d.n_tiles > 0) {
     size_t smem = 0;
     for (int t = 0; t < d.n_types; ++t)
       if (d.P[t] <= SMALL_P && d.N[t] > 0) smem = small_smem(d.P[t]) > smem ? small_smem(d.P[t]) : smem;
     k_prop_small<<<d.n_tiles, PROP_THREADS, smem, s>>>(d, mode);
+    ++n;
   }
   for (int t = 0; t < d.n_types; ++t) {
     if (d.P[t] <= SMALL_P || d.N[t] == 0) continue;
@@ -602,29 +628,34 @@ void launch_prop(const Dev& d, cudaStream_t s, int mode) {
     if (mode & (PM_IMPORT | PM_END | PM_START)) {
       const size_t smem = sizeof(double) * ((size_t)d.P[t] + 3 * (size_t)BIG_MB * C + C);
       k_big_fwd<<<nb, BIG_THREADS, smem, s>>>(d, t, mode);
+      ++n;
     }
     if (mode & (PM_START | PM_QCART | PM_PCART)) {
       const size_t smem = sizeof(double) * ((size_t)d.P[t] + (size_t)(BIG_MB + 1) * C);
       k_big_inv<<<nb, BIG_THREADS, smem, s>>>(d, t, mode);
+      ++n;
     }
   }
+  return n;
 }
 
-void launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type) {
-  k_final<<<1, 256, 0, s>>>(d, mode, slot_type);
+int launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type) {
+  k_final<<<1, 1024, 0, s>>>(d, mode, slot_type);
+  return 1;
 }
 
-void launch_forces_out(const Dev& d, cudaStream_t s) {
+int launch_forces_out(const Dev& d, cudaStream_t s) {
   k_forces_out<<<296, 256, 0, s>>>(d);
   k_energy_out<<<1, 32, 0, s>>>(d);
+  return 2;
 }
 
-void launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n,
-                  float* out) {
+int launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out) {
   long blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   k_gauss<<<(int)blocks, 256, 0, s>>>(d, step, stage, dof0, n, out);
+  return 1;
 }
 
 }  // namespace mx

@@ -67,6 +67,8 @@ struct Plan {
   std::vector<int> bond_atoms, ang_atoms;
   std::vector<double> bond_par, ang_par;
   std::vector<double> cm;
+  std::vector<double> dsf;     // DSF interval table
+  int dsf_nint = 0, dsf_elo = -2;
   std::vector<int> cm_off, mc_off, big_slot0;
   std::vector<ModeCoef> mc;
   std::vector<PropTile> tiles;
@@ -80,11 +82,11 @@ struct Plan {
   // workspace offsets
   Arena ar;
   size_t o_tab = 0, tab_bytes = 0;
-  size_t o_ainfo, o_pos_atom, o_pos_mol, o_atom_of_tk, o_ainfo_atom, o_is_pseudo, o_pseudo_atom, o_pinfo,
+  size_t o_ainfo, o_pos_atom, o_pos_mol, o_atom_of_tk, o_ainfo_atom, o_pos_of_atom, o_is_pseudo, o_pseudo_atom, o_pinfo,
       o_pairpar, o_pspar, o_bitems, o_bond_atoms, o_bond_par, o_ang_atoms, o_ang_par, o_cm, o_mc, o_tiles,
-      o_slot_type;
+      o_slot_type, o_dsf;
   size_t o_state = 0, state_bytes = 0;
-  size_t o_qnm, o_pnm, o_ffix, o_xw, o_xf, o_xl, o_ref, o_spread, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
+  size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_ref, o_refd, o_reff, o_spread, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
       o_err, o_step, o_heat, o_est, o_parts;
 };
 
@@ -111,6 +113,78 @@ void pseudo_at(const PseudoPar& pp, double r, double* v, double* dv) {
   const double ex = exp(-r / pp.b);
   *v = -pp.kq * gg + pp.A * ex;
   *dv = -pp.kq * dg - (pp.A / pp.b) * ex;
+}
+
+// Unit-charge DSF potential G(s) = erfc(a r)/r - erfc(a rc)/rc + cf (r - rc),
+// s = r^2, and -2 G'(s), tabulated as quintics in x = s - s0 on 64
+// equal sub-intervals of every octave [2^e, 2^(e+1)) of s from 2^elo up past
+// rc^2. Each quintic interpolates its function at the six Chebyshev nodes of
+// the interval (values in long double). Row layout: c0..c5 of G, then
+// c0..c5 of -2 G'.
+static void fit_quintic(const long double* tn, const long double* val, long double h, double* out) {
+  typedef long double LD;
+  LD A[6][7];
+  for (int i = 0; i < 6; ++i) {
+    LD tp = 1.0L;
+    for (int j = 0; j < 6; ++j) {
+      A[i][j] = tp;
+      tp *= tn[i];
+    }
+    A[i][6] = val[i];
+  }
+  for (int c = 0; c < 6; ++c) {  // Gauss-Jordan, partial pivoting
+    int pv = c;
+    for (int r = c + 1; r < 6; ++r)
+      if (fabsl(A[r][c]) > fabsl(A[pv][c])) pv = r;
+    for (int j = 0; j < 7; ++j) std::swap(A[c][j], A[pv][j]);
+    for (int r = 0; r < 6; ++r) {
+      if (r == c) continue;
+      const LD f = A[r][c] / A[c][c];
+      for (int j = c; j < 7; ++j) A[r][j] -= f * A[c][j];
+    }
+  }
+  LD hk = 1.0L;
+  for (int j = 0; j < 6; ++j) {
+    out[j] = (double)(A[j][6] / A[j][j] / hk);
+    hk *= h;
+  }
+}
+
+std::vector<double> dsf_table(double alpha, double rc, int elo, int* nint_out) {
+  typedef long double LD;
+  const LD a = alpha, R = rc;
+  const LD pil = 3.141592653589793238462643383279502884L;
+  const LD erc = erfcl(a * R);
+  const LD gg = 2.0L * a / sqrtl(pil);
+  const LD cf = erc / (R * R) + gg * expl(-a * a * R * R) / R;
+  auto G = [&](LD sv) {
+    const LD r = sqrtl(sv);
+    return erfcl(a * r) / r - erc / R + cf * (r - R);
+  };
+  auto dG = [&](LD sv) {  // -2 dG/ds = -(dG/dr) / r, the force over r per unit charge product
+    const LD r = sqrtl(sv);
+    return -(-erfcl(a * r) / (r * r) - gg * expl(-a * a * sv) / r + cf) / r;
+  };
+  int ehi = elo;
+  while (ldexp(1.0, ehi) <= rc * rc) ++ehi;
+  const int nint = (ehi - elo) * 64;
+  std::vector<double> tab(12 * (size_t)nint);
+  LD tn[6];
+  for (int i = 0; i < 6; ++i) tn[i] = (1.0L - cosl((2 * i + 1) * pil / 12.0L)) / 2.0L;
+  for (int k = 0; k < nint; ++k) {
+    const int oct = k / 64, sub = k % 64;
+    const LD s0 = ldexpl(1.0L + sub / 64.0L, elo + oct);
+    const LD h = ldexpl(1.0L / 64.0L, elo + oct);
+    LD v[6], dv[6];
+    for (int i = 0; i < 6; ++i) {
+      v[i] = G(s0 + tn[i] * h);
+      dv[i] = dG(s0 + tn[i] * h);
+    }
+    fit_quintic(tn, v, h, &tab[12 * (size_t)k]);
+    fit_quintic(tn, dv, h, &tab[12 * (size_t)k + 6]);
+  }
+  *nint_out = nint;
+  return tab;
 }
 
 Plan make_plan(const mixts_system* s, const mixts_params* prm) {
@@ -188,8 +262,8 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
     p.ainfo.push_back(p.ainfo_atom[a]);
     p.pos_of_atom[a] = i;
   }
-  if ((long long)p.n_nonp >= (1LL << 24)) {
-    fail(p, MIXTS_ERR_ARG, "too many atoms for the 25-bit list entries");
+  if ((long long)p.n_nonp >= (1LL << 24) || (long long)p.off[p.nt] >= (1LL << 20)) {
+    fail(p, MIXTS_ERR_ARG, "list entries hold bead rows below 2^20 and atom positions below 2^24");
     return p;
   }
   // classes
@@ -290,6 +364,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
     p.ang_par.push_back(s->angle_theta0[g]);
     for (int sl = 0; sl < Ps; ++sl) p.bitems.push_back(BondItem{1, g, sl, 0});
   }
+  p.dsf = dsf_table(prm->dsf_alpha, prm->r_cut, p.dsf_elo, &p.dsf_nint);
   // normal modes, thermostat, rotation
   const double kT = u.kB * prm->T;
   const double bh = u.hbar / kT;
@@ -382,6 +457,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_pos_mol = A.add(sizeof(int) * std::max(1, p.n_nonp));
   p.o_atom_of_tk = A.add(sizeof(int) * p.na);
   p.o_ainfo_atom = A.add(sizeof(AtomInfo) * p.na);
+  p.o_pos_of_atom = A.add(sizeof(int) * p.na);
   p.o_is_pseudo = A.add(sizeof(int) * p.na);
   p.o_pseudo_atom = A.add(sizeof(int) * std::max(1, p.n_pseudo));
   p.o_pinfo = A.add(sizeof(AtomInfo) * std::max(1, p.n_pseudo));
@@ -396,21 +472,24 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_mc = A.add(sizeof(ModeCoef) * p.mc.size());
   p.o_tiles = A.add(sizeof(PropTile) * std::max<size_t>(1, p.tiles.size()));
   p.o_slot_type = A.add(sizeof(int) * std::max<size_t>(1, p.slot_type.size()));
+  p.o_dsf = A.add(sizeof(double) * p.dsf.size());
   p.tab_bytes = A.size;
   const size_t nb3 = (size_t)p.n_beads * 3;
   p.o_qnm = A.add(sizeof(double) * nb3);
   p.o_pnm = A.add(sizeof(double) * nb3);
   p.o_ffix = A.add(sizeof(unsigned long long) * nb3);
   p.o_xw = A.add(sizeof(double4_32a) * p.n_beads);
+  p.o_xi = A.add(sizeof(longlong4_32a) * p.n_beads);
   p.o_xf = A.add(sizeof(float4) * p.n_beads);
-  p.o_xl = A.add(sizeof(float4) * p.n_beads);
   p.o_ref = A.add(sizeof(double) * 3 * p.na);
+  p.o_refd = A.add(sizeof(double4_32a) * std::max(1, p.n_nonp));
+  p.o_reff = A.add(sizeof(float4) * std::max(1, p.n_nonp));
   p.o_spread = A.add(sizeof(double) * (size_t)p.na * p.spread_slots);
   p.o_nl = A.add(sizeof(int) * (size_t)std::max(1, p.n_nonp) * p.nl_cap);
   p.o_nlcnt = A.add(sizeof(int) * std::max(1, p.n_nonp));
   p.o_pl = A.add(sizeof(int) * (size_t)std::max(1, p.n_pseudo) * p.pl_cap);
   p.o_plcnt = A.add(sizeof(int) * std::max(1, p.n_pseudo));
-  p.o_thresh = A.add(sizeof(double) * 4);
+  p.o_thresh = A.add(sizeof(double) * 8);
   p.o_efix = A.add(sizeof(unsigned long long) * E_NSLOTS);
   p.o_err = A.add(sizeof(int) * 4);
   p.o_step = A.add(sizeof(long long));
@@ -428,8 +507,19 @@ void put(std::vector<unsigned char>& img, size_t off, const std::vector<T>& v) {
 
 }  // namespace
 
+struct Timer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, size_t>> recs;  // (phase, index of the start event)
+  double ms[MIXTS_N_PHASES] = {0};
+  long long calls[MIXTS_N_PHASES] = {0};
+};
+
 struct mixts_ctx {
   Dev d;
+  Timer tm;
+  long long kernels = 0;
   Plan plan;
   cudaStream_t stream = nullptr;
   unsigned char* ws = nullptr;
@@ -442,6 +532,44 @@ struct mixts_ctx {
   std::string err;
   int device = 0;
 };
+
+static void timer_fold(mixts_handle h) {
+  Timer& T = h->tm;
+  if (T.recs.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& r : T.recs) {
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, T.pool[r.second], T.pool[r.second + 1]);
+    T.ms[r.first] += ms;
+    T.calls[r.first] += 1;
+  }
+  T.recs.clear();
+  T.used = 0;
+}
+
+// run one launcher inside a timed phase
+template <class F>
+static void phase(mixts_handle h, int ph, F&& launch) {
+  Timer& T = h->tm;
+  if (!T.on) {
+    h->kernels += launch();
+    return;
+  }
+  if (T.used + 2 > T.pool.size()) timer_fold(h);
+  if (T.pool.size() < 4096) {
+    while (T.pool.size() < 4096) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      T.pool.push_back(e);
+    }
+  }
+  const size_t a = T.used;
+  cudaEventRecord(T.pool[a], h->stream);
+  h->kernels += launch();
+  cudaEventRecord(T.pool[a + 1], h->stream);
+  T.used += 2;
+  T.recs.push_back({ph, a});
+}
 
 static mixts_status set_err(mixts_handle h, mixts_status s, const std::string& why) {
   if (h) h->err = why;
@@ -508,6 +636,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   put(img, p.o_pos_mol, p.pos_mol);
   put(img, p.o_atom_of_tk, p.atom_of_tk);
   put(img, p.o_ainfo_atom, p.ainfo_atom);
+  put(img, p.o_pos_of_atom, p.pos_of_atom);
   put(img, p.o_is_pseudo, p.atom_is_pseudo);
   put(img, p.o_pseudo_atom, p.pseudo_atom);
   put(img, p.o_pinfo, p.pinfo);
@@ -522,6 +651,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   put(img, p.o_mc, p.mc);
   put(img, p.o_tiles, p.tiles);
   put(img, p.o_slot_type, p.slot_type);
+  put(img, p.o_dsf, p.dsf);
   mixts_status st = cuda_check(h, cudaMemcpy(h->ws, img.data(), p.tab_bytes, cudaMemcpyHostToDevice), "upload tables");
   if (st == MIXTS_OK)
     st = cuda_check(h, cudaMemsetAsync(h->ws + p.tab_bytes, 0, p.ar.size - p.tab_bytes, h->stream), "clear state");
@@ -557,6 +687,13 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.dsf_erfc_rc_over_rc = erfc(prm->dsf_alpha * prm->r_cut) / prm->r_cut;
   d.dsf_cf = erfc(prm->dsf_alpha * prm->r_cut) / (prm->r_cut * prm->r_cut) +
              d.dsf_g * exp(-prm->dsf_alpha * prm->dsf_alpha * prm->r_cut * prm->r_cut) / prm->r_cut;
+  d.dsf_tab = (const double*)(h->ws + p.o_dsf);
+  d.dsf_nint = p.dsf_nint;
+  d.dsf_base = (1023 + p.dsf_elo) << 6;
+  d.dsf_smin = ldexp(1.0, p.dsf_elo);
+  d.box_hi = (float)(rint(sys->box * 4096.0) / 4096.0);
+  d.box_fix = llrint(sys->box * 281474976710656.0);
+  d.screen_rc2 = (float)((prm->r_cut + 2e-3) * (prm->r_cut + 2e-3));
   d.dt = prm->dt;
   d.kcal = u.kcal;
   d.kB = u.kB;
@@ -608,9 +745,12 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.p_nm = (double*)(w + p.o_pnm);
   d.F_fix = (unsigned long long*)(w + p.o_ffix);
   d.Xw = (double4_32a*)(w + p.o_xw);
+  d.Xi = (longlong4_32a*)(w + p.o_xi);
   d.Xf = (float4*)(w + p.o_xf);
-  d.Xl = (float4*)(w + p.o_xl);
   d.ref = (double*)(w + p.o_ref);
+  d.refd = (double4_32a*)(w + p.o_refd);
+  d.reff = (float4*)(w + p.o_reff);
+  d.pos_of_atom = (const int*)(w + p.o_pos_of_atom);
   d.spread = (double*)(w + p.o_spread);
   d.nl = (int*)(w + p.o_nl);
   d.nl_cnt = (int*)(w + p.o_nlcnt);
@@ -628,9 +768,21 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
 }
 
 static mixts_status eval_forces(mixts_handle h) {
-  launch_nlist(h->d, h->stream, h->atom_is_pseudo);
-  launch_forces(h->d, h->stream, h->ainfo_atom);
+  const Dev& d = h->d;
+  cudaStream_t s = h->stream;
+  phase(h, 0, [&] { return launch_nlist(d, s, h->atom_is_pseudo); });
+  phase(h, 1, [&] { return launch_pair(d, s); });
+  phase(h, 2, [&] { return launch_bonded(d, s, h->ainfo_atom); });
+  phase(h, 3, [&] { return launch_pseudo(d, s); });
   return cuda_check(h, cudaGetLastError(), "force launch");
+}
+
+static void prop(mixts_handle h, int mode) {
+  phase(h, 4, [&] { return launch_prop(h->d, h->stream, mode); });
+}
+
+static void fin(mixts_handle h, int mode) {
+  phase(h, 5, [&] { return launch_final(h->d, h->stream, mode, h->slot_type); });
 }
 
 mixts_status mixts_forces(mixts_handle h, double* energy_host) {
@@ -638,10 +790,10 @@ mixts_status mixts_forces(mixts_handle h, double* energy_host) {
   // a fresh evaluation from the caller's q: clear the accumulators first
   cudaMemsetAsync(h->d.F_fix, 0, sizeof(unsigned long long) * 3 * (size_t)h->d.n_beads, h->stream);
   cudaMemsetAsync(h->d.E_fix, 0, sizeof(unsigned long long) * E_NSLOTS, h->stream);
-  launch_prop(h->d, h->stream, PM_MIRROR);
+  prop(h, PM_MIRROR);
   mixts_status st = eval_forces(h);
   if (st != MIXTS_OK) return st;
-  launch_forces_out(h->d, h->stream);
+  phase(h, 6, [&] { return launch_forces_out(h->d, h->stream); });
   st = cuda_check(h, cudaGetLastError(), "forces out");
   if (st != MIXTS_OK) return st;
   h->nm_valid = false;
@@ -659,28 +811,28 @@ mixts_status mixts_step(mixts_handle h, int n_steps) {
   if (n_steps == 0) return MIXTS_OK;
   cudaStream_t s = h->stream;
   if (!h->nm_valid) {
-    launch_prop(h->d, s, PM_IMPORT);
+    prop(h, PM_IMPORT);
     h->nm_valid = true;
     h->f_valid = false;
   }
   if (!h->f_valid) {
     cudaMemsetAsync(h->d.F_fix, 0, sizeof(unsigned long long) * 3 * (size_t)h->d.n_beads, s);
     cudaMemsetAsync(h->d.E_fix, 0, sizeof(unsigned long long) * E_NSLOTS, s);
-    launch_prop(h->d, s, PM_QCART);
+    prop(h, PM_QCART);
     mixts_status st = eval_forces(h);
     if (st != MIXTS_OK) return st;
     h->f_valid = true;
   }
-  launch_prop(h->d, s, PM_START);
-  launch_final(h->d, s, PM_START, h->slot_type);
+  prop(h, PM_START);
+  fin(h, PM_START);
   for (int i = 1; i < n_steps; ++i) {
     eval_forces(h);
-    launch_prop(h->d, s, PM_END | PM_EST | PM_START);
-    launch_final(h->d, s, PM_END | PM_EST | PM_START, h->slot_type);
+    prop(h, PM_END | PM_EST | PM_START);
+    fin(h, PM_END | PM_EST | PM_START);
   }
   eval_forces(h);
-  launch_prop(h->d, s, PM_END | PM_EST | PM_PCART);
-  launch_final(h->d, s, PM_END | PM_EST, h->slot_type);
+  prop(h, PM_END | PM_EST | PM_PCART);
+  fin(h, PM_END | PM_EST);
   h->steps_done += n_steps;
   return cuda_check(h, cudaGetLastError(), "step launch");
 }
@@ -708,6 +860,7 @@ mixts_status mixts_estimators(mixts_handle h, mixts_estimates* out) {
   out->H_conserved = e[12];
   out->n_evals = e[13];
   out->n_pseudo_evals = e[14];
+  out->n_lj_evals = e[16 + 4 * MT];
   out->step = (int64_t)e[15];
   for (int t = 0; t < h->d.n_types; ++t) {
     out->KE_prim[t] = e[16 + 4 * t];
@@ -747,9 +900,16 @@ mixts_status mixts_nlist(mixts_handle h, int kind, int* out3, long cap, long* n_
     const int c = std::min(cnt[r], rcap);
     for (int k = 0; k < c; ++k) {
       const int e = ent[(size_t)r * rcap + k];
+      int partner;
+      if (kind == 0) {  // (bead-0 row << 11) | (type << 7) | code
+        const int t = (e >> 7) & 15, row0 = e >> 11;
+        partner = p.atom_of_tk[p.atoff[t] + (row0 - p.off[t])];
+      } else {          // (sorted position << 7) | code
+        partner = p.pos_atom[e >> 7];
+      }
       if (out3 && n < cap) {
         out3[3 * n] = owner;
-        out3[3 * n + 1] = p.pos_atom[e >> 7];
+        out3[3 * n + 1] = partner;
         out3[3 * n + 2] = e & 127;
       }
       ++n;
@@ -801,17 +961,55 @@ mixts_status mixts_set_state(mixts_handle h, const void* blob, size_t bytes) {
   h->nm_valid = true;
   h->f_valid = false;
   // Cartesian q, p for the caller
-  launch_prop(h->d, s, PM_QCART | PM_PCART);
+  prop(h, PM_QCART | PM_PCART);
   return cuda_check(h, cudaGetLastError(), "set state export");
+}
+
+mixts_status mixts_reload(mixts_handle h) {
+  if (!h) return MIXTS_ERR_ARG;
+  h->nm_valid = false;
+  h->f_valid = false;
+  return MIXTS_OK;
+}
+
+mixts_status mixts_set_timing(mixts_handle h, int on) {
+  if (!h) return MIXTS_ERR_ARG;
+  timer_fold(h);
+  if (on) {
+    for (int i = 0; i < MIXTS_N_PHASES; ++i) {
+      h->tm.ms[i] = 0.0;
+      h->tm.calls[i] = 0;
+    }
+  }
+  h->tm.on = on != 0;
+  return MIXTS_OK;
+}
+
+mixts_status mixts_get_timing(mixts_handle h, double* ms, long long* calls, long long* kernels) {
+  if (!h) return MIXTS_ERR_ARG;
+  timer_fold(h);
+  for (int i = 0; i < MIXTS_N_PHASES; ++i) {
+    if (ms) ms[i] = h->tm.ms[i];
+    if (calls) calls[i] = h->tm.calls[i];
+  }
+  if (kernels) *kernels = h->kernels;
+  return cuda_check(h, cudaStreamSynchronize(h->stream), "timing");
 }
 
 mixts_status mixts_gaussians(mixts_handle h, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out) {
   if (!h || !out || n < 0) return MIXTS_ERR_ARG;
-  launch_gauss(h->d, h->stream, step, stage, dof0, n, out);
+  h->kernels += launch_gauss(h->d, h->stream, step, stage, dof0, n, out);
   return cuda_check(h, cudaGetLastError(), "gaussians");
 }
 
-void mixts_destroy(mixts_handle h) { delete h; }
+void mixts_destroy(mixts_handle h) {
+  if (!h) return;
+  if (!h->tm.pool.empty()) {
+    cudaStreamSynchronize(h->stream);
+    for (auto e : h->tm.pool) cudaEventDestroy(e);
+  }
+  delete h;
+}
 
 const char* mixts_last_error(mixts_handle h) { return h ? h->err.c_str() : "NULL handle"; }
 

@@ -26,14 +26,14 @@ constexpr double FMAX = 262144.0;             // |single contribution| limit, kc
 enum : int { ERR_NLIST = 1, ERR_NONFINITE = 2, ERR_BOX = 4, ERR_TIMEOUT = 8, ERR_PLIST = 16 };
 
 // energy accumulator slots (fixed point) and counters
-enum : int { E_LJ = 0, E_COUL, E_BOND, E_ANGLE, E_PSEUDO, E_VIRIAL, E_NEVAL, E_NPEVAL, E_NSLOTS };
+enum : int { E_LJ = 0, E_COUL, E_BOND, E_ANGLE, E_PSEUDO, E_VIRIAL, E_NEVAL, E_NPEVAL, E_NLJEVAL, E_NSLOTS };
 
 // estimator partial slots per propagation block: per type 4 values + heat
 constexpr int PART_PER_TYPE = 4;  // KE, spring energy, centroid-virial sum, Rg sum
 constexpr int PART_STRIDE = MT * PART_PER_TYPE + 2;
 
 // estimate record (device), see mixts_estimates
-constexpr int EST_N = 16 + 4 * MT;
+constexpr int EST_N = 16 + 4 * MT + 4;  // tail: [16+4MT] LJ eval count
 
 struct AtomInfo {  // one non-pseudo atom, by sorted position
   int row0;        // bead-0 row in the flat layout
@@ -90,6 +90,13 @@ struct Dev {
   int precision;
   double box, rc, rc2, alpha;
   double dsf_erfc_rc_over_rc, dsf_cf, dsf_g;
+  // DSF interval table: s in [dsf_smin, 2^e_hi), 64 sub-intervals per octave
+  const double* dsf_tab;
+  int dsf_nint, dsf_base;   // interval count; (1023 + e_lo) << 6
+  double dsf_smin;          // 2^e_lo
+  float box_hi;             // box edge rounded to the 2^-12 A grid
+  long long box_fix;        // box edge in 2^-48 A fixed point
+  float screen_rc2;         // binary32 screen radius^2 (r_cut + 2e-3)^2
   double dt, kcal, kT, kB;
   uint64_t seed;
   // per type
@@ -127,9 +134,12 @@ struct Dev {
   double* p_nm;
   unsigned long long* F_fix;   // [n_beads*3], two's-complement fixed point
   double4_32a* Xw;                 // [n_beads] positions shifted so bead 0 of each atom lies in the box
-  float4* Xf;                  // [n_beads] FP32 mirror (hi parts) for the FP32 force path
-  float4* Xl;                  // [n_beads] FP32 mirror (lo parts)
+  longlong4_32a* Xi;               // [n_beads] the same in 2^-48 A fixed point (exact differences)
+  float4* Xf;                  // [n_beads] binary32 positions on the 2^-12 A grid (screens)
   double* ref;                 // [n_atoms*3] wrapped bead-0 reference positions
+  double4_32a* refd;           // [n_nonp] the same by sorted position
+  float4* reff;                // [n_nonp] binary32 copy, .w = log2 P (int bits)
+  const int* pos_of_atom;      // [n_atoms] sorted position, -1 for pseudo particles
   double* spread;              // [n_atoms*spread_slots] max |q_b - q_0| partials
   int* nl;                     // [n_nonp*nl_cap] (partner position << 7) | image code
   int* nl_cnt;                 // [n_nonp]
@@ -143,6 +153,67 @@ struct Dev {
   double* est;                 // [EST_N]
   double* parts;               // [n_part_slots * PART_STRIDE]
 };
+
+// ---------------------------------------------------------------------------
+// Conversions by integer instructions. On this part the FP64 unit is narrow
+// (2 lanes per clock per SM) and int<->float conversions share it, so hot
+// loops assemble binary64 values from their bit fields instead.
+// ---------------------------------------------------------------------------
+// Fixed point without the FP64 pipe: v * 2^scale_log2 rounded to the nearest
+// integer (halves away from zero), from the binary64 bit fields (integer
+// instructions only). Flags |v 2^scale_log2| >= 2^62 (and inf/NaN) in *bad.
+// fix44(v, w) is the force scale 2^44 with a power-of-two weight 2^-w.
+__device__ __forceinline__ long long fixs(double v, int scale_log2, int* bad) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int sh = e - 1075 + scale_log2;  // v * 2^s = mantissa * 2^(e - 1075 + s)
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+  long long r;
+  if (e == 0x7FF || sh > 9) {
+    *bad = 1;
+    r = 0;
+  } else if (sh >= 0) {
+    r = m << sh;
+  } else if (sh >= -53) {
+    r = (m + (1LL << (-sh - 1))) >> (-sh);
+  } else {
+    r = 0;
+  }
+  return b < 0 ? -r : r;
+}
+
+__device__ __forceinline__ long long fix44(double v, int wshift, int* bad) { return fixs(v, 44 - wshift, bad); }
+
+// Binary64 value of v * 2^-scale_log2 by integer instructions (normalise
+// with a leading-zero count, assemble exponent and mantissa); exact for
+// |v| < 2^53, truncated beyond.
+__device__ __forceinline__ double fix_to_dbl(long long v, int scale_log2) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int msb = 63 - __clzll((long long)a);
+  const unsigned long long m = msb <= 52 ? a << (52 - msb) : a >> (msb - 52);
+  const unsigned long long e = (unsigned long long)(msb - scale_log2 + 1023);
+  return __longlong_as_double((long long)(sgn | (e << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+__device__ __forceinline__ double fixpos_to_double(long long v) { return fix_to_dbl(v, 48); }
+
+// exact binary32 -> binary64 for zero and normal numbers (bit fields)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int ex = (u >> 23) & 0xFFu;
+  if (ex == 0u) return 0.0;
+  const unsigned long long sg = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long e = (unsigned long long)(ex + 896u) << 52;
+  const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  return __longlong_as_double((long long)(sg | e | m));
+}
+
+// binary32 value of a small integer k, |k| < 2^22, without a conversion
+__device__ __forceinline__ float small_int_float(int k) {
+  return __int_as_float(0x4B000000 + (k + (1 << 22))) - 12582912.0f;
+}
 
 // ---------------------------------------------------------------------------
 // fixed-point accumulation
@@ -169,7 +240,8 @@ __device__ __forceinline__ void eadd(unsigned long long* E, int slot, double v) 
 }
 
 __device__ __forceinline__ double fix_to_double(unsigned long long v, double inv) {
-  return (double)(long long)v * inv;
+  (void)inv;
+  return fix_to_dbl((long long)v, 44);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -285,14 +357,16 @@ __device__ __forceinline__ float gauss_dof(uint64_t seed, uint32_t step, uint32_
   return __fmul_rn(rho, (lane & 1) ? sn : cs);
 }
 
-// kernel launchers (defined in the .cu files)
-void launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo);
-void launch_forces(const Dev& d, cudaStream_t s, const AtomInfo* ainfo_atom);
-void launch_prop(const Dev& d, cudaStream_t s, int mode);
-void launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type);
-void launch_forces_out(const Dev& d, cudaStream_t s);
-void launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n,
-                  float* out);
+// kernel launchers (defined in the .cu files); each returns the number of
+// kernels it launched
+int launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo);
+int launch_pair(const Dev& d, cudaStream_t s);
+int launch_bonded(const Dev& d, cudaStream_t s, const AtomInfo* ainfo_atom);
+int launch_pseudo(const Dev& d, cudaStream_t s);
+int launch_prop(const Dev& d, cudaStream_t s, int mode);
+int launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type);
+int launch_forces_out(const Dev& d, cudaStream_t s);
+int launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out);
 
 // propagation modes
 enum : int {

@@ -57,7 +57,7 @@ class _Params(C.Structure):
 class _Estimates(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "V", "V_lj", "V_coul", "V_bond", "V_angle", "V_pseudo", "KE_beads", "E_spring", "virial",
-        "T_beads", "H_mix", "heat", "H_conserved", "n_evals", "n_pseudo_evals")] + [
+        "T_beads", "H_mix", "heat", "H_conserved", "n_evals", "n_pseudo_evals", "n_lj_evals")] + [
         ("KE_prim", C.c_double * MAX_TYPES), ("KE_cv", C.c_double * MAX_TYPES),
         ("Rg2", C.c_double * MAX_TYPES), ("E_spring_t", C.c_double * MAX_TYPES),
         ("step", C.c_int64)]
@@ -84,6 +84,10 @@ def lib():
         L.mixts_get_state.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
         L.mixts_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
         L.mixts_gaussians.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint64, C.c_long, C.c_void_p]
+        L.mixts_reload.argtypes = [C.c_void_p]
+        L.mixts_set_timing.argtypes = [C.c_void_p, C.c_int]
+        L.mixts_get_timing.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                       C.POINTER(C.c_longlong)]
         L.mixts_destroy.argtypes = [C.c_void_p]
         L.mixts_last_error.argtypes = [C.c_void_p]
         L.mixts_last_error.restype = C.c_char_p
@@ -94,7 +98,9 @@ def lib():
 
 EXPORTED = ["mixts_workspace_size", "mixts_init", "mixts_forces", "mixts_step", "mixts_estimators",
             "mixts_nlist", "mixts_state_size", "mixts_get_state", "mixts_set_state", "mixts_gaussians",
-            "mixts_destroy", "mixts_last_error", "mixts_version"]
+            "mixts_destroy", "mixts_last_error", "mixts_version", "mixts_reload", "mixts_set_timing",
+            "mixts_get_timing"]
+PHASES = ["nlist", "pair", "bonded", "pseudo", "prop", "final", "other"]
 
 
 def _ptr(a, ct):
@@ -185,7 +191,7 @@ class MixTS:
     def estimators(self) -> dict:
         out = _Estimates()
         self._check(lib().mixts_estimators(self.h, C.byref(out)))
-        d = {n: getattr(out, n) for n, _ in _Estimates._fields_[:15]}
+        d = {n: getattr(out, n) for n, _ in _Estimates._fields_[:16]}
         nt = self.n_types
         for n in ("KE_prim", "KE_cv", "Rg2", "E_spring_t"):
             d[n] = list(getattr(out, n))[:nt]
@@ -218,6 +224,21 @@ class MixTS:
         self._check(lib().mixts_gaussians(self.h, int(step), int(stage), int(dof0), int(n),
                                           C.c_void_p(out.data_ptr())))
         return out
+
+    def reload(self):
+        """Declare that q and/or p were rewritten in place (host-resident state)."""
+        self._check(lib().mixts_reload(self.h))
+
+    def set_timing(self, on=True):
+        self._check(lib().mixts_set_timing(self.h, 1 if on else 0))
+
+    def timing(self):
+        """(ms per phase dict, calls per phase dict, kernels launched since init)."""
+        ms = (C.c_double * len(PHASES))()
+        calls = (C.c_longlong * len(PHASES))()
+        k = C.c_longlong(0)
+        self._check(lib().mixts_get_timing(self.h, ms, calls, C.byref(k)))
+        return dict(zip(PHASES, list(ms))), dict(zip(PHASES, list(calls))), int(k.value)
 
     def synchronize(self):
         self.stream.synchronize()
