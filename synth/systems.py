@@ -101,6 +101,19 @@ class System:
         return s
 
 
+def _beads_from_atoms(sysm: System, pos: np.ndarray) -> np.ndarray:
+    """Every bead of every atom at the atom's position, in the bead layout."""
+    q = np.empty((sysm.n_beads, 3))
+    off = sysm.type_offsets()
+    n_t = sysm.n_of_type()
+    rank = sysm.rank_in_type()
+    for t in range(sysm.n_types):
+        atoms = np.where(sysm.type_of_atom == t)[0]
+        for b in range(int(sysm.P_type[t])):
+            q[off[t] + b * n_t[t] + rank[atoms]] = pos[atoms]
+    return q
+
+
 def density_box_length(n_waters: int, density_g_cm3: float = 0.997) -> float:
     """Cubic box edge (A) holding n waters at the given mass density."""
     mol_mass = 18.01528
@@ -230,10 +243,7 @@ def water_box(n_waters: int, box: float, P_H: int, P_O: int, seed: int = 0,
         angle_k=np.full(na, w["angle_k"]),
         angle_theta0=np.full(na, math.radians(w["angle_theta0_deg"])),
     )
-    q = np.empty((sysm.n_beads, 3))
-    for atom in range(sysm.n_atoms):
-        rows = sysm.bead_rows(atom)
-        q[rows] = pos[atom]
+    q = _beads_from_atoms(sysm, np.asarray(pos))
     if electron_P is not None:
         e_atom = sysm.n_atoms - 1
         rows = sysm.bead_rows(e_atom)
