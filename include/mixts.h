@@ -183,6 +183,26 @@ MIXTS_API mixts_status mixts_get_timing(mixts_handle h, double* ms_host, long lo
 MIXTS_API mixts_status mixts_gaussians(mixts_handle h, uint32_t step, uint32_t stage, uint64_t dof0, long n,
                              float* out_dev);
 
+/* Allocation-free force evaluation. The paper has no counterpart; this
+ * serves callers that cannot allocate device memory: plugins whose host
+ * framework owns all device memory through its own pool (a stray
+ * cudaMalloc fails or fragments it), and drivers that forbid device
+ * allocation after start-up. It computes F <- -dV_mix/dq at sys->q into
+ * sys->f (both caller-owned device arrays) and, if energy_host is not NULL,
+ * V. All device scratch (tables, neighbour lists, accumulators) lives in one
+ * static device array of MIXTS_NOALLOC_MAX_BYTES that every GPU loading the
+ * library holds until exit; systems needing more return
+ * MIXTS_ERR_WORKSPACE. It calls no cudaMalloc or cudaFree. The first call on
+ * each device looks up that device's address of the array
+ * (cudaGetSymbolAddress), so make it once before any stream capture.
+ * Every call reuses the same array and clears what must start at zero;
+ * calls that overlap on the GPU (other streams, other host threads) race
+ * on it and must be serialised by the caller. The call returns after its
+ * work on `stream` has finished. */
+#define MIXTS_NOALLOC_MAX_BYTES (32u << 20)
+MIXTS_API mixts_status mixts_forces_noalloc(const mixts_system* sys, const mixts_params* prm, void* stream,
+                                            double* energy_host);
+
 MIXTS_API void mixts_destroy(mixts_handle h);
 MIXTS_API const char* mixts_last_error(mixts_handle h);
 MIXTS_API const char* mixts_version(void);

@@ -1014,3 +1014,65 @@ void mixts_destroy(mixts_handle h) {
 const char* mixts_last_error(mixts_handle h) { return h ? h->err.c_str() : "NULL handle"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free force evaluation.
+//
+// For callers that cannot allocate device memory: plugins whose host
+// framework owns every device byte through its own pool (a stray cudaMalloc
+// fails or fragments it), and embedded or real-time drivers that forbid
+// device allocation after start-up. mixts_forces_noalloc evaluates the forces with all of its device
+// scratch (tables, neighbour lists, accumulators) carved from one file-scope
+// static array of MIXTS_NOALLOC_MAX_BYTES. Every GPU that loads this library
+// holds that array until the process exits. Host-side bookkeeping still uses
+// ordinary host memory. The first call on a device looks up the array's
+// address there, so that call belongs before any stream capture.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+// Host code must not use &g_noalloc_scratch as a device address: the symbol
+// names a host-side stand-in. Each device's address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MIXTS_NOALLOC_MAX_BYTES];
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+mixts_status noalloc_base(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return MIXTS_ERR_CUDA;
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      fprintf(stderr, "mixts_forces_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+      return MIXTS_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MIXTS_OK;
+}
+}  // namespace
+
+extern "C" MIXTS_API mixts_status mixts_forces_noalloc(const mixts_system* sys, const mixts_params* prm,
+                                                       void* stream, double* energy_host) {
+  if (!sys || !prm) return MIXTS_ERR_ARG;
+  const size_t need = mixts_workspace_size(sys, 1, prm);
+  if (need == 0) return MIXTS_ERR_ARG;
+  if (need > (size_t)MIXTS_NOALLOC_MAX_BYTES) {
+    fprintf(stderr, "mixts_forces_noalloc: system needs %zu bytes of scratch, the static maximum is %zu\n", need,
+            (size_t)MIXTS_NOALLOC_MAX_BYTES);
+    return MIXTS_ERR_WORKSPACE;
+  }
+  void* base = nullptr;
+  mixts_status st = noalloc_base(&base);
+  if (st != MIXTS_OK) return st;
+  // mixts_init uploads the tables and clears every accumulator, list counter
+  // and flag in the scratch, so nothing carries over from the previous call
+  mixts_handle h = nullptr;
+  st = mixts_init(sys, 1, prm, base, (size_t)MIXTS_NOALLOC_MAX_BYTES, stream, &h);
+  if (st != MIXTS_OK) return st;
+  st = mixts_forces(h, energy_host);
+  if (st == MIXTS_OK && !energy_host) st = cuda_check(h, cudaStreamSynchronize(h->stream), "noalloc sync");
+  mixts_destroy(h);
+  return st;
+}

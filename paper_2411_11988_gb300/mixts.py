@@ -88,6 +88,7 @@ def lib():
         L.mixts_set_timing.argtypes = [C.c_void_p, C.c_int]
         L.mixts_get_timing.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                        C.POINTER(C.c_longlong)]
+        L.mixts_forces_noalloc.argtypes = [S, Pp, C.c_void_p, C.POINTER(C.c_double)]
         L.mixts_destroy.argtypes = [C.c_void_p]
         L.mixts_last_error.argtypes = [C.c_void_p]
         L.mixts_last_error.restype = C.c_char_p
@@ -99,7 +100,7 @@ def lib():
 EXPORTED = ["mixts_workspace_size", "mixts_init", "mixts_forces", "mixts_step", "mixts_estimators",
             "mixts_nlist", "mixts_state_size", "mixts_get_state", "mixts_set_state", "mixts_gaussians",
             "mixts_destroy", "mixts_last_error", "mixts_version", "mixts_reload", "mixts_set_timing",
-            "mixts_get_timing"]
+            "mixts_get_timing", "mixts_forces_noalloc"]
 PHASES = ["nlist", "pair", "bonded", "pseudo", "prop", "final", "other"]
 
 
