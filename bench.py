@@ -36,6 +36,16 @@ FLOPS_PAIR = 43
 FLOPS_LJ_EXTRA = 20
 # FP64 ALU peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 ALU peak: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# algorithmic FP32 flops per pair term of the FP32 kernel (counted once,
+# though the full-list kernel evaluates it from both atoms): hi/lo
+# displacement 12, r^2 5, table 21, scaling 3, accumulation 12 -> 53;
+# Lennard-Jones adds 22
+FLOPS32_PAIR = 53
+FLOPS32_LJ_EXTRA = 22
+ION_ELECTRON = dict(workload="256 waters H8/O1 + ion(+3) + electron P=1024, 18.6 A box, dt 0.1 fs",
+                    n_waters=256, box_A=18.6, P_H=8, P_O=1, P_e=1024, dt_fs=0.1)
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -145,6 +155,24 @@ def single_call_ms(m, torch, stream, steps, flush):
     return sum(a.elapsed_time(b) for a, b in ev) / steps
 
 
+def variant(torch, stream, flush, dev, sysm, dt, precision, steps, seed):
+    from paper_2411_11988_gb300 import MixTS
+    m = MixTS(sysm, T=300.0, dt=dt, tau=100.0, seed=seed, device=str(dev), stream=stream, precision=precision)
+    ms, ph, calls, _, _ = timed_run(m, torch, stream, steps, 3, flush)
+    e = m.estimators()
+    m.close()
+    pair_ms = ph["pair"] / max(1, calls["pair"])
+    out = {"ns_per_day": ns_per_day(ms, dt), "ms_per_step": ms, "steps": steps, "pair_kernel_ms": pair_ms,
+           "phase_ms_per_call": {k: ph[k] / max(1, calls[k]) for k in ph if calls[k]},
+           "bead_pair_evals_per_step": e["n_evals"], "pseudo_evals_per_step": e["n_pseudo_evals"]}
+    if precision == 1:
+        flops = (e["n_evals"] - e["n_lj_evals"]) * FLOPS32_PAIR + e["n_lj_evals"] * (FLOPS32_PAIR + FLOPS32_LJ_EXTRA)
+        ach = flops / (pair_ms * 1e-3) / 1e12
+        out["roofline_pair"] = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": ach / FP32_PEAK_TFLOPS, "note": "algorithmic flops count each term once"}
+    return out
+
+
 def e2e_run(m, torch, stream, steps):
     """Host-resident state through the public API: per step upload q, p from
     pinned host memory, step, download q, p and the estimates."""
@@ -200,6 +228,9 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="force precision of the main line (fp32: FP32 pair forces, FP64 integration)")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.warmup < 3 and args.impl == "ours":
@@ -214,7 +245,7 @@ def main():
         ms, cb = cpu_baseline(k, warmup=min(args.warmup, 3))
         line = {"metric": METRIC, "value": cb["value"], "unit": "ns/day", "n_gpus": args.gpus,
                 "steps": k, "warmup": min(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32 forces, f64 integration", "data": "synthetic", "impl": "reference",
                 "config": dict(WORKLOAD, l2="n/a (host)"), "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -233,7 +264,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     s = build_system(WORKLOAD["P_H"], WORKLOAD["P_O"], seed=rank)
-    m = MixTS(s, T=300.0, dt=DT, tau=100.0, seed=rank, device=str(dev), stream=stream)
+    prec = 1 if args.precision == "fp32" else 0
+    m = MixTS(s, T=300.0, dt=DT, tau=100.0, seed=rank, device=str(dev), stream=stream, precision=prec)
     step_ms, ph_ms, ph_calls, kernels, clk = timed_run(m, torch, stream, args.steps, args.warmup, flush,
                                                        clocks_idx=local)
     est = m.estimators()
@@ -245,7 +277,14 @@ def main():
     value = ns_per_day(step_ms) * world
     evals = est["n_evals"]
     pair_ms = ph_ms["pair"] / max(1, ph_calls["pair"])
-    flops = (evals - est["n_lj_evals"]) * FLOPS_PAIR + est["n_lj_evals"] * (FLOPS_PAIR + FLOPS_LJ_EXTRA)
+    if prec == 1:
+        flops = (evals - est["n_lj_evals"]) * FLOPS32_PAIR + est["n_lj_evals"] * (FLOPS32_PAIR + FLOPS32_LJ_EXTRA)
+        peak, kname = FP32_PEAK_TFLOPS, "k_pair32"
+        peak_src = "FP32 ALU: 152 SM x 128 FMA/clk x 2 x 2.07 GHz"
+    else:
+        flops = (evals - est["n_lj_evals"]) * FLOPS_PAIR + est["n_lj_evals"] * (FLOPS_PAIR + FLOPS_LJ_EXTRA)
+        peak, kname = FP64_PEAK_TFLOPS, "k_pair64"
+        peak_src = "FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2.07 GHz (nominal 1.25 TFLOP/s)"
     achieved = flops / (pair_ms * 1e-3) / 1e12
     e2e_ms, h2d, d2h = e2e_run(m, torch, stream, max(3, args.steps // 2))
 
@@ -261,6 +300,21 @@ def main():
                "pair_kernel_ms": phu["pair"] / max(1, callsu["pair"])}
         mu.close()
 
+    variants = None
+    if not args.no_variants:
+        import synth
+        vs = max(10, args.steps)
+        variants = {
+            "fp32_forces_water512_H32O4": variant(torch, stream, flush, dev, build_system(32, 4, rank), DT, 1, vs,
+                                                  rank),
+        }
+        ie = ION_ELECTRON
+        for prec, key in [(1, "fp32_forces_ion_electron"), (0, "fp64_ion_electron")]:
+            sie = synth.water_box(ie["n_waters"], ie["box_A"], ie["P_H"], ie["P_O"], seed=rank,
+                                  ion=dict(synth.systems.ION3), electron_P=ie["P_e"])
+            variants[key] = variant(torch, stream, flush, dev, sie, ie["dt_fs"], prec, vs, rank)
+            variants[key]["workload"] = ie["workload"]
+
     cb = None
     if rank == 0 and not args.no_cpu:
         _, cb = cpu_baseline(args.cpu_steps)
@@ -270,7 +324,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded lattice water, Maxwell-Boltzmann momenta)",
+            "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32 forces, f64 integration", "data": "synthetic (seeded lattice water, Maxwell-Boltzmann momenta)",
             "config": dict(WORKLOAD, l2=f"flushed (256 MiB write, untimed) before every timed chunk of {CHUNK} "
                                         "steps; steps in a chunk run back to back as in production",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
@@ -278,11 +332,11 @@ def main():
             "bead_pair_evals_per_step": evals,
             "ms_per_step_single_calls": single_ms,
             "uniform_fp64": uni,
+            "variants": variants,
             "mixts_speedup_vs_uniform": (uni["ms_per_step"] / step_ms) if uni else None,
-            "roofline": {"bound": "alu", "kernel": "k_pair64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                         "peak_source": "FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                         "flops_per_launch": flops, "launch_ms": pair_ms},
+            "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_src, "flops_per_launch": flops, "launch_ms": pair_ms},
             "phase_ms_per_call": per_phase,
             "cpu_baseline": cb,
             "e2e": {"value": ns_per_day(e2e_ms) * world, "unit": "ns/day", "h2d_bytes_per_step": h2d,

@@ -8,6 +8,8 @@
 // fixed-point accumulator, so the result is independent of atomic order.
 #include <math.h>
 
+#include <algorithm>
+
 #include "mixts_internal.cuh"
 
 namespace mx {
@@ -63,10 +65,13 @@ __device__ __forceinline__ unsigned img_mask(float dd, float Lf, float Rlin) {
 // runs on integer instructions
 __device__ double reduce_spread_kind(const Dev& d, const int* atom_is_pseudo, int want, long long* red) {
   long long m = 0;
-  const int n = d.n_atoms * d.spread_slots;
-  for (int a = threadIdx.x; a < n; a += blockDim.x) {
-    const int atom = a / d.spread_slots;
-    if (atom_is_pseudo[atom] == want) m = max(m, __double_as_longlong(d.spread[a]));
+  for (int a = threadIdx.x; a < d.n_atoms; a += blockDim.x)
+    if (atom_is_pseudo[a] == want) m = max(m, __double_as_longlong(d.spread[a]));
+  for (int t = 0; t < d.n_types; ++t) {
+    if (d.P[t] <= SMALL_P || d.pseudo[t] != want) continue;
+    const int n = d.N[t] * (d.P[t] / BIG_MB);
+    for (int a = threadIdx.x; a < n; a += blockDim.x)
+      m = max(m, __double_as_longlong(d.spread_big[d.sb_off[t] + a]));
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -134,58 +139,86 @@ __global__ void __launch_bounds__(NL_THREADS) k_nlist(Dev d, int nchunk) {
   const int moli = d.pos_mol[i];
   int* row = d.nl + (size_t)i * d.nl_cap;
   const int c0 = chunk * 32 * NL_CPL;
+  constexpr int MAXE = 8;  // entries one lane keeps per candidate (images)
 #pragma unroll 1
   for (int t = 0; t < NL_CPL; ++t) {
     const int c = c0 + t * 32 + lane;
-    if (c >= d.n_nonp || c == i) continue;
-    const float4 rc4 = d.reff[c];
-    const int Pc = __float_as_int(rc4.w);
-    bool own;
-    if (Pi != Pc) {
-      own = Pi > Pc;
-    } else {
-      const int lo = i < c ? i : c;
-      own = (((i + c) & 1) == 0) ? (i == lo) : (i != lo);
-    }
-    if (!own) continue;
-    const float dfx = rc4.x - ri.x, dfy = rc4.y - ri.y, dfz = rc4.z - ri.z;
-    const unsigned mx = img_mask(dfx, Lf, Rlin);
-    if (!mx) continue;
-    const unsigned my = img_mask(dfy, Lf, Rlin);
-    if (!my) continue;
-    const unsigned mz = img_mask(dfz, Lf, Rlin);
-    if (!mz) continue;
-    const bool same = d.pos_mol[c] == moli;
-    for (unsigned bx = mx; bx; bx &= bx - 1) {
-      const int kx = __ffs(bx) - 1;
-      const float ex = dfx + img_of(kx) * Lf;
-      for (unsigned by = my; by; by &= by - 1) {
-        const int ky = __ffs(by) - 1;
-        const float ey = dfy + img_of(ky) * Lf;
-        for (unsigned bz = mz; bz; bz &= bz - 1) {
-          const int kz = __ffs(bz) - 1;
-          if (same && kx == 2 && ky == 2 && kz == 2) continue;
-          const float ez = dfz + img_of(kz) * Lf;
-          const float d2f = ex * ex + ey * ey + ez * ez;
-          bool keep;
-          if (d2f < R2lo) {
-            keep = true;
-          } else if (d2f > R2hi) {
-            keep = false;
-          } else {
-            const double4_32a a = d.refd[i], bb = d.refd[c];
-            keep = exact_d2(__dsub_rn(bb.x, a.x), __dsub_rn(bb.y, a.y), __dsub_rn(bb.z, a.z), kx - 2, ky - 2,
-                            kz - 2, L) < R2;
-          }
-          if (keep) {
-            const int slot = atomicAdd(&d.nl_cnt[i], 1);
-            if (slot < d.nl_cap)
-              row[slot] = (d.ainfo[c].row0 << 11) | (d.ainfo[c].type << 7) | (kx * 25 + ky * 5 + kz);
-            else
-              atomicOr(d.err, ERR_NLIST);
+    int ne = 0;
+    int ents[MAXE];
+    if (c < d.n_nonp && c != i) {
+      const float4 rc4 = d.reff[c];
+      const int Pc = __float_as_int(rc4.w);
+      bool own;
+      if (d.full_list) {
+        own = true;
+      } else if (Pi != Pc) {
+        own = Pi > Pc;
+      } else {
+        const int lo = i < c ? i : c;
+        own = (((i + c) & 1) == 0) ? (i == lo) : (i != lo);
+      }
+      const float dfx = rc4.x - ri.x, dfy = rc4.y - ri.y, dfz = rc4.z - ri.z;
+      const unsigned mx = own ? img_mask(dfx, Lf, Rlin) : 0u;
+      const unsigned my = mx ? img_mask(dfy, Lf, Rlin) : 0u;
+      const unsigned mz = my ? img_mask(dfz, Lf, Rlin) : 0u;
+      if (mz) {
+        const bool same = d.pos_mol[c] == moli;
+        const int tag = (d.ainfo[c].row0 << 11) | (d.ainfo[c].type << 7);
+        for (unsigned bx = mx; bx; bx &= bx - 1) {
+          const int kx = __ffs(bx) - 1;
+          const float ex = dfx + img_of(kx) * Lf;
+          for (unsigned by = my; by; by &= by - 1) {
+            const int ky = __ffs(by) - 1;
+            const float ey = dfy + img_of(ky) * Lf;
+            for (unsigned bz = mz; bz; bz &= bz - 1) {
+              const int kz = __ffs(bz) - 1;
+              if (same && kx == 2 && ky == 2 && kz == 2) continue;
+              const float ez = dfz + img_of(kz) * Lf;
+              const float d2f = ex * ex + ey * ey + ez * ez;
+              bool keep;
+              if (d2f < R2lo) {
+                keep = true;
+              } else if (d2f > R2hi) {
+                keep = false;
+              } else {
+                const double4_32a a = d.refd[i], bb = d.refd[c];
+                keep = exact_d2(__dsub_rn(bb.x, a.x), __dsub_rn(bb.y, a.y), __dsub_rn(bb.z, a.z), kx - 2, ky - 2,
+                                kz - 2, L) < R2;
+              }
+              if (keep) {
+                const int en = tag | (kx * 25 + ky * 5 + kz);
+                if (ne < MAXE) {
+                  ents[ne++] = en;
+                } else {  // many images of one partner (small boxes): append alone
+                  const int slot = atomicAdd(&d.nl_cnt[i], 1);
+                  if (slot < d.nl_cap)
+                    row[slot] = en;
+                  else
+                    atomicOr(d.err, ERR_NLIST);
+                }
+              }
+            }
           }
         }
       }
+    }
+    // one reservation per warp: inclusive prefix of the lane counts
+    int incl = ne;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(&d.nl_cnt[i], total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    const int first = base + incl - ne;
+    for (int k = 0; k < ne; ++k) {
+      if (first + k < d.nl_cap)
+        row[first + k] = ents[k];
+      else
+        atomicOr(d.err, ERR_NLIST);
     }
   }
 }
@@ -310,8 +343,10 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= d.n_pitems) return;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  // persistent: the tables above are loaded once per CTA; warps stride over
+  // the (owner atom, bead) items
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < d.n_pitems; w += nwarps) {
   int pos, b;
   item_of_warp(d, w, &pos, &b);
   const AtomInfo ai = d.ainfo[pos];
@@ -413,6 +448,183 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
     atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nlj);
     atomicAdd(d.E_fix + E_NEVAL, (unsigned long long)nev);
     if (bad) atomicOr(d.err, ERR_NONFINITE);
+  }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// nonbonded pair sweep, FP32 forces (precision MIXTS_FP32_FORCES)
+//
+// Full neighbour lists (every row lists all partners) and one warp per
+// (atom i, slice s of the finest grid of the non-pseudo atoms): the pair
+// (i, j) contributes at slice s iff s is a multiple of P_max/P*, P* =
+// max(P_i, P_j), with weight 1/P*, bead s P_i/P_max of i and bead
+// s P_j/P_max of j -- the terms of Eq. (mts-hamiltonian) regrouped by slice.
+// Only i's bead is written, so there are no reaction atomics; every term is
+// evaluated from both sides and the energies carry a factor 1/2.
+// Displacements are exact hi parts (2^-12 A grid) plus binary32 remainders;
+// the DSF comes from the binary32 copy of the interval table; per-lane
+// binary32 partial sums are combined across the warp in binary64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void dsf_table32(const float* tab, int bits, float s, float* g, float* fg) {
+  const float s0 = __int_as_float((bits >> 17) << 17);
+  const float x = s - s0;
+  const float* c = tab;
+  float p = fmaf(c[5], x, c[4]);
+  float q = fmaf(c[11], x, c[10]);
+  p = fmaf(p, x, c[3]);
+  q = fmaf(q, x, c[9]);
+  p = fmaf(p, x, c[2]);
+  q = fmaf(q, x, c[8]);
+  p = fmaf(p, x, c[1]);
+  q = fmaf(q, x, c[7]);
+  *g = fmaf(p, x, c[0]);
+  *fg = fmaf(q, x, c[6]);
+}
+
+__global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
+  extern __shared__ float ftab[];   // DSF interval table, 12 floats per interval
+  __shared__ float qqt[MT * MT], e4t[MT * MT], s2t[MT * MT], vrct[MT * MT], dvrct[MT * MT];
+  __shared__ float4 shh[125], shl[125];
+  __shared__ int tN[MT], tLg[MT];
+  __shared__ int woff[PAIR_THREADS / 32][MT];  // per warp: partner-type bead-row offset, -1 inactive
+  __shared__ float wwt[PAIR_THREADS / 32][MT]; // per warp: 1/P* per partner type
+  const int nt = d.n_types;
+  for (int e = threadIdx.x; e < 12 * d.dsf_nint; e += blockDim.x) ftab[e] = d.dsf_tab32[e];
+  for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
+    const PairPar pp = d.pairpar[(e / nt) * MT + (e % nt)];
+    qqt[e] = (float)pp.qq;
+    e4t[e] = (float)pp.e4;
+    s2t[e] = (float)pp.s2;
+    vrct[e] = (float)pp.vrc;
+    dvrct[e] = (float)pp.dvrc;
+  }
+  for (int e = threadIdx.x; e < nt; e += blockDim.x) {
+    tN[e] = d.N[e];
+    tLg[e] = d.log2P[e];
+  }
+  for (int e = threadIdx.x; e < 125; e += blockDim.x) {
+    const int nx = e / 25 - 2, ny = (e / 5) % 5 - 2, nz = e % 5 - 2;
+    const double lo = d.box - (double)d.box_hi;
+    shh[e] = make_float4(nx * d.box_hi, ny * d.box_hi, nz * d.box_hi, 0.0f);
+    shl[e] = make_float4((float)(nx * lo), (float)(ny * lo), (float)(nz * lo), 0.0f);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < d.n_items32; w += nwarps) {
+  const int sl = w / d.n_nonp;             // slice of the finest grid
+  const int pos = w - sl * d.n_nonp;
+  const int lgM = d.lgPmax_nb;
+  const AtomInfo ai = d.ainfo[pos];
+  const int row_i = ai.row0 + (sl >> (lgM - ai.log2P)) * ai.stride;
+  const float4 xih = d.Xf[row_i], xil = d.Xl[row_i];
+  const int cnt = min(d.nl_cnt[pos], d.nl_cap);
+  const int* lst = d.nl + (size_t)pos * d.nl_cap;
+  const float rc = (float)d.rc, rc2 = (float)d.rc2, slo = (float)d.dsf_smin;
+  const float scr2 = d.screen_rc2;
+  const int base = (127 + (d.dsf_base >> 6) - 1023) << 6;
+  const int trow = ai.type * nt;
+  const int wib = threadIdx.x >> 5;
+  __syncwarp();
+  if (lane < nt) {
+    const int lgs = max(ai.log2P, tLg[lane]);  // log2 P*
+    const bool act = (sl & ((1 << (lgM - lgs)) - 1)) == 0;
+    woff[wib][lane] = act ? (sl >> (lgM - tLg[lane])) * tN[lane] : -1;
+    wwt[wib][lane] = __int_as_float((127 - lgs) << 23);
+  }
+  __syncwarp();
+  float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, ec = 0.f, vir = 0.f;
+  int nev = 0, nlj = 0;
+  int ent_next = lane < cnt ? lst[lane] : 0;
+  for (int e = lane; e < cnt; e += 32) {
+    const int ent = ent_next;
+    ent_next = e + 32 < cnt ? lst[e + 32] : 0;
+    const int tj = (ent >> 7) & 15;
+    const int oj = woff[wib][tj];
+    if (oj < 0) continue;  // pair inactive at this slice
+    const int row_j = (ent >> 11) + oj;
+    const float4 hj = d.Xf[row_j];
+    const float4 sh = shh[ent & 127];
+    // exact grid-point displacement first; the remainders move it by at
+    // most 2^-11 A per axis, so only candidates passing the screen go on
+    const float hx = (hj.x - xih.x) + sh.x, hy = (hj.y - xih.y) + sh.y, hz = (hj.z - xih.z) + sh.z;
+    if (fmaf(hz, hz, fmaf(hy, hy, hx * hx)) > scr2) continue;
+    const float4 lj = d.Xl[row_j];
+    const float4 sm = shl[ent & 127];
+    const float dx = hx + ((lj.x - xil.x) + sm.x);
+    const float dy = hy + ((lj.y - xil.y) + sm.y);
+    const float dz = hz + ((lj.z - xil.z) + sm.z);
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    if (!(r2 < rc2)) continue;
+    const int k = trow + tj;
+    const float wgt = wwt[wib][tj];  // 1/P*
+    float fr = 0.f, et = 0.f, lt = 0.f;
+    const float qq = qqt[k];
+    if (qq != 0.f) {
+      float g, fg;
+      if (r2 >= slo) {
+        const int bits = __float_as_int(r2);
+        dsf_table32(ftab + 12 * ((bits >> 17) - base), bits, r2, &g, &fg);
+      } else {
+        const float r = sqrtf(r2), rinv = 1.0f / r;
+        const float erc = erfcf((float)d.alpha * r), ex = expf(-(float)(d.alpha * d.alpha) * r2);
+        g = erc * rinv - (float)d.dsf_erfc_rc_over_rc + (float)d.dsf_cf * (r - rc);
+        fg = (erc * rinv * rinv + (float)d.dsf_g * ex * rinv - (float)d.dsf_cf) * rinv;
+      }
+      et = qq * g;
+      fr = qq * fg;
+    }
+    const float e4 = e4t[k];
+    if (e4 != 0.f) {
+      const float rinv = rsqrtf(r2);
+      const float r = r2 * rinv, rinv2 = rinv * rinv;
+      const float sr2 = s2t[k] * rinv2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
+      lt = e4 * (sr12 - sr6) - vrct[k] - (r - rc) * dvrct[k];
+      fr += (6.0f * e4 * (2.0f * sr12 - sr6) * rinv + dvrct[k]) * rinv;
+      ++nlj;
+    }
+    fr *= wgt;
+    // force on i is minus the force on j along d = x_j - x_i
+    fx = fmaf(-fr, dx, fx);
+    fy = fmaf(-fr, dy, fy);
+    fz = fmaf(-fr, dz, fz);
+    ec = fmaf(wgt, et, ec);
+    elj = fmaf(wgt, lt, elj);
+    vir = fmaf(fr, r2, vir);
+    ++nev;
+  }
+  // lane partials to fixed point by bit assembly, summed with integer
+  // shuffles: exact and free of FP64 instructions
+  int bad = 0;
+  long long kx = fixs(f2d_bits(fx), 44, &bad), ky = fixs(f2d_bits(fy), 44, &bad), kz = fixs(f2d_bits(fz), 44, &bad);
+  // every term is seen from both of its atoms: energies carry a factor 1/2
+  long long kl = fixs(f2d_bits(elj), 39, &bad), kc = fixs(f2d_bits(ec), 39, &bad), kv = fixs(f2d_bits(vir), 39, &bad);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    kx += __shfl_xor_sync(0xffffffffu, kx, o);
+    ky += __shfl_xor_sync(0xffffffffu, ky, o);
+    kz += __shfl_xor_sync(0xffffffffu, kz, o);
+    kl += __shfl_xor_sync(0xffffffffu, kl, o);
+    kc += __shfl_xor_sync(0xffffffffu, kc, o);
+    kv += __shfl_xor_sync(0xffffffffu, kv, o);
+  }
+  nev = warp_sumi(nev);
+  nlj = warp_sumi(nlj);
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nlj);
+    unsigned long long* fi = d.F_fix + 3 * (size_t)row_i;
+    atomicAdd(fi + 0, (unsigned long long)kx);
+    atomicAdd(fi + 1, (unsigned long long)ky);
+    atomicAdd(fi + 2, (unsigned long long)kz);
+    atomicAdd(d.E_fix + E_LJ, (unsigned long long)kl);
+    atomicAdd(d.E_fix + E_COUL, (unsigned long long)kc);
+    atomicAdd(d.E_fix + E_VIRIAL, (unsigned long long)kv);
+    atomicAdd(d.E_fix + E_NEVAL, (unsigned long long)nev);
+    if (bad) atomicOr(d.err, ERR_NONFINITE);
+  }
   }
 }
 
@@ -532,8 +744,10 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
     sh[e] = make_double3((e / 25 - 2) * d.box, ((e / 5) % 5 - 2) * d.box, (e % 5 - 2) * d.box);
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= d.n_ppitems) return;
+  const int wc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nch = d.pseudo_chunks;
+  if (wc >= d.n_ppitems * nch) return;
+  const int w = wc / nch, chunk = wc - w * nch;  // (pseudo bead, slice of its site list)
   // items: pseudo particles in order, all beads of each
   int e = 0, base = 0;
   while (e + 1 < d.n_pseudo && w >= base + (1 << d.pinfo[e].log2P)) {
@@ -550,7 +764,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
   const double rc = d.rc, rc2 = d.rc2;
   double fex = 0.0, fey = 0.0, fez = 0.0, ep = 0.0, vir = 0.0;
   int nev = 0;
-  for (int k = lane; k < cnt; k += 32) {
+  for (int k = chunk * 32 + lane; k < cnt; k += 32 * nch) {
     const int ent = lst[k];
     const int c = ent >> 7;
     const AtomInfo ac = d.ainfo[c];
@@ -592,6 +806,113 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
   }
 }
 
+
+// pseudopotential in FP32 (precision MIXTS_FP32_FORCES): one warp per
+// (pseudo particle, bead), lanes over sites; site reactions through
+// fixed-point atomics assembled from the bit fields
+__global__ void __launch_bounds__(PAIR_THREADS) k_pseudo32(Dev d) {
+  __shared__ float pk[MT], psg[MT], pA[MT], pb[MT], pvr[MT], pdv[MT];
+  __shared__ float4 shh[125], shl[125];
+  for (int e = threadIdx.x; e < d.n_types; e += blockDim.x) {
+    const PseudoPar pp = d.pspar[e];
+    pk[e] = (float)pp.kq;
+    psg[e] = (float)pp.sig;
+    pA[e] = (float)pp.A;
+    pb[e] = (float)pp.b;
+    pvr[e] = (float)pp.vrc;
+    pdv[e] = (float)pp.dvrc;
+  }
+  for (int e = threadIdx.x; e < 125; e += blockDim.x) {
+    const int nx = e / 25 - 2, ny = (e / 5) % 5 - 2, nz = e % 5 - 2;
+    const double lo = d.box - (double)d.box_hi;
+    shh[e] = make_float4(nx * d.box_hi, ny * d.box_hi, nz * d.box_hi, 0.0f);
+    shl[e] = make_float4((float)(nx * lo), (float)(ny * lo), (float)(nz * lo), 0.0f);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int wc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nch = d.pseudo_chunks;
+  if (wc >= d.n_ppitems * nch) return;
+  const int w = wc / nch, chunk = wc - w * nch;  // (pseudo bead, slice of its site list)
+  int e = 0, base = 0;
+  while (e + 1 < d.n_pseudo && w >= base + (1 << d.pinfo[e].log2P)) {
+    base += 1 << d.pinfo[e].log2P;
+    ++e;
+  }
+  const int sb = w - base;
+  const AtomInfo pe = d.pinfo[e];
+  const int row_e = pe.row0 + sb * pe.stride;
+  const float4 eh = d.Xf[row_e], el = d.Xl[row_e];
+  const float wgt = __int_as_float((127 - pe.log2P) << 23);
+  const int cnt = min(d.pl_cnt[e], d.pl_cap);
+  const int* lst = d.pl + (size_t)e * d.pl_cap;
+  const float rc = (float)d.rc, rc2 = (float)d.rc2;
+  float fex = 0.f, fey = 0.f, fez = 0.f, ep = 0.f, vir = 0.f;
+  int nev = 0, bad = 0;
+  for (int k = chunk * 32 + lane; k < cnt; k += 32 * nch) {
+    const int ent = lst[k];
+    const AtomInfo ac = d.ainfo[ent >> 7];
+    const int row_c = ac.row0 + (sb >> (pe.log2P - ac.log2P)) * ac.stride;
+    const float4 ch = d.Xf[row_c], cl = d.Xl[row_c];
+    const float4 sh = shh[ent & 127], sm = shl[ent & 127];
+    const float dx = ((ch.x - eh.x) + sh.x) + ((cl.x - el.x) + sm.x);
+    const float dy = ((ch.y - eh.y) + sh.y) + ((cl.y - el.y) + sm.y);
+    const float dz = ((ch.z - eh.z) + sh.z) + ((cl.z - el.z) + sm.z);
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    if (!(r2 < rc2)) continue;
+    const int t = ac.type;
+    const float r = sqrtf(r2);
+    const float x = r / psg[t];
+    float gg, dg;
+    if (x < 1.0e-3f) {
+      const float x2 = x * x, c = 1.1283791670955126f / psg[t];
+      gg = c * (1.0f - x2 / 3.0f + x2 * x2 / 10.0f);
+      dg = c / psg[t] * (-2.0f * x / 3.0f + 0.4f * x2 * x);
+    } else {
+      const float ef = erff(x);
+      gg = ef / r;
+      dg = 1.1283791670955126f * expf(-x * x) / (psg[t] * r) - ef / r2;
+    }
+    const float ex = expf(-r / pb[t]);
+    const float v = -pk[t] * gg + pA[t] * ex;
+    const float dv = -pk[t] * dg - (pA[t] / pb[t]) * ex;
+    ep = fmaf(wgt, v - pvr[t] - (r - rc) * pdv[t], ep);
+    const float fr = -wgt * (dv - pdv[t]) / r;  // force on the site along d
+    const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
+    fex -= fx;
+    fey -= fy;
+    fez -= fz;
+    vir = fmaf(fr, r2, vir);
+    ++nev;
+    unsigned long long* fc = d.F_fix + 3 * (size_t)row_c;
+    atomicAdd(fc + 0, (unsigned long long)fixs(f2d_bits(fx), 44, &bad));
+    atomicAdd(fc + 1, (unsigned long long)fixs(f2d_bits(fy), 44, &bad));
+    atomicAdd(fc + 2, (unsigned long long)fixs(f2d_bits(fz), 44, &bad));
+  }
+  long long kx = fixs(f2d_bits(fex), 44, &bad), ky = fixs(f2d_bits(fey), 44, &bad), kz = fixs(f2d_bits(fez), 44, &bad);
+  long long ke = fixs(f2d_bits(ep), 40, &bad), kv = fixs(f2d_bits(vir), 40, &bad);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    kx += __shfl_xor_sync(0xffffffffu, kx, o);
+    ky += __shfl_xor_sync(0xffffffffu, ky, o);
+    kz += __shfl_xor_sync(0xffffffffu, kz, o);
+    ke += __shfl_xor_sync(0xffffffffu, ke, o);
+    kv += __shfl_xor_sync(0xffffffffu, kv, o);
+  }
+  nev = warp_sumi(nev);
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    unsigned long long* fe = d.F_fix + 3 * (size_t)row_e;
+    atomicAdd(fe + 0, (unsigned long long)kx);
+    atomicAdd(fe + 1, (unsigned long long)ky);
+    atomicAdd(fe + 2, (unsigned long long)kz);
+    atomicAdd(d.E_fix + E_PSEUDO, (unsigned long long)ke);
+    atomicAdd(d.E_fix + E_VIRIAL, (unsigned long long)kv);
+    atomicAdd(d.E_fix + E_NPEVAL, (unsigned long long)nev);
+    if (bad) atomicOr(d.err, ERR_NONFINITE);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -613,8 +934,33 @@ int launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo) {
   return n;
 }
 
+// persistent grid sizes: resident CTAs per SM times SMs
+void pair_grids(int nt, int nint, int* g64, int* g32) {
+  int dev = 0, sms = 0, b64 = 0, b32 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  (void)nt;
+  cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_pair64, PAIR_THREADS, sizeof(double) * 12 * (size_t)nint);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_pair32, PAIR_THREADS, sizeof(float) * 12 * (size_t)nint);
+  *g64 = std::max(1, b64) * std::max(1, sms);
+  *g32 = std::max(1, b32) * std::max(1, sms);
+}
+
 int launch_pair(const Dev& d, cudaStream_t s) {
   const int wpb = PAIR_THREADS / 32;
+  if (d.precision == MIXTS_FP32_FORCES) {
+    if (d.n_items32 == 0) return 0;
+    const size_t smem = sizeof(float) * 12 * (size_t)d.dsf_nint;
+    static bool attr32 = false;
+    if (!attr32) {
+      cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      attr32 = true;
+    }
+    k_pair32<<<min((d.n_items32 + wpb - 1) / wpb, d.pair32_grid), PAIR_THREADS, smem, s>>>(d);
+    return 1;
+  }
   if (d.n_pitems == 0) return 0;
   const size_t smem = sizeof(double) * 12 * (size_t)d.dsf_nint;
   static bool attr = false;
@@ -622,7 +968,7 @@ int launch_pair(const Dev& d, cudaStream_t s) {
     cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr = true;
   }
-  k_pair64<<<(d.n_pitems + wpb - 1) / wpb, PAIR_THREADS, smem, s>>>(d);
+  k_pair64<<<min((d.n_pitems + wpb - 1) / wpb, d.pair_grid), PAIR_THREADS, smem, s>>>(d);
   return 1;
 }
 
@@ -635,7 +981,12 @@ int launch_bonded(const Dev& d, cudaStream_t s, const AtomInfo* ainfo_atom) {
 int launch_pseudo(const Dev& d, cudaStream_t s) {
   const int wpb = PAIR_THREADS / 32;
   if (d.n_ppitems == 0 || d.n_nonp == 0) return 0;
-  k_pseudo64<<<(d.n_ppitems + wpb - 1) / wpb, PAIR_THREADS, 0, s>>>(d);
+  const int items = d.n_ppitems * d.pseudo_chunks;
+  if (d.precision == MIXTS_FP32_FORCES) {
+    k_pseudo32<<<(items + wpb - 1) / wpb, PAIR_THREADS, 0, s>>>(d);
+    return 1;
+  }
+  k_pseudo64<<<(items + wpb - 1) / wpb, PAIR_THREADS, 0, s>>>(d);
   return 1;
 }
 

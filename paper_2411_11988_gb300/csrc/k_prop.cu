@@ -59,6 +59,8 @@ __device__ __forceinline__ void write_mirror(const Dev& d, int row, double x, do
             gz = (int)((iz + (1LL << 35)) >> 36);
   d.Xf[row] = make_float4(small_int_float(gx) * 0x1p-12f, small_int_float(gy) * 0x1p-12f,
                           small_int_float(gz) * 0x1p-12f, 0.0f);
+  d.Xl[row] = make_float4((float)(ix - ((long long)gx << 36)) * 0x1p-48f, (float)(iy - ((long long)gy << 36)) * 0x1p-48f,
+                          (float)(iz - ((long long)gz << 36)) * 0x1p-48f, 0.0f);
   if (bad) atomicOr(d.err, ERR_NONFINITE);
 }
 
@@ -236,8 +238,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop_small(Dev d, int mode) {
     __syncthreads();
     for (int a = tid; a < na; a += nt) {
       const int atom = d.atom_of_tk[d.atoff[t] + k0 + a];
-      d.spread[(size_t)atom * d.spread_slots] = __dsqrt_rn(__longlong_as_double(s_d2[a]));
-      for (int s2 = 1; s2 < d.spread_slots; ++s2) d.spread[(size_t)atom * d.spread_slots + s2] = 0.0;
+      d.spread[atom] = __dsqrt_rn(__longlong_as_double(s_d2[a]));
     }
   }
   if (mode & PM_PCART) {
@@ -284,8 +285,11 @@ __global__ void k_mirror_from_q(Dev d) {
       sp = dd > sp ? dd : sp;
     }
   }
-  d.spread[(size_t)atom * d.spread_slots] = sp;
-  for (int s = 1; s < d.spread_slots; ++s) d.spread[(size_t)atom * d.spread_slots + s] = 0.0;
+  d.spread[atom] = sp;
+  if (P > SMALL_P) {  // a large-P atom: its block partials must not keep older values
+    const int nb = P / BIG_MB;
+    for (int s = 0; s < nb; ++s) d.spread_big[d.sb_off[t] + k * nb + s] = 0.0;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -483,7 +487,8 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_inv(Dev d, int t, int mode)
       for (int o = 16; o > 0; o >>= 1) sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, o));
       if (lane == 0) {
         const int atom = d.atom_of_tk[d.atoff[t] + a];
-        d.spread[(size_t)atom * d.spread_slots + blockIdx.x] = sp;
+        d.spread_big[d.sb_off[t] + a * gridDim.x + blockIdx.x] = sp;
+        if (blockIdx.x == 0) d.spread[atom] = 0.0;
       }
     }
   }
@@ -544,9 +549,11 @@ __global__ void k_final(Dev d, int mode, const int* slot_type) {
     est[7] = es;
     est[8] = v[E_VIRIAL];
     // counters are integers carried in the fixed-point slots
-    est[13] = (double)(long long)d.E_fix[E_NEVAL];
+    // full lists (FP32 forces) see every pair term from both atoms
+    const double cnt_scale = d.full_list ? 0.5 : 1.0;
+    est[13] = cnt_scale * (double)(long long)d.E_fix[E_NEVAL];
     est[14] = (double)(long long)d.E_fix[E_NPEVAL];
-    est[16 + 4 * MT] = (double)(long long)d.E_fix[E_NLJEVAL];
+    est[16 + 4 * MT] = cnt_scale * (double)(long long)d.E_fix[E_NLJEVAL];
     est[9] = 2.0 * ke * kc / (3.0 * (double)d.n_beads * d.kB);
     est[11] = heat;
     est[10] = ke + es + V;
@@ -589,9 +596,10 @@ __global__ void k_energy_out(Dev d) {
   d.est[4] = v[E_ANGLE];
   d.est[5] = v[E_PSEUDO];
   d.est[8] = v[E_VIRIAL];
-  d.est[13] = (double)(long long)d.E_fix[E_NEVAL];
+  const double cnt_scale = d.full_list ? 0.5 : 1.0;
+  d.est[13] = cnt_scale * (double)(long long)d.E_fix[E_NEVAL];
   d.est[14] = (double)(long long)d.E_fix[E_NPEVAL];
-  d.est[16 + 4 * MT] = (double)(long long)d.E_fix[E_NLJEVAL];
+  d.est[16 + 4 * MT] = cnt_scale * (double)(long long)d.E_fix[E_NLJEVAL];
   for (int i = 0; i < E_NSLOTS; ++i) d.E_fix[i] = 0ull;
 }
 

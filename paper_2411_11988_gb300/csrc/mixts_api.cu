@@ -69,7 +69,8 @@ struct Plan {
   std::vector<double> cm;
   std::vector<double> dsf;     // DSF interval table
   int dsf_nint = 0, dsf_elo = -2;
-  std::vector<int> cm_off, mc_off, big_slot0;
+  std::vector<int> cm_off, mc_off, big_slot0, sb_off;
+  int n_spread_big = 0;
   std::vector<ModeCoef> mc;
   std::vector<PropTile> tiles;
   std::vector<int> slot_type;
@@ -84,9 +85,9 @@ struct Plan {
   size_t o_tab = 0, tab_bytes = 0;
   size_t o_ainfo, o_pos_atom, o_pos_mol, o_atom_of_tk, o_ainfo_atom, o_pos_of_atom, o_is_pseudo, o_pseudo_atom, o_pinfo,
       o_pairpar, o_pspar, o_bitems, o_bond_atoms, o_bond_par, o_ang_atoms, o_ang_par, o_cm, o_mc, o_tiles,
-      o_slot_type, o_dsf;
+      o_slot_type, o_dsf, o_dsf32;
   size_t o_state = 0, state_bytes = 0;
-  size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_ref, o_refd, o_reff, o_spread, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
+  size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_xl, o_ref, o_refd, o_reff, o_spread, o_spread_big, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
       o_err, o_step, o_heat, o_est, o_parts;
 };
 
@@ -203,6 +204,10 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   if (!s->type_of_atom || !s->mol_of_atom || !s->P_type || !s->mass_type || !s->charge_type || !s->lj_eps ||
       !s->lj_sig || !s->pseudo_type || !s->pp_sigma || !s->pp_A_eV || !s->pp_b) {
     fail(p, MIXTS_ERR_ARG, "NULL per-type or per-atom array");
+    return p;
+  }
+  if (prm->precision != MIXTS_FP64 && prm->precision != MIXTS_FP32_FORCES) {
+    fail(p, MIXTS_ERR_ARG, "unknown precision");
     return p;
   }
   if (!(s->box > 0.0) || !(prm->r_cut > 0.0) || !(prm->dt > 0.0) || !(prm->T > 0.0)) {
@@ -371,6 +376,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.cm_off.assign(MT, 0);
   p.mc_off.assign(MT, 0);
   p.big_slot0.assign(MT, 0);
+  p.sb_off.assign(MT, 0);
   for (int t = 0; t < p.nt; ++t) {
     const int P = s->P_type[t];
     const double m = s->mass_type[t];
@@ -433,6 +439,8 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
     p.big_slot0[t] = (int)p.slot_type.size();
     for (int b = 0; b < P / BIG_MB; ++b) p.slot_type.push_back(t);
     p.spread_slots = std::max(p.spread_slots, P / BIG_MB);
+    p.sb_off[t] = p.n_spread_big;
+    p.n_spread_big += p.N[t] * (P / BIG_MB);
   }
   // neighbour-list capacities
   const double vol = s->box * s->box * s->box;
@@ -473,6 +481,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_tiles = A.add(sizeof(PropTile) * std::max<size_t>(1, p.tiles.size()));
   p.o_slot_type = A.add(sizeof(int) * std::max<size_t>(1, p.slot_type.size()));
   p.o_dsf = A.add(sizeof(double) * p.dsf.size());
+  p.o_dsf32 = A.add(sizeof(float) * p.dsf.size());
   p.tab_bytes = A.size;
   const size_t nb3 = (size_t)p.n_beads * 3;
   p.o_qnm = A.add(sizeof(double) * nb3);
@@ -481,10 +490,12 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_xw = A.add(sizeof(double4_32a) * p.n_beads);
   p.o_xi = A.add(sizeof(longlong4_32a) * p.n_beads);
   p.o_xf = A.add(sizeof(float4) * p.n_beads);
+  p.o_xl = A.add(sizeof(float4) * p.n_beads);
   p.o_ref = A.add(sizeof(double) * 3 * p.na);
   p.o_refd = A.add(sizeof(double4_32a) * std::max(1, p.n_nonp));
   p.o_reff = A.add(sizeof(float4) * std::max(1, p.n_nonp));
-  p.o_spread = A.add(sizeof(double) * (size_t)p.na * p.spread_slots);
+  p.o_spread = A.add(sizeof(double) * (size_t)p.na);
+  p.o_spread_big = A.add(sizeof(double) * (size_t)std::max(1, p.n_spread_big));
   p.o_nl = A.add(sizeof(int) * (size_t)std::max(1, p.n_nonp) * p.nl_cap);
   p.o_nlcnt = A.add(sizeof(int) * std::max(1, p.n_nonp));
   p.o_pl = A.add(sizeof(int) * (size_t)std::max(1, p.n_pseudo) * p.pl_cap);
@@ -652,6 +663,10 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   put(img, p.o_tiles, p.tiles);
   put(img, p.o_slot_type, p.slot_type);
   put(img, p.o_dsf, p.dsf);
+  {
+    std::vector<float> t32(p.dsf.begin(), p.dsf.end());
+    put(img, p.o_dsf32, t32);
+  }
   mixts_status st = cuda_check(h, cudaMemcpy(h->ws, img.data(), p.tab_bytes, cudaMemcpyHostToDevice), "upload tables");
   if (st == MIXTS_OK)
     st = cuda_check(h, cudaMemsetAsync(h->ws + p.tab_bytes, 0, p.ar.size - p.tab_bytes, h->stream), "clear state");
@@ -688,6 +703,10 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.dsf_cf = erfc(prm->dsf_alpha * prm->r_cut) / (prm->r_cut * prm->r_cut) +
              d.dsf_g * exp(-prm->dsf_alpha * prm->dsf_alpha * prm->r_cut * prm->r_cut) / prm->r_cut;
   d.dsf_tab = (const double*)(h->ws + p.o_dsf);
+  d.dsf_tab32 = (const float*)(h->ws + p.o_dsf32);
+  d.full_list = prm->precision == MIXTS_FP32_FORCES ? 1 : 0;
+  d.lgPmax_nb = p.n_classes > 0 ? p.cls_log2P[0] : 0;
+  d.n_items32 = p.n_nonp << d.lgPmax_nb;
   d.dsf_nint = p.dsf_nint;
   d.dsf_base = (1023 + p.dsf_elo) << 6;
   d.dsf_smin = ldexp(1.0, p.dsf_elo);
@@ -709,6 +728,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
     d.cm_off[t] = p.cm_off[t];
     d.mc_off[t] = p.mc_off[t];
     d.big_slot0[t] = p.big_slot0[t];
+    d.sb_off[t] = p.sb_off[t];
     d.mass[t] = sys->mass_type[t];
   }
   for (int c = 0; c < p.n_classes; ++c) {
@@ -747,11 +767,15 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.Xw = (double4_32a*)(w + p.o_xw);
   d.Xi = (longlong4_32a*)(w + p.o_xi);
   d.Xf = (float4*)(w + p.o_xf);
+  d.Xl = (float4*)(w + p.o_xl);
   d.ref = (double*)(w + p.o_ref);
   d.refd = (double4_32a*)(w + p.o_refd);
   d.reff = (float4*)(w + p.o_reff);
   d.pos_of_atom = (const int*)(w + p.o_pos_of_atom);
   d.spread = (double*)(w + p.o_spread);
+  d.spread_big = (double*)(w + p.o_spread_big);
+  pair_grids(p.nt, p.dsf_nint, &d.pair_grid, &d.pair32_grid);
+  d.pseudo_chunks = 8;
   d.nl = (int*)(w + p.o_nl);
   d.nl_cnt = (int*)(w + p.o_nlcnt);
   d.pl = (int*)(w + p.o_pl);

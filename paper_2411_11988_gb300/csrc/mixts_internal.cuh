@@ -97,6 +97,10 @@ struct Dev {
   float box_hi;             // box edge rounded to the 2^-12 A grid
   long long box_fix;        // box edge in 2^-48 A fixed point
   float screen_rc2;         // binary32 screen radius^2 (r_cut + 2e-3)^2
+  const float* dsf_tab32;   // the DSF interval table rounded to binary32 (FP32 force path)
+  int full_list;            // 1: every row lists all partners (FP32 force path)
+  int lgPmax_nb;            // log2 of the largest bead count among non-pseudo atoms
+  int n_items32;            // FP32 pair items: n_nonp * 2^lgPmax_nb
   double dt, kcal, kT, kB;
   uint64_t seed;
   // per type
@@ -104,6 +108,8 @@ struct Dev {
   int cm_off[MT];       // offset of C (P <= SMALL_P) or the cos table (P > SMALL_P)
   int mc_off[MT];       // offset of the ModeCoef rows
   int big_slot0[MT];    // first estimator partial slot of a large-P type
+  int sb_off[MT];       // offset of a large-P type's spread partials
+  int pair_grid, pair32_grid, pseudo_chunks;  // persistent grid sizes, site-list split
   double mass[MT];
   // sorted classes of non-pseudo atoms (P descending)
   int cls_P[MAX_CLASSES], cls_log2P[MAX_CLASSES], cls_pos0[MAX_CLASSES], cls_n[MAX_CLASSES],
@@ -136,11 +142,13 @@ struct Dev {
   double4_32a* Xw;                 // [n_beads] positions shifted so bead 0 of each atom lies in the box
   longlong4_32a* Xi;               // [n_beads] the same in 2^-48 A fixed point (exact differences)
   float4* Xf;                  // [n_beads] binary32 positions on the 2^-12 A grid (screens)
+  float4* Xl;                  // [n_beads] binary32 remainders: Xw = Xf + Xl to ~2^-37 A
   double* ref;                 // [n_atoms*3] wrapped bead-0 reference positions
   double4_32a* refd;           // [n_nonp] the same by sorted position
   float4* reff;                // [n_nonp] binary32 copy, .w = log2 P (int bits)
   const int* pos_of_atom;      // [n_atoms] sorted position, -1 for pseudo particles
-  double* spread;              // [n_atoms*spread_slots] max |q_b - q_0| partials
+  double* spread;              // [n_atoms] max |q_b - q_0| (0 for large-P atoms)
+  double* spread_big;          // large-P atoms: one partial per bead block, at sb_off[t] + rank * (P/BIG_MB)
   int* nl;                     // [n_nonp*nl_cap] (partner position << 7) | image code
   int* nl_cnt;                 // [n_nonp]
   int* pl;                     // [n_pseudo*pl_cap]
@@ -366,6 +374,7 @@ int launch_pseudo(const Dev& d, cudaStream_t s);
 int launch_prop(const Dev& d, cudaStream_t s, int mode);
 int launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type);
 int launch_forces_out(const Dev& d, cudaStream_t s);
+void pair_grids(int nt, int nint, int* g64, int* g32);
 int launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out);
 
 // propagation modes

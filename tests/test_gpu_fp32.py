@@ -1,0 +1,92 @@
+"""FP32-forces precision mode against the FP64 oracle (GPU only).
+
+Tolerances (FP32 pair forces, FP64 integration and reductions): forces
+max|F_gpu - F_or| / RMS(F_or) <= 1e-5, energies |V_gpu - V_or| / |V_or| <= 1e-5.
+The full neighbour list of this mode equals the oracle's owner list plus every
+entry seen from the other atom, bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+FTOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2411_11988_gb300 as P
+    return P
+
+
+def _case(name):
+    if name == "c1":
+        return synth.water_box(32, 9.865, 8, 2, seed=0)
+    if name == "c1_spread":
+        s = synth.water_box(32, 9.865, 8, 2, seed=2)
+        s.q = s.q + np.random.default_rng(9).normal(0, 0.1, s.q.shape)
+        return s
+    if name == "mixed":
+        s = synth.water_box(8, 8.4, 8, 2, seed=3, ion=dict(synth.systems.ION3), electron_P=128)
+        s.q = s.q + np.random.default_rng(103).normal(0, 0.08, s.q.shape)
+        return s
+    if name == "c2":
+        return synth.water_box(512, 24.83, 32, 4, seed=0)
+    if name == "c3":
+        return synth.water_box(256, 18.6, 8, 1, seed=0, ion=dict(synth.systems.ION3), electron_P=1024)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["c1", "c1_spread", "mixed", "c2", "c3"])
+def test_fp32_forces(gpu, name):
+    s = _case(name)
+    m = gpu.MixTS(s, precision=gpu.FP32_FORCES)
+    f, V = m.forces()
+    F = f.cpu().numpy()
+    F_or, parts = oracle.forces(s)
+    rms = np.sqrt(np.mean(F_or ** 2))
+    err = np.abs(F - F_or).max() / rms
+    assert err < FTOL32, err
+    assert abs(V - parts[0]) <= FTOL32 * abs(parts[0])
+    est = m.estimators()
+    assert abs(est["n_evals"] - parts[7]) <= 1e-5 * parts[7] + 2
+    m.close()
+
+
+def test_fp32_full_list_bit_exact(gpu):
+    s = _case("c1_spread")
+    m = gpu.MixTS(s, precision=gpu.FP32_FORCES)
+    m.forces()
+    tl, th = m.nlist(0)
+    ol, dmax, R = oracle.nlist(s)
+    assert th[0] == dmax and th[1] == R
+    rev = ol[:, [1, 0, 2]].copy()
+    code = rev[:, 2]
+    nx, ny, nz = code // 25 - 2, (code // 5) % 5 - 2, code % 5 - 2
+    rev[:, 2] = (-nx + 2) * 25 + (-ny + 2) * 5 + (-nz + 2)
+    full = np.concatenate([ol, rev])
+    full = full[np.lexsort((full[:, 2], full[:, 1], full[:, 0]))]
+    assert np.array_equal(tl, full)
+    m.close()
+
+
+def test_fp32_step_tracks_fp64(gpu):
+    s = _case("c1")
+    a = gpu.MixTS(s, precision=gpu.FP32_FORCES, seed=4)
+    b = gpu.MixTS(s, precision=gpu.FP64, seed=4)
+    a.step(10)
+    b.step(10)
+    qa, qb = a.q.cpu().numpy(), b.q.cpu().numpy()
+    assert np.abs(qa - qb).max() < 1e-6
+    ea, eb = a.estimators(), b.estimators()
+    for k in ["V", "KE_beads", "E_spring", "H_mix"]:
+        assert abs(ea[k] - eb[k]) <= 1e-5 * max(abs(eb[k]), 1.0), k
+    a.close()
+    b.close()
