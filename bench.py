@@ -212,6 +212,19 @@ def cpu_baseline(steps, warmup=0):
                 "ms_per_step": ms}
 
 
+def replica_reduce(step_ms, world, device=None):
+    """Replicas only: every rank advances its own system; the job's step time
+    is the slowest rank's, and the simulated time adds up over ranks.
+    Returns (max step ms over ranks, aggregate ns/day)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(step_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    return step_ms, ns_per_day(step_ms) * world
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -270,11 +283,7 @@ def main():
                                                        clocks_idx=local)
     est = m.estimators()
     single_ms = single_call_ms(m, torch, stream, max(3, args.steps // 2), flush)
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = ns_per_day(step_ms) * world
+    step_ms, value = replica_reduce(step_ms, world, dev)
     evals = est["n_evals"]
     pair_ms = ph_ms["pair"] / max(1, ph_calls["pair"])
     if prec == 1:

@@ -183,6 +183,22 @@ MIXTS_API mixts_status mixts_get_timing(mixts_handle h, double* ms_host, long lo
 MIXTS_API mixts_status mixts_gaussians(mixts_handle h, uint32_t step, uint32_t stage, uint64_t dof0, long n,
                              float* out_dev);
 
+/* Potential and gradients for the differentiation variant (Eq.
+ * mts-hamiltonian with force-field parameters theta). theta (8 doubles, host)
+ * = (sigma_a, A_a [eV], b_a, sigma_b, A_b [eV], b_b, q_a, eps_aa) for the
+ * site types a = type_a and b = type_b: the pseudopotential parameters of
+ * both, the charge of a, and the a-a Lennard-Jones epsilon; every other
+ * Lennard-Jones epsilon of a is rescaled by sqrt(eps_aa / eps_aa at init)
+ * (Lorentz-Berthelot). Evaluated in FP64 at the caller's current q without
+ * changing the handle's parameters. V_host (may be NULL) gets V_mix;
+ * dVdq_dev (device [n_beads][3], may be NULL) gets grad_out * dV/dq;
+ * dVdtheta_host (8, may be NULL) gets grad_out * dV/dtheta in kcal/mol per
+ * unit of theta. Pair terms are recomputed, not stored. Synchronises; the
+ * next mixts_step restarts from the caller's q and p. */
+MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int type_a, int type_b, const double* theta,
+                                            double grad_out, double* V_host, double* dVdq_dev,
+                                            double* dVdtheta_host);
+
 /* Allocation-free force evaluation. The paper has no counterpart; this
  * serves callers that cannot allocate device memory: plugins whose host
  * framework owns all device memory through its own pool (a stray

@@ -951,3 +951,156 @@ void or_estimators(const or_system* s, const or_params* prm, const double* q, co
   out[12] = parts[8];
   lay_free(&L);
 }
+
+/* ---------------------------------------------------------------------------
+ * Parameter gradient dV_mix/dtheta, theta = (sigma_a, A_a [eV], b_a,
+ * sigma_b, A_b [eV], b_b, q_a, eps_aa) for site types a and b. Charges enter
+ * every Coulomb term (DSF, and the pseudopotential's -k_e q erf(r/sigma)/r);
+ * eps_aa enters a-a Lennard-Jones directly and every other a-x
+ * Lennard-Jones term through eps_ax = sqrt(eps_aa eps_xx) (Lorentz-Berthelot),
+ * so d eps_ax / d eps_aa = eps_ax / (2 eps_aa). Each term is differentiated
+ * by hand, including the shifted-force corrections at r_cut.
+ * ------------------------------------------------------------------------- */
+static void dsf_unit(double alpha, double rc, double r, double* v) {
+  double dv;
+  dsf_raw(alpha, rc, r, v, &dv);
+}
+
+/* V, dV/dr of the raw pseudopotential and their derivatives with respect to
+ * (sigma, A [kcal/mol], b, q) at distance r */
+static void pseudo_param_derivs(double kq_unit, double q, double sig, double A, double b, double r, double dv[4],
+                                double ddv[4]) {
+  const double sp = sqrt(OR_PI);
+  double x = r / sig;
+  double ex = exp(-x * x), eb = exp(-r / b);
+  double erfx = erf(x);
+  /* d/dsigma */
+  dv[0] = kq_unit * q * (2.0 / sp) * ex / (sig * sig);
+  ddv[0] = -kq_unit * q * (2.0 / sp) * ex * 2.0 * r / (sig * sig * sig * sig);
+  /* d/dA */
+  dv[1] = eb;
+  ddv[1] = -eb / b;
+  /* d/db */
+  dv[2] = A * eb * r / (b * b);
+  ddv[2] = A * eb * (b - r) / (b * b * b);
+  /* d/dq */
+  dv[3] = -kq_unit * erfx / r;
+  ddv[3] = -kq_unit * ((2.0 / (sig * sp)) * ex / r - erfx / (r * r));
+}
+
+void or_grad_theta(const or_system* s, const double* q, int ta, int tb, double* g) {
+  lay_t L;
+  lay_init(s, &L);
+  cst_t c = get_cst();
+  const double rc = s->r_cut, rc2 = rc * rc, Lb = s->box;
+  for (int k = 0; k < 8; ++k) g[k] = 0.0;
+  int nt = s->n_types;
+  double eaa = s->lj_eps[ta * nt + ta];
+  /* nonbonded terms */
+  for (int a = 0; a < s->n_atoms; ++a) {
+    if (s->pseudo_type[s->type_of_atom[a]]) continue;
+    for (int cc = a + 1; cc < s->n_atoms; ++cc) {
+      if (s->pseudo_type[s->type_of_atom[cc]]) continue;
+      int i = a, j = cc;
+      if (s->P_type[s->type_of_atom[cc]] > s->P_type[s->type_of_atom[a]]) {
+        i = cc;
+        j = a;
+      }
+      int ti = s->type_of_atom[i], tj = s->type_of_atom[j];
+      int Ni = s->P_type[ti], Nj = s->P_type[tj];
+      int dq_ij = (ti == ta) + (tj == ta); /* how many charges are q_a */
+      double epsij = s->lj_eps[ti * nt + tj];
+      /* d eps_ij / d eps_aa: 1 for the a-a pair; eps_ax = eps_ax0 sqrt(eps_aa /
+         eps_aa0) for the cross pairs, held fixed when eps_aa0 = 0 */
+      double deps = 0.0;
+      if (ti == ta && tj == ta) deps = 1.0;
+      else if ((ti == ta || tj == ta) && eaa > 0.0) deps = epsij / (2.0 * eaa);
+      if (dq_ij == 0 && deps == 0.0) continue;
+      int* bi = (int*)malloc(sizeof(int) * (size_t)Ni);
+      int* bj = (int*)malloc(sizeof(int) * (size_t)Ni);
+      int n = or_pair_map(Ni, Nj, bi, bj);
+      double w = 1.0 / Ni;
+      int same = s->mol_of_atom[i] == s->mol_of_atom[j];
+      for (int m = 0; m < n; ++m) {
+        long ri = row_of(s, &L, i, bi[m]), rj = row_of(s, &L, j, bj[m]);
+        double d0[3];
+        int n0[3];
+        for (int d = 0; d < 3; ++d) {
+          d0[d] = q[3 * rj + d] - q[3 * ri + d];
+          n0[d] = -(int)nearbyint(d0[d] / Lb);
+        }
+        for (int ix = -2; ix <= 2; ++ix)
+          for (int iy = -2; iy <= 2; ++iy)
+            for (int iz = -2; iz <= 2; ++iz) {
+              if (same && n0[0] + ix == 0 && n0[1] + iy == 0 && n0[2] + iz == 0) continue;
+              double dx = d0[0] + (n0[0] + ix) * Lb, dy = d0[1] + (n0[1] + iy) * Lb, dz = d0[2] + (n0[2] + iz) * Lb;
+              double r2 = dx * dx + dy * dy + dz * dz;
+              if (r2 >= rc2) continue;
+              double r = sqrt(r2);
+              if (dq_ij) {
+                /* d(k_e q_i q_j G)/dq_a, G the unit-charge DSF */
+                double G;
+                dsf_unit(s->dsf_alpha, rc, r, &G);
+                double other = (dq_ij == 2) ? 2.0 * s->charge_type[ta]
+                                            : ((ti == ta) ? s->charge_type[tj] : s->charge_type[ti]);
+                g[6] += w * c.ke * other * G;
+              }
+              if (deps != 0.0) {
+                double v, dv, vc, dvc;
+                /* V_LJ is eps_ij times the unit-epsilon shifted-force term */
+                lj_raw(1.0, s->lj_sig[ti * nt + tj], r, &v, &dv);
+                lj_raw(1.0, s->lj_sig[ti * nt + tj], rc, &vc, &dvc);
+                g[7] += w * (v - vc - (r - rc) * dvc) * deps;
+              }
+            }
+      }
+      free(bi);
+      free(bj);
+    }
+  }
+  /* pseudopotential terms */
+  for (int e = 0; e < s->n_atoms; ++e) {
+    if (!s->pseudo_type[s->type_of_atom[e]]) continue;
+    for (int cc = 0; cc < s->n_atoms; ++cc) {
+      int tc = s->type_of_atom[cc];
+      if (s->pseudo_type[tc] || (tc != ta && tc != tb)) continue;
+      int Ne = s->P_type[s->type_of_atom[e]], Nc = s->P_type[tc];
+      int* bi = (int*)malloc(sizeof(int) * (size_t)Ne);
+      int* bj = (int*)malloc(sizeof(int) * (size_t)Ne);
+      int n = or_pair_map(Ne, Nc, bi, bj);
+      double w = 1.0 / Ne;
+      double sig = s->pp_sigma[tc], A = s->pp_A_eV[tc] * c.ev_kcal, b = s->pp_b[tc];
+      double dvc[4], ddvc[4];
+      pseudo_param_derivs(c.ke, s->charge_type[tc], sig, A, b, rc, dvc, ddvc);
+      int off = (tc == ta) ? 0 : 3;
+      for (int m = 0; m < n; ++m) {
+        long re = row_of(s, &L, e, bi[m]), rs = row_of(s, &L, cc, bj[m]);
+        double d0[3];
+        int n0[3];
+        for (int d = 0; d < 3; ++d) {
+          d0[d] = q[3 * rs + d] - q[3 * re + d];
+          n0[d] = -(int)nearbyint(d0[d] / Lb);
+        }
+        for (int ix = -2; ix <= 2; ++ix)
+          for (int iy = -2; iy <= 2; ++iy)
+            for (int iz = -2; iz <= 2; ++iz) {
+              double dx = d0[0] + (n0[0] + ix) * Lb, dy = d0[1] + (n0[1] + iy) * Lb, dz = d0[2] + (n0[2] + iz) * Lb;
+              double r2 = dx * dx + dy * dy + dz * dz;
+              if (r2 >= rc2) continue;
+              double r = sqrt(r2);
+              double dv[4], ddv[4];
+              pseudo_param_derivs(c.ke, s->charge_type[tc], sig, A, b, r, dv, ddv);
+              double t[4];
+              for (int k = 0; k < 4; ++k) t[k] = w * (dv[k] - dvc[k] - (r - rc) * ddvc[k]);
+              g[off + 0] += t[0];
+              g[off + 1] += t[1] * c.ev_kcal; /* per eV */
+              g[off + 2] += t[2];
+              if (tc == ta) g[6] += t[3];
+            }
+      }
+      free(bi);
+      free(bj);
+    }
+  }
+  lay_free(&L);
+}

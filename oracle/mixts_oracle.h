@@ -110,6 +110,12 @@ void or_step(const or_system* s, const or_params* prm, double* q, double* p, dou
 void or_estimators(const or_system* s, const or_params* prm, const double* q, const double* p,
                    const double* F, const double* parts, double* out);
 
+/* dV_mix/dtheta, theta = (sigma_a, A_a [eV], b_a, sigma_b, A_b [eV], b_b,
+ * q_a, eps_aa) for site types a = ta, b = tb; the cross Lennard-Jones terms
+ * of a scale as eps_ax = eps_ax0 sqrt(eps_aa / eps_aa0) (Lorentz-Berthelot),
+ * and are held fixed when eps_aa0 = 0. Units kcal/mol per unit of theta. */
+void or_grad_theta(const or_system* s, const double* q, int ta, int tb, double* dVdtheta8);
+
 /* Philox4x32-10 */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* standard normals of the thermostat stream for dofs [dof0, dof0+n) */

@@ -79,6 +79,7 @@ def _declare(L):
     L.or_nm_matrix.argtypes = [C.c_int, _dp]
     L.or_nm_freqs.argtypes = [C.c_int, C.c_double, _dp]
     L.or_step.argtypes = [S, Pp, _dp, _dp, _dp, C.c_uint64, _dp, _dp]
+    L.or_grad_theta.argtypes = [S, _dp, C.c_int, C.c_int, _dp]
     L.or_estimators.argtypes = [S, Pp, _dp, _dp, _dp, _dp, _dp]
     L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
     L.or_gaussians.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_long,
@@ -196,6 +197,46 @@ def pseudo_list(sysm, q=None, r_cut=R_CUT, cap=None):
     t = out[:n]
     order = np.lexsort((t[:, 2], t[:, 1], t[:, 0]))
     return t[order], th
+
+
+THETA_NAMES = ["sigma_a", "A_a", "b_a", "sigma_b", "A_b", "b_b", "q_a", "eps_aa"]
+
+
+def theta_of(sysm, ta, tb):
+    """Current theta = (sigma_a, A_a [eV], b_a, sigma_b, A_b, b_b, q_a, eps_aa)."""
+    return np.array([sysm.pp_sigma[ta], sysm.pp_A_eV[ta], sysm.pp_b[ta], sysm.pp_sigma[tb], sysm.pp_A_eV[tb],
+                     sysm.pp_b[tb], sysm.charge_type[ta], sysm.lj_eps[ta, ta]], dtype=np.float64)
+
+
+def with_theta(sysm, ta, tb, theta):
+    """Copy of the system with theta applied; cross LJ of type a rescaled by
+    sqrt(eps_aa'/eps_aa) (Lorentz-Berthelot), or left as they are when the
+    system's eps_aa is 0."""
+    s = sysm.copy()
+    s.pp_sigma = sysm.pp_sigma.copy()
+    s.pp_A_eV = sysm.pp_A_eV.copy()
+    s.pp_b = sysm.pp_b.copy()
+    s.charge_type = sysm.charge_type.copy()
+    s.lj_eps = sysm.lj_eps.copy()
+    s.pp_sigma[ta], s.pp_A_eV[ta], s.pp_b[ta] = theta[0], theta[1], theta[2]
+    s.pp_sigma[tb], s.pp_A_eV[tb], s.pp_b[tb] = theta[3], theta[4], theta[5]
+    s.charge_type[ta] = theta[6]
+    e0 = sysm.lj_eps[ta, ta]
+    scale = np.sqrt(theta[7] / e0) if e0 > 0 else 1.0  # cross terms held fixed when eps_aa = 0
+    for x in range(s.n_types):
+        if x != ta:
+            s.lj_eps[ta, x] = sysm.lj_eps[ta, x] * scale
+            s.lj_eps[x, ta] = sysm.lj_eps[x, ta] * scale
+    s.lj_eps[ta, ta] = theta[7]
+    return s
+
+
+def grad_theta(sysm, ta, tb, q=None, r_cut=R_CUT, alpha=DSF_ALPHA):
+    b = _Bound(sysm, r_cut, alpha)
+    q = np.ascontiguousarray(sysm.q if q is None else q, dtype=np.float64)
+    g = np.zeros(8)
+    lib().or_grad_theta(C.byref(b.s), _p(q, C.c_double), int(ta), int(tb), _p(g, C.c_double))
+    return g
 
 
 def nm_matrix(P):

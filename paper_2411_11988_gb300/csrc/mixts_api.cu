@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -68,6 +69,7 @@ struct Plan {
   std::vector<double> bond_par, ang_par;
   std::vector<double> cm;
   std::vector<double> dsf;     // DSF interval table
+  std::vector<double> charge, eps, sig, pp_sig, pp_A, pp_b;  // raw force-field parameters (theta variant)
   int dsf_nint = 0, dsf_elo = -2;
   std::vector<int> cm_off, mc_off, big_slot0, sb_off;
   int n_spread_big = 0;
@@ -85,7 +87,7 @@ struct Plan {
   size_t o_tab = 0, tab_bytes = 0;
   size_t o_ainfo, o_pos_atom, o_pos_mol, o_atom_of_tk, o_ainfo_atom, o_pos_of_atom, o_is_pseudo, o_pseudo_atom, o_pinfo,
       o_pairpar, o_pspar, o_bitems, o_bond_atoms, o_bond_par, o_ang_atoms, o_ang_par, o_cm, o_mc, o_tiles,
-      o_slot_type, o_dsf, o_dsf32;
+      o_slot_type, o_dsf, o_dsf32, o_pairpar_alt, o_pspar_alt, o_pc, o_gacc;
   size_t o_state = 0, state_bytes = 0;
   size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_xl, o_ref, o_refd, o_reff, o_spread, o_spread_big, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
       o_err, o_step, o_heat, o_est, o_parts;
@@ -305,6 +307,13 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
     p.n_ppitems += s->P_type[s->type_of_atom[a]];
   }
   p.n_pseudo = (int)p.pseudo_atom.size();
+  // raw parameters, kept for parameter-gradient evaluations
+  p.charge.assign(s->charge_type, s->charge_type + p.nt);
+  p.eps.assign(s->lj_eps, s->lj_eps + p.nt * p.nt);
+  p.sig.assign(s->lj_sig, s->lj_sig + p.nt * p.nt);
+  p.pp_sig.assign(s->pp_sigma, s->pp_sigma + p.nt);
+  p.pp_A.assign(s->pp_A_eV, s->pp_A_eV + p.nt);
+  p.pp_b.assign(s->pp_b, s->pp_b + p.nt);
   // pair parameters
   const double rc = prm->r_cut;
   p.pairpar.assign(MT * MT, PairPar{0, 0, 1, 0, 0});
@@ -482,6 +491,10 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_slot_type = A.add(sizeof(int) * std::max<size_t>(1, p.slot_type.size()));
   p.o_dsf = A.add(sizeof(double) * p.dsf.size());
   p.o_dsf32 = A.add(sizeof(float) * p.dsf.size());
+  p.o_pairpar_alt = A.add(sizeof(PairPar) * MT * MT);
+  p.o_pspar_alt = A.add(sizeof(PseudoPar) * MT);
+  p.o_pc = A.add(sizeof(double) * 8 * MT);
+  p.o_gacc = A.add(sizeof(unsigned long long) * (2 * MT * MT + 8));
   p.tab_bytes = A.size;
   const size_t nb3 = (size_t)p.n_beads * 3;
   p.o_qnm = A.add(sizeof(double) * nb3);
@@ -1038,6 +1051,151 @@ void mixts_destroy(mixts_handle h) {
 const char* mixts_last_error(mixts_handle h) { return h ? h->err.c_str() : "NULL handle"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Parameter gradient (the differentiation variant).
+// ---------------------------------------------------------------------------
+namespace {
+// parameter derivatives (sigma, A [kcal/mol], b, q) of the raw
+// pseudopotential V and of dV/dr at distance r
+void pseudo_param_derivs_host(double ke, double q, double sig, double A, double b, double r, double* dv,
+                              double* ddv) {
+  const double sp = sqrt(PI), x = r / sig, ex = exp(-x * x), eb = exp(-r / b), erfx = erf(x);
+  dv[0] = ke * q * (2.0 / sp) * ex / (sig * sig);
+  ddv[0] = -ke * q * (2.0 / sp) * ex * 2.0 * r / (sig * sig * sig * sig);
+  dv[1] = eb;
+  ddv[1] = -eb / b;
+  dv[2] = A * eb * r / (b * b);
+  ddv[2] = A * eb * (b - r) / (b * b * b);
+  dv[3] = -ke * erfx / r;
+  ddv[3] = -ke * ((2.0 / (sig * sp)) * ex / r - erfx / (r * r));
+}
+}  // namespace
+
+namespace mx {
+int launch_grad(const Dev& d, cudaStream_t s, int ta, int tb, double ke, const double* pc, unsigned long long* acc,
+                double grad_out, double* dvdq);
+}
+
+extern "C" MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int ta, int tb, const double* theta,
+                                                       double grad_out, double* V_host, double* dVdq_dev,
+                                                       double* dVdtheta_host) {
+  if (!h || !theta) return MIXTS_ERR_ARG;
+  const Plan& p = h->plan;
+  const int nt = p.nt;
+  if (ta < 0 || ta >= nt || tb < 0 || tb >= nt || ta == tb || h->d.pseudo[ta] || h->d.pseudo[tb])
+    return set_err(h, MIXTS_ERR_ARG, "theta types must be two distinct site types");
+  const double e0 = p.eps[ta * nt + ta];
+  if (!(theta[0] > 0.0) || !(theta[2] > 0.0) || !(theta[3] > 0.0) || !(theta[5] > 0.0) ||
+      !(e0 > 0.0 ? theta[7] > 0.0 : theta[7] >= 0.0))
+    return set_err(h, MIXTS_ERR_ARG, "sigma and b must be positive, eps_aa positive (non-negative if 0 at init)");
+  for (int k = 0; k < 8; ++k)
+    if (!std::isfinite(theta[k])) return set_err(h, MIXTS_ERR_ARG, "theta must be finite");
+  const Units u = units();
+  const double rc = h->d.rc;
+  // theta applied to a copy of the raw parameters
+  std::vector<double> q = p.charge, eps = p.eps, psig = p.pp_sig, pA = p.pp_A, pb = p.pp_b;
+  q[ta] = theta[6];
+  // cross terms follow eps_ax = eps_ax0 sqrt(eps_aa / eps_aa0), fixed if eps_aa0 = 0
+  const double scale = e0 > 0.0 ? sqrt(theta[7] / e0) : 1.0;
+  for (int x = 0; x < nt; ++x)
+    if (x != ta) {
+      eps[ta * nt + x] = p.eps[ta * nt + x] * scale;
+      eps[x * nt + ta] = p.eps[x * nt + ta] * scale;
+    }
+  eps[ta * nt + ta] = theta[7];
+  psig[ta] = theta[0];
+  pA[ta] = theta[1];
+  pb[ta] = theta[2];
+  psig[tb] = theta[3];
+  pA[tb] = theta[4];
+  pb[tb] = theta[5];
+  std::vector<PairPar> pairpar(MT * MT, PairPar{0, 0, 1, 0, 0});
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      PairPar pp;
+      pp.qq = u.ke * q[a] * q[b];
+      pp.e4 = 4.0 * eps[a * nt + b];
+      pp.s2 = p.sig[a * nt + b] * p.sig[a * nt + b];
+      pp.vrc = pp.dvrc = 0.0;
+      if (pp.e4 != 0.0) lj_at(pp.e4, pp.s2, rc, &pp.vrc, &pp.dvrc);
+      pairpar[a * MT + b] = pp;
+    }
+  std::vector<PseudoPar> pspar(MT, PseudoPar{0, 1, 0, 1, 0, 0});
+  std::vector<double> pc(8 * MT, 0.0);
+  for (int t = 0; t < nt; ++t) {
+    PseudoPar pp;
+    pp.kq = u.ke * q[t];
+    pp.sig = psig[t];
+    pp.A = pA[t] * u.ev_kcal;
+    pp.b = pb[t];
+    pp.vrc = pp.dvrc = 0.0;
+    if (pp.sig > 0.0 && pp.b > 0.0) {
+      pseudo_at(pp, rc, &pp.vrc, &pp.dvrc);
+      pseudo_param_derivs_host(u.ke, q[t], pp.sig, pp.A, pp.b, rc, &pc[8 * t], &pc[8 * t + 4]);
+    }
+    pspar[t] = pp;
+  }
+  cudaStream_t s = h->stream;
+  unsigned char* w = h->ws;
+  Dev dd = h->d;
+  dd.pairpar = (const PairPar*)(w + p.o_pairpar_alt);
+  dd.pspar = (const PseudoPar*)(w + p.o_pspar_alt);
+  dd.precision = MIXTS_FP64;
+  dd.full_list = 0;
+  unsigned long long* gacc = (unsigned long long*)(w + p.o_gacc);
+  cudaMemcpyAsync(w + p.o_pairpar_alt, pairpar.data(), sizeof(PairPar) * MT * MT, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(w + p.o_pspar_alt, pspar.data(), sizeof(PseudoPar) * MT, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(w + p.o_pc, pc.data(), sizeof(double) * 8 * MT, cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(gacc, 0, sizeof(unsigned long long) * (2 * MT * MT + 8), s);
+  cudaMemsetAsync(dd.F_fix, 0, sizeof(unsigned long long) * 3 * (size_t)dd.n_beads, s);
+  cudaMemsetAsync(dd.E_fix, 0, sizeof(unsigned long long) * E_NSLOTS, s);
+  // forward terms recomputed with theta (forces give dV/dq), then the adjoint sums
+  phase(h, 4, [&] { return launch_prop(dd, s, PM_MIRROR); });
+  phase(h, 0, [&] { return launch_nlist(dd, s, h->atom_is_pseudo); });
+  phase(h, 1, [&] { return launch_pair(dd, s); });
+  phase(h, 2, [&] { return launch_bonded(dd, s, h->ainfo_atom); });
+  phase(h, 3, [&] { return launch_pseudo(dd, s); });
+  phase(h, 6, [&] { return launch_grad(dd, s, ta, tb, u.ke, (const double*)(w + p.o_pc), gacc, grad_out, dVdq_dev); });
+  phase(h, 6, [&] { return launch_forces_out(dd, s); });
+  h->nm_valid = false;
+  h->f_valid = false;
+  mixts_status st = device_error(h);
+  if (st != MIXTS_OK) return st;
+  if (V_host) cudaMemcpy(V_host, h->d.est, sizeof(double), cudaMemcpyDeviceToHost);
+  if (dVdtheta_host) {
+    std::vector<long long> g(2 * MT * MT + 8);
+    st = cuda_check(h, cudaMemcpy(g.data(), gacc, sizeof(long long) * g.size(), cudaMemcpyDeviceToHost), "grad");
+    if (st != MIXTS_OK) return st;
+    auto SG = [&](int a, int b) { return (double)g[2 * (a * MT + b)] * EINV; };
+    auto SL = [&](int a, int b) { return (double)g[2 * (a * MT + b) + 1] * EINV; };
+    const long long* gp = g.data() + 2 * MT * MT;
+    double out[8];
+    out[0] = (double)gp[0] * EINV;
+    out[1] = (double)gp[1] * EINV * u.ev_kcal;
+    out[2] = (double)gp[2] * EINV;
+    out[3] = (double)gp[4] * EINV;
+    out[4] = (double)gp[5] * EINV * u.ev_kcal;
+    out[5] = (double)gp[6] * EINV;
+    // V_coul = sum over type pairs of k_e q_t q_u G_tu: linear in q_a
+    double dq = (double)gp[3] * EINV;
+    for (int x = 0; x < nt; ++x) {
+      if (x == ta)
+        dq += u.ke * 2.0 * q[ta] * SG(ta, ta);
+      else
+        dq += u.ke * q[x] * (SG(ta, x) + SG(x, ta));
+    }
+    out[6] = dq;
+    // V_LJ = sum over type pairs of eps_tu U_tu, U at unit epsilon
+    double de = SL(ta, ta);
+    if (e0 > 0.0)
+      for (int x = 0; x < nt; ++x)
+        if (x != ta) de += eps[ta * nt + x] / (2.0 * theta[7]) * (SL(ta, x) + SL(x, ta));
+    out[7] = de;
+    for (int k = 0; k < 8; ++k) dVdtheta_host[k] = grad_out * out[k];
+  }
+  return MIXTS_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free force evaluation.

@@ -89,6 +89,8 @@ def lib():
         L.mixts_get_timing.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                        C.POINTER(C.c_longlong)]
         L.mixts_forces_noalloc.argtypes = [S, Pp, C.c_void_p, C.POINTER(C.c_double)]
+        L.mixts_potential_grad.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_double,
+                                           C.POINTER(C.c_double), C.c_void_p, C.POINTER(C.c_double)]
         L.mixts_destroy.argtypes = [C.c_void_p]
         L.mixts_last_error.argtypes = [C.c_void_p]
         L.mixts_last_error.restype = C.c_char_p
@@ -100,7 +102,9 @@ def lib():
 EXPORTED = ["mixts_workspace_size", "mixts_init", "mixts_forces", "mixts_step", "mixts_estimators",
             "mixts_nlist", "mixts_state_size", "mixts_get_state", "mixts_set_state", "mixts_gaussians",
             "mixts_destroy", "mixts_last_error", "mixts_version", "mixts_reload", "mixts_set_timing",
-            "mixts_get_timing", "mixts_forces_noalloc"]
+            "mixts_get_timing", "mixts_forces_noalloc", "mixts_potential_grad"]
+# force-field parameters of the differentiation variant, in mixts_potential_grad's order
+THETA_NAMES = ["sigma_a", "A_a_eV", "b_a", "sigma_b", "A_b_eV", "b_b", "q_a", "eps_aa"]
 PHASES = ["nlist", "pair", "bonded", "pseudo", "prop", "final", "other"]
 
 
@@ -226,6 +230,19 @@ class MixTS:
                                           C.c_void_p(out.data_ptr())))
         return out
 
+    def potential_grad(self, type_a, type_b, theta, grad_out=1.0, want_dvdq=True):
+        """V_mix(q, theta), grad_out * dV/dq (device tensor or None), grad_out * dV/dtheta (8 floats).
+
+        theta follows THETA_NAMES; it is applied to this evaluation only.
+        """
+        th = (C.c_double * 8)(*[float(x) for x in theta])
+        v = C.c_double(0.0)
+        g = (C.c_double * 8)()
+        dq = self.torch.empty_like(self.q) if want_dvdq else None
+        self._check(lib().mixts_potential_grad(self.h, int(type_a), int(type_b), th, float(grad_out), C.byref(v),
+                                               C.c_void_p(dq.data_ptr()) if want_dvdq else None, g))
+        return v.value, dq, np.array(list(g))
+
     def reload(self):
         """Declare that q and/or p were rewritten in place (host-resident state)."""
         self._check(lib().mixts_reload(self.h))
@@ -254,3 +271,48 @@ class MixTS:
             self.close()
         except Exception:
             pass
+
+
+def _potential_fn():
+    import torch
+
+    class MixTSPotential(torch.autograd.Function):
+        """V_mix as a differentiable function of (theta, q) for one MixTS engine.
+
+        ``theta`` is a float64 CPU tensor of 8 parameters (THETA_NAMES order),
+        ``q`` a float64 device tensor [n_beads, 3]. The forward pass runs the
+        force kernels and the adjoint sums in one call; the backward pass only
+        scales the stored gradients by the incoming one.
+        """
+
+        @staticmethod
+        def forward(ctx, theta, q, engine, type_a, type_b):
+            if q.data_ptr() != engine.q.data_ptr():
+                engine.q.copy_(q)
+            v, dq, g = engine.potential_grad(type_a, type_b, theta.detach().cpu().tolist(), 1.0,
+                                             want_dvdq=ctx.needs_input_grad[1])
+            ctx.save_for_backward(torch.from_numpy(g), dq if dq is not None else torch.empty(0))
+            return torch.tensor(v, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gv):
+            g, dq = ctx.saved_tensors
+            gth = gq = None
+            if ctx.needs_input_grad[0]:
+                gth = (gv.cpu() * g).to(torch.float64)
+            if ctx.needs_input_grad[1]:
+                gq = dq * gv.to(dq.device)
+            return gth, gq, None, None, None
+
+    return MixTSPotential
+
+
+_MixTSPotential = None
+
+
+def mixts_potential(theta, q, engine, type_a, type_b):
+    """Differentiable V_mix(theta, q) evaluated by the engine's kernels."""
+    global _MixTSPotential
+    if _MixTSPotential is None:
+        _MixTSPotential = _potential_fn()
+    return _MixTSPotential.apply(theta, q, engine, type_a, type_b)
