@@ -47,6 +47,12 @@ FLOPS32_LJ_EXTRA = 22
 ION_ELECTRON = dict(workload="256 waters H8/O1 + ion(+3) + electron P=1024, 18.6 A box, dt 0.1 fs",
                     n_waters=256, box_A=18.6, P_H=8, P_O=1, P_e=1024, dt_fs=0.1)
 L2_FLUSH_BYTES = 256 << 20
+BATCH = dict(workload="64 independent water boxes at 0.997 g/cm3, waters drawn from {32..512}, H beads from "
+                      "{4..64}, O = H/4 (min 1), seeds 0-63, FP32 forces + FP64 integration, dt 0.25 fs",
+             n_systems=64, draw_seed=1000)
+GRAD = dict(workload="512 waters + ion(+3) + electron P=1024, 24.83 A box, H16/O2: V_mix, dV/dq, dV/dtheta "
+                     "(theta = sigma, A, b of O and H, q_O, eps_OO)",
+            n_waters=512, box_A=24.83, P_H=16, P_O=2, P_e=1024)
 
 
 def ns_per_day(ms_per_step, dt=DT):
@@ -112,13 +118,16 @@ CHUNK = 10
 
 def timed_run(m, torch, stream, steps, warmup, flush, clocks_idx=None, chunk=CHUNK):
     """Device time of exactly `steps` steps, run as chunks of `chunk` steps
-    (one mixts_step call each, the production loop); L2 is flushed before
-    every chunk, outside the timed events."""
+    (one mixts_step call each, the production loop: one captured-graph
+    launch per chunk); L2 is flushed before every chunk, outside the timed
+    events. A second pass of the same chunks with per-phase event timing on
+    (plain launches) gives the per-kernel durations."""
     for _ in range(warmup):
         flush.zero_()
         m.step(1)
+    flush.zero_()
+    m.step(chunk)  # captures the step graph outside the timed region
     stream.synchronize()
-    m.set_timing(True)
     k0 = m.timing()[2]
     sizes = [min(chunk, steps - i) for i in range(0, steps, chunk)]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in sizes]
@@ -136,7 +145,13 @@ def timed_run(m, torch, stream, steps, warmup, flush, clocks_idx=None, chunk=CHU
     if clk:
         clk.__exit__()
     ms = [a.elapsed_time(b) for a, b in ev]
-    ph_ms, ph_calls, k1 = m.timing()
+    k1 = m.timing()[2]
+    m.set_timing(True)
+    with torch.cuda.stream(stream):
+        for n in sizes:
+            flush.zero_()
+            m.step(n)
+    ph_ms, ph_calls, _ = m.timing()
     m.set_timing(False)
     return sum(ms) / steps, ph_ms, ph_calls, k1 - k0, (clk.summary() if clk else None)
 
@@ -171,6 +186,100 @@ def variant(torch, stream, flush, dev, sysm, dt, precision, steps, seed):
         out["roofline_pair"] = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": ach / FP32_PEAK_TFLOPS, "note": "algorithmic flops count each term once"}
     return out
+
+
+def batch_variant(torch, stream, flush, dev, steps):
+    """The batched workload: tune the graph shapes, then time `steps` steps of
+    all systems as graph launches of CHUNK steps (L2 flushed before each)."""
+    import synth
+    from paper_2411_11988_gb300 import MixTSBatch
+    draws = synth.systems.batched_draws(BATCH["n_systems"], BATCH["draw_seed"])
+    systems = [synth.water_box(w, synth.density_box_length(w), ph, po, seed=i)
+               for i, (w, ph, po) in enumerate(draws)]
+    b = MixTSBatch(systems, T=300.0, dt=DT, tau=100.0, precision=1, seeds=range(len(systems)), device=str(dev),
+                   stream=stream)
+    b.step(3)
+    t0 = time.perf_counter()
+    tune = b.tune(steps_per_launch=CHUNK)
+    tune_s = time.perf_counter() - t0
+    b.step(CHUNK)
+    stream.synchronize()
+    k0 = b.timing()[2]
+    sizes = [min(CHUNK, steps - i) for i in range(0, steps, CHUNK)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in sizes]
+    with torch.cuda.stream(stream):
+        for (a, c), n in zip(ev, sizes):
+            flush.zero_()
+            a.record(stream)
+            b.step(n)
+            c.record(stream)
+    stream.synchronize()
+    ms = sum(a.elapsed_time(c) for a, c in ev) / steps
+    k1 = b.timing()[2]
+    est = b.estimators()
+    evals = sum(e["n_evals"] for e in est)
+    # serialised per-phase device times of the same step, members one by one
+    b.set_timing(True)
+    b.step(2)
+    ph, calls, _ = b.timing()
+    b.set_timing(False)
+    b.close()
+    pair_ms = ph["pair"] / 2.0
+    flops = sum((e["n_evals"] - e["n_lj_evals"]) * FLOPS32_PAIR + e["n_lj_evals"] * (FLOPS32_PAIR + FLOPS32_LJ_EXTRA)
+                for e in est)
+    return {"workload": BATCH["workload"], "draws": [list(d) for d in draws],
+            "total_beads": int(sum(x.n_beads for x in systems)),
+            "ns_per_day_aggregate": len(systems) * ns_per_day(ms), "ms_per_step": ms, "steps": steps,
+            "bead_pair_evals_per_step": evals, "bead_pair_evals_per_s": evals * 1000.0 / ms,
+            "gpu_launches": k1 - k0, "tuning": tune, "tuning_s": tune_s,
+            "serialised_phase_ms_per_step": {k: v / 2.0 for k, v in ph.items() if calls[k]},
+            "roofline_pair_serialised": {"bound": "alu", "achieved": flops / (pair_ms * 1e-3) / 1e12,
+                                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                         "frac": flops / (pair_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                                         "note": "sum of the members' k_pair32 launches timed one by one"}}
+
+
+def grad_variant(torch, stream, dev, snapshots):
+    """Forward + backward of the differentiable potential on snapshots of a
+    short run; each gradient is checked against central differences of the
+    GPU potential (h = 1e-5 relative)."""
+    import numpy as np
+    import synth
+    from paper_2411_11988_gb300 import MixTS, mixts_potential
+    g = GRAD
+    s = synth.water_box(g["n_waters"], g["box_A"], g["P_H"], g["P_O"], seed=0, ion=dict(synth.systems.ION3),
+                        electron_P=g["P_e"])
+    m = MixTS(s, T=300.0, dt=0.1, tau=100.0, seed=0, device=str(dev), stream=stream)
+    th0 = np.array([s.pp_sigma[0], s.pp_A_eV[0], s.pp_b[0], s.pp_sigma[1], s.pp_A_eV[1], s.pp_b[1],
+                    s.charge_type[0], s.lj_eps[0, 0]], dtype=np.float64)  # the system's own parameters
+    times, errs = [], []
+    for k in range(snapshots):
+        m.step(5)
+        with torch.cuda.stream(stream):
+            q = m.q.clone().requires_grad_(True)
+            th = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            V = mixts_potential(th, q, m, 0, 1)
+            V.backward()
+            stream.synchronize()
+            times.append((time.perf_counter() - t0) * 1000.0)
+        gth = th.grad.numpy()
+        worst = 0.0
+        for j in range(8):
+            h = 1e-5 * abs(th0[j])
+            tp, tm = th0.copy(), th0.copy()
+            tp[j] += h
+            tm[j] -= h
+            fd = (m.potential_grad(0, 1, tp, want_dvdq=False)[0] - m.potential_grad(0, 1, tm, want_dvdq=False)[0]) / (2 * h)
+            worst = max(worst, abs(gth[j] - fd) / max(abs(fd), 1e-6 * abs(V.item())))
+        errs.append(worst)
+        m.reload()
+    m.close()
+    return {"workload": g["workload"], "snapshots": snapshots,
+            "forward_backward_ms_median": float(np.median(times)), "forward_backward_ms_max": float(np.max(times)),
+            "max_rel_err_vs_central_fd": float(np.max(errs)),
+            "note": "host wall time per snapshot (one synchronising call); FD step 1e-5 relative"}
 
 
 def e2e_run(m, torch, stream, steps):
@@ -258,7 +367,7 @@ def main():
         ms, cb = cpu_baseline(k, warmup=min(args.warmup, 3))
         line = {"metric": METRIC, "value": cb["value"], "unit": "ns/day", "n_gpus": args.gpus,
                 "steps": k, "warmup": min(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32 forces, f64 integration", "data": "synthetic", "impl": "reference",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
                 "config": dict(WORKLOAD, l2="n/a (host)"), "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -323,6 +432,8 @@ def main():
                                   ion=dict(synth.systems.ION3), electron_P=ie["P_e"])
             variants[key] = variant(torch, stream, flush, dev, sie, ie["dt_fs"], prec, vs, rank)
             variants[key]["workload"] = ie["workload"]
+        variants["batched_64_fp32"] = batch_variant(torch, stream, flush, dev, vs)
+        variants["grad_ion_electron512"] = grad_variant(torch, stream, dev, 10)
 
     cb = None
     if rank == 0 and not args.no_cpu:

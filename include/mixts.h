@@ -124,13 +124,33 @@ typedef struct {
   int64_t step;                    /* completed steps */
 } mixts_estimates;
 
+/* Launch shapes of a batched handle (n_sys > 1), chosen by mixts_batch_tune. */
+typedef struct {
+  double grid_scale;    /* persistent force-kernel CTAs of all members together, in SM-filling grids,
+                           shared out by each member's share of the force work */
+  int streams;          /* parallel branches of the captured step graph */
+  int nl_cpl;           /* neighbour-list candidates per lane of one list warp */
+  int steps_per_launch; /* steps captured in one graph launch */
+  double ms_per_step;   /* measured for this shape (whole batch, one step) */
+  int candidates;       /* shapes the tuner timed */
+} mixts_batch_tuning;
+
 /* Bytes of device workspace mixts_init needs for these systems. */
 MIXTS_API size_t mixts_workspace_size(const mixts_system* sys, int n_sys, const mixts_params* prm);
 
 /* Validate, build tables, carve the workspace (256-byte aligned, owned by
  * the caller, must outlive the handle). stream is a cudaStream_t (NULL:
  * legacy default stream). The current CUDA device must hold q, p, f and the
- * workspace. n_sys must be 1 in this version. */
+ * workspace. n_sys > 1 makes a batched handle over n_sys independent
+ * systems (each with its own q, p, f, seed, box, types and bead counts; one
+ * mixts_params for all): mixts_forces, mixts_step, mixts_estimators,
+ * mixts_get_state/set_state, mixts_reload and the timing calls then act on
+ * every member (arrays of n_sys results, state blobs back to back); the
+ * per-system queries (mixts_nlist, mixts_gaussians, mixts_potential_grad)
+ * take a member handle from mixts_batch_member. A batched mixts_step of at
+ * least steps_per_launch steps runs as CUDA graph launches, each advancing
+ * every member by steps_per_launch steps; trajectories are bit-identical to
+ * stepping each system alone. */
 MIXTS_API mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* prm, void* workspace,
                         size_t ws_bytes, void* stream, mixts_handle* out);
 
@@ -141,8 +161,17 @@ MIXTS_API mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixt
 MIXTS_API mixts_status mixts_forces(mixts_handle h, double* energy_host);
 
 /* Advance n_steps OBABO steps (asynchronous). On return (in stream order)
- * sys.q, sys.p and sys.f hold the state after the last step. */
+ * sys.q, sys.p and sys.f hold the state after the last step. With timing off
+ * and n_steps >= the handle's steps per graph launch (default 10, see
+ * mixts_set_graph), whole multiples of it run as replays of one captured
+ * CUDA graph (captured on first use on a library-owned stream, launched on
+ * the handle's stream) and the remainder as plain launches; the results are
+ * bit-identical either way. */
 MIXTS_API mixts_status mixts_step(mixts_handle h, int n_steps);
+
+/* Steps per captured graph launch of mixts_step (0: never capture; a
+ * batched handle needs >= 1). Drops any graph captured so far. */
+MIXTS_API mixts_status mixts_set_graph(mixts_handle h, int steps_per_launch);
 
 /* Synchronise and return the estimates of the last completed step. */
 MIXTS_API mixts_status mixts_estimators(mixts_handle h, mixts_estimates* out_host);
@@ -198,6 +227,34 @@ MIXTS_API mixts_status mixts_gaussians(mixts_handle h, uint32_t step, uint32_t s
 MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int type_a, int type_b, const double* theta,
                                             double grad_out, double* V_host, double* dVdq_dev,
                                             double* dVdtheta_host);
+
+/* Radial distribution function g_ab(r) of site types a, b (Sec. "Output and
+ * Analysis"): ordered pairs of a-atoms and b-atoms (the zero image of a
+ * same-molecule pair excluded), every slice of the pair's fine grid with
+ * weight 1/max(P_a, P_b), bins [k dr, (k+1) dr), n_bins dr <= r_cut.
+ * mixts_rdf_accumulate adds the configuration of the last force evaluation
+ * (after mixts_step or mixts_forces) to hist_dev (device, n_bins uint64,
+ * caller-owned and zeroed by the caller), asynchronously; each unit is
+ * 2^-L of a pair, 2^L the largest site bead count. mixts_rdf_normalise (host
+ * arithmetic only) turns a histogram summed over n_frames configurations into
+ * g_host[k] = hist_k 2^-L / (n_frames N_a rho_b V_shell,k), with
+ * rho_b = (N_b - [a == b]) / L^3. */
+#define MIXTS_RDF_MAX_BINS 4096
+MIXTS_API mixts_status mixts_rdf_accumulate(mixts_handle h, int type_a, int type_b, double dr, int n_bins,
+                                            unsigned long long* hist_dev);
+MIXTS_API mixts_status mixts_rdf_normalise(mixts_handle h, int type_a, int type_b, double dr, int n_bins,
+                                           long long n_frames, const unsigned long long* hist_host,
+                                           double* g_host);
+
+/* Member i of a batched handle (borrowed; valid until the batch is destroyed). */
+MIXTS_API mixts_status mixts_batch_member(mixts_handle h, int i, mixts_handle* member);
+
+/* Autotune the launch shapes of a batched handle: time captured graphs of
+ * candidate shapes (branch count x force-grid scale, then list candidates
+ * per warp) on the live systems, keep the fastest, capture steps_per_launch
+ * steps with it. The trial steps are undone (state saved and restored), so
+ * the trajectory is unchanged. Synchronises. out (may be NULL) gets the shape. */
+MIXTS_API mixts_status mixts_batch_tune(mixts_handle h, int steps_per_launch, mixts_batch_tuning* out);
 
 /* Allocation-free force evaluation. The paper has no counterpart; this
  * serves callers that cannot allocate device memory: plugins whose host

@@ -1104,3 +1104,57 @@ void or_grad_theta(const or_system* s, const double* q, int ta, int tb, double* 
   }
   lay_free(&L);
 }
+
+/* ---------------------------------------------------------------------------
+ * Radial distribution histogram (Sec. "Output and Analysis"): every ordered
+ * pair of atoms (a of type ta, c != a of type tb), every slice of the pair's
+ * fine grid through the pair map of Eq. (mts-hamiltonian) with its weight
+ * 1/max(P_a, P_c), and every lattice image with
+ * r = |q_c - q_a + nL| < nbins dr (the zero image of a same-molecule pair
+ * excluded): hist[floor(r / dr)] += weight.
+ * ------------------------------------------------------------------------- */
+void or_rdf(const or_system* s, const double* q, int ta, int tb, double dr, int nbins, double* hist) {
+  lay_t L;
+  lay_init(s, &L);
+  const double Lb = s->box, rmax = nbins * dr;
+  for (int k = 0; k < nbins; ++k) hist[k] = 0.0;
+  for (int a = 0; a < s->n_atoms; ++a) {
+    if (s->type_of_atom[a] != ta) continue;
+    for (int cc = 0; cc < s->n_atoms; ++cc) {
+      if (cc == a || s->type_of_atom[cc] != tb) continue;
+      int i = a, j = cc; /* i: the finer of the two */
+      if (s->P_type[s->type_of_atom[cc]] > s->P_type[s->type_of_atom[a]]) {
+        i = cc;
+        j = a;
+      }
+      int Ni = s->P_type[s->type_of_atom[i]], Nj = s->P_type[s->type_of_atom[j]];
+      int* bi = (int*)malloc(sizeof(int) * (size_t)Ni);
+      int* bj = (int*)malloc(sizeof(int) * (size_t)Ni);
+      int n = or_pair_map(Ni, Nj, bi, bj);
+      double w = 1.0 / Ni;
+      int same = s->mol_of_atom[a] == s->mol_of_atom[cc];
+      for (int m = 0; m < n; ++m) {
+        long ri = row_of(s, &L, i, bi[m]), rj = row_of(s, &L, j, bj[m]);
+        double d0[3];
+        int n0[3];
+        for (int d = 0; d < 3; ++d) {
+          d0[d] = q[3 * rj + d] - q[3 * ri + d];
+          n0[d] = -(int)nearbyint(d0[d] / Lb);
+        }
+        for (int ix = -2; ix <= 2; ++ix)
+          for (int iy = -2; iy <= 2; ++iy)
+            for (int iz = -2; iz <= 2; ++iz) {
+              if (same && n0[0] + ix == 0 && n0[1] + iy == 0 && n0[2] + iz == 0) continue;
+              double dx = d0[0] + (n0[0] + ix) * Lb, dy = d0[1] + (n0[1] + iy) * Lb, dz = d0[2] + (n0[2] + iz) * Lb;
+              double r = sqrt(dx * dx + dy * dy + dz * dz);
+              if (r >= rmax) continue;
+              int k = (int)floor(r / dr);
+              if (k < nbins) hist[k] += w;
+            }
+      }
+      free(bi);
+      free(bj);
+    }
+  }
+  lay_free(&L);
+}

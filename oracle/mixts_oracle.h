@@ -116,6 +116,10 @@ void or_estimators(const or_system* s, const or_params* prm, const double* q, co
  * and are held fixed when eps_aa0 = 0. Units kcal/mol per unit of theta. */
 void or_grad_theta(const or_system* s, const double* q, int ta, int tb, double* dVdtheta8);
 
+/* Weighted pair-distance histogram of the radial distribution function of
+ * site types ta, tb (ordered pairs; bins of width dr from 0). */
+void or_rdf(const or_system* s, const double* q, int ta, int tb, double dr, int nbins, double* hist);
+
 /* Philox4x32-10 */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* standard normals of the thermostat stream for dofs [dof0, dof0+n) */

@@ -80,6 +80,7 @@ def _declare(L):
     L.or_nm_freqs.argtypes = [C.c_int, C.c_double, _dp]
     L.or_step.argtypes = [S, Pp, _dp, _dp, _dp, C.c_uint64, _dp, _dp]
     L.or_grad_theta.argtypes = [S, _dp, C.c_int, C.c_int, _dp]
+    L.or_rdf.argtypes = [S, _dp, C.c_int, C.c_int, C.c_double, C.c_int, _dp]
     L.or_estimators.argtypes = [S, Pp, _dp, _dp, _dp, _dp, _dp]
     L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
     L.or_gaussians.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_long,
@@ -237,6 +238,24 @@ def grad_theta(sysm, ta, tb, q=None, r_cut=R_CUT, alpha=DSF_ALPHA):
     g = np.zeros(8)
     lib().or_grad_theta(C.byref(b.s), _p(q, C.c_double), int(ta), int(tb), _p(g, C.c_double))
     return g
+
+
+def rdf_hist(sysm, ta, tb, dr=0.02, nbins=400, q=None):
+    """Weighted pair-distance histogram (sum of 1/P* over ordered pairs and slices)."""
+    b = _Bound(sysm, R_CUT, DSF_ALPHA)
+    q = np.ascontiguousarray(sysm.q if q is None else q, dtype=np.float64)
+    h = np.zeros(int(nbins))
+    lib().or_rdf(C.byref(b.s), _p(q, C.c_double), int(ta), int(tb), float(dr), int(nbins), _p(h, C.c_double))
+    return h
+
+
+def rdf_normalise(hist, n_frames, N_a, N_b, same, box, dr):
+    """g(r) per bin: histogram / (frames * N_a * rho_b * shell volume), rho_b =
+    (N_b - [a == b]) / V."""
+    k = np.arange(len(hist))
+    shell = 4.0 / 3.0 * np.pi * ((k + 1) ** 3 - k ** 3) * dr ** 3
+    rho = (N_b - (1 if same else 0)) / box ** 3
+    return hist / (n_frames * N_a * rho * shell)
 
 
 def nm_matrix(P):

@@ -83,7 +83,6 @@ __device__ double reduce_spread_kind(const Dev& d, const int* atom_is_pseudo, in
 }
 
 constexpr int NL_THREADS = 256;
-constexpr int NL_CPL = 4;  // candidates per lane of one list warp
 
 // Once per list build: d_max of sites and of pseudo particles, the two list
 // radii (binary64, in the order the definition states), and cleared row
@@ -117,7 +116,7 @@ __global__ void k_list_prep(Dev d, const int* atom_is_pseudo) {
   }
 }
 
-// One warp per (owner row, chunk of 32 * NL_CPL candidates); entries are
+// One warp per (owner row, chunk of 32 * nl_cpl candidates); entries are
 // appended with a per-row counter, so the row order is arbitrary.
 __global__ void __launch_bounds__(NL_THREADS) k_nlist(Dev d, int nchunk) {
   const int lane = threadIdx.x & 31;
@@ -138,10 +137,11 @@ __global__ void __launch_bounds__(NL_THREADS) k_nlist(Dev d, int nchunk) {
   const int Pi = __float_as_int(ri.w);
   const int moli = d.pos_mol[i];
   int* row = d.nl + (size_t)i * d.nl_cap;
-  const int c0 = chunk * 32 * NL_CPL;
+  const int cpl = d.nl_cpl;
+  const int c0 = chunk * 32 * cpl;
   constexpr int MAXE = 8;  // entries one lane keeps per candidate (images)
 #pragma unroll 1
-  for (int t = 0; t < NL_CPL; ++t) {
+  for (int t = 0; t < cpl; ++t) {
     const int c = c0 + t * 32 + lane;
     int ne = 0;
     int ents[MAXE];
@@ -920,7 +920,7 @@ int launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo) {
   int n = 1;
   k_list_prep<<<1, 1024, 0, s>>>(d, atom_is_pseudo);
   if (d.n_nonp > 0) {
-    const int nchunk = (d.n_nonp + 32 * NL_CPL - 1) / (32 * NL_CPL);
+    const int nchunk = (d.n_nonp + 32 * d.nl_cpl - 1) / (32 * d.nl_cpl);
     const long long warps = (long long)d.n_nonp * nchunk;
     const int wpb = NL_THREADS / 32;
     k_nlist<<<(int)((warps + wpb - 1) / wpb), NL_THREADS, 0, s>>>(d, nchunk);

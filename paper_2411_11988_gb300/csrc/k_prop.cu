@@ -616,8 +616,19 @@ static size_t small_smem(int P) {
   return sizeof(double) * ((size_t)P * P + 5 * (size_t)P * C);
 }
 
+// dynamic shared memory beyond the 48 KB default needs an opt-in per kernel
+static void prop_smem_optin() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_prop_small, cudaFuncAttributeMaxDynamicSharedMemorySize, PROP_SMEM_MAX);
+  cudaFuncSetAttribute(k_big_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, PROP_SMEM_MAX);
+  cudaFuncSetAttribute(k_big_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, PROP_SMEM_MAX);
+  done = true;
+}
+
 int launch_prop(const Dev& d, cudaStream_t s, int mode) {
   int n = 0;
+  prop_smem_optin();
   if (mode & PM_MIRROR) {
     k_mirror_from_q<<<(d.n_atoms + 127) / 128, 128, 0, s>>>(d);
     return 1;

@@ -386,6 +386,11 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.mc_off.assign(MT, 0);
   p.big_slot0.assign(MT, 0);
   p.sb_off.assign(MT, 0);
+  for (int t = 0; t < p.nt; ++t)
+    if (s->P_type[t] > SMALL_P && big_prop_smem(s->P_type[t], p.N[t]) > (size_t)PROP_SMEM_MAX) {
+      fail(p, MIXTS_ERR_ARG, "a type with more than 64 beads holds too many atoms for one transform block");
+      return p;
+    }
   for (int t = 0; t < p.nt; ++t) {
     const int P = s->P_type[t];
     const double m = s->mass_type[t];
@@ -555,6 +560,21 @@ struct mixts_ctx {
   long long steps_done = 0;
   std::string err;
   int device = 0;
+  int full_grid64 = 0, full_grid32 = 0;  // SM-filling persistent grids
+  // batched handle (n_sys > 1): one sub-context per system, advanced by one
+  // captured graph whose branches run the systems concurrently
+  std::vector<mixts_ctx*> kids;
+  std::vector<cudaStream_t> fork;
+  std::vector<cudaEvent_t> fev;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_steps = 0;
+  long long g_kernels = 0;
+  mixts_batch_tuning tune{};
+  // single handle: steps per captured graph launch (0: eager launches)
+  int graph_steps = 10;
+  bool capturing = false;
+  bool list_valid = false;  // neighbour lists and position mirrors match the current q
 };
 
 static void timer_fold(mixts_handle h) {
@@ -624,7 +644,12 @@ extern "C" {
 
 const char* mixts_version(void) { return "mixts-gb300 0.1 (sm_103a)"; }
 
+static size_t batch_workspace_size(const mixts_system* sys, int n_sys, const mixts_params* prm);
+static mixts_status batch_init(const mixts_system* sys, int n_sys, const mixts_params* prm, void* workspace,
+                               size_t ws_bytes, void* stream, mixts_handle* out);
+
 size_t mixts_workspace_size(const mixts_system* sys, int n_sys, const mixts_params* prm) {
+  if (n_sys > 1 && sys) return batch_workspace_size(sys, n_sys, prm);
   if (n_sys != 1 || !sys) return 0;
   Plan p = make_plan(sys, prm);
   if (p.st != MIXTS_OK) return 0;
@@ -635,6 +660,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
                         size_t ws_bytes, void* stream, mixts_handle* out) {
   if (!out) return MIXTS_ERR_ARG;
   *out = nullptr;
+  if (n_sys > 1 && sys && prm) return batch_init(sys, n_sys, prm, workspace, ws_bytes, stream, out);
   if (n_sys != 1 || !sys || !prm) return MIXTS_ERR_ARG;
   if (!sys->q || !sys->p || !sys->f) return MIXTS_ERR_ARG;
   mixts_handle h = new mixts_ctx();
@@ -788,7 +814,10 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.spread = (double*)(w + p.o_spread);
   d.spread_big = (double*)(w + p.o_spread_big);
   pair_grids(p.nt, p.dsf_nint, &d.pair_grid, &d.pair32_grid);
+  h->full_grid64 = d.pair_grid;
+  h->full_grid32 = d.pair32_grid;
   d.pseudo_chunks = 8;
+  d.nl_cpl = 4;
   d.nl = (int*)(w + p.o_nl);
   d.nl_cnt = (int*)(w + p.o_nlcnt);
   d.pl = (int*)(w + p.o_pl);
@@ -807,6 +836,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
 static mixts_status eval_forces(mixts_handle h) {
   const Dev& d = h->d;
   cudaStream_t s = h->stream;
+  h->list_valid = true;
   phase(h, 0, [&] { return launch_nlist(d, s, h->atom_is_pseudo); });
   phase(h, 1, [&] { return launch_pair(d, s); });
   phase(h, 2, [&] { return launch_bonded(d, s, h->ainfo_atom); });
@@ -824,6 +854,13 @@ static void fin(mixts_handle h, int mode) {
 
 mixts_status mixts_forces(mixts_handle h, double* energy_host) {
   if (!h) return MIXTS_ERR_ARG;
+  if (!h->kids.empty()) {
+    for (size_t i = 0; i < h->kids.size(); ++i) {
+      mixts_status st = mixts_forces(h->kids[i], energy_host ? energy_host + i : nullptr);
+      if (st != MIXTS_OK) return set_err(h, st, "system " + std::to_string(i) + ": " + h->kids[i]->err);
+    }
+    return MIXTS_OK;
+  }
   // a fresh evaluation from the caller's q: clear the accumulators first
   cudaMemsetAsync(h->d.F_fix, 0, sizeof(unsigned long long) * 3 * (size_t)h->d.n_beads, h->stream);
   cudaMemsetAsync(h->d.E_fix, 0, sizeof(unsigned long long) * E_NSLOTS, h->stream);
@@ -843,9 +880,9 @@ mixts_status mixts_forces(mixts_handle h, double* energy_host) {
   return st;
 }
 
-mixts_status mixts_step(mixts_handle h, int n_steps) {
-  if (!h || n_steps < 0) return MIXTS_ERR_ARG;
-  if (n_steps == 0) return MIXTS_OK;
+// bring a handle to the steady state of the step loop: modes imported from
+// the Cartesian state, forces at the current positions
+static mixts_status step_prologue(mixts_handle h) {
   cudaStream_t s = h->stream;
   if (!h->nm_valid) {
     prop(h, PM_IMPORT);
@@ -859,6 +896,24 @@ mixts_status mixts_step(mixts_handle h, int n_steps) {
     mixts_status st = eval_forces(h);
     if (st != MIXTS_OK) return st;
     h->f_valid = true;
+  }
+  return MIXTS_OK;
+}
+
+static mixts_status batch_step(mixts_handle h, int n_steps);
+static mixts_status single_graph_steps(mixts_handle h, int n_steps, int* done);
+
+mixts_status mixts_step(mixts_handle h, int n_steps) {
+  if (!h || n_steps < 0) return MIXTS_ERR_ARG;
+  if (n_steps == 0) return MIXTS_OK;
+  if (!h->kids.empty()) return batch_step(h, n_steps);
+  mixts_status st = step_prologue(h);
+  if (st != MIXTS_OK) return st;
+  if (!h->capturing && !h->tm.on && h->graph_steps > 0 && n_steps >= h->graph_steps) {
+    int done = 0;
+    if ((st = single_graph_steps(h, n_steps, &done)) != MIXTS_OK) return st;
+    n_steps -= done;
+    if (n_steps == 0) return MIXTS_OK;
   }
   prop(h, PM_START);
   fin(h, PM_START);
@@ -876,6 +931,13 @@ mixts_status mixts_step(mixts_handle h, int n_steps) {
 
 mixts_status mixts_estimators(mixts_handle h, mixts_estimates* out) {
   if (!h || !out) return MIXTS_ERR_ARG;
+  if (!h->kids.empty()) {
+    for (size_t i = 0; i < h->kids.size(); ++i) {
+      mixts_status st = mixts_estimators(h->kids[i], out + i);
+      if (st != MIXTS_OK) return set_err(h, st, "system " + std::to_string(i) + ": " + h->kids[i]->err);
+    }
+    return MIXTS_OK;
+  }
   mixts_status st = device_error(h);
   if (st != MIXTS_OK) return st;
   double e[EST_N];
@@ -910,6 +972,7 @@ mixts_status mixts_estimators(mixts_handle h, mixts_estimates* out) {
 
 mixts_status mixts_nlist(mixts_handle h, int kind, int* out3, long cap, long* n_out, double* thresh) {
   if (!h || !n_out || (kind != 0 && kind != 1)) return MIXTS_ERR_ARG;
+  if (!h->kids.empty()) return set_err(h, MIXTS_ERR_ARG, "batched handle: query a member (mixts_batch_member)");
   mixts_status st = device_error(h);
   if (st != MIXTS_OK) return st;
   const Plan& p = h->plan;
@@ -958,11 +1021,26 @@ mixts_status mixts_nlist(mixts_handle h, int kind, int* out3, long cap, long* n_
 
 size_t mixts_state_size(mixts_handle h) {
   if (!h) return 0;
+  if (!h->kids.empty()) {
+    size_t n = 0;
+    for (auto k : h->kids) n += mixts_state_size(k);
+    return n;
+  }
   return 64 + sizeof(double) * 6 * (size_t)h->d.n_beads;
 }
 
 mixts_status mixts_get_state(mixts_handle h, void* blob, size_t bytes) {
   if (!h || !blob || bytes < mixts_state_size(h)) return MIXTS_ERR_ARG;
+  if (!h->kids.empty()) {  // members' blobs back to back
+    unsigned char* b = (unsigned char*)blob;
+    for (auto k : h->kids) {
+      const size_t nk = mixts_state_size(k);
+      mixts_status st = mixts_get_state(k, b, nk);
+      if (st != MIXTS_OK) return set_err(h, st, k->err);
+      b += nk;
+    }
+    return MIXTS_OK;
+  }
   mixts_status st = device_error(h);
   if (st != MIXTS_OK) return st;
   if (!h->nm_valid) return set_err(h, MIXTS_ERR_STATE, "no mode-space state yet: call mixts_step first");
@@ -981,6 +1059,16 @@ mixts_status mixts_get_state(mixts_handle h, void* blob, size_t bytes) {
 
 mixts_status mixts_set_state(mixts_handle h, const void* blob, size_t bytes) {
   if (!h || !blob || bytes < mixts_state_size(h)) return MIXTS_ERR_ARG;
+  if (!h->kids.empty()) {
+    const unsigned char* b = (const unsigned char*)blob;
+    for (auto k : h->kids) {
+      const size_t nk = mixts_state_size(k);
+      mixts_status st = mixts_set_state(k, b, nk);
+      if (st != MIXTS_OK) return set_err(h, st, k->err);
+      b += nk;
+    }
+    return MIXTS_OK;
+  }
   const unsigned char* b = (const unsigned char*)blob;
   uint64_t magic, nb;
   memcpy(&magic, b, 8);
@@ -997,6 +1085,7 @@ mixts_status mixts_set_state(mixts_handle h, const void* blob, size_t bytes) {
   if (st != MIXTS_OK) return st;
   h->nm_valid = true;
   h->f_valid = false;
+  h->list_valid = false;
   // Cartesian q, p for the caller
   prop(h, PM_QCART | PM_PCART);
   return cuda_check(h, cudaGetLastError(), "set state export");
@@ -1004,6 +1093,8 @@ mixts_status mixts_set_state(mixts_handle h, const void* blob, size_t bytes) {
 
 mixts_status mixts_reload(mixts_handle h) {
   if (!h) return MIXTS_ERR_ARG;
+  for (auto k : h->kids) mixts_reload(k);
+  h->list_valid = false;
   h->nm_valid = false;
   h->f_valid = false;
   return MIXTS_OK;
@@ -1011,6 +1102,7 @@ mixts_status mixts_reload(mixts_handle h) {
 
 mixts_status mixts_set_timing(mixts_handle h, int on) {
   if (!h) return MIXTS_ERR_ARG;
+  for (auto k : h->kids) mixts_set_timing(k, on);
   timer_fold(h);
   if (on) {
     for (int i = 0; i < MIXTS_N_PHASES; ++i) {
@@ -1030,17 +1122,45 @@ mixts_status mixts_get_timing(mixts_handle h, double* ms, long long* calls, long
     if (calls) calls[i] = h->tm.calls[i];
   }
   if (kernels) *kernels = h->kernels;
+  for (auto k : h->kids) {  // members' sums (eager launches) plus the graph launches
+    double km[MIXTS_N_PHASES];
+    long long kc[MIXTS_N_PHASES], kk = 0;
+    mixts_status st = mixts_get_timing(k, km, kc, &kk);
+    if (st != MIXTS_OK) return st;
+    for (int i = 0; i < MIXTS_N_PHASES; ++i) {
+      if (ms) ms[i] += km[i];
+      if (calls) calls[i] += kc[i];
+    }
+    if (kernels) *kernels += kk;
+  }
   return cuda_check(h, cudaStreamSynchronize(h->stream), "timing");
 }
 
 mixts_status mixts_gaussians(mixts_handle h, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out) {
   if (!h || !out || n < 0) return MIXTS_ERR_ARG;
+  if (!h->kids.empty()) return set_err(h, MIXTS_ERR_ARG, "batched handle: query a member (mixts_batch_member)");
   h->kernels += launch_gauss(h->d, h->stream, step, stage, dof0, n, out);
   return cuda_check(h, cudaGetLastError(), "gaussians");
 }
 
 void mixts_destroy(mixts_handle h) {
   if (!h) return;
+  if (h->kids.empty() && (h->gexec || h->cap)) {
+    cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    h->gexec = nullptr;
+    h->cap = nullptr;
+  }
+  if (!h->kids.empty()) {
+    cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (auto e : h->fev) cudaEventDestroy(e);
+    for (auto f : h->fork) cudaStreamDestroy(f);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    for (auto k : h->kids) mixts_destroy(k);
+    h->kids.clear();
+  }
   if (!h->tm.pool.empty()) {
     cudaStreamSynchronize(h->stream);
     for (auto e : h->tm.pool) cudaEventDestroy(e);
@@ -1051,6 +1171,385 @@ void mixts_destroy(mixts_handle h) {
 const char* mixts_last_error(mixts_handle h) { return h ? h->err.c_str() : "NULL handle"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched variant: many independent systems of uneven size advanced together.
+// Each system keeps its own sub-context (tables, lists, state) in its slice
+// of the workspace; a step of the whole batch is one CUDA graph launch whose
+// parallel branches carry the systems' kernel chains (longest first, greedy
+// to the least-loaded branch). The shapes of that graph -- branch count,
+// persistent force-kernel CTAs per system, list candidates per warp -- come
+// from an autotuner that times captured candidates on the live batch.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t BATCH_ALIGN = 256;
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// estimated force work of a member: pair items times list capacity
+double member_work(const mixts_ctx* k) {
+  const Dev& d = k->d;
+  const double items = d.precision == MIXTS_FP32_FORCES ? (double)d.n_items32 : (double)d.n_pitems;
+  return items * (double)d.nl_cap + (double)d.n_ppitems * d.pl_cap + 1.0;
+}
+
+// apply a tuning to every member: force grids shared out by work
+void apply_tuning(mixts_handle h, const mixts_batch_tuning& t) {
+  double W = 0.0;
+  for (auto k : h->kids) W += member_work(k);
+  for (auto k : h->kids) {
+    const double share = member_work(k) / W;
+    const int g64 = (int)ceil(t.grid_scale * k->full_grid64 * share);
+    const int g32 = (int)ceil(t.grid_scale * k->full_grid32 * share);
+    k->d.pair_grid = std::max(1, std::min(k->full_grid64, g64));
+    k->d.pair32_grid = std::max(1, std::min(k->full_grid32, g32));
+    k->d.nl_cpl = t.nl_cpl;
+  }
+  h->tune = t;
+}
+
+void drop_graph(mixts_handle h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  h->g_steps = 0;
+  h->g_kernels = 0;
+}
+}  // namespace
+
+static size_t batch_workspace_size(const mixts_system* sys, int n_sys, const mixts_params* prm) {
+  size_t total = 0;
+  for (int i = 0; i < n_sys; ++i) {
+    const size_t n = mixts_workspace_size(sys + i, 1, prm);
+    if (n == 0) return 0;
+    total += round_up(n, BATCH_ALIGN);
+  }
+  return total + BATCH_ALIGN;
+}
+
+static mixts_status batch_init(const mixts_system* sys, int n_sys, const mixts_params* prm, void* workspace,
+                               size_t ws_bytes, void* stream, mixts_handle* out) {
+  *out = nullptr;
+  if (!workspace || ((uintptr_t)workspace & 255)) return MIXTS_ERR_WORKSPACE;
+  mixts_handle h = new mixts_ctx();
+  cudaGetDevice(&h->device);
+  h->stream = (cudaStream_t)stream;
+  h->ws = (unsigned char*)workspace;
+  size_t off = 0;
+  for (int i = 0; i < n_sys; ++i) {
+    const size_t n = mixts_workspace_size(sys + i, 1, prm);
+    if (n == 0 || off + n > ws_bytes) {
+      mixts_destroy(h);
+      return n == 0 ? MIXTS_ERR_ARG : MIXTS_ERR_WORKSPACE;
+    }
+    mixts_handle k = nullptr;
+    const mixts_status st = mixts_init(sys + i, 1, prm, h->ws + off, ws_bytes - off, stream, &k);
+    if (st != MIXTS_OK) {
+      fprintf(stderr, "mixts_init: batch member %d rejected\n", i);
+      mixts_destroy(h);
+      return st;
+    }
+    k->graph_steps = 0;  // members are captured into the batch graph, never on their own
+    h->kids.push_back(k);
+    off += round_up(n, BATCH_ALIGN);
+  }
+  mixts_batch_tuning t{};
+  t.grid_scale = 2.0;
+  t.streams = std::min(n_sys, 16);
+  t.nl_cpl = 4;
+  t.steps_per_launch = 10;
+  apply_tuning(h, t);
+  *out = h;
+  return MIXTS_OK;
+}
+
+// capture steps_per_launch steps of every member into one executable graph
+static mixts_status batch_capture(mixts_handle h) {
+  drop_graph(h);
+  const mixts_batch_tuning& t = h->tune;
+  const int S = std::max(1, std::min(t.streams, (int)h->kids.size()));
+  const int K = std::max(1, t.steps_per_launch);
+  if (!h->cap) {
+    mixts_status st = cuda_check(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "capture stream");
+    if (st != MIXTS_OK) return st;
+  }
+  while ((int)h->fork.size() < S) {
+    cudaStream_t f;
+    mixts_status st = cuda_check(h, cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking), "branch stream");
+    if (st != MIXTS_OK) return st;
+    h->fork.push_back(f);
+  }
+  while ((int)h->fev.size() < S + 1) {
+    cudaEvent_t e;
+    mixts_status st = cuda_check(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "branch event");
+    if (st != MIXTS_OK) return st;
+    h->fev.push_back(e);
+  }
+  // longest member first onto the least-loaded branch
+  std::vector<int> order(h->kids.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(),
+            [&](int a, int b) { return member_work(h->kids[a]) > member_work(h->kids[b]); });
+  std::vector<double> load(S, 0.0);
+  std::vector<long long> k0(h->kids.size()), s0(h->kids.size());
+  for (size_t i = 0; i < h->kids.size(); ++i) {
+    k0[i] = h->kids[i]->kernels;
+    s0[i] = h->kids[i]->steps_done;
+  }
+  mixts_status st = cuda_check(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (st != MIXTS_OK) return st;
+  cudaEventRecord(h->fev[0], h->cap);
+  for (int b = 0; b < S; ++b) cudaStreamWaitEvent(h->fork[b], h->fev[0], 0);
+  mixts_status step_st = MIXTS_OK;
+  for (int i : order) {
+    const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[b] += member_work(h->kids[i]);
+    mixts_handle k = h->kids[i];
+    cudaStream_t keep = k->stream;
+    k->stream = h->fork[b];
+    const mixts_status si = mixts_step(k, K);
+    k->stream = keep;
+    if (si != MIXTS_OK && step_st == MIXTS_OK) step_st = si;
+  }
+  for (int b = 0; b < S; ++b) {
+    cudaEventRecord(h->fev[1 + b], h->fork[b]);
+    cudaStreamWaitEvent(h->cap, h->fev[1 + b], 0);
+  }
+  cudaGraph_t g = nullptr;
+  st = cuda_check(h, cudaStreamEndCapture(h->cap, &g), "end capture");
+  long long nk = 0;
+  for (size_t i = 0; i < h->kids.size(); ++i) {  // capture launched nothing
+    nk += h->kids[i]->kernels - k0[i];
+    h->kids[i]->kernels = k0[i];
+    h->kids[i]->steps_done = s0[i];
+  }
+  if (st == MIXTS_OK && step_st != MIXTS_OK) st = set_err(h, step_st, "capture of a member step failed");
+  if (st == MIXTS_OK) st = cuda_check(h, cudaGraphInstantiate(&h->gexec, g, 0), "graph instantiate");
+  if (g) cudaGraphDestroy(g);
+  if (st != MIXTS_OK) {
+    drop_graph(h);
+    return st;
+  }
+  h->g_steps = K;
+  h->g_kernels = nk;
+  return MIXTS_OK;
+}
+
+static mixts_status batch_step(mixts_handle h, int n_steps) {
+  bool timing = false;
+  for (auto k : h->kids) timing = timing || k->tm.on;
+  mixts_status st;
+  if (timing || n_steps < h->tune.steps_per_launch) {  // eager, member by member
+    for (auto k : h->kids)
+      if ((st = mixts_step(k, n_steps)) != MIXTS_OK) return set_err(h, st, k->err);
+    return MIXTS_OK;
+  }
+  for (auto k : h->kids)
+    if ((st = step_prologue(k)) != MIXTS_OK) return set_err(h, st, k->err);
+  if (!h->gexec && (st = batch_capture(h)) != MIXTS_OK) return st;
+  const int reps = n_steps / h->g_steps, rem = n_steps % h->g_steps;
+  for (int r = 0; r < reps; ++r) {
+    st = cuda_check(h, cudaGraphLaunch(h->gexec, h->stream), "graph launch");
+    if (st != MIXTS_OK) return st;
+    h->kernels += h->g_kernels;
+  }
+  for (auto k : h->kids) k->steps_done += (long long)reps * h->g_steps;
+  if (rem)
+    for (auto k : h->kids)
+      if ((st = mixts_step(k, rem)) != MIXTS_OK) return set_err(h, st, k->err);
+  h->steps_done += n_steps;
+  return MIXTS_OK;
+}
+
+// single handle: capture graph_steps steps once, replay it for the whole
+// multiples of graph_steps in n_steps; the remainder runs eagerly
+static mixts_status single_graph_steps(mixts_handle h, int n_steps, int* done) {
+  *done = 0;
+  mixts_status st;
+  if (!h->gexec) {
+    if (!h->cap && (st = cuda_check(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "capture stream")) !=
+                       MIXTS_OK)
+      return st;
+    const long long k0 = h->kernels, s0 = h->steps_done;
+    cudaStream_t keep = h->stream;
+    if ((st = cuda_check(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture")) !=
+        MIXTS_OK)
+      return st;
+    h->stream = h->cap;
+    h->capturing = true;
+    const mixts_status si = mixts_step(h, h->graph_steps);
+    h->capturing = false;
+    h->stream = keep;
+    cudaGraph_t g = nullptr;
+    st = cuda_check(h, cudaStreamEndCapture(h->cap, &g), "end capture");
+    const long long nk = h->kernels - k0;
+    h->kernels = k0;
+    h->steps_done = s0;
+    if (st == MIXTS_OK && si != MIXTS_OK) st = si;
+    if (st == MIXTS_OK) st = cuda_check(h, cudaGraphInstantiate(&h->gexec, g, 0), "graph instantiate");
+    if (g) cudaGraphDestroy(g);
+    if (st != MIXTS_OK) {
+      drop_graph(h);
+      return st;
+    }
+    h->g_steps = h->graph_steps;
+    h->g_kernels = nk;
+  }
+  const int reps = n_steps / h->g_steps;
+  for (int r = 0; r < reps; ++r) {
+    if ((st = cuda_check(h, cudaGraphLaunch(h->gexec, h->stream), "graph launch")) != MIXTS_OK) return st;
+    h->kernels += h->g_kernels;
+  }
+  *done = reps * h->g_steps;
+  h->steps_done += *done;
+  return MIXTS_OK;
+}
+
+extern "C" MIXTS_API mixts_status mixts_set_graph(mixts_handle h, int steps_per_launch) {
+  if (!h || steps_per_launch < 0) return MIXTS_ERR_ARG;
+  drop_graph(h);
+  if (!h->kids.empty()) {
+    if (steps_per_launch == 0) return set_err(h, MIXTS_ERR_ARG, "a batched handle always steps by graph");
+    h->tune.steps_per_launch = steps_per_launch;
+  } else {
+    h->graph_steps = steps_per_launch;
+  }
+  return MIXTS_OK;
+}
+
+extern "C" MIXTS_API mixts_status mixts_batch_member(mixts_handle h, int i, mixts_handle* out) {
+  if (!h || !out || i < 0 || i >= (int)h->kids.size()) return MIXTS_ERR_ARG;
+  *out = h->kids[i];
+  return MIXTS_OK;
+}
+
+extern "C" MIXTS_API mixts_status mixts_batch_tune(mixts_handle h, int steps_per_launch, mixts_batch_tuning* out) {
+  if (!h || h->kids.empty() || steps_per_launch < 1) return MIXTS_ERR_ARG;
+  mixts_status st;
+  for (auto k : h->kids)
+    if (k->tm.on) return set_err(h, MIXTS_ERR_ARG, "switch timing off before tuning");
+  for (auto k : h->kids)
+    if ((st = step_prologue(k)) != MIXTS_OK) return set_err(h, st, k->err);
+  // the trial steps advance the systems: save and restore the state
+  std::vector<unsigned char> saved(mixts_state_size(h));
+  if ((st = mixts_get_state(h, saved.data(), saved.size())) != MIXTS_OK) return st;
+  std::vector<long long> done(h->kids.size());
+  for (size_t i = 0; i < h->kids.size(); ++i) done[i] = h->kids[i]->steps_done;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int n = (int)h->kids.size();
+  const int trial_steps = std::min(steps_per_launch, 2);
+  auto time_shape = [&](mixts_batch_tuning t, double* ms) -> mixts_status {
+    t.steps_per_launch = trial_steps;
+    apply_tuning(h, t);
+    mixts_status s2 = batch_capture(h);
+    if (s2 != MIXTS_OK) return s2;
+    cudaGraphLaunch(h->gexec, h->stream);  // warm
+    cudaEventRecord(e0, h->stream);
+    const int reps = 3;
+    for (int r = 0; r < reps; ++r) cudaGraphLaunch(h->gexec, h->stream);
+    cudaEventRecord(e1, h->stream);
+    s2 = cuda_check(h, cudaEventSynchronize(e1), "tuning sync");
+    if (s2 != MIXTS_OK) return s2;
+    float f = 0.0f;
+    cudaEventElapsedTime(&f, e0, e1);
+    *ms = f / (reps * trial_steps);
+    return MIXTS_OK;
+  };
+  mixts_batch_tuning best{};
+  double best_ms = 1e30;
+  int cands = 0;
+  const double scales[] = {0.5, 1.0, 2.0, 4.0, 1e9};
+  const int branches[] = {4, 8, 16, 32, 64};
+  for (int S : branches) {
+    if (S > n && S != branches[0]) continue;
+    for (double sc : scales) {
+      mixts_batch_tuning t{};
+      t.grid_scale = sc;
+      t.streams = std::min(S, n);
+      t.nl_cpl = 4;
+      double ms = 0.0;
+      if ((st = time_shape(t, &ms)) != MIXTS_OK) goto done_tuning;
+      ++cands;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+  }
+  for (int cpl : {2, 8}) {
+    mixts_batch_tuning t = best;
+    t.nl_cpl = cpl;
+    double ms = 0.0;
+    if ((st = time_shape(t, &ms)) != MIXTS_OK) goto done_tuning;
+    ++cands;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  best.steps_per_launch = steps_per_launch;
+  best.ms_per_step = best_ms;
+  best.candidates = cands;
+  apply_tuning(h, best);
+  drop_graph(h);
+  st = MIXTS_OK;
+done_tuning:
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MIXTS_OK) return st;
+  if ((st = mixts_set_state(h, saved.data(), saved.size())) != MIXTS_OK) return st;
+  for (size_t i = 0; i < h->kids.size(); ++i) h->kids[i]->steps_done = done[i];
+  for (auto k : h->kids)
+    if ((st = step_prologue(k)) != MIXTS_OK) return set_err(h, st, k->err);
+  if ((st = batch_capture(h)) != MIXTS_OK) return st;
+  if (out) *out = h->tune;
+  return MIXTS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Radial distribution function.
+// ---------------------------------------------------------------------------
+namespace mx {
+int launch_rdf(const Dev& d, cudaStream_t s, int ta, int tb, double dr, int nbins, unsigned long long* hist);
+}
+
+static mixts_status rdf_args(mixts_handle h, int ta, int tb, double dr, int nbins) {
+  if (!h) return MIXTS_ERR_ARG;
+  if (!h->kids.empty()) return set_err(h, MIXTS_ERR_ARG, "batched handle: query a member (mixts_batch_member)");
+  const int nt = h->d.n_types;
+  if (ta < 0 || tb < 0 || ta >= nt || tb >= nt || h->d.pseudo[ta] || h->d.pseudo[tb])
+    return set_err(h, MIXTS_ERR_ARG, "rdf types must be site types");
+  if (!(dr > 0.0) || nbins < 1 || nbins > MIXTS_RDF_MAX_BINS || nbins * dr > h->d.rc)
+    return set_err(h, MIXTS_ERR_ARG, "rdf bins must lie inside r_cut");
+  return MIXTS_OK;
+}
+
+extern "C" MIXTS_API mixts_status mixts_rdf_accumulate(mixts_handle h, int ta, int tb, double dr, int nbins,
+                                                       unsigned long long* hist_dev) {
+  mixts_status st = rdf_args(h, ta, tb, dr, nbins);
+  if (st != MIXTS_OK) return st;
+  if (!hist_dev) return MIXTS_ERR_ARG;
+  if (!h->list_valid) return set_err(h, MIXTS_ERR_STATE, "no neighbour list at the current q: step or force first");
+  phase(h, 6, [&] { return launch_rdf(h->d, h->stream, ta, tb, dr, nbins, hist_dev); });
+  return cuda_check(h, cudaGetLastError(), "rdf launch");
+}
+
+extern "C" MIXTS_API mixts_status mixts_rdf_normalise(mixts_handle h, int ta, int tb, double dr, int nbins,
+                                                      long long n_frames, const unsigned long long* hist_host,
+                                                      double* g_host) {
+  mixts_status st = rdf_args(h, ta, tb, dr, nbins);
+  if (st != MIXTS_OK) return st;
+  if (!hist_host || !g_host || n_frames < 1) return MIXTS_ERR_ARG;
+  const double unit = ldexp(1.0, -h->d.lgPmax_nb);
+  const double V = h->d.box * h->d.box * h->d.box;
+  const double Na = h->d.N[ta], rho = (h->d.N[tb] - (ta == tb ? 1.0 : 0.0)) / V;
+  for (int k = 0; k < nbins; ++k) {
+    const double shell = 4.0 / 3.0 * PI * ((double)(k + 1) * (k + 1) * (k + 1) - (double)k * k * k) * dr * dr * dr;
+    const double ideal = (double)n_frames * Na * rho * shell;
+    g_host[k] = ideal > 0.0 ? (double)hist_host[k] * unit / ideal : 0.0;
+  }
+  return MIXTS_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Parameter gradient (the differentiation variant).
@@ -1081,6 +1580,7 @@ extern "C" MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int ta, i
                                                        double grad_out, double* V_host, double* dVdq_dev,
                                                        double* dVdtheta_host) {
   if (!h || !theta) return MIXTS_ERR_ARG;
+  if (!h->kids.empty()) return set_err(h, MIXTS_ERR_ARG, "batched handle: query a member (mixts_batch_member)");
   const Plan& p = h->plan;
   const int nt = p.nt;
   if (ta < 0 || ta >= nt || tb < 0 || tb >= nt || ta == tb || h->d.pseudo[ta] || h->d.pseudo[tb])

@@ -13,6 +13,10 @@ constexpr int MT = MIXTS_MAX_TYPES;
 constexpr int MAX_CLASSES = 12;
 constexpr int SMALL_P = 64;     // types with P <= SMALL_P propagate in one fused tile kernel
 constexpr int BIG_MB = 8;       // modes (or beads) per CTA of the large-P transforms
+constexpr int PROP_SMEM_MAX = 200 * 1024;  // dynamic shared memory cap of the propagation kernels
+// shared memory of one large-P transform CTA: the cos table and BIG_MB rows
+// of the 3N columns (forward: forces, q and p modes, plus the centroids)
+inline size_t big_prop_smem(int P, int N) { return sizeof(double) * ((size_t)P + (3 * (size_t)BIG_MB + 1) * 3 * N); }
 
 // Forces and energies are accumulated in 64-bit fixed point, so that sums
 // are exact integers whatever order the atomics land in: the whole step is
@@ -110,6 +114,7 @@ struct Dev {
   int big_slot0[MT];    // first estimator partial slot of a large-P type
   int sb_off[MT];       // offset of a large-P type's spread partials
   int pair_grid, pair32_grid, pseudo_chunks;  // persistent grid sizes, site-list split
+  int nl_cpl;                                 // list candidates per lane of one list warp
   double mass[MT];
   // sorted classes of non-pseudo atoms (P descending)
   int cls_P[MAX_CLASSES], cls_log2P[MAX_CLASSES], cls_pos0[MAX_CLASSES], cls_n[MAX_CLASSES],

@@ -54,6 +54,11 @@ class _Params(C.Structure):
                 ("precision", C.c_int), ("nlist_cap", C.c_int)]
 
 
+class _Tuning(C.Structure):
+    _fields_ = [("grid_scale", C.c_double), ("streams", C.c_int), ("nl_cpl", C.c_int),
+                ("steps_per_launch", C.c_int), ("ms_per_step", C.c_double), ("candidates", C.c_int)]
+
+
 class _Estimates(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "V", "V_lj", "V_coul", "V_bond", "V_angle", "V_pseudo", "KE_beads", "E_spring", "virial",
@@ -89,6 +94,12 @@ def lib():
         L.mixts_get_timing.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                        C.POINTER(C.c_longlong)]
         L.mixts_forces_noalloc.argtypes = [S, Pp, C.c_void_p, C.POINTER(C.c_double)]
+        L.mixts_set_graph.argtypes = [C.c_void_p, C.c_int]
+        L.mixts_rdf_accumulate.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.c_void_p]
+        L.mixts_rdf_normalise.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.c_longlong,
+                                          C.POINTER(C.c_uint64), C.POINTER(C.c_double)]
+        L.mixts_batch_member.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]
+        L.mixts_batch_tune.argtypes = [C.c_void_p, C.c_int, C.POINTER(_Tuning)]
         L.mixts_potential_grad.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_double,
                                            C.POINTER(C.c_double), C.c_void_p, C.POINTER(C.c_double)]
         L.mixts_destroy.argtypes = [C.c_void_p]
@@ -102,7 +113,8 @@ def lib():
 EXPORTED = ["mixts_workspace_size", "mixts_init", "mixts_forces", "mixts_step", "mixts_estimators",
             "mixts_nlist", "mixts_state_size", "mixts_get_state", "mixts_set_state", "mixts_gaussians",
             "mixts_destroy", "mixts_last_error", "mixts_version", "mixts_reload", "mixts_set_timing",
-            "mixts_get_timing", "mixts_forces_noalloc", "mixts_potential_grad"]
+            "mixts_get_timing", "mixts_forces_noalloc", "mixts_potential_grad", "mixts_batch_member",
+            "mixts_batch_tune", "mixts_set_graph", "mixts_rdf_accumulate", "mixts_rdf_normalise"]
 # force-field parameters of the differentiation variant, in mixts_potential_grad's order
 THETA_NAMES = ["sigma_a", "A_a_eV", "b_a", "sigma_b", "A_b_eV", "b_b", "q_a", "eps_aa"]
 PHASES = ["nlist", "pair", "bonded", "pseudo", "prop", "final", "other"]
@@ -230,6 +242,23 @@ class MixTS:
                                           C.c_void_p(out.data_ptr())))
         return out
 
+    def rdf_accumulate(self, type_a, type_b, hist, dr=0.02):
+        """Add the current configuration's pair histogram to ``hist`` (int64 device tensor)."""
+        self._check(lib().mixts_rdf_accumulate(self.h, int(type_a), int(type_b), float(dr), int(hist.numel()),
+                                               C.c_void_p(hist.data_ptr())))
+
+    def rdf_normalise(self, type_a, type_b, hist, n_frames, dr=0.02):
+        """g(r) per bin from a histogram summed over n_frames configurations."""
+        h = np.ascontiguousarray(hist.cpu().numpy() if hasattr(hist, "cpu") else hist).astype(np.uint64)
+        g = np.zeros(h.size)
+        self._check(lib().mixts_rdf_normalise(self.h, int(type_a), int(type_b), float(dr), int(h.size),
+                                              int(n_frames), _ptr(h, C.c_uint64), _ptr(g, C.c_double)))
+        return g
+
+    def set_graph(self, steps_per_launch):
+        """Steps per captured CUDA graph launch of step() (0: plain launches)."""
+        self._check(lib().mixts_set_graph(self.h, int(steps_per_launch)))
+
     def potential_grad(self, type_a, type_b, theta, grad_out=1.0, want_dvdq=True):
         """V_mix(q, theta), grad_out * dV/dq (device tensor or None), grad_out * dV/dtheta (8 floats).
 
@@ -263,7 +292,8 @@ class MixTS:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().mixts_destroy(self.h)
+            if not getattr(self, "_borrowed", False):
+                lib().mixts_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -316,3 +346,133 @@ def mixts_potential(theta, q, engine, type_a, type_b):
     if _MixTSPotential is None:
         _MixTSPotential = _potential_fn()
     return _MixTSPotential.apply(theta, q, engine, type_a, type_b)
+
+
+class MixTSBatch:
+    """Many independent systems (uneven sizes and bead counts) behind one
+    batched handle; a multi-step ``step`` runs as captured CUDA graph launches.
+
+    ``q[i]``, ``p[i]``, ``f[i]`` are the device state tensors of system i.
+    """
+
+    def __init__(self, systems, T=300.0, dt=0.25, tau=100.0, pile_lambda=1.0, r_cut=9.0, alpha=0.2,
+                 precision=FP64, nlist_cap=0, seeds=None, device="cuda:0", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("MixTSBatch needs a CUDA device")
+        L = lib()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        n = len(systems)
+        if n < 2:
+            raise ValueError("a batch holds at least two systems")
+        seeds = list(range(n)) if seeds is None else list(seeds)
+        self.q, self.p, self.f, self.n_types = [], [], [], []
+        structs, keep = [], []
+        with torch.cuda.device(self.device):
+            for sysm, seed in zip(systems, seeds):
+                q = torch.from_numpy(np.asarray(sysm.q, dtype=np.float64).copy()).to(self.device)
+                p = torch.from_numpy(np.asarray(sysm.p, dtype=np.float64).copy()).to(self.device)
+                f = torch.zeros_like(q)
+                self.q.append(q)
+                self.p.append(p)
+                self.f.append(f)
+                self.n_types.append(int(len(sysm.P_type)))
+                st, k = pack_system(sysm, q.data_ptr(), p.data_ptr(), f.data_ptr(), seed)
+                structs.append(st)
+                keep.append(k)
+        arr = (_System * n)(*structs)
+        self.n = n
+        self.params = _Params(float(T), float(dt), float(tau), float(pile_lambda), float(r_cut), float(alpha),
+                              int(precision), int(nlist_cap))
+        nbytes = L.mixts_workspace_size(arr, n, C.byref(self.params))
+        if nbytes == 0:
+            raise MixtsError(1, "mixts_workspace_size rejected the batch")
+        self.ws = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.ws.data_ptr() + 255) & ~255
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = L.mixts_init(arr, n, C.byref(self.params), C.c_void_p(aligned), int(nbytes),
+                              C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        del keep
+        if st != 0:
+            raise MixtsError(st, "mixts_init failed for the batch")
+        self.h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise MixtsError(st, lib().mixts_last_error(self.h).decode())
+
+    def forces(self):
+        e = (C.c_double * self.n)()
+        self._check(lib().mixts_forces(self.h, e))
+        return list(e)
+
+    def step(self, n=1):
+        self._check(lib().mixts_step(self.h, int(n)))
+
+    def tune(self, steps_per_launch=10):
+        t = _Tuning()
+        self._check(lib().mixts_batch_tune(self.h, int(steps_per_launch), C.byref(t)))
+        return {n: getattr(t, n) for n, _ in _Tuning._fields_}
+
+    def estimators(self):
+        out = (_Estimates * self.n)()
+        self._check(lib().mixts_estimators(self.h, out))
+        res = []
+        for i in range(self.n):
+            d = {n: getattr(out[i], n) for n, _ in _Estimates._fields_[:16]}
+            for n in ("KE_prim", "KE_cv", "Rg2", "E_spring_t"):
+                d[n] = list(getattr(out[i], n))[:self.n_types[i]]
+            d["step"] = int(out[i].step)
+            res.append(d)
+        return res
+
+    def get_state(self) -> bytes:
+        nb = lib().mixts_state_size(self.h)
+        buf = (C.c_ubyte * nb)()
+        self._check(lib().mixts_get_state(self.h, buf, nb))
+        return bytes(buf)
+
+    def set_state(self, blob: bytes):
+        buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+        self._check(lib().mixts_set_state(self.h, buf, len(blob)))
+
+    def reload(self):
+        self._check(lib().mixts_reload(self.h))
+
+    def set_timing(self, on=True):
+        self._check(lib().mixts_set_timing(self.h, 1 if on else 0))
+
+    def timing(self):
+        ms = (C.c_double * len(PHASES))()
+        calls = (C.c_longlong * len(PHASES))()
+        k = C.c_longlong(0)
+        self._check(lib().mixts_get_timing(self.h, ms, calls, C.byref(k)))
+        return dict(zip(PHASES, list(ms))), dict(zip(PHASES, list(calls))), int(k.value)
+
+    def member(self, i):
+        """A MixTS view of system i (borrowed handle; per-system queries)."""
+        mh = C.c_void_p()
+        self._check(lib().mixts_batch_member(self.h, int(i), C.byref(mh)))
+        m = MixTS.__new__(MixTS)
+        m.torch, m.device, m.stream = self.torch, self.device, self.stream
+        m.q, m.p, m.f = self.q[i], self.p[i], self.f[i]
+        m.n_beads, m.n_types = self.q[i].shape[0], self.n_types[i]
+        m.h, m._borrowed, m._batch = mh, True, self
+        return m
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mixts_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -50,8 +50,24 @@ def test_workspace_size_positive(P):
     prm = _params(P)
     n = P.lib().mixts_workspace_size(C.byref(st), 1, C.byref(prm))
     assert n > 0
-    # a batch size other than one is not accepted by this version
-    assert P.lib().mixts_workspace_size(C.byref(st), 2, C.byref(prm)) == 0
+
+
+def test_batch_workspace_is_sum_of_members(P):
+    prm = _params(P)
+    systems = [synth.water_box(32, 9.865, 8, 2, seed=0), synth.water_box(8, 6.21, 4, 1, seed=1),
+               synth.water_box(27, 9.3, 16, 4, seed=2)]
+    packed = [_sys_struct(P, s) for s in systems]
+    arr = (P.mixts._System * 3)(*[x[0] for x in packed])
+    singles = [P.lib().mixts_workspace_size(C.byref(x[0]), 1, C.byref(prm)) for x in packed]
+    total = P.lib().mixts_workspace_size(arr, 3, C.byref(prm))
+    assert total == sum((n + 255) // 256 * 256 for n in singles) + 256
+    # a batch with one invalid member is rejected as a whole
+    bad = synth.water_box(8, 6.21, 4, 3, seed=3)
+    bad.P_type = np.array([3, 4], dtype=np.int32)
+    bad_st, bad_keep = _sys_struct(P, bad)
+    arr2 = (P.mixts._System * 2)(packed[0][0], bad_st)
+    assert P.lib().mixts_workspace_size(arr2, 2, C.byref(prm)) == 0
+    assert P.lib().mixts_workspace_size(arr, 0, C.byref(prm)) == 0
 
 
 @pytest.mark.parametrize("bad", [(3, 2), (8, 0), (2048, 2)])

@@ -121,3 +121,23 @@ def test_potential_grad_rejects_bad_theta(gpu):
     with pytest.raises(gpu.MixtsError):
         m.potential_grad(0, 3, th)  # the electron is not a site type
     m.close()
+
+
+def test_grad_full_size_ion_electron_512(gpu):
+    """512 waters + ion + 1024-bead electron (H16/O2): seeded snapshots, GPU
+    gradient against the oracle's."""
+    base = synth.water_box(512, 24.83, 16, 2, seed=0, ion=dict(synth.systems.ION3), electron_P=1024)
+    for k in range(2):
+        s = base.copy()
+        s.q = base.q + np.random.default_rng(300 + k).normal(0, 0.05, base.q.shape)
+        m = gpu.MixTS(s)
+        th = oracle.theta_of(s, 0, 1)
+        V, dq, g = m.potential_grad(0, 1, th)
+        F_or, parts = oracle.forces(s)
+        assert abs(V - parts[0]) <= 1e-11 * abs(parts[0])
+        rms = np.sqrt(np.mean(F_or ** 2))
+        assert np.abs(dq.cpu().numpy() + F_or).max() <= 1e-11 * rms
+        g_or = oracle.grad_theta(s, 0, 1)
+        for j in range(8):
+            assert abs(g[j] - g_or[j]) <= 1e-9 * abs(g_or[j]) + _gtol(V), (gpu.THETA_NAMES[j], g[j], g_or[j])
+        m.close()
