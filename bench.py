@@ -239,6 +239,82 @@ def batch_variant(torch, stream, flush, dev, steps):
                                          "note": "sum of the members' k_pair32 launches timed one by one"}}
 
 
+def _run_observables(torch, stream, dev, sysm, dt, precision, n_eq, n_samp, every, pairs, dr=0.02, nbins=400):
+    """Equilibrate, then sample every `every` steps: per-type KE_cv and R_g^2
+    (mean and 8-block standard error) and g(r) of the given type pairs."""
+    import numpy as np
+    from paper_2411_11988_gb300 import MixTS
+    m = MixTS(sysm, T=300.0, dt=dt, tau=100.0, seed=0, device=str(dev), stream=stream, precision=precision)
+    m.step(n_eq)
+    hist = {k: torch.zeros(nbins, dtype=torch.int64, device=dev) for k in pairs}
+    ke, rg = [], []
+    frames = n_samp // every
+    with torch.cuda.stream(stream):
+        for _ in range(frames):
+            m.step(every)
+            for (a, b), h in hist.items():
+                m.rdf_accumulate(a, b, h, dr)
+            e = m.estimators()
+            ke.append(e["KE_cv"])
+            rg.append(e["Rg2"])
+    g = {k: m.rdf_normalise(k[0], k[1], h, frames, dr) for k, h in hist.items()}
+    m.close()
+
+    def stat(x):
+        x = np.asarray(x, dtype=np.float64)
+        b = x[: len(x) // 8 * 8].reshape(8, -1, *x.shape[1:]).mean(axis=1)
+        return b.mean(axis=0), b.std(axis=0, ddof=1) / np.sqrt(8)
+
+    return stat(ke), stat(rg), g
+
+
+def observables(torch, stream, dev):
+    """Sampled observables of the plain method at size (mixTS H32/O4 against
+    uniform 32 beads, FP64) and of the precision variant (FP32 forces against
+    FP64 forces on the ion + electron system, both on the GPU; the FP64 path
+    matches the FP64 oracle per step to 1e-11)."""
+    import numpy as np
+    import synth
+    names = {0: "O", 1: "H"}
+    out = {}
+    # bench workload: 1,000 equilibration + 3,000 sampled steps each
+    res = {}
+    for key, (ph, po) in {"mixts_H32_O4": (32, 4), "uniform_32": (32, 32)}.items():
+        (ke_m, ke_e), _, g = _run_observables(torch, stream, dev, build_system(ph, po, 0), DT, 0, 1000, 3000, 10,
+                                              [(0, 0), (0, 1), (1, 1)])
+        res[key] = (ke_m, ke_e, g)
+    r = (np.arange(400) + 0.5) * 0.02
+    water = {"steps": "1000 equilibration + 3000 sampled (every 10), dt 0.25 fs, FP64, RDF bins 0.02 A to 8 A"}
+    for key, (ke_m, ke_e, g) in res.items():
+        water[key] = {"KE_cv_kcal_mol": {names[t]: [float(ke_m[t]), float(ke_e[t])] for t in (0, 1)},
+                      "rdf_first_peak": {f"{names[a]}{names[b]}": [float(r[np.argmax(gg[60:]) + 60]),
+                                                                   float(np.max(gg[60:]))]
+                                         for (a, b), gg in g.items()}}
+    water["rdf_max_abs_diff_mixts_vs_uniform"] = {
+        f"{names[a]}{names[b]}": float(np.max(np.abs(res["mixts_H32_O4"][2][(a, b)] - res["uniform_32"][2][(a, b)])))
+        for (a, b) in [(0, 0), (0, 1), (1, 1)]}
+    out["water512"] = water
+    # precision variant: ion + electron, FP32 forces against FP64 forces
+    ie = ION_ELECTRON
+    sie = synth.water_box(ie["n_waters"], ie["box_A"], ie["P_H"], ie["P_O"], seed=0, ion=dict(synth.systems.ION3),
+                          electron_P=ie["P_e"])
+    res = {}
+    for key, prec in {"fp64": 0, "fp32_forces": 1}.items():
+        _, (rg_m, rg_e), g = _run_observables(torch, stream, dev, sie, ie["dt_fs"], prec, 2000, 8000, 10, [(2, 0)])
+        res[key] = (rg_m[3], rg_e[3], g[(2, 0)])
+    rg64, rg32 = res["fp64"], res["fp32_forces"]
+    out["ion_electron"] = {
+        "steps": "2000 equilibration + 8000 sampled (every 10), dt 0.1 fs",
+        "electron_Rg_A": {"fp64": [float(np.sqrt(rg64[0])), float(rg64[1] / (2 * np.sqrt(rg64[0])))],
+                          "fp32_forces": [float(np.sqrt(rg32[0])), float(rg32[1] / (2 * np.sqrt(rg32[0])))]},
+        "ion_O_rdf_first_peak": {k: [float(r[np.argmax(v[2][50:]) + 50]), float(np.max(v[2][50:]))]
+                                 for k, v in res.items()},
+        "ion_O_rdf_max_abs_diff_fp32_vs_fp64": float(np.max(np.abs(rg32[2] - rg64[2]))),
+        "note": "[mean, 8-block standard error]; the FP64 run stands for the FP64 oracle, which it matches "
+                "per step to 1e-11 (the oracle itself runs ~0.4 s per step here)"}
+    return out
+
+
 def grad_variant(torch, stream, dev, snapshots):
     """Forward + backward of the differentiable potential on snapshots of a
     short run; each gradient is checked against central differences of the
@@ -351,6 +427,7 @@ def main():
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-observables", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="force precision of the main line (fp32: FP32 pair forces, FP64 integration)")
     args = ap.parse_args()
@@ -434,6 +511,9 @@ def main():
             variants[key]["workload"] = ie["workload"]
         variants["batched_64_fp32"] = batch_variant(torch, stream, flush, dev, vs)
         variants["grad_ion_electron512"] = grad_variant(torch, stream, dev, 10)
+    obs = None
+    if not args.no_observables:
+        obs = observables(torch, stream, dev)
 
     cb = None
     if rank == 0 and not args.no_cpu:
@@ -453,6 +533,7 @@ def main():
             "ms_per_step_single_calls": single_ms,
             "uniform_fp64": uni,
             "variants": variants,
+            "observables": obs,
             "mixts_speedup_vs_uniform": (uni["ms_per_step"] / step_ms) if uni else None,
             "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,

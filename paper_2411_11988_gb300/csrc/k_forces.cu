@@ -454,44 +454,30 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
 
 
 // ---------------------------------------------------------------------------
-// nonbonded pair sweep, FP32 forces (precision MIXTS_FP32_FORCES)
+// nonbonded pair sweep, FP32 forces (precision MIXTS_FP32_FORCES), the terms
+// of Eq. (mts-hamiltonian) regrouped by slice of the finest grid.
 //
-// Full neighbour lists (every row lists all partners) and one warp per
-// (atom i, slice s of the finest grid of the non-pseudo atoms): the pair
-// (i, j) contributes at slice s iff s is a multiple of P_max/P*, P* =
-// max(P_i, P_j), with weight 1/P*, bead s P_i/P_max of i and bead
-// s P_j/P_max of j -- the terms of Eq. (mts-hamiltonian) regrouped by slice.
-// Only i's bead is written, so there are no reaction atomics; every term is
-// evaluated from both sides and the energies carry a factor 1/2.
-// Displacements are exact hi parts (2^-12 A grid) plus binary32 remainders;
-// the DSF comes from the binary32 copy of the interval table; per-lane
-// binary32 partial sums are combined across the warp in binary64.
+// Full neighbour lists (every row lists all partners): only the owner's bead
+// is written, so there are no reaction atomics; every term is evaluated from
+// both sides and the energies carry a factor 1/2.
+//
+// One warp per (owner atom, block of slices, chunk of its full list). The
+// lanes are slices s of the finest grid: P' = min(P_max, 32) lanes per group
+// and G = 32 / P' groups taking different list entries, so an entry is decoded
+// once per group and every lane evaluates the same atom pair on its own slice
+// (owner bead s >> (lgP_max - lgP_i), partner bead s >> (lgP_max - lgP_j));
+// the pair is active at s iff s is a multiple of P_max / P*. Displacements are
+// the bead-0 displacement (exact grid part plus remainder, binary32) plus the
+// two beads' offsets from their bead 0, so the result carries no large
+// cancellation. The damped-shifted-force Coulomb uses the erfc approximation
+// of Abramowitz & Stegun, Handbook of Mathematical Functions, eq. 7.1.26
+// (|error| <= 1.5e-7), with the exact Gaussian in the force.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void dsf_table32(const float* tab, int bits, float s, float* g, float* fg) {
-  const float s0 = __int_as_float((bits >> 17) << 17);
-  const float x = s - s0;
-  const float* c = tab;
-  float p = fmaf(c[5], x, c[4]);
-  float q = fmaf(c[11], x, c[10]);
-  p = fmaf(p, x, c[3]);
-  q = fmaf(q, x, c[9]);
-  p = fmaf(p, x, c[2]);
-  q = fmaf(q, x, c[8]);
-  p = fmaf(p, x, c[1]);
-  q = fmaf(q, x, c[7]);
-  *g = fmaf(p, x, c[0]);
-  *fg = fmaf(q, x, c[6]);
-}
-
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
-  extern __shared__ float ftab[];   // DSF interval table, 12 floats per interval
   __shared__ float qqt[MT * MT], e4t[MT * MT], s2t[MT * MT], vrct[MT * MT], dvrct[MT * MT];
   __shared__ float4 shh[125], shl[125];
   __shared__ int tN[MT], tLg[MT];
-  __shared__ int woff[PAIR_THREADS / 32][MT];  // per warp: partner-type bead-row offset, -1 inactive
-  __shared__ float wwt[PAIR_THREADS / 32][MT]; // per warp: 1/P* per partner type
   const int nt = d.n_types;
-  for (int e = threadIdx.x; e < 12 * d.dsf_nint; e += blockDim.x) ftab[e] = d.dsf_tab32[e];
   for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
     const PairPar pp = d.pairpar[(e / nt) * MT + (e % nt)];
     qqt[e] = (float)pp.qq;
@@ -513,118 +499,119 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < d.n_items32; w += nwarps) {
-  const int sl = w / d.n_nonp;             // slice of the finest grid
-  const int pos = w - sl * d.n_nonp;
   const int lgM = d.lgPmax_nb;
-  const AtomInfo ai = d.ainfo[pos];
-  const int row_i = ai.row0 + (sl >> (lgM - ai.log2P)) * ai.stride;
-  const float4 xih = d.Xf[row_i], xil = d.Xl[row_i];
-  const int cnt = min(d.nl_cnt[pos], d.nl_cap);
-  const int* lst = d.nl + (size_t)pos * d.nl_cap;
-  const float rc = (float)d.rc, rc2 = (float)d.rc2, slo = (float)d.dsf_smin;
-  const float scr2 = d.screen_rc2;
-  const int base = (127 + (d.dsf_base >> 6) - 1023) << 6;
-  const int trow = ai.type * nt;
-  const int wib = threadIdx.x >> 5;
-  __syncwarp();
-  if (lane < nt) {
-    const int lgs = max(ai.log2P, tLg[lane]);  // log2 P*
-    const bool act = (sl & ((1 << (lgM - lgs)) - 1)) == 0;
-    woff[wib][lane] = act ? (sl >> (lgM - tLg[lane])) * tN[lane] : -1;
-    wwt[wib][lane] = __int_as_float((127 - lgs) << 23);
-  }
-  __syncwarp();
-  float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, ec = 0.f, vir = 0.f;
-  int nev = 0, nlj = 0;
-  int ent_next = lane < cnt ? lst[lane] : 0;
-  for (int e = lane; e < cnt; e += 32) {
-    const int ent = ent_next;
-    ent_next = e + 32 < cnt ? lst[e + 32] : 0;
-    const int tj = (ent >> 7) & 15;
-    const int oj = woff[wib][tj];
-    if (oj < 0) continue;  // pair inactive at this slice
-    const int row_j = (ent >> 11) + oj;
-    const float4 hj = d.Xf[row_j];
-    const float4 sh = shh[ent & 127];
-    // exact grid-point displacement first; the remainders move it by at
-    // most 2^-11 A per axis, so only candidates passing the screen go on
-    const float hx = (hj.x - xih.x) + sh.x, hy = (hj.y - xih.y) + sh.y, hz = (hj.z - xih.z) + sh.z;
-    if (fmaf(hz, hz, fmaf(hy, hy, hx * hx)) > scr2) continue;
-    const float4 lj = d.Xl[row_j];
-    const float4 sm = shl[ent & 127];
-    const float dx = hx + ((lj.x - xil.x) + sm.x);
-    const float dy = hy + ((lj.y - xil.y) + sm.y);
-    const float dz = hz + ((lj.z - xil.z) + sm.z);
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    if (!(r2 < rc2)) continue;
-    const int k = trow + tj;
-    const float wgt = wwt[wib][tj];  // 1/P*
-    float fr = 0.f, et = 0.f, lt = 0.f;
-    const float qq = qqt[k];
-    if (qq != 0.f) {
-      float g, fg;
-      if (r2 >= slo) {
-        const int bits = __float_as_int(r2);
-        dsf_table32(ftab + 12 * ((bits >> 17) - base), bits, r2, &g, &fg);
-      } else {
-        const float r = sqrtf(r2), rinv = 1.0f / r;
-        const float erc = erfcf((float)d.alpha * r), ex = expf(-(float)(d.alpha * d.alpha) * r2);
-        g = erc * rinv - (float)d.dsf_erfc_rc_over_rc + (float)d.dsf_cf * (r - rc);
-        fg = (erc * rinv * rinv + (float)d.dsf_g * ex * rinv - (float)d.dsf_cf) * rinv;
-      }
-      et = qq * g;
-      fr = qq * fg;
-    }
-    const float e4 = e4t[k];
-    if (e4 != 0.f) {
+  const int lgPp = lgM < 5 ? lgM : 5;  // log2 P'
+  const int lgG = 5 - lgPp;
+  const int sl = lane & ((1 << lgPp) - 1), grp = lane >> lgPp;
+  const int nsb = 1 << (lgM - lgPp), nch = d.p32_nch;
+  const int n_items = d.n_nonp * nsb * nch;
+  const float rc = (float)d.rc, rc2 = (float)d.rc2;
+  const float alpha = (float)d.alpha, alpha2 = (float)(d.alpha * d.alpha);
+  const float g2a = (float)d.dsf_g, cf = (float)d.dsf_cf, c0 = (float)d.dsf_erfc_rc_over_rc;
+  // erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x)
+  const float ap = 0.3275911f, a1 = 0.254829592f, a2 = -0.284496736f, a3 = 1.421413741f, a4 = -1.453152027f,
+              a5 = 1.061405429f;
+  const float log2e = 1.4426950408889634f;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_items; w += nwarps) {
+    const int ch = w % nch;
+    const int rest = w / nch;
+    const int sb = rest % nsb, pos = rest / nsb;
+    const int cnt = min(d.nl_cnt[pos], d.nl_cap);
+    const int e0 = ch * P32_CH;
+    if (e0 >= cnt) continue;
+    const int e1 = min(cnt, e0 + P32_CH);
+    const AtomInfo ai = d.ainfo[pos];
+    const int s = (sb << lgPp) + sl;  // slice of the finest grid
+    const int row_i = ai.row0 + (s >> (lgM - ai.log2P)) * ai.stride;
+    const float4 di = d.Xd[row_i];
+    const float4 hi0 = d.Xf[ai.row0], lo0 = d.Xl[ai.row0];
+    const int* lst = d.nl + (size_t)pos * d.nl_cap;
+    const int trow = ai.type * nt;
+    float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, ec = 0.f, vir = 0.f;
+    int nev = 0, nlj = 0;
+    for (int e = e0 + grp; e < e1; e += (1 << lgG)) {
+      const int ent = lst[e];
+      const int tj = (ent >> 7) & 15;
+      const int lgPj = tLg[tj];
+      const int lgS = ai.log2P > lgPj ? ai.log2P : lgPj;  // log2 P*
+      const int row0j = ent >> 11;
+      const float4 hj = d.Xf[row0j], lj = d.Xl[row0j];
+      const float4 dj = d.Xd[row0j + (s >> (lgM - lgPj)) * tN[tj]];
+      const float4 sh = shh[ent & 127], sm = shl[ent & 127];
+      const float dx = (((hj.x - hi0.x) + sh.x) + ((lj.x - lo0.x) + sm.x)) + (dj.x - di.x);
+      const float dy = (((hj.y - hi0.y) + sh.y) + ((lj.y - lo0.y) + sm.y)) + (dj.y - di.y);
+      const float dz = (((hj.z - hi0.z) + sh.z) + ((lj.z - lo0.z) + sm.z)) + (dj.z - di.z);
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      const bool act = (s & ((1 << (lgM - lgS)) - 1)) == 0;
+      if (!(act && r2 < rc2)) continue;
+      const int k = trow + tj;
+      const float wgt = __int_as_float((127 - lgS) << 23);  // 1/P*
       const float rinv = rsqrtf(r2);
-      const float r = r2 * rinv, rinv2 = rinv * rinv;
-      const float sr2 = s2t[k] * rinv2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
-      lt = e4 * (sr12 - sr6) - vrct[k] - (r - rc) * dvrct[k];
-      fr += (6.0f * e4 * (2.0f * sr12 - sr6) * rinv + dvrct[k]) * rinv;
-      ++nlj;
+      const float r = r2 * rinv;
+      float fr = 0.f, et = 0.f, lt = 0.f;
+      const float qq = qqt[k];
+      if (qq != 0.f) {
+        const float t = __fdividef(1.0f, fmaf(ap, alpha * r, 1.0f));
+        const float ex = exp2f(-alpha2 * r2 * log2e);
+        const float pl = fmaf(fmaf(fmaf(fmaf(a5, t, a4), t, a3), t, a2), t, a1) * t;
+        const float erc = pl * ex;
+        et = qq * (fmaf(erc, rinv, -c0) + cf * (r - rc));
+        fr = qq * (fmaf(erc * rinv, rinv, fmaf(g2a * ex, rinv, -cf)) * rinv);
+      }
+      const float e4 = e4t[k];
+      if (e4 != 0.f) {
+        const float rinv2 = rinv * rinv;
+        const float sr2 = s2t[k] * rinv2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
+        lt = e4 * (sr12 - sr6) - vrct[k] - (r - rc) * dvrct[k];
+        fr += (6.0f * e4 * (2.0f * sr12 - sr6) * rinv + dvrct[k]) * rinv;
+        ++nlj;
+      }
+      fr *= wgt;
+      // force on i is minus the force on j along d = x_j - x_i
+      fx = fmaf(-fr, dx, fx);
+      fy = fmaf(-fr, dy, fy);
+      fz = fmaf(-fr, dz, fz);
+      ec = fmaf(wgt, et, ec);
+      elj = fmaf(wgt, lt, elj);
+      vir = fmaf(fr, r2, vir);
+      ++nev;
     }
-    fr *= wgt;
-    // force on i is minus the force on j along d = x_j - x_i
-    fx = fmaf(-fr, dx, fx);
-    fy = fmaf(-fr, dy, fy);
-    fz = fmaf(-fr, dz, fz);
-    ec = fmaf(wgt, et, ec);
-    elj = fmaf(wgt, lt, elj);
-    vir = fmaf(fr, r2, vir);
-    ++nev;
-  }
-  // lane partials to fixed point by bit assembly, summed with integer
-  // shuffles: exact and free of FP64 instructions
-  int bad = 0;
-  long long kx = fixs(f2d_bits(fx), 44, &bad), ky = fixs(f2d_bits(fy), 44, &bad), kz = fixs(f2d_bits(fz), 44, &bad);
-  // every term is seen from both of its atoms: energies carry a factor 1/2
-  long long kl = fixs(f2d_bits(elj), 39, &bad), kc = fixs(f2d_bits(ec), 39, &bad), kv = fixs(f2d_bits(vir), 39, &bad);
+    // lane partials to fixed point by bit assembly, then exact integer sums
+    int bad = 0;
+    long long kx = fixs(f2d_bits(fx), 44, &bad), ky = fixs(f2d_bits(fy), 44, &bad), kz = fixs(f2d_bits(fz), 44, &bad);
+    // over the groups (same slice) and over slices that share the owner's bead
+    const int lgShare = lgM - ai.log2P < lgPp ? lgM - ai.log2P : lgPp;
+    for (int o = 1; o < 32; o <<= 1) {
+      if (o < (1 << lgPp) && o >= (1 << lgShare)) continue;
+      kx += __shfl_xor_sync(0xffffffffu, kx, o);
+      ky += __shfl_xor_sync(0xffffffffu, ky, o);
+      kz += __shfl_xor_sync(0xffffffffu, kz, o);
+    }
+    if (grp == 0 && (sl & ((1 << lgShare) - 1)) == 0 && (kx | ky | kz) != 0) {
+      unsigned long long* fi = d.F_fix + 3 * (size_t)row_i;
+      atomicAdd(fi + 0, (unsigned long long)kx);
+      atomicAdd(fi + 1, (unsigned long long)ky);
+      atomicAdd(fi + 2, (unsigned long long)kz);
+    }
+    // every term is seen from both of its atoms: energies carry a factor 1/2
+    long long kl = fixs(f2d_bits(elj), 39, &bad), kc = fixs(f2d_bits(ec), 39, &bad), kv = fixs(f2d_bits(vir), 39, &bad);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    kx += __shfl_xor_sync(0xffffffffu, kx, o);
-    ky += __shfl_xor_sync(0xffffffffu, ky, o);
-    kz += __shfl_xor_sync(0xffffffffu, kz, o);
-    kl += __shfl_xor_sync(0xffffffffu, kl, o);
-    kc += __shfl_xor_sync(0xffffffffu, kc, o);
-    kv += __shfl_xor_sync(0xffffffffu, kv, o);
-  }
-  nev = warp_sumi(nev);
-  nlj = warp_sumi(nlj);
-  bad = __any_sync(0xffffffffu, bad);
-  if (lane == 0) {
-    atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nlj);
-    unsigned long long* fi = d.F_fix + 3 * (size_t)row_i;
-    atomicAdd(fi + 0, (unsigned long long)kx);
-    atomicAdd(fi + 1, (unsigned long long)ky);
-    atomicAdd(fi + 2, (unsigned long long)kz);
-    atomicAdd(d.E_fix + E_LJ, (unsigned long long)kl);
-    atomicAdd(d.E_fix + E_COUL, (unsigned long long)kc);
-    atomicAdd(d.E_fix + E_VIRIAL, (unsigned long long)kv);
-    atomicAdd(d.E_fix + E_NEVAL, (unsigned long long)nev);
-    if (bad) atomicOr(d.err, ERR_NONFINITE);
-  }
+    for (int o = 16; o > 0; o >>= 1) {
+      kl += __shfl_xor_sync(0xffffffffu, kl, o);
+      kc += __shfl_xor_sync(0xffffffffu, kc, o);
+      kv += __shfl_xor_sync(0xffffffffu, kv, o);
+    }
+    nev = warp_sumi(nev);
+    nlj = warp_sumi(nlj);
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      if (kl) atomicAdd(d.E_fix + E_LJ, (unsigned long long)kl);
+      if (kc) atomicAdd(d.E_fix + E_COUL, (unsigned long long)kc);
+      if (kv) atomicAdd(d.E_fix + E_VIRIAL, (unsigned long long)kv);
+      if (nev) atomicAdd(d.E_fix + E_NEVAL, (unsigned long long)nev);
+      if (nlj) atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nlj);
+      if (bad) atomicOr(d.err, ERR_NONFINITE);
+    }
   }
 }
 
@@ -941,9 +928,8 @@ void pair_grids(int nt, int nint, int* g64, int* g32) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   (void)nt;
   cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_pair64, PAIR_THREADS, sizeof(double) * 12 * (size_t)nint);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_pair32, PAIR_THREADS, sizeof(float) * 12 * (size_t)nint);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_pair32, PAIR_THREADS, 0);
   *g64 = std::max(1, b64) * std::max(1, sms);
   *g32 = std::max(1, b32) * std::max(1, sms);
 }
@@ -951,14 +937,10 @@ void pair_grids(int nt, int nint, int* g64, int* g32) {
 int launch_pair(const Dev& d, cudaStream_t s) {
   const int wpb = PAIR_THREADS / 32;
   if (d.precision == MIXTS_FP32_FORCES) {
-    if (d.n_items32 == 0) return 0;
-    const size_t smem = sizeof(float) * 12 * (size_t)d.dsf_nint;
-    static bool attr32 = false;
-    if (!attr32) {
-      cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-      attr32 = true;
-    }
-    k_pair32<<<min((d.n_items32 + wpb - 1) / wpb, d.pair32_grid), PAIR_THREADS, smem, s>>>(d);
+    if (d.n_nonp == 0) return 0;
+    const int lgPp = d.lgPmax_nb < 5 ? d.lgPmax_nb : 5;
+    const long long items = (long long)d.n_nonp * (1 << (d.lgPmax_nb - lgPp)) * d.p32_nch;
+    k_pair32<<<(int)std::min<long long>((items + wpb - 1) / wpb, d.pair32_grid), PAIR_THREADS, 0, s>>>(d);
     return 1;
   }
   if (d.n_pitems == 0) return 0;

@@ -13,7 +13,8 @@ constexpr int MT = MIXTS_MAX_TYPES;
 constexpr int MAX_CLASSES = 12;
 constexpr int SMALL_P = 64;     // types with P <= SMALL_P propagate in one fused tile kernel
 constexpr int BIG_MB = 8;       // modes (or beads) per CTA of the large-P transforms
-constexpr int PROP_SMEM_MAX = 200 * 1024;  // dynamic shared memory cap of the propagation kernels
+constexpr int PROP_SMEM_MAX = 200 * 1024;
+constexpr int P32_CH = 128;     // list candidates per FP32 pair item  // dynamic shared memory cap of the propagation kernels
 // shared memory of one large-P transform CTA: the cos table and BIG_MB rows
 // of the 3N columns (forward: forces, q and p modes, plus the centroids)
 inline size_t big_prop_smem(int P, int N) { return sizeof(double) * ((size_t)P + (3 * (size_t)BIG_MB + 1) * 3 * N); }
@@ -115,6 +116,7 @@ struct Dev {
   int sb_off[MT];       // offset of a large-P type's spread partials
   int pair_grid, pair32_grid, pseudo_chunks;  // persistent grid sizes, site-list split
   int nl_cpl;                                 // list candidates per lane of one list warp
+  int p32_nch;                                // FP32 pair items per owner row and slice block (list chunks)
   double mass[MT];
   // sorted classes of non-pseudo atoms (P descending)
   int cls_P[MAX_CLASSES], cls_log2P[MAX_CLASSES], cls_pos0[MAX_CLASSES], cls_n[MAX_CLASSES],
@@ -148,6 +150,7 @@ struct Dev {
   longlong4_32a* Xi;               // [n_beads] the same in 2^-48 A fixed point (exact differences)
   float4* Xf;                  // [n_beads] binary32 positions on the 2^-12 A grid (screens)
   float4* Xl;                  // [n_beads] binary32 remainders: Xw = Xf + Xl to ~2^-37 A
+  float4* Xd;                  // [n_beads] binary32 offset of each bead from its atom's bead 0 (FP32 path; else null)
   double* ref;                 // [n_atoms*3] wrapped bead-0 reference positions
   double4_32a* refd;           // [n_nonp] the same by sorted position
   float4* reff;                // [n_nonp] binary32 copy, .w = log2 P (int bits)
