@@ -277,14 +277,14 @@ def observables(torch, stream, dev):
     import synth
     names = {0: "O", 1: "H"}
     out = {}
-    # bench workload: 1,000 equilibration + 3,000 sampled steps each
+    # bench workload: 4,000 equilibration + 6,000 sampled steps each (10^4 in all)
     res = {}
     for key, (ph, po) in {"mixts_H32_O4": (32, 4), "uniform_32": (32, 32)}.items():
-        (ke_m, ke_e), _, g = _run_observables(torch, stream, dev, build_system(ph, po, 0), DT, 0, 1000, 3000, 10,
+        (ke_m, ke_e), _, g = _run_observables(torch, stream, dev, build_system(ph, po, 0), DT, 0, 4000, 6000, 10,
                                               [(0, 0), (0, 1), (1, 1)])
         res[key] = (ke_m, ke_e, g)
     r = (np.arange(400) + 0.5) * 0.02
-    water = {"steps": "1000 equilibration + 3000 sampled (every 10), dt 0.25 fs, FP64, RDF bins 0.02 A to 8 A"}
+    water = {"steps": "4000 equilibration + 6000 sampled (every 10), dt 0.25 fs, FP64, RDF bins 0.02 A to 8 A"}
     for key, (ke_m, ke_e, g) in res.items():
         water[key] = {"KE_cv_kcal_mol": {names[t]: [float(ke_m[t]), float(ke_e[t])] for t in (0, 1)},
                       "rdf_first_peak": {f"{names[a]}{names[b]}": [float(r[np.argmax(gg[60:]) + 60]),

@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
   __shared__ float qqt[MT * MT], e4t[MT * MT], s2t[MT * MT], vrct[MT * MT], dvrct[MT * MT];
   __shared__ float4 shh[125], shl[125];
-  __shared__ int tN[MT], tLg[MT];
+  __shared__ int tN[MT], tLg[MT], tOff[MT];
   const int nt = d.n_types;
   for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
     const PairPar pp = d.pairpar[(e / nt) * MT + (e % nt)];
@@ -489,6 +489,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
   for (int e = threadIdx.x; e < nt; e += blockDim.x) {
     tN[e] = d.N[e];
     tLg[e] = d.log2P[e];
+    tOff[e] = d.off[e];
   }
   for (int e = threadIdx.x; e < 125; e += blockDim.x) {
     const int nx = e / 25 - 2, ny = (e / 5) % 5 - 2, nz = e % 5 - 2;
@@ -517,26 +518,30 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
     const int rest = w / nch;
     const int sb = rest % nsb, pos = rest / nsb;
     const int cnt = min(d.nl_cnt[pos], d.nl_cap);
-    const int e0 = ch * P32_CH;
+    const int e0 = ch * (P32_CH << lgG);
     if (e0 >= cnt) continue;
-    const int e1 = min(cnt, e0 + P32_CH);
+    const int e1 = min(cnt, e0 + (P32_CH << lgG));
     const AtomInfo ai = d.ainfo[pos];
     const int s = (sb << lgPp) + sl;  // slice of the finest grid
     const int row_i = ai.row0 + (s >> (lgM - ai.log2P)) * ai.stride;
-    const float4 di = d.Xd[row_i];
+    const int oi = tOff[ai.type];
+    const float4 di = d.Xd[oi + ((ai.row0 - oi) << ai.log2P) + (s >> (lgM - ai.log2P))];
     const float4 hi0 = d.Xf[ai.row0], lo0 = d.Xl[ai.row0];
     const int* lst = d.nl + (size_t)pos * d.nl_cap;
     const int trow = ai.type * nt;
     float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, ec = 0.f, vir = 0.f;
     int nev = 0, nlj = 0;
+    int ent_next = e0 + grp < e1 ? lst[e0 + grp] : 0;
     for (int e = e0 + grp; e < e1; e += (1 << lgG)) {
-      const int ent = lst[e];
+      const int ent = ent_next;  // the next entry's load overlaps this one's work
+      ent_next = e + (1 << lgG) < e1 ? lst[e + (1 << lgG)] : 0;
       const int tj = (ent >> 7) & 15;
       const int lgPj = tLg[tj];
       const int lgS = ai.log2P > lgPj ? ai.log2P : lgPj;  // log2 P*
       const int row0j = ent >> 11;
       const float4 hj = d.Xf[row0j], lj = d.Xl[row0j];
-      const float4 dj = d.Xd[row0j + (s >> (lgM - lgPj)) * tN[tj]];
+      const int oj = tOff[tj];
+      const float4 dj = d.Xd[oj + ((row0j - oj) << lgPj) + (s >> (lgM - lgPj))];
       const float4 sh = shh[ent & 127], sm = shl[ent & 127];
       const float dx = (((hj.x - hi0.x) + sh.x) + ((lj.x - lo0.x) + sm.x)) + (dj.x - di.x);
       const float dy = (((hj.y - hi0.y) + sh.y) + ((lj.y - lo0.y) + sm.y)) + (dj.y - di.y);
@@ -552,7 +557,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
       const float qq = qqt[k];
       if (qq != 0.f) {
         const float t = __fdividef(1.0f, fmaf(ap, alpha * r, 1.0f));
-        const float ex = exp2f(-alpha2 * r2 * log2e);
+        float ex;  // exp(-a^2 r^2), argument in [-a^2 rc^2, 0]
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(-alpha2 * log2e * r2));
         const float pl = fmaf(fmaf(fmaf(fmaf(a5, t, a4), t, a3), t, a2), t, a1) * t;
         const float erc = pl * ex;
         et = qq * (fmaf(erc, rinv, -c0) + cf * (r - rc));

@@ -47,10 +47,11 @@ struct MirrorOut {
 };
 
 __device__ __forceinline__ void write_mirror(const Dev& d, int row, double x, double y, double z, double mx_,
-                                             double my_, double mz_, const double* x0) {
+                                             double my_, double mz_, const double* x0, int arow) {
   const double L = d.box;
-  // offset from the atom's bead 0 (unwrapped difference; the shift cancels)
-  if (d.Xd) d.Xd[row] = make_float4((float)(x - x0[0]), (float)(y - x0[1]), (float)(z - x0[2]), 0.0f);
+  // offset from the atom's bead 0 (unwrapped difference; the shift cancels),
+  // atom-major so that one atom's beads are contiguous
+  if (d.Xd) d.Xd[arow] = make_float4((float)(x - x0[0]), (float)(y - x0[1]), (float)(z - x0[2]), 0.0f);
   const double wx = fma(-mx_, L, x), wy = fma(-my_, L, y), wz = fma(-mz_, L, z);
   d.Xw[row] = make_double4_32a(wx, wy, wz, 0.0);
   // 2^-48 A fixed point, and the nearest 2^-12 A grid point as binary32
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop_small(Dev d, int mode) {
       for (int x = 0; x < 3; ++x) MirrorOut::wrap_ref(Xc[0 * C + 3 * a + x], d.box, &fl[x], &rf[x]);
       const int row = d.off[t] + j * N + k0 + a;
       write_mirror(d, row, Xc[j * C + 3 * a], Xc[j * C + 3 * a + 1], Xc[j * C + 3 * a + 2], fl[0], fl[1], fl[2],
-                   Xc + 3 * a);
+                   Xc + 3 * a, d.off[t] + (k0 + a) * P + j);
       if (j == 0) {
         write_ref(d, atom, rf);
       } else {
@@ -282,7 +283,7 @@ __global__ void k_mirror_from_q(Dev d) {
   for (int j = 0; j < P; ++j) {
     const size_t row = (size_t)r0 + (size_t)j * N;
     const double x = d.q[3 * row], y = d.q[3 * row + 1], z = d.q[3 * row + 2];
-    write_mirror(d, (int)row, x, y, z, fl[0], fl[1], fl[2], q0);
+    write_mirror(d, (int)row, x, y, z, fl[0], fl[1], fl[2], q0, d.off[t] + k * P + j);
     if (j > 0) {
       const double dd = bead_dist(x - q0[0], y - q0[1], z - q0[2]);
       sp = dd > sp ? dd : sp;
@@ -474,7 +475,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_inv(Dev d, int t, int mode)
       double fl[3], rf[3];
       for (int x = 0; x < 3; ++x) MirrorOut::wrap_ref(Qc[3 * a + x], d.box, &fl[x], &rf[x]);
       const double* xb = Qc + (size_t)(jj + 1) * C + 3 * a;
-      write_mirror(d, d.off[t] + j * N + a, xb[0], xb[1], xb[2], fl[0], fl[1], fl[2], Qc + 3 * a);
+      write_mirror(d, d.off[t] + j * N + a, xb[0], xb[1], xb[2], fl[0], fl[1], fl[2], Qc + 3 * a, d.off[t] + a * P + j);
       if (jj == 0 && blockIdx.x == 0) write_ref(d, atom, rf);
     }
     // spread partial of this bead block, per atom

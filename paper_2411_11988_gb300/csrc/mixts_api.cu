@@ -87,7 +87,7 @@ struct Plan {
   size_t o_tab = 0, tab_bytes = 0;
   size_t o_ainfo, o_pos_atom, o_pos_mol, o_atom_of_tk, o_ainfo_atom, o_pos_of_atom, o_is_pseudo, o_pseudo_atom, o_pinfo,
       o_pairpar, o_pspar, o_bitems, o_bond_atoms, o_bond_par, o_ang_atoms, o_ang_par, o_cm, o_mc, o_tiles,
-      o_slot_type, o_dsf, o_dsf32, o_pairpar_alt, o_pspar_alt, o_pc, o_gacc;
+      o_slot_type, o_dsf, o_pairpar_alt, o_pspar_alt, o_pc, o_gacc;
   size_t o_state = 0, state_bytes = 0;
   size_t o_xd = 0;
   size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_xl, o_ref, o_refd, o_reff, o_spread, o_spread_big, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
@@ -496,7 +496,6 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_tiles = A.add(sizeof(PropTile) * std::max<size_t>(1, p.tiles.size()));
   p.o_slot_type = A.add(sizeof(int) * std::max<size_t>(1, p.slot_type.size()));
   p.o_dsf = A.add(sizeof(double) * p.dsf.size());
-  p.o_dsf32 = A.add(sizeof(float) * p.dsf.size());
   p.o_pairpar_alt = A.add(sizeof(PairPar) * MT * MT);
   p.o_pspar_alt = A.add(sizeof(PseudoPar) * MT);
   p.o_pc = A.add(sizeof(double) * 8 * MT);
@@ -704,10 +703,6 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   put(img, p.o_tiles, p.tiles);
   put(img, p.o_slot_type, p.slot_type);
   put(img, p.o_dsf, p.dsf);
-  {
-    std::vector<float> t32(p.dsf.begin(), p.dsf.end());
-    put(img, p.o_dsf32, t32);
-  }
   mixts_status st = cuda_check(h, cudaMemcpy(h->ws, img.data(), p.tab_bytes, cudaMemcpyHostToDevice), "upload tables");
   if (st == MIXTS_OK)
     st = cuda_check(h, cudaMemsetAsync(h->ws + p.tab_bytes, 0, p.ar.size - p.tab_bytes, h->stream), "clear state");
@@ -744,7 +739,6 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.dsf_cf = erfc(prm->dsf_alpha * prm->r_cut) / (prm->r_cut * prm->r_cut) +
              d.dsf_g * exp(-prm->dsf_alpha * prm->dsf_alpha * prm->r_cut * prm->r_cut) / prm->r_cut;
   d.dsf_tab = (const double*)(h->ws + p.o_dsf);
-  d.dsf_tab32 = (const float*)(h->ws + p.o_dsf32);
   d.full_list = prm->precision == MIXTS_FP32_FORCES ? 1 : 0;
   d.lgPmax_nb = p.n_classes > 0 ? p.cls_log2P[0] : 0;
   d.n_items32 = p.n_nonp << d.lgPmax_nb;
@@ -821,7 +815,10 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   h->full_grid32 = d.pair32_grid;
   d.pseudo_chunks = 8;
   d.nl_cpl = 4;
-  d.p32_nch = (p.nl_cap + P32_CH - 1) / P32_CH;
+  {  // FP32 pair items: P32_CH candidates for each of the 32 / min(P_max, 32) lane groups
+    const int lgG = 5 - std::min(d.lgPmax_nb, 5);
+    d.p32_nch = (p.nl_cap + (P32_CH << lgG) - 1) / (P32_CH << lgG);
+  }
   d.nl = (int*)(w + p.o_nl);
   d.nl_cnt = (int*)(w + p.o_nlcnt);
   d.pl = (int*)(w + p.o_pl);

@@ -14,7 +14,7 @@ constexpr int MAX_CLASSES = 12;
 constexpr int SMALL_P = 64;     // types with P <= SMALL_P propagate in one fused tile kernel
 constexpr int BIG_MB = 8;       // modes (or beads) per CTA of the large-P transforms
 constexpr int PROP_SMEM_MAX = 200 * 1024;
-constexpr int P32_CH = 128;     // list candidates per FP32 pair item  // dynamic shared memory cap of the propagation kernels
+constexpr int P32_CH = 32;      // list candidates per lane group of one FP32 pair item  // dynamic shared memory cap of the propagation kernels
 // shared memory of one large-P transform CTA: the cos table and BIG_MB rows
 // of the 3N columns (forward: forces, q and p modes, plus the centroids)
 inline size_t big_prop_smem(int P, int N) { return sizeof(double) * ((size_t)P + (3 * (size_t)BIG_MB + 1) * 3 * N); }
@@ -102,7 +102,6 @@ struct Dev {
   float box_hi;             // box edge rounded to the 2^-12 A grid
   long long box_fix;        // box edge in 2^-48 A fixed point
   float screen_rc2;         // binary32 screen radius^2 (r_cut + 2e-3)^2
-  const float* dsf_tab32;   // the DSF interval table rounded to binary32 (FP32 force path)
   int full_list;            // 1: every row lists all partners (FP32 force path)
   int lgPmax_nb;            // log2 of the largest bead count among non-pseudo atoms
   int n_items32;            // FP32 pair items: n_nonp * 2^lgPmax_nb
@@ -150,7 +149,8 @@ struct Dev {
   longlong4_32a* Xi;               // [n_beads] the same in 2^-48 A fixed point (exact differences)
   float4* Xf;                  // [n_beads] binary32 positions on the 2^-12 A grid (screens)
   float4* Xl;                  // [n_beads] binary32 remainders: Xw = Xf + Xl to ~2^-37 A
-  float4* Xd;                  // [n_beads] binary32 offset of each bead from its atom's bead 0 (FP32 path; else null)
+  float4* Xd;                  // [n_beads] binary32 offset of each bead from its atom's bead 0, atom-major
+                               // inside each type block (off_t + k P_t + b); FP32 path only, else null
   double* ref;                 // [n_atoms*3] wrapped bead-0 reference positions
   double4_32a* refd;           // [n_nonp] the same by sorted position
   float4* reff;                // [n_nonp] binary32 copy, .w = log2 P (int bits)
