@@ -10,6 +10,7 @@
 
 #include <algorithm>
 
+#include "fixmath.cuh"
 #include "mixts_internal.cuh"
 
 namespace mx {
@@ -307,6 +308,20 @@ __device__ __forceinline__ void dsf_table(const double* tab, int hi, double s, d
   *fg = fma(q, x, c[6]);
 }
 
+// the same two quintics at a given offset x = s - s0 inside the interval
+__device__ __forceinline__ void dsf_poly(const double* c, double x, double* g, double* fg) {
+  double p = fma(c[5], x, c[4]);
+  double q = fma(c[11], x, c[10]);
+  p = fma(p, x, c[3]);
+  q = fma(q, x, c[9]);
+  p = fma(p, x, c[2]);
+  q = fma(q, x, c[8]);
+  p = fma(p, x, c[1]);
+  q = fma(q, x, c[7]);
+  *g = fma(p, x, c[0]);
+  *fg = fma(q, x, c[6]);
+}
+
 // analytic G and -2 dG/ds (r below the table range)
 __device__ __forceinline__ void dsf_direct(const Dev& d, double s, double* g, double* fg) {
   const double r = sqrt(s);
@@ -357,8 +372,19 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   const int cnt = min(d.nl_cnt[pos], d.nl_cap);
   const int* lst = d.nl + (size_t)pos * d.nl_cap;
   const double rc = d.rc;
-  const long long rc2_bits = __double_as_longlong(d.rc2);
-  const int slo_hi = __double2hiint(d.dsf_smin);
+  // r_cut^2 in the 2^-96 A^2 units of the integer squared distances (exact)
+  fm::u128 rc2q;
+  {
+    const unsigned long long b = fm::dbl_bits(d.rc2);
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const int sh = (int)((b >> 52) & 0x7FF) - 1075 + 96;  // in [0, 75] for 2^-44 <= r_cut^2 < 2^23
+    if (sh >= 64)
+      rc2q = fm::u128{m << (sh - 64), 0ull};
+    else if (sh > 0)
+      rc2q = fm::u128{m >> (64 - sh), m << sh};
+    else
+      rc2q = fm::u128{0ull, sh > -53 ? m >> (-sh) : 0ull};
+  }
   const float scr2 = d.screen_rc2;
   const int base = d.dsf_base;
   const int trow = ai.type * nt;
@@ -380,21 +406,23 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
     const float4 sf = shf[ent & 127];
     const float hx = (xjf.x - xif.x) + sf.x, hy = (xjf.y - xif.y) + sf.y, hz = (xjf.z - xif.z) + sf.z;
     if (hx * hx + hy * hy + hz * hz > scr2) continue;
-    // exact displacement in 2^-48 A fixed point, converted without the FP64 pipe
+    // exact displacement in 2^-48 A fixed point and its exact square in
+    // 2^-96 A^2: the cut-off test, the table interval and the offset inside
+    // it need no FP64 instruction
     const longlong4_32a sv = shi[ent & 127];
-    const double dx = fixpos_to_double((xj.x - xi.x) + sv.x);
-    const double dy = fixpos_to_double((xj.y - xi.y) + sv.y);
-    const double dz = fixpos_to_double((xj.z - xi.z) + sv.z);
-    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-    if (__double_as_longlong(r2) < rc2_bits) {
+    const long long ix = (xj.x - xi.x) + sv.x, iy = (xj.y - xi.y) + sv.y, iz = (xj.z - xi.z) + sv.z;
+    const fm::u128 q2 = fm::norm2(ix, iy, iz);
+    if (fm::lt128(q2, rc2q)) {
+      const int pq = fm::msb128(q2);
+      const double r2 = pq >= 0 ? fm::u128_to_dbl(q2, pq, 96) : 0.0;
       const int fl = flg[trow + tj];
       const PairPar pp = tab[trow + tj];
       double fr = 0.0;
       if (fl & 1) {
-        double g, fg;
-        const int hi = __double2hiint(r2);
-        if (hi >= slo_hi)
-          dsf_table(dtab + 12 * ((hi >> 14) - base), hi, r2, &g, &fg);
+        double g, fg, x = 0.0;
+        const int key = pq >= 6 ? fm::dsf_key(q2, pq, &x) : 0;
+        if (key >= base)
+          dsf_poly(dtab + 12 * (key - base), x, &g, &fg);
         else
           dsf_direct(d, r2, &g, &fg);
         ec = fma(pp.qq, g, ec);
@@ -411,8 +439,10 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
         fr += (6.0 * pp.e4 * (2.0 * sr12 - sr6) * rinv + pp.dvrc) * rinv;
         ++nlj;
       }
-      const long long kx = fix44(fr * dx, wsh, &bad), ky = fix44(fr * dy, wsh, &bad),
-                      kz = fix44(fr * dz, wsh, &bad);
+      // f d in the 2^-44 (times 1/P_i) fixed point, rounded once from the
+      // exact product of the mantissa of f and the integer displacement
+      const long long kx = fm::mulfix(fr, ix, 4 + wsh, &bad), ky = fm::mulfix(fr, iy, 4 + wsh, &bad),
+                      kz = fm::mulfix(fr, iz, 4 + wsh, &bad);
       fix -= kx;
       fiy -= ky;
       fiz -= kz;
