@@ -240,32 +240,13 @@ def batch_variant(torch, stream, flush, dev, steps):
 
 
 def _run_observables(torch, stream, dev, sysm, dt, precision, n_eq, n_samp, every, pairs, dr=0.02, nbins=400):
-    """Equilibrate, then sample every `every` steps: per-type KE_cv and R_g^2
-    (mean and 8-block standard error) and g(r) of the given type pairs."""
-    import numpy as np
-    from paper_2411_11988_gb300 import MixTS
+    """One sampled run through the package's analysis module: (KE_cv stats,
+    Rg2 stats, g(r) per pair)."""
+    from paper_2411_11988_gb300 import MixTS, analysis
     m = MixTS(sysm, T=300.0, dt=dt, tau=100.0, seed=0, device=str(dev), stream=stream, precision=precision)
-    m.step(n_eq)
-    hist = {k: torch.zeros(nbins, dtype=torch.int64, device=dev) for k in pairs}
-    ke, rg = [], []
-    frames = n_samp // every
-    with torch.cuda.stream(stream):
-        for _ in range(frames):
-            m.step(every)
-            for (a, b), h in hist.items():
-                m.rdf_accumulate(a, b, h, dr)
-            e = m.estimators()
-            ke.append(e["KE_cv"])
-            rg.append(e["Rg2"])
-    g = {k: m.rdf_normalise(k[0], k[1], h, frames, dr) for k, h in hist.items()}
+    res = analysis.sample(m, n_eq, n_samp, every, pairs, dr, nbins)
     m.close()
-
-    def stat(x):
-        x = np.asarray(x, dtype=np.float64)
-        b = x[: len(x) // 8 * 8].reshape(8, -1, *x.shape[1:]).mean(axis=1)
-        return b.mean(axis=0), b.std(axis=0, ddof=1) / np.sqrt(8)
-
-    return stat(ke), stat(rg), g
+    return res["KE_cv"], res["Rg2"], res["g"]
 
 
 def observables(torch, stream, dev):
@@ -303,6 +284,13 @@ def observables(torch, stream, dev):
         _, (rg_m, rg_e), g = _run_observables(torch, stream, dev, sie, ie["dt_fs"], prec, 2000, 8000, 10, [(2, 0)])
         res[key] = (rg_m[3], rg_e[3], g[(2, 0)])
     rg64, rg32 = res["fp64"], res["fp32_forces"]
+    # partial quantisation (Sec. "System I"): H and O bead counts chosen independently
+    from paper_2411_11988_gb300 import analysis
+    combos = [(1, 1), (4, 1), (1, 4), (4, 4), (32, 1), (32, 4), (32, 32)]
+    out["partial_quantisation"] = dict(
+        steps="2000 equilibration + 3000 sampled (every 10) per bead-count pair, dt 0.25 fs, FP64",
+        **analysis.quantisation_sweep(lambda ph, po: build_system(ph, po, 0), combos, dt=DT, n_eq=2000, n_samp=3000,
+                                      every=10, device=str(dev), stream=stream))
     out["ion_electron"] = {
         "steps": "2000 equilibration + 8000 sampled (every 10), dt 0.1 fs",
         "electron_Rg_A": {"fp64": [float(np.sqrt(rg64[0])), float(rg64[1] / (2 * np.sqrt(rg64[0])))],

@@ -308,18 +308,25 @@ __device__ __forceinline__ void dsf_table(const double* tab, int hi, double s, d
   *fg = fma(q, x, c[6]);
 }
 
-// the same two quintics at a given offset x = s - s0 inside the interval
-__device__ __forceinline__ void dsf_poly(const double* c, double x, double* g, double* fg) {
-  double p = fma(c[5], x, c[4]);
-  double q = fma(c[11], x, c[10]);
-  p = fma(p, x, c[3]);
-  q = fma(q, x, c[9]);
-  p = fma(p, x, c[2]);
-  q = fma(q, x, c[8]);
-  p = fma(p, x, c[1]);
-  q = fma(q, x, c[7]);
-  *g = fma(p, x, c[0]);
-  *fg = fma(q, x, c[6]);
+constexpr size_t PAIR64_SMEM_PER_INTERVAL = 6 * sizeof(double) + 8 * sizeof(float);
+
+// The same two quintics at a given offset x = s - s0 inside the interval,
+// split by order: c0 + c1 x + c2 x^2 in binary64 (c = the interval's
+// [c0 c1 c2 q0 q1 q2]) and x^3 (c3 + c4 x + c5 x^2) in binary32 (t = [c3 c4 c5
+// - q3 q4 q5 -]). With x below 1.1 % of s the cubic tail is below ~1e-6 of
+// the value, so its binary32 rounding stays near 1e-13 relative.
+__device__ __forceinline__ void dsf_poly_split(const double* c, const float* t, double x, double* g, double* fg) {
+  // binary32 x by truncating the binary64 bit fields (x >= 0)
+  const unsigned long long xb = (unsigned long long)__double_as_longlong(x);
+  const int fe = (int)((xb >> 52) & 0x7FF) - 1023 + 127;
+  const float xf = fe > 0 ? __uint_as_float(((unsigned)fe << 23) | (unsigned)((xb >> 29) & 0x7FFFFFull)) : 0.0f;
+  const float x3 = xf * xf * xf;
+  const float tg = fmaf(fmaf(t[2], xf, t[1]), xf, t[0]) * x3;
+  const float tq = fmaf(fmaf(t[6], xf, t[5]), xf, t[4]) * x3;
+  const double p = fma(fma(c[2], x, c[1]), x, c[0]);
+  const double q = fma(fma(c[5], x, c[4]), x, c[3]);
+  *g = p + f2d_bits(tg);
+  *fg = q + f2d_bits(tq);
 }
 
 // analytic G and -2 dG/ds (r below the table range)
@@ -334,14 +341,25 @@ __device__ __forceinline__ void dsf_direct(const Dev& d, double s, double* g, do
 }
 
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
-  extern __shared__ double dtab[];  // DSF interval table, 12 doubles per interval
+  extern __shared__ double dtab[];  // DSF interval table: 6 doubles, then 8 floats per interval
   __shared__ PairPar tab[MT * MT];
   __shared__ int flg[MT * MT];      // bit 0: Coulomb, bit 1: Lennard-Jones
   __shared__ longlong4_32a shi[125];
   __shared__ float4 shf[125];
   __shared__ int tN[MT], tLg[MT];
   const int nt = d.n_types;
-  for (int e = threadIdx.x; e < 12 * d.dsf_nint; e += blockDim.x) dtab[e] = d.dsf_tab[e];
+  float* ftab = (float*)(dtab + 6 * d.dsf_nint);
+  for (int e = threadIdx.x; e < d.dsf_nint; e += blockDim.x) {
+    const double* c = d.dsf_tab + 12 * e;
+    for (int k = 0; k < 3; ++k) {
+      dtab[6 * e + k] = c[k];
+      dtab[6 * e + 3 + k] = c[6 + k];
+      ftab[8 * e + k] = (float)c[3 + k];
+      ftab[8 * e + 4 + k] = (float)c[9 + k];
+    }
+    ftab[8 * e + 3] = 0.0f;
+    ftab[8 * e + 7] = 0.0f;
+  }
   for (int e = threadIdx.x; e < nt; e += blockDim.x) {
     tN[e] = d.N[e];
     tLg[e] = d.log2P[e];
@@ -422,7 +440,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
         double g, fg, x = 0.0;
         const int key = pq >= 6 ? fm::dsf_key(q2, pq, &x) : 0;
         if (key >= base)
-          dsf_poly(dtab + 12 * (key - base), x, &g, &fg);
+          dsf_poly_split(dtab + 6 * (key - base), ftab + 8 * (key - base), x, &g, &fg);
         else
           dsf_direct(d, r2, &g, &fg);
         ec = fma(pp.qq, g, ec);
@@ -964,7 +982,7 @@ void pair_grids(int nt, int nint, int* g64, int* g32) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   (void)nt;
   cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_pair64, PAIR_THREADS, sizeof(double) * 12 * (size_t)nint);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_pair64, PAIR_THREADS, PAIR64_SMEM_PER_INTERVAL * (size_t)nint);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_pair32, PAIR_THREADS, 0);
   *g64 = std::max(1, b64) * std::max(1, sms);
   *g32 = std::max(1, b32) * std::max(1, sms);
@@ -980,7 +998,7 @@ int launch_pair(const Dev& d, cudaStream_t s) {
     return 1;
   }
   if (d.n_pitems == 0) return 0;
-  const size_t smem = sizeof(double) * 12 * (size_t)d.dsf_nint;
+  const size_t smem = PAIR64_SMEM_PER_INTERVAL * (size_t)d.dsf_nint;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
