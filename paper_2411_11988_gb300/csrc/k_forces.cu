@@ -345,7 +345,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   __shared__ PairPar tab[MT * MT];
   __shared__ int flg[MT * MT];      // bit 0: Coulomb, bit 1: Lennard-Jones
   __shared__ longlong4_32a shi[125];
-  __shared__ float4 shf[125];
   __shared__ int tN[MT], tLg[MT];
   const int nt = d.n_types;
   float* ftab = (float*)(dtab + 6 * d.dsf_nint);
@@ -372,7 +371,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   for (int e = threadIdx.x; e < 125; e += blockDim.x) {
     const int nx = e / 25 - 2, ny = (e / 5) % 5 - 2, nz = e % 5 - 2;
     shi[e] = make_longlong4_32a(nx * d.box_fix, ny * d.box_fix, nz * d.box_fix, 0);
-    shf[e] = make_float4(nx * d.box_hi, ny * d.box_hi, nz * d.box_hi, 0.0f);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -385,7 +383,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   const AtomInfo ai = d.ainfo[pos];
   const int row_i = ai.row0 + b * ai.stride;
   const longlong4_32a xi = d.Xi[row_i];
-  const float4 xif = d.Xf[row_i];
   const int wsh = ai.log2P;  // weight 1/P_i = 2^-wsh
   const int cnt = min(d.nl_cnt[pos], d.nl_cap);
   const int* lst = d.nl + (size_t)pos * d.nl_cap;
@@ -403,7 +400,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
     else
       rc2q = fm::u128{0ull, sh > -53 ? m >> (-sh) : 0ull};
   }
-  const float scr2 = d.screen_rc2;
   const int base = d.dsf_base;
   const int trow = ai.type * nt;
   long long fix = 0, fiy = 0, fiz = 0;
@@ -417,13 +413,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
     const int tj = (ent >> 7) & 15;
     const int bj = b >> (ai.log2P - tLg[tj]);
     const int row_j = (ent >> 11) + bj * tN[tj];
-    const float4 xjf = d.Xf[row_j];
     const longlong4_32a xj = d.Xi[row_j];
-    // binary32 screen on the 2^-12 A grid: exact differences, error of the
-    // dropped low parts bounded; only candidates near or inside r_cut go on
-    const float4 sf = shf[ent & 127];
-    const float hx = (xjf.x - xif.x) + sf.x, hy = (xjf.y - xif.y) + sf.y, hz = (xjf.z - xif.z) + sf.z;
-    if (hx * hx + hy * hy + hz * hz > scr2) continue;
     // exact displacement in 2^-48 A fixed point and its exact square in
     // 2^-96 A^2: the cut-off test, the table interval and the offset inside
     // it need no FP64 instruction
