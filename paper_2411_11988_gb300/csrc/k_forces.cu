@@ -794,7 +794,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
   const int* lst = d.pl + (size_t)e * d.pl_cap;
   const double rc = d.rc, rc2 = d.rc2;
   double fex = 0.0, fey = 0.0, fez = 0.0, ep = 0.0, vir = 0.0;
-  int nev = 0;
+  int nev = 0, bad = 0;
+  const int ps_hi_min = __double2hiint(d.ps_smin);
   for (int k = chunk * 32 + lane; k < cnt; k += 32 * nch) {
     const int ent = lst[k];
     const int c = ent >> 7;
@@ -808,19 +809,30 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
     const double dz = (xc.z - xe.z) + sv.z;
     const double r2 = dx * dx + dy * dy + dz * dz;
     if (r2 < rc2) {
-      const PseudoPar pp = tab[ac.type];
-      const double r = sqrt(r2);
-      double v, dv;
-      pseudo_raw(pp, r, &v, &dv);
-      ep += wgt * (v - pp.vrc - (r - rc) * pp.dvrc);
-      const double fr = -wgt * (dv - pp.dvrc) / r;  // force on the site along d
+      // shifted-force value and -(dV/dr - dV/dr(rc)) / r: from the site
+      // type's interval table, or analytic below its range (and when the
+      // parameters differ from the tabulated ones)
+      double vsf, fru;
+      const int hi = __double2hiint(r2);
+      if (d.ps_tab && hi >= ps_hi_min) {
+        dsf_table(d.ps_tab + 12 * ((size_t)ac.type * d.ps_nint + ((hi >> 14) - d.ps_base)), hi, r2, &vsf, &fru);
+      } else {
+        const PseudoPar pp = tab[ac.type];
+        const double r = sqrt(r2);
+        double v, dv;
+        pseudo_raw(pp, r, &v, &dv);
+        vsf = v - pp.vrc - (r - rc) * pp.dvrc;
+        fru = -(dv - pp.dvrc) / r;
+      }
+      ep += wgt * vsf;
+      const double fr = wgt * fru;  // force on the site along d
       const double fx = fr * dx, fy = fr * dy, fz = fr * dz;
       fex -= fx;
       fey -= fy;
       fez -= fz;
       vir += fr * r2;
       ++nev;
-      fadd3(d.F_fix, row_c, fx, fy, fz, d.err);
+      fadd3w(d.F_fix, row_c, fx, fy, fz, &bad);
     }
   }
   fex = warp_sum(fex);
@@ -829,8 +841,10 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
   ep = warp_sum(ep);
   vir = warp_sum(vir);
   nev = warp_sumi(nev);
+  bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
     fadd3(d.F_fix, row_e, fex, fey, fez, d.err);
+    if (bad) atomicOr(d.err, ERR_NONFINITE);
     eadd(d.E_fix, E_PSEUDO, ep);
     eadd(d.E_fix, E_VIRIAL, vir);
     atomicAdd(d.E_fix + E_NPEVAL, (unsigned long long)nev);

@@ -71,6 +71,8 @@ struct Plan {
   std::vector<double> dsf;     // DSF interval table
   std::vector<double> charge, eps, sig, pp_sig, pp_A, pp_b;  // raw force-field parameters (theta variant)
   int dsf_nint = 0, dsf_elo = -2;
+  std::vector<double> ps_tab;  // pseudopotential tables (electron systems)
+  int ps_nint = 0, ps_elo = -6;
   std::vector<int> cm_off, mc_off, big_slot0, sb_off;
   int n_spread_big = 0;
   std::vector<ModeCoef> mc;
@@ -87,7 +89,7 @@ struct Plan {
   size_t o_tab = 0, tab_bytes = 0;
   size_t o_ainfo, o_pos_atom, o_pos_mol, o_atom_of_tk, o_ainfo_atom, o_pos_of_atom, o_is_pseudo, o_pseudo_atom, o_pinfo,
       o_pairpar, o_pspar, o_bitems, o_bond_atoms, o_bond_par, o_ang_atoms, o_ang_par, o_cm, o_mc, o_tiles,
-      o_slot_type, o_dsf, o_pairpar_alt, o_pspar_alt, o_pc, o_gacc;
+      o_slot_type, o_dsf, o_pstab, o_pairpar_alt, o_pspar_alt, o_pc, o_gacc;
   size_t o_state = 0, state_bytes = 0;
   size_t o_xd = 0;
   size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_xl, o_ref, o_refd, o_reff, o_spread, o_spread_big, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
@@ -152,6 +154,53 @@ static void fit_quintic(const long double* tn, const long double* val, long doub
     out[j] = (double)(A[j][6] / A[j][j] / hk);
     hk *= h;
   }
+}
+
+// Interval table of a function of s = r^2 and of a second one (the force
+// over r), 64 sub-intervals per octave from 2^elo to past rc^2, a quintic of
+// each fitted at Chebyshev nodes in long double.
+template <class F1, class F2>
+static std::vector<double> interval_table(F1 f, F2 df, double rc, int elo, int* nint_out) {
+  typedef long double LD;
+  const LD pil = 3.141592653589793238462643383279502884L;
+  int ehi = elo;
+  while (ldexp(1.0, ehi) <= rc * rc) ++ehi;
+  const int nint = (ehi - elo) * 64;
+  std::vector<double> tab(12 * (size_t)nint);
+  LD tn[6];
+  for (int i = 0; i < 6; ++i) tn[i] = (1.0L - cosl((2 * i + 1) * pil / 12.0L)) / 2.0L;
+  for (int k = 0; k < nint; ++k) {
+    const int oct = k / 64, sub = k % 64;
+    const LD s0 = ldexpl(1.0L + sub / 64.0L, elo + oct);
+    const LD h = ldexpl(1.0L / 64.0L, elo + oct);
+    LD v[6], dv[6];
+    for (int i = 0; i < 6; ++i) {
+      v[i] = f(s0 + tn[i] * h);
+      dv[i] = df(s0 + tn[i] * h);
+    }
+    fit_quintic(tn, v, h, &tab[12 * (size_t)k]);
+    fit_quintic(tn, dv, h, &tab[12 * (size_t)k + 6]);
+  }
+  *nint_out = nint;
+  return tab;
+}
+
+// Shifted-force pseudopotential of one site type (Sec. "System II": V(r) =
+// -k_e q erf(r/sigma)/r + A exp(-r/b), truncated at r_cut with value and slope
+// shifted to zero): the value and -(dV/dr - dV/dr(r_cut)) / r as functions
+// of s = r^2.
+static std::vector<double> pseudo_table(double kq, double sig, double A, double b, double rc, int elo,
+                                        int* nint_out) {
+  typedef long double LD;
+  const LD pil = 3.141592653589793238462643383279502884L;
+  auto V = [&](LD r) { return -(LD)kq * erfl(r / sig) / r + (LD)A * expl(-r / b); };
+  auto dV = [&](LD r) {
+    const LD x = r / sig;
+    return -(LD)kq * (2.0L / sqrtl(pil) * expl(-x * x) / (sig * r) - erfl(x) / (r * r)) - (LD)A / b * expl(-r / b);
+  };
+  const LD R = rc, vr = V(R), dvr = dV(R);
+  return interval_table([&](LD s) { const LD r = sqrtl(s); return V(r) - vr - (r - R) * dvr; },
+                        [&](LD s) { const LD r = sqrtl(s); return -(dV(r) - dvr) / r; }, rc, elo, nint_out);
 }
 
 std::vector<double> dsf_table(double alpha, double rc, int elo, int* nint_out) {
@@ -473,6 +522,23 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
     const double full = rho * 4.0 / 3.0 * PI * Rp * Rp * Rp;
     p.pl_cap = std::max(64, std::min((int)(1.3 * full) + 128, 125 * std::max(1, p.n_nonp)));
   }
+  if (p.n_pseudo > 0) {  // pseudopotential tables of the site types
+    for (int t = 0; t < p.nt; ++t) {
+      const PseudoPar& pp = p.pspar[t];
+      std::vector<double> tt;
+      int nint = 0;
+      if (!s->pseudo_type[t] && pp.sig > 0.0 && pp.b > 0.0) {
+        tt = pseudo_table(pp.kq, pp.sig, pp.A, pp.b, prm->r_cut, p.ps_elo, &nint);
+      } else {
+        int ehi = p.ps_elo;
+        while (ldexp(1.0, ehi) <= prm->r_cut * prm->r_cut) ++ehi;
+        nint = (ehi - p.ps_elo) * 64;
+        tt.assign(12 * (size_t)nint, 0.0);
+      }
+      p.ps_nint = nint;
+      p.ps_tab.insert(p.ps_tab.end(), tt.begin(), tt.end());
+    }
+  }
   // workspace layout: read-only tables first, then the state
   Arena& A = p.ar;
   p.o_ainfo = A.add(sizeof(AtomInfo) * std::max(1, p.n_nonp));
@@ -496,6 +562,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_tiles = A.add(sizeof(PropTile) * std::max<size_t>(1, p.tiles.size()));
   p.o_slot_type = A.add(sizeof(int) * std::max<size_t>(1, p.slot_type.size()));
   p.o_dsf = A.add(sizeof(double) * p.dsf.size());
+  p.o_pstab = A.add(sizeof(double) * std::max<size_t>(1, p.ps_tab.size()));
   p.o_pairpar_alt = A.add(sizeof(PairPar) * MT * MT);
   p.o_pspar_alt = A.add(sizeof(PseudoPar) * MT);
   p.o_pc = A.add(sizeof(double) * 8 * MT);
@@ -703,6 +770,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   put(img, p.o_tiles, p.tiles);
   put(img, p.o_slot_type, p.slot_type);
   put(img, p.o_dsf, p.dsf);
+  if (!p.ps_tab.empty()) put(img, p.o_pstab, p.ps_tab);
   mixts_status st = cuda_check(h, cudaMemcpy(h->ws, img.data(), p.tab_bytes, cudaMemcpyHostToDevice), "upload tables");
   if (st == MIXTS_OK)
     st = cuda_check(h, cudaMemsetAsync(h->ws + p.tab_bytes, 0, p.ar.size - p.tab_bytes, h->stream), "clear state");
@@ -745,6 +813,10 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.dsf_nint = p.dsf_nint;
   d.dsf_base = (1023 + p.dsf_elo) << 6;
   d.dsf_smin = ldexp(1.0, p.dsf_elo);
+  d.ps_tab = p.ps_tab.empty() ? nullptr : (const double*)(h->ws + p.o_pstab);
+  d.ps_nint = p.ps_nint;
+  d.ps_base = (1023 + p.ps_elo) << 6;
+  d.ps_smin = ldexp(1.0, p.ps_elo);
   d.box_hi = (float)(rint(sys->box * 4096.0) / 4096.0);
   d.box_fix = llrint(sys->box * 281474976710656.0);
   d.screen_rc2 = (float)((prm->r_cut + 2e-3) * (prm->r_cut + 2e-3));
@@ -1644,6 +1716,7 @@ extern "C" MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int ta, i
   dd.pspar = (const PseudoPar*)(w + p.o_pspar_alt);
   dd.precision = MIXTS_FP64;
   dd.full_list = 0;
+  dd.ps_tab = nullptr;  // the tables hold the handle's parameters, not theta's
   unsigned long long* gacc = (unsigned long long*)(w + p.o_gacc);
   cudaMemcpyAsync(w + p.o_pairpar_alt, pairpar.data(), sizeof(PairPar) * MT * MT, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(w + p.o_pspar_alt, pspar.data(), sizeof(PseudoPar) * MT, cudaMemcpyHostToDevice, s);

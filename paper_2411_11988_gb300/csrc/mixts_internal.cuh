@@ -99,6 +99,11 @@ struct Dev {
   const double* dsf_tab;
   int dsf_nint, dsf_base;   // interval count; (1023 + e_lo) << 6
   double dsf_smin;          // 2^e_lo
+  // pseudopotential interval tables, one per site type (same layout as the
+  // DSF table: shifted-force V and -(dV/dr - dV/dr(rc)) / r); null: analytic
+  const double* ps_tab;     // [n_types][ps_nint][12]
+  int ps_nint, ps_base;     // intervals per type; (1023 + e_lo) << 6
+  double ps_smin;           // 2^e_lo
   float box_hi;             // box edge rounded to the 2^-12 A grid
   long long box_fix;        // box edge in 2^-48 A fixed point
   float screen_rc2;         // binary32 screen radius^2 (r_cut + 2e-3)^2
