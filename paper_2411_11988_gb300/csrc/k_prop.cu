@@ -299,12 +299,16 @@ __global__ void k_mirror_from_q(Dev d) {
 // ---------------------------------------------------------------------------
 // large-P path
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double cjk(const double* T, int P, int j, int k, double rP, double r2P) {
+// element (j, k) of the orthonormal normal-mode matrix; T holds
+// sqrt(2/P) cos(2 pi m / P), so the cos and sin modes need no multiply
+__device__ __forceinline__ double cjk(const double* T, int P, int j, int k, double rP) {
   if (k == 0) return rP;
-  if (2 * k < P) return r2P * T[(j * k) & (P - 1)];
+  if (2 * k < P) return T[(j * k) & (P - 1)];
   if (2 * k == P) return (j & 1) ? -rP : rP;
-  return r2P * T[(j * k - P / 4) & (P - 1)];  // sin(2 pi jk / P) = cos(2 pi (jk - P/4) / P)
+  return T[(j * k - P / 4) & (P - 1)];  // sin(2 pi jk / P) = cos(2 pi (jk - P/4) / P)
 }
+
+constexpr int BIG_CC = 3;  // columns (one atom's x, y, z) per warp of the large-P transforms
 
 constexpr int BIG_THREADS = 256;
 
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_fwd(Dev d, int t, int mode)
   __shared__ long long s_step;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int kb = blockIdx.x * BIG_MB;
-  const double rP = rsqrt((double)P), r2P = sqrt(2.0 / P);
+  const double rP = rsqrt((double)P);
   const double* cmg = d.cm + d.cm_off[t];
   const ModeCoef* mcf = d.mc + d.mc_off[t];
   const size_t base = (size_t)d.off[t] * 3;  // element (j, c) at base + j*C + c
@@ -331,25 +335,42 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_fwd(Dev d, int t, int mode)
   __syncthreads();
   const bool need_f = (mode & (PM_END | PM_START)) != 0;
   const int nout = BIG_MB * C;
-  for (int o = warp; o < nout; o += nw) {
-    const int k = kb + o / C, c = o - (o / C) * C;
-    double af = 0.0, aq = 0.0, ap = 0.0;
+  // one warp per (mode, group of BIG_CC columns): each matrix element is
+  // looked up once and feeds BIG_CC independent FMA chains
+  const int ncg = (C + BIG_CC - 1) / BIG_CC;
+  for (int o = warp; o < BIG_MB * ncg; o += nw) {
+    const int kk = o / ncg, c0 = (o - kk * ncg) * BIG_CC;
+    const int k = kb + kk;
+    const int ncol = min(BIG_CC, C - c0);
+    double af[BIG_CC], aq[BIG_CC], ap[BIG_CC];
+#pragma unroll
+    for (int u = 0; u < BIG_CC; ++u) af[u] = aq[u] = ap[u] = 0.0;
     for (int j = lane; j < P; j += 32) {
-      const double cj = cjk(T, P, j, k, rP, r2P);
-      const size_t g = base + (size_t)j * C + c;
-      if (need_f) af = fma(cj, fix_to_double(d.F_fix[g], FINV), af);
-      if (mode & PM_IMPORT) {
-        aq = fma(cj, d.q[g], aq);
-        ap = fma(cj, d.p[g], ap);
+      const double cj = cjk(T, P, j, k, rP);
+      const size_t g = base + (size_t)j * C + c0;
+#pragma unroll
+      for (int u = 0; u < BIG_CC; ++u) {
+        if (u < ncol) {
+          if (need_f) af[u] = fma(cj, fix_to_double(d.F_fix[g + u], FINV), af[u]);
+          if (mode & PM_IMPORT) {
+            aq[u] = fma(cj, d.q[g + u], aq[u]);
+            ap[u] = fma(cj, d.p[g + u], ap[u]);
+          }
+        }
       }
     }
-    af = warp_sum(af);
-    aq = warp_sum(aq);
-    ap = warp_sum(ap);
-    if (lane == 0) {
-      Fn[o] = af;
-      Qi[o] = aq;
-      Pi[o] = ap;
+#pragma unroll
+    for (int u = 0; u < BIG_CC; ++u) {
+      if (need_f) af[u] = warp_sum(af[u]);
+      if (mode & PM_IMPORT) {
+        aq[u] = warp_sum(aq[u]);
+        ap[u] = warp_sum(ap[u]);
+      }
+      if (lane == 0 && u < ncol) {
+        Fn[kk * C + c0 + u] = af[u];
+        Qi[kk * C + c0 + u] = aq[u];
+        Pi[kk * C + c0 + u] = ap[u];
+      }
     }
   }
   double part[NPART] = {0, 0, 0, 0, 0, 0};
@@ -436,7 +457,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_inv(Dev d, int t, int mode)
   double* Qc = T + P;                 // [(BIG_MB+1)*C], row 0 = bead 0, rows 1.. = own beads
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int jb = blockIdx.x * BIG_MB;
-  const double rP = rsqrt((double)P), r2P = sqrt(2.0 / P);
+  const double rP = rsqrt((double)P);
   const double* cmg = d.cm + d.cm_off[t];
   const size_t base = (size_t)d.off[t] * 3;
   for (int e = tid; e < P; e += blockDim.x) T[e] = cmg[e];
@@ -444,21 +465,34 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_inv(Dev d, int t, int mode)
   const bool qc = (mode & (PM_START | PM_QCART)) != 0;
   const int nout = (BIG_MB + 1) * C;
   if (qc || (mode & PM_PCART)) {
-    for (int o = warp; o < nout; o += nw) {
-      const int r = o / C, c = o - (o / C) * C;
+    // one warp per (bead, group of BIG_CC columns), as in the forward pass
+    const int ncg = (C + BIG_CC - 1) / BIG_CC;
+    for (int o = warp; o < (BIG_MB + 1) * ncg; o += nw) {
+      const int r = o / ncg, c0 = (o - r * ncg) * BIG_CC;
       const int j = r == 0 ? 0 : jb + r - 1;
-      double aq = 0.0, ap = 0.0;
+      const int ncol = min(BIG_CC, C - c0);
+      double aq[BIG_CC], ap[BIG_CC];
+#pragma unroll
+      for (int u = 0; u < BIG_CC; ++u) aq[u] = ap[u] = 0.0;
       for (int k = lane; k < P; k += 32) {
-        const double cj = cjk(T, P, j, k, rP, r2P);
-        const size_t g = base + (size_t)k * C + c;
-        if (qc) aq = fma(cj, d.q_nm[g], aq);
-        if (mode & PM_PCART) ap = fma(cj, d.p_nm[g], ap);
+        const double cj = cjk(T, P, j, k, rP);
+        const size_t g = base + (size_t)k * C + c0;
+#pragma unroll
+        for (int u = 0; u < BIG_CC; ++u) {
+          if (u < ncol) {
+            if (qc) aq[u] = fma(cj, d.q_nm[g + u], aq[u]);
+            if (mode & PM_PCART) ap[u] = fma(cj, d.p_nm[g + u], ap[u]);
+          }
+        }
       }
-      aq = warp_sum(aq);
-      ap = warp_sum(ap);
-      if (lane == 0) {
-        if (qc) Qc[o] = aq;
-        if ((mode & PM_PCART) && r > 0) d.p[base + (size_t)j * C + c] = ap;
+#pragma unroll
+      for (int u = 0; u < BIG_CC; ++u) {
+        if (qc) aq[u] = warp_sum(aq[u]);
+        if (mode & PM_PCART) ap[u] = warp_sum(ap[u]);
+        if (lane == 0 && u < ncol) {
+          if (qc) Qc[r * C + c0 + u] = aq[u];
+          if ((mode & PM_PCART) && r > 0) d.p[base + (size_t)j * C + c0 + u] = ap[u];
+        }
       }
     }
   }

@@ -462,8 +462,9 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
             v = r2P * T[(j * k - P / 4) & (P - 1)];
           p.cm.push_back(v);
         }
-    } else {
-      for (int k = 0; k < P; ++k) p.cm.push_back(T[k]);
+    } else {  // cosine table pre-scaled by sqrt(2/P), the weight of the cos/sin modes
+      const double r2P = sqrt(2.0 / P);
+      for (int k = 0; k < P; ++k) p.cm.push_back(r2P * T[k]);
     }
     p.mc_off[t] = (int)p.mc.size();
     for (int k = 0; k < P; ++k) {
