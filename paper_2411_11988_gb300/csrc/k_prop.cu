@@ -310,11 +310,15 @@ __device__ __forceinline__ double cjk(const double* T, int P, int j, int k, doub
 
 constexpr int BIG_CC = 3;  // columns (one atom's x, y, z) per warp of the large-P transforms
 
-constexpr int BIG_THREADS = 256;
+// launch shapes of the large-P transforms, and the number of warps that
+// share one output group's sum (measured: the forward pass is fastest with 8
+// warps and no split, the inverse with 32 warps and a 4-way split)
+constexpr int FWD_THREADS = 256, FWD_SPLIT = 1;
+constexpr int INV_THREADS = 1024, INV_SPLIT = 4;
 
 // forward transforms (C^T x) of this block's BIG_MB modes and the elementwise
 // step on them
-__global__ void __launch_bounds__(BIG_THREADS) k_big_fwd(Dev d, int t, int mode) {
+__global__ void __launch_bounds__(FWD_THREADS) k_big_fwd(Dev d, int t, int mode) {
   extern __shared__ double sm[];
   const int P = d.P[t], N = d.N[t], C = 3 * N;
   double* T = sm;                       // [P]
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_fwd(Dev d, int t, int mode)
   double* Qi = Fn + BIG_MB * C;         // [BIG_MB*C] imported q modes
   double* Pi = Qi + BIG_MB * C;         // [BIG_MB*C]
   double* qbar = Pi + BIG_MB * C;       // [C]
-  __shared__ double red[(BIG_THREADS / 32) * NPART];
+  __shared__ double red[(FWD_THREADS / 32) * NPART];
   __shared__ long long s_step;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int kb = blockIdx.x * BIG_MB;
@@ -335,17 +339,22 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_fwd(Dev d, int t, int mode)
   __syncthreads();
   const bool need_f = (mode & (PM_END | PM_START)) != 0;
   const int nout = BIG_MB * C;
-  // one warp per (mode, group of BIG_CC columns): each matrix element is
-  // looked up once and feeds BIG_CC independent FMA chains
+  // FWD_SPLIT warps per (mode, group of BIG_CC columns), each over a share of
+  // the beads: every matrix element is looked up once and feeds BIG_CC
+  // independent FMA chains; the shares are added in a fixed order
+  __shared__ double pbuf[FWD_THREADS / 32][3 * BIG_CC];
   const int ncg = (C + BIG_CC - 1) / BIG_CC;
-  for (int o = warp; o < BIG_MB * ncg; o += nw) {
-    const int kk = o / ncg, c0 = (o - kk * ncg) * BIG_CC;
-    const int k = kb + kk;
-    const int ncol = min(BIG_CC, C - c0);
+  const int items = BIG_MB * ncg, slots = nw / FWD_SPLIT;
+  const int qs = warp % FWD_SPLIT, slot = warp / FWD_SPLIT;
+  for (int b0 = 0; b0 < items; b0 += slots) {
+    const int o = b0 + slot;
     double af[BIG_CC], aq[BIG_CC], ap[BIG_CC];
 #pragma unroll
     for (int u = 0; u < BIG_CC; ++u) af[u] = aq[u] = ap[u] = 0.0;
-    for (int j = lane; j < P; j += 32) {
+    const int kk = o / ncg, c0 = (o - kk * ncg) * BIG_CC;
+    const int k = kb + kk;
+    const int ncol = o < items ? min(BIG_CC, C - c0) : 0;
+    for (int j = lane + 32 * qs; ncol > 0 && j < P; j += 32 * FWD_SPLIT) {
       const double cj = cjk(T, P, j, k, rP);
       const size_t g = base + (size_t)j * C + c0;
 #pragma unroll
@@ -366,12 +375,26 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_fwd(Dev d, int t, int mode)
         aq[u] = warp_sum(aq[u]);
         ap[u] = warp_sum(ap[u]);
       }
-      if (lane == 0 && u < ncol) {
-        Fn[kk * C + c0 + u] = af[u];
-        Qi[kk * C + c0 + u] = aq[u];
-        Pi[kk * C + c0 + u] = ap[u];
+      if (lane == 0) {
+        pbuf[warp][u] = af[u];
+        pbuf[warp][BIG_CC + u] = aq[u];
+        pbuf[warp][2 * BIG_CC + u] = ap[u];
       }
     }
+    __syncthreads();
+    if (tid < slots * 3 * BIG_CC) {
+      const int sl = tid / (3 * BIG_CC), v = tid - sl * (3 * BIG_CC);
+      const int kind = v / BIG_CC, u = v - kind * BIG_CC;
+      const int oo = b0 + sl;
+      const int kk2 = oo / ncg, c2 = (oo - kk2 * ncg) * BIG_CC;
+      if (oo < items && u < min(BIG_CC, C - c2)) {
+        double sum = 0.0;
+        for (int w = 0; w < FWD_SPLIT; ++w) sum += pbuf[sl * FWD_SPLIT + w][v];
+        double* dst = kind == 0 ? Fn : (kind == 1 ? Qi : Pi);
+        dst[kk2 * C + c2 + u] = sum;
+      }
+    }
+    __syncthreads();
   }
   double part[NPART] = {0, 0, 0, 0, 0, 0};
   if ((mode & PM_END) && (mode & PM_EST)) {
@@ -450,7 +473,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_fwd(Dev d, int t, int mode)
 }
 
 // inverse transforms (C x) of this block's BIG_MB beads, mirrors, spread
-__global__ void __launch_bounds__(BIG_THREADS) k_big_inv(Dev d, int t, int mode) {
+__global__ void __launch_bounds__(INV_THREADS) k_big_inv(Dev d, int t, int mode) {
   extern __shared__ double sm[];
   const int P = d.P[t], N = d.N[t], C = 3 * N;
   double* T = sm;
@@ -465,16 +488,20 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_inv(Dev d, int t, int mode)
   const bool qc = (mode & (PM_START | PM_QCART)) != 0;
   const int nout = (BIG_MB + 1) * C;
   if (qc || (mode & PM_PCART)) {
-    // one warp per (bead, group of BIG_CC columns), as in the forward pass
+    // INV_SPLIT warps per (bead, group of BIG_CC columns), as in the forward pass
+    __shared__ double pbuf[INV_THREADS / 32][2 * BIG_CC];
     const int ncg = (C + BIG_CC - 1) / BIG_CC;
-    for (int o = warp; o < (BIG_MB + 1) * ncg; o += nw) {
+    const int items = (BIG_MB + 1) * ncg, slots = nw / INV_SPLIT;
+    const int qs = warp % INV_SPLIT, slot = warp / INV_SPLIT;
+    for (int b0 = 0; b0 < items; b0 += slots) {
+      const int o = b0 + slot;
       const int r = o / ncg, c0 = (o - r * ncg) * BIG_CC;
       const int j = r == 0 ? 0 : jb + r - 1;
-      const int ncol = min(BIG_CC, C - c0);
+      const int ncol = o < items ? min(BIG_CC, C - c0) : 0;
       double aq[BIG_CC], ap[BIG_CC];
 #pragma unroll
       for (int u = 0; u < BIG_CC; ++u) aq[u] = ap[u] = 0.0;
-      for (int k = lane; k < P; k += 32) {
+      for (int k = lane + 32 * qs; ncol > 0 && k < P; k += 32 * INV_SPLIT) {
         const double cj = cjk(T, P, j, k, rP);
         const size_t g = base + (size_t)k * C + c0;
 #pragma unroll
@@ -489,11 +516,26 @@ __global__ void __launch_bounds__(BIG_THREADS) k_big_inv(Dev d, int t, int mode)
       for (int u = 0; u < BIG_CC; ++u) {
         if (qc) aq[u] = warp_sum(aq[u]);
         if (mode & PM_PCART) ap[u] = warp_sum(ap[u]);
-        if (lane == 0 && u < ncol) {
-          if (qc) Qc[r * C + c0 + u] = aq[u];
-          if ((mode & PM_PCART) && r > 0) d.p[base + (size_t)j * C + c0 + u] = ap[u];
+        if (lane == 0) {
+          pbuf[warp][u] = aq[u];
+          pbuf[warp][BIG_CC + u] = ap[u];
         }
       }
+      __syncthreads();
+      if (tid < slots * 2 * BIG_CC) {
+        const int sl = tid / (2 * BIG_CC), v = tid - sl * (2 * BIG_CC);
+        const int kind = v / BIG_CC, u = v - kind * BIG_CC;
+        const int oo = b0 + sl;
+        const int r2 = oo / ncg, c2 = (oo - r2 * ncg) * BIG_CC;
+        const int j2 = r2 == 0 ? 0 : jb + r2 - 1;
+        if (oo < items && u < min(BIG_CC, C - c2)) {
+          double sum = 0.0;
+          for (int w = 0; w < INV_SPLIT; ++w) sum += pbuf[sl * INV_SPLIT + w][v];
+          if (kind == 0 && qc) Qc[r2 * C + c2 + u] = sum;
+          if (kind == 1 && (mode & PM_PCART) && r2 > 0) d.p[base + (size_t)j2 * C + c2 + u] = sum;
+        }
+      }
+      __syncthreads();
     }
   }
   __syncthreads();
@@ -684,12 +726,12 @@ int launch_prop(const Dev& d, cudaStream_t s, int mode) {
     const int nb = d.P[t] / BIG_MB;
     if (mode & (PM_IMPORT | PM_END | PM_START)) {
       const size_t smem = sizeof(double) * ((size_t)d.P[t] + 3 * (size_t)BIG_MB * C + C);
-      k_big_fwd<<<nb, BIG_THREADS, smem, s>>>(d, t, mode);
+      k_big_fwd<<<nb, FWD_THREADS, smem, s>>>(d, t, mode);
       ++n;
     }
     if (mode & (PM_START | PM_QCART | PM_PCART)) {
       const size_t smem = sizeof(double) * ((size_t)d.P[t] + (size_t)(BIG_MB + 1) * C);
-      k_big_inv<<<nb, BIG_THREADS, smem, s>>>(d, t, mode);
+      k_big_inv<<<nb, INV_THREADS, smem, s>>>(d, t, mode);
       ++n;
     }
   }
