@@ -835,19 +835,30 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
       fadd3w(d.F_fix, row_c, fx, fy, fz, &bad);
     }
   }
-  fex = warp_sum(fex);
-  fey = warp_sum(fey);
-  fez = warp_sum(fez);
-  ep = warp_sum(ep);
-  vir = warp_sum(vir);
+  // lane partials to fixed point by bit assembly, then exact integer sums
+  long long kx = fix44(fex, 0, &bad), ky = fix44(fey, 0, &bad), kz = fix44(fez, 0, &bad);
+  long long ke = fixs(ep, 40, &bad), kv = fixs(vir, 40, &bad);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    kx += __shfl_xor_sync(0xffffffffu, kx, o);
+    ky += __shfl_xor_sync(0xffffffffu, ky, o);
+    kz += __shfl_xor_sync(0xffffffffu, kz, o);
+    ke += __shfl_xor_sync(0xffffffffu, ke, o);
+    kv += __shfl_xor_sync(0xffffffffu, kv, o);
+  }
   nev = warp_sumi(nev);
   bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
-    fadd3(d.F_fix, row_e, fex, fey, fez, d.err);
+    unsigned long long* fe = d.F_fix + 3 * (size_t)row_e;
+    if (kx | ky | kz) {
+      atomicAdd(fe + 0, (unsigned long long)kx);
+      atomicAdd(fe + 1, (unsigned long long)ky);
+      atomicAdd(fe + 2, (unsigned long long)kz);
+    }
+    if (ke) atomicAdd(d.E_fix + E_PSEUDO, (unsigned long long)ke);
+    if (kv) atomicAdd(d.E_fix + E_VIRIAL, (unsigned long long)kv);
+    if (nev) atomicAdd(d.E_fix + E_NPEVAL, (unsigned long long)nev);
     if (bad) atomicOr(d.err, ERR_NONFINITE);
-    eadd(d.E_fix, E_PSEUDO, ep);
-    eadd(d.E_fix, E_VIRIAL, vir);
-    atomicAdd(d.E_fix + E_NPEVAL, (unsigned long long)nev);
   }
 }
 

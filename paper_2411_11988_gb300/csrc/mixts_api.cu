@@ -886,7 +886,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   pair_grids(p.nt, p.dsf_nint, &d.pair_grid, &d.pair32_grid);
   h->full_grid64 = d.pair_grid;
   h->full_grid32 = d.pair32_grid;
-  d.pseudo_chunks = 8;
+  d.pseudo_chunks = prm->precision == MIXTS_FP32_FORCES ? 8 : 4;  // site-list slices per pseudo bead (measured)
   d.nl_cpl = 4;
   {  // FP32 pair items: P32_CH candidates for each of the 32 / min(P_max, 32) lane groups
     const int lgG = 5 - std::min(d.lgPmax_nb, 5);
