@@ -385,7 +385,7 @@ def cpu_baseline(steps, warmup=0):
                 "ms_per_step": ms}
 
 
-def replica_reduce(step_ms, world, device=None):
+def replica_reduce(step_ms, world, device=None, dt=DT):
     """Replicas only: every rank advances its own system; the job's step time
     is the slowest rank's, and the simulated time adds up over ranks.
     Returns (max step ms over ranks, aggregate ns/day)."""
@@ -395,7 +395,7 @@ def replica_reduce(step_ms, world, device=None):
         t = torch.tensor([float(step_ms)], dtype=torch.float64, device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_ms = float(t.item())
-    return step_ms, ns_per_day(step_ms) * world
+    return step_ms, ns_per_day(step_ms, dt) * world
 
 
 def dist_init():
@@ -416,6 +416,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-observables", action="store_true")
+    ap.add_argument("--workload", default="water512", choices=["water512", "ion_electron"],
+                    help="system of the main line (ion_electron: 256 waters + ion + 1024-bead electron, dt 0.1 fs; "
+                         "for profiling that workload)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="force precision of the main line (fp32: FP32 pair forces, FP64 integration)")
     args = ap.parse_args()
@@ -450,14 +453,22 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    s = build_system(WORKLOAD["P_H"], WORKLOAD["P_O"], seed=rank)
+    if args.workload == "ion_electron":
+        import synth
+        ie = ION_ELECTRON
+        s = synth.water_box(ie["n_waters"], ie["box_A"], ie["P_H"], ie["P_O"], seed=rank,
+                            ion=dict(synth.systems.ION3), electron_P=ie["P_e"])
+        dt_main, cfg_main = ie["dt_fs"], dict(ie)
+    else:
+        s = build_system(WORKLOAD["P_H"], WORKLOAD["P_O"], seed=rank)
+        dt_main, cfg_main = DT, dict(WORKLOAD)
     prec = 1 if args.precision == "fp32" else 0
-    m = MixTS(s, T=300.0, dt=DT, tau=100.0, seed=rank, device=str(dev), stream=stream, precision=prec)
+    m = MixTS(s, T=300.0, dt=dt_main, tau=100.0, seed=rank, device=str(dev), stream=stream, precision=prec)
     step_ms, ph_ms, ph_calls, kernels, clk = timed_run(m, torch, stream, args.steps, args.warmup, flush,
                                                        clocks_idx=local)
     est = m.estimators()
     single_ms = single_call_ms(m, torch, stream, max(3, args.steps // 2), flush)
-    step_ms, value = replica_reduce(step_ms, world, dev)
+    step_ms, value = replica_reduce(step_ms, world, dev, dt_main)
     evals = est["n_evals"]
     pair_ms = ph_ms["pair"] / max(1, ph_calls["pair"])
     if prec == 1:
@@ -513,7 +524,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32 forces, f64 integration", "data": "synthetic (seeded lattice water, Maxwell-Boltzmann momenta)",
-            "config": dict(WORKLOAD, l2=f"flushed (256 MiB write, untimed) before every timed chunk of {CHUNK} "
+            "config": dict(cfg_main, l2=f"flushed (256 MiB write, untimed) before every timed chunk of {CHUNK} "
                                         "steps; steps in a chunk run back to back as in production",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "bead_pair_evals_per_s": evals * 1000.0 / step_ms * world,
@@ -528,7 +539,7 @@ def main():
                          "peak_source": peak_src, "flops_per_launch": flops, "launch_ms": pair_ms},
             "phase_ms_per_call": per_phase,
             "cpu_baseline": cb,
-            "e2e": {"value": ns_per_day(e2e_ms) * world, "unit": "ns/day", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": ns_per_day(e2e_ms, dt_main) * world, "unit": "ns/day", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                     "note": "host-resident state: upload q,p, re-import and recompute forces, step, download"},
             "gpu_launches": kernels,
