@@ -280,14 +280,6 @@ __global__ void k_plist(Dev d) {
 // ---------------------------------------------------------------------------
 constexpr int PAIR_THREADS = 256;
 
-__device__ __forceinline__ void item_of_warp(const Dev& d, int w, int* pos, int* bead) {
-  int c = 0;
-  while (c + 1 < d.n_classes && w >= d.cls_item0[c + 1]) ++c;
-  const int local = w - d.cls_item0[c];
-  *bead = local / d.cls_n[c];
-  *pos = d.cls_pos0[c] + (local - *bead * d.cls_n[c]);
-}
-
 // Unit-charge DSF potential G(s), s = r^2, and -2 dG/ds from the interval
 // table: each is a quintic in x = s - s0 on each of 64 geometric
 // sub-intervals per octave of s; the interval and s0 come straight from the
@@ -340,12 +332,27 @@ __device__ __forceinline__ void dsf_direct(const Dev& d, double s, double* g, do
   *fg = (ec * rinv * rinv + d.dsf_g * ex * rinv - d.dsf_cf) * rinv;
 }
 
+// ---------------------------------------------------------------------------
+// nonbonded pair sweep, FP64, slice-parallel over the half list.
+//
+// The owner of a listed pair is its finer atom (P_i >= P_j), so the terms of
+// Eq. (mts-hamiltonian) for one entry are exactly the owner's beads b, each
+// meeting the partner's bead b >> (lgP_i - lgP_j) with weight 1/P_i. One warp
+// takes (owner atom, block of 32 of its beads, chunk of its list); the lanes
+// are the owner's beads (groups of min(P_i, 32) lanes take different
+// entries), so an entry is decoded once per group and the partner's beads
+// are read from the atom-major copy of the fixed-point positions, contiguous
+// for the lanes. Per term the arithmetic is that of the sweep above: exact
+// 128-bit r^2 and cut-off, table interval and offset from the integer bits,
+// binary64 quadratics with binary32 tails, forces rounded once into the fixed
+// point; the partner's bead gets the reaction.
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   extern __shared__ double dtab[];  // DSF interval table: 6 doubles, then 8 floats per interval
   __shared__ PairPar tab[MT * MT];
   __shared__ int flg[MT * MT];      // bit 0: Coulomb, bit 1: Lennard-Jones
   __shared__ longlong4_32a shi[125];
-  __shared__ int tN[MT], tLg[MT];
+  __shared__ int tN[MT], tLg[MT], tOff[MT];
   const int nt = d.n_types;
   float* ftab = (float*)(dtab + 6 * d.dsf_nint);
   for (int e = threadIdx.x; e < d.dsf_nint; e += blockDim.x) {
@@ -362,6 +369,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   for (int e = threadIdx.x; e < nt; e += blockDim.x) {
     tN[e] = d.N[e];
     tLg[e] = d.log2P[e];
+    tOff[e] = d.off[e];
   }
   for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
     const PairPar pp = d.pairpar[(e / nt) * MT + (e % nt)];
@@ -375,24 +383,17 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  // persistent: the tables above are loaded once per CTA; warps stride over
-  // the (owner atom, bead) items
-  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < d.n_pitems; w += nwarps) {
-  int pos, b;
-  item_of_warp(d, w, &pos, &b);
-  const AtomInfo ai = d.ainfo[pos];
-  const int row_i = ai.row0 + b * ai.stride;
-  const longlong4_32a xi = d.Xi[row_i];
-  const int wsh = ai.log2P;  // weight 1/P_i = 2^-wsh
-  const int cnt = min(d.nl_cnt[pos], d.nl_cap);
-  const int* lst = d.nl + (size_t)pos * d.nl_cap;
+  const int lgM = d.lgPmax_nb;
+  const int nsbm = lgM > 5 ? 1 << (lgM - 5) : 1;
+  const int nch = d.p64_nch;
+  const int n_items = d.n_nonp * nsbm * nch;
   const double rc = d.rc;
   // r_cut^2 in the 2^-96 A^2 units of the integer squared distances (exact)
   fm::u128 rc2q;
   {
-    const unsigned long long b = fm::dbl_bits(d.rc2);
-    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-    const int sh = (int)((b >> 52) & 0x7FF) - 1075 + 96;  // in [0, 75] for 2^-44 <= r_cut^2 < 2^23
+    const unsigned long long bb = fm::dbl_bits(d.rc2);
+    const unsigned long long m = (bb & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const int sh = (int)((bb >> 52) & 0x7FF) - 1075 + 96;
     if (sh >= 64)
       rc2q = fm::u128{m << (sh - 64), 0ull};
     else if (sh > 0)
@@ -401,26 +402,41 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
       rc2q = fm::u128{0ull, sh > -53 ? m >> (-sh) : 0ull};
   }
   const int base = d.dsf_base;
-  const int trow = ai.type * nt;
-  long long fix = 0, fiy = 0, fiz = 0;
-  double elj = 0.0, ec = 0.0, vir = 0.0;
-  int nev = 0, nlj = 0, bad = 0;
-  int ent_next = lane < cnt ? lst[lane] : 0;
-  for (int e = lane; e < cnt; e += 32) {
-    // entry: (bead-0 row of the partner << 11) | (partner type << 7) | image code
-    const int ent = ent_next;
-    ent_next = e + 32 < cnt ? lst[e + 32] : 0;
-    const int tj = (ent >> 7) & 15;
-    const int bj = b >> (ai.log2P - tLg[tj]);
-    const int row_j = (ent >> 11) + bj * tN[tj];
-    const longlong4_32a xj = d.Xi[row_j];
-    // exact displacement in 2^-48 A fixed point and its exact square in
-    // 2^-96 A^2: the cut-off test, the table interval and the offset inside
-    // it need no FP64 instruction
-    const longlong4_32a sv = shi[ent & 127];
-    const long long ix = (xj.x - xi.x) + sv.x, iy = (xj.y - xi.y) + sv.y, iz = (xj.z - xi.z) + sv.z;
-    const fm::u128 q2 = fm::norm2(ix, iy, iz);
-    if (fm::lt128(q2, rc2q)) {
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_items; w += nwarps) {
+    const int ch = w % nch;
+    const int rest = w / nch;
+    const int sb = rest % nsbm, pos = rest / nsbm;
+    const AtomInfo ai = d.ainfo[pos];
+    const int lgPi = ai.log2P;
+    const int lgPp = lgPi < 5 ? lgPi : 5;  // log2 of the lanes per group
+    const int lgG = 5 - lgPp;
+    if (sb >= (1 << (lgPi - lgPp))) continue;
+    const int cnt = min(d.nl_cnt[pos], d.nl_cap);
+    const int e0 = ch * (P32_CH << lgG);
+    if (e0 >= cnt) continue;
+    const int e1 = min(cnt, e0 + (P32_CH << lgG));
+    const int sl = lane & ((1 << lgPp) - 1), grp = lane >> lgPp;
+    const int b = (sb << lgPp) + sl;  // owner bead of this lane
+    const int oi = tOff[ai.type];
+    const longlong4_32a xi = d.XiA[oi + ((ai.row0 - oi) << lgPi) + b];
+    const int row_i = ai.row0 + b * ai.stride;
+    const int wsh = lgPi;  // weight 1/P_i = 2^-wsh
+    const int trow = ai.type * nt;
+    const int* lst = d.nl + (size_t)pos * d.nl_cap;
+    long long fix = 0, fiy = 0, fiz = 0;
+    double elj = 0.0, ec = 0.0, vir = 0.0;
+    int nev = 0, nlj = 0, bad = 0;
+    for (int e = e0 + grp; e < e1; e += (1 << lgG)) {
+      const int ent = lst[e];
+      const int tj = (ent >> 7) & 15;
+      const int lgPj = tLg[tj];
+      const int row0j = ent >> 11, oj = tOff[tj];
+      const int bj = b >> (lgPi - lgPj);
+      const longlong4_32a xj = d.XiA[oj + ((row0j - oj) << lgPj) + bj];
+      const longlong4_32a sv = shi[ent & 127];
+      const long long ix = (xj.x - xi.x) + sv.x, iy = (xj.y - xi.y) + sv.y, iz = (xj.z - xi.z) + sv.z;
+      const fm::u128 q2 = fm::norm2(ix, iy, iz);
+      if (!fm::lt128(q2, rc2q)) continue;
       const int pq = fm::msb128(q2);
       const double r2 = pq >= 0 ? fm::u128_to_dbl(q2, pq, 96) : 0.0;
       const int fl = flg[trow + tj];
@@ -447,8 +463,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
         fr += (6.0 * pp.e4 * (2.0 * sr12 - sr6) * rinv + pp.dvrc) * rinv;
         ++nlj;
       }
-      // f d in the 2^-44 (times 1/P_i) fixed point, rounded once from the
-      // exact product of the mantissa of f and the integer displacement
       const long long kx = fm::mulfix(fr, ix, 4 + wsh, &bad), ky = fm::mulfix(fr, iy, 4 + wsh, &bad),
                       kz = fm::mulfix(fr, iz, 4 + wsh, &bad);
       fix -= kx;
@@ -456,40 +470,44 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
       fiz -= kz;
       vir = fma(fr, r2, vir);
       ++nev;
-      unsigned long long* fj = d.F_fix + 3 * (size_t)row_j;
+      unsigned long long* fj = d.F_fix + 3 * (size_t)(row0j + bj * tN[tj]);
       atomicAdd(fj + 0, (unsigned long long)kx);
       atomicAdd(fj + 1, (unsigned long long)ky);
       atomicAdd(fj + 2, (unsigned long long)kz);
     }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    fix += __shfl_xor_sync(0xffffffffu, fix, o);
-    fiy += __shfl_xor_sync(0xffffffffu, fiy, o);
-    fiz += __shfl_xor_sync(0xffffffffu, fiz, o);
-  }
-  elj = warp_sum(elj);
-  ec = warp_sum(ec);
-  vir = warp_sum(vir);
-  nev = warp_sumi(nev);
-  nlj = warp_sumi(nlj);
-  bad = __any_sync(0xffffffffu, bad);
-  if (lane == 0) {
+    // the owner's force: lanes of the same bead (one per group) summed exactly
+    for (int o = 1 << lgPp; o < 32; o <<= 1) {
+      fix += __shfl_xor_sync(0xffffffffu, fix, o);
+      fiy += __shfl_xor_sync(0xffffffffu, fiy, o);
+      fiz += __shfl_xor_sync(0xffffffffu, fiz, o);
+    }
+    if (grp == 0 && (fix | fiy | fiz) != 0) {
+      unsigned long long* fi = d.F_fix + 3 * (size_t)row_i;
+      atomicAdd(fi + 0, (unsigned long long)fix);
+      atomicAdd(fi + 1, (unsigned long long)fiy);
+      atomicAdd(fi + 2, (unsigned long long)fiz);
+    }
     // energies carry the weight 1/P_i as an exponent offset of the fixed point
-    unsigned long long* fi = d.F_fix + 3 * (size_t)row_i;
-    atomicAdd(fi + 0, (unsigned long long)fix);
-    atomicAdd(fi + 1, (unsigned long long)fiy);
-    atomicAdd(fi + 2, (unsigned long long)fiz);
-    atomicAdd(d.E_fix + E_LJ, (unsigned long long)fixs(elj, 40 - wsh, &bad));
-    atomicAdd(d.E_fix + E_COUL, (unsigned long long)fixs(ec, 40 - wsh, &bad));
-    atomicAdd(d.E_fix + E_VIRIAL, (unsigned long long)fixs(vir, 40 - wsh, &bad));
-    atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nlj);
-    atomicAdd(d.E_fix + E_NEVAL, (unsigned long long)nev);
-    if (bad) atomicOr(d.err, ERR_NONFINITE);
-  }
+    long long kl = fixs(elj, 40 - wsh, &bad), kc = fixs(ec, 40 - wsh, &bad), kv = fixs(vir, 40 - wsh, &bad);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kl += __shfl_xor_sync(0xffffffffu, kl, o);
+      kc += __shfl_xor_sync(0xffffffffu, kc, o);
+      kv += __shfl_xor_sync(0xffffffffu, kv, o);
+    }
+    nev = warp_sumi(nev);
+    nlj = warp_sumi(nlj);
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      if (kl) atomicAdd(d.E_fix + E_LJ, (unsigned long long)kl);
+      if (kc) atomicAdd(d.E_fix + E_COUL, (unsigned long long)kc);
+      if (kv) atomicAdd(d.E_fix + E_VIRIAL, (unsigned long long)kv);
+      if (nev) atomicAdd(d.E_fix + E_NEVAL, (unsigned long long)nev);
+      if (nlj) atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nlj);
+      if (bad) atomicOr(d.err, ERR_NONFINITE);
+    }
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // nonbonded pair sweep, FP32 forces (precision MIXTS_FP32_FORCES), the terms
@@ -1019,7 +1037,9 @@ int launch_pair(const Dev& d, cudaStream_t s) {
     cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr = true;
   }
-  k_pair64<<<min((d.n_pitems + wpb - 1) / wpb, d.pair_grid), PAIR_THREADS, smem, s>>>(d);
+  const int nsbm = d.lgPmax_nb > 5 ? 1 << (d.lgPmax_nb - 5) : 1;
+  const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;
+  k_pair64<<<(int)std::min<long long>((items + wpb - 1) / wpb, d.pair_grid), PAIR_THREADS, smem, s>>>(d);
   return 1;
 }
 

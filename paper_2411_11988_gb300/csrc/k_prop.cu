@@ -58,6 +58,7 @@ __device__ __forceinline__ void write_mirror(const Dev& d, int row, double x, do
   int bad = 0;
   const long long ix = fixs(wx, 48, &bad), iy = fixs(wy, 48, &bad), iz = fixs(wz, 48, &bad);
   d.Xi[row] = make_longlong4_32a(ix, iy, iz, 0);
+  if (d.XiA) d.XiA[arow] = make_longlong4_32a(ix, iy, iz, 0);
   const int gx = (int)((ix + (1LL << 35)) >> 36), gy = (int)((iy + (1LL << 35)) >> 36),
             gz = (int)((iz + (1LL << 35)) >> 36);
   d.Xf[row] = make_float4(small_int_float(gx) * 0x1p-12f, small_int_float(gy) * 0x1p-12f,

@@ -91,7 +91,7 @@ struct Plan {
       o_pairpar, o_pspar, o_bitems, o_bond_atoms, o_bond_par, o_ang_atoms, o_ang_par, o_cm, o_mc, o_tiles,
       o_slot_type, o_dsf, o_pstab, o_pairpar_alt, o_pspar_alt, o_pc, o_gacc;
   size_t o_state = 0, state_bytes = 0;
-  size_t o_xd = 0;
+  size_t o_xd = 0, o_xia = 0;
   size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_xl, o_ref, o_refd, o_reff, o_spread, o_spread_big, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
       o_err, o_step, o_heat, o_est, o_parts;
 };
@@ -578,6 +578,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_xf = A.add(sizeof(float4) * p.n_beads);
   p.o_xl = A.add(sizeof(float4) * p.n_beads);
   if (prm->precision == MIXTS_FP32_FORCES) p.o_xd = A.add(sizeof(float4) * p.n_beads);
+  else p.o_xia = A.add(sizeof(longlong4_32a) * p.n_beads);
   p.o_ref = A.add(sizeof(double) * 3 * p.na);
   p.o_refd = A.add(sizeof(double4_32a) * std::max(1, p.n_nonp));
   p.o_reff = A.add(sizeof(float4) * std::max(1, p.n_nonp));
@@ -877,6 +878,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.Xf = (float4*)(w + p.o_xf);
   d.Xl = (float4*)(w + p.o_xl);
   d.Xd = p.o_xd ? (float4*)(w + p.o_xd) : nullptr;
+  d.XiA = p.o_xia ? (longlong4_32a*)(w + p.o_xia) : nullptr;
   d.ref = (double*)(w + p.o_ref);
   d.refd = (double4_32a*)(w + p.o_refd);
   d.reff = (float4*)(w + p.o_reff);
@@ -888,6 +890,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   h->full_grid32 = d.pair32_grid;
   d.pseudo_chunks = prm->precision == MIXTS_FP32_FORCES ? 8 : 4;  // site-list slices per pseudo bead (measured)
   d.nl_cpl = 4;
+  d.p64_nch = (p.nl_cap + P32_CH - 1) / P32_CH;  // at most: one lane group, P32_CH entries per item
   {  // FP32 pair items: P32_CH candidates for each of the 32 / min(P_max, 32) lane groups
     const int lgG = 5 - std::min(d.lgPmax_nb, 5);
     d.p32_nch = (p.nl_cap + (P32_CH << lgG) - 1) / (P32_CH << lgG);

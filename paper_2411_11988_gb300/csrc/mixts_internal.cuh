@@ -121,6 +121,7 @@ struct Dev {
   int pair_grid, pair32_grid, pseudo_chunks;  // persistent grid sizes, site-list split
   int nl_cpl;                                 // list candidates per lane of one list warp
   int p32_nch;                                // FP32 pair items per owner row and slice block (list chunks)
+  int p64_nch;                                // FP64 slice-parallel items per owner row and slice block
   double mass[MT];
   // sorted classes of non-pseudo atoms (P descending)
   int cls_P[MAX_CLASSES], cls_log2P[MAX_CLASSES], cls_pos0[MAX_CLASSES], cls_n[MAX_CLASSES],
@@ -154,6 +155,7 @@ struct Dev {
   longlong4_32a* Xi;               // [n_beads] the same in 2^-48 A fixed point (exact differences)
   float4* Xf;                  // [n_beads] binary32 positions on the 2^-12 A grid (screens)
   float4* Xl;                  // [n_beads] binary32 remainders: Xw = Xf + Xl to ~2^-37 A
+  longlong4_32a* XiA;          // [n_beads] Xi atom-major inside each type block (off_t + k P_t + b); FP64 path only
   float4* Xd;                  // [n_beads] binary32 offset of each bead from its atom's bead 0, atom-major
                                // inside each type block (off_t + k P_t + b); FP32 path only, else null
   double* ref;                 // [n_atoms*3] wrapped bead-0 reference positions
