@@ -457,11 +457,12 @@ void or_bead_force(const or_system* s, const double* q, int atom, int bead, doub
  * Neighbour list definition (integer output, matched bit for bit).
  *   r_a = q_{a,0} - L floor(q_{a,0}/L)          wrapped bead-0 reference
  *   d_max = max over non-pseudo beads of |q_{a,b} - q_{a,0}|
- *   R = r_cut + 2 d_max; keep (owner, other, n) with |r_o - r_w + nL|^2 < R^2,
- *   n in [-2,2]^3, skipping same-molecule n = 0 and a == c.
- * Owner: atoms ordered by (P descending, index ascending); of a pair the
- * finer atom owns it; between equal P the lower position owns it when the
- * two positions sum to an even number, the higher one otherwise.
+ *   R = r_cut + 2 d_max; the list is the set of unordered atom pairs with a
+ *   lattice image, written canonically as (i, j, n) with i < j, for which
+ *   |(r_j - r_i) + n L|^2 < R^2, n in [-2,2]^3, skipping same-molecule
+ *   n = 0. Which atom of a pair a force kernel makes the owner of the entry
+ *   is the kernel's business; the set does not depend on it, because every
+ *   operation below is odd under swapping i and j with n -> -n.
  * Every product and sum below is one IEEE operation in the order written.
  * ------------------------------------------------------------------------- */
 static void wrapped_refs(const or_system* s, const lay_t* L, const double* q, double* ref) {
@@ -499,10 +500,11 @@ static double max_spread(const or_system* s, const lay_t* L, const double* q, in
 
 static int image_code(int nx, int ny, int nz) { return (nx + 2) * 25 + (ny + 2) * 5 + (nz + 2); }
 
-static double disp2(const double* ro, const double* rw, int nx, int ny, int nz, double Lb) {
-  double dx = (ro[0] - rw[0]) + (double)nx * Lb;
-  double dy = (ro[1] - rw[1]) + (double)ny * Lb;
-  double dz = (ro[2] - rw[2]) + (double)nz * Lb;
+/* squared length of (r_to - r_from) + n L */
+static double disp2(const double* r_to, const double* r_from, int nx, int ny, int nz, double Lb) {
+  double dx = (r_to[0] - r_from[0]) + (double)nx * Lb;
+  double dy = (r_to[1] - r_from[1]) + (double)ny * Lb;
+  double dz = (r_to[2] - r_from[2]) + (double)nz * Lb;
   double d2 = dx * dx;
   d2 = d2 + dy * dy;
   d2 = d2 + dz * dz;
@@ -522,43 +524,21 @@ long or_nlist(const or_system* s, const double* q, long cap, int* out3, double* 
     out_thresh[0] = dm;
     out_thresh[1] = R;
   }
-  /* sorted position of each atom: (P descending, index ascending) */
-  int* pos = (int*)malloc(sizeof(int) * (size_t)na);
-  int np = 0;
-  for (int Pv = 1 << 20; Pv >= 1; Pv >>= 1)
-    for (int a = 0; a < na; ++a) {
-      int t = s->type_of_atom[a];
-      if (s->pseudo_type[t]) {
-        pos[a] = -1;
-        continue;
-      }
-      if (s->P_type[t] == Pv) pos[a] = np++;
-    }
   long n = 0;
-  for (int a = 0; a < na; ++a) {
-    if (pos[a] < 0) continue;
-    for (int c = a + 1; c < na; ++c) {
-      if (pos[c] < 0) continue;
-      int lo = pos[a] < pos[c] ? a : c, hi = pos[a] < pos[c] ? c : a;
-      int Plo = s->P_type[s->type_of_atom[lo]], Phi = s->P_type[s->type_of_atom[hi]];
-      int owner, other;
-      if (Plo > Phi || ((pos[lo] + pos[hi]) % 2 == 0)) {
-        owner = lo;
-        other = hi;
-      } else {
-        owner = hi;
-        other = lo;
-      }
-      int same = s->mol_of_atom[a] == s->mol_of_atom[c];
+  for (int i = 0; i < na; ++i) {
+    if (s->pseudo_type[s->type_of_atom[i]]) continue;
+    for (int j = i + 1; j < na; ++j) {
+      if (s->pseudo_type[s->type_of_atom[j]]) continue;
+      int same = s->mol_of_atom[i] == s->mol_of_atom[j];
       for (int nx = -2; nx <= 2; ++nx)
         for (int ny = -2; ny <= 2; ++ny)
           for (int nz = -2; nz <= 2; ++nz) {
             if (same && nx == 0 && ny == 0 && nz == 0) continue;
-            double d2 = disp2(ref + 3 * other, ref + 3 * owner, nx, ny, nz, s->box);
+            double d2 = disp2(ref + 3 * j, ref + 3 * i, nx, ny, nz, s->box);
             if (d2 < R2) {
               if (n < cap) {
-                out3[3 * n] = owner;
-                out3[3 * n + 1] = other;
+                out3[3 * n] = i;
+                out3[3 * n + 1] = j;
                 out3[3 * n + 2] = image_code(nx, ny, nz);
               }
               ++n;
@@ -566,7 +546,6 @@ long or_nlist(const or_system* s, const double* q, long cap, int* out3, double* 
           }
     }
   }
-  free(pos);
   free(ref);
   lay_free(&L);
   return n <= cap ? n : -n;

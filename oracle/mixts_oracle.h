@@ -84,9 +84,10 @@ void or_forces(const or_system* s, const double* q, double* F, double* parts);
 /* force on one bead only (sum over all its terms) */
 void or_bead_force(const or_system* s, const double* q, int atom, int bead, double* F3);
 
-/* neighbour list: triplets (owner atom, partner atom, image code); returns
- * the count (or -needed if cap is too small). out_thresh[0]=d_max,
- * [1]=threshold r_cut + 2 d_max. */
+/* neighbour list: the canonical set of unordered atom pairs with an image,
+ * triplets (i, j, image code of n) with i < j and |r_j - r_i + nL| below the
+ * list radius; returns the count (or -needed if cap is too small).
+ * out_thresh[0]=d_max, [1]=threshold r_cut + 2 d_max. */
 long or_nlist(const or_system* s, const double* q, long cap, int* out3, double* out_thresh);
 /* pseudo-particle site list: (pseudo atom, site atom, image code).
  * out_thresh[0]=d_max sites, [1]=d_max pseudo, [2]=threshold */

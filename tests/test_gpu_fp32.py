@@ -2,14 +2,15 @@
 
 Tolerances (FP32 pair forces, FP64 integration and reductions): forces
 max|F_gpu - F_or| / RMS(F_or) <= 1e-5, energies |V_gpu - V_or| / |V_or| <= 1e-5.
-The full neighbour list of this mode equals the oracle's owner list plus every
-entry seen from the other atom, bit for bit.
+The full neighbour list of this mode equals the oracle's canonical list plus
+every entry seen from the other atom, bit for bit.
 """
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from list_util import both_ways
 
 pytestmark = pytest.mark.gpu
 FTOL32 = 1e-5
@@ -67,12 +68,7 @@ def test_fp32_full_list_bit_exact(gpu):
     tl, th = m.nlist(0)
     ol, dmax, R = oracle.nlist(s)
     assert th[0] == dmax and th[1] == R
-    rev = ol[:, [1, 0, 2]].copy()
-    code = rev[:, 2]
-    nx, ny, nz = code // 25 - 2, (code // 5) % 5 - 2, code % 5 - 2
-    rev[:, 2] = (-nx + 2) * 25 + (-ny + 2) * 5 + (-nz + 2)
-    full = np.concatenate([ol, rev])
-    full = full[np.lexsort((full[:, 2], full[:, 1], full[:, 0]))]
+    full = both_ways(ol)
     assert np.array_equal(tl, full)
     m.close()
 

@@ -9,6 +9,8 @@
 * Free ring polymer: <R_g^2> = (P^2 - 1) beta hbar^2 / (4 P^2 m).
 * Thermostat: bead kinetic temperature equals T.
 * NVE (thermostat off): H_mix is conserved with fluctuations scaling as dt^2.
+* Thermostat bookkeeping: with PILE on, H_mix + heat is conserved to the NVE
+  level while H_mix itself swings by the exchanged heat.
 """
 import math
 
@@ -163,3 +165,28 @@ def test_nve_conservation_dt2(orc):
     assert np.abs(h1 - h1[0]).max() < 0.005 * np.std(ke1)
     # second-order splitting: halving dt divides the fluctuation by ~4
     assert 3.0 < f1 / f2 < 5.5, (f1, f2)
+
+
+def test_thermostat_heat_conserves_effective_energy(orc):
+    """With PILE on, H_mix swings by the heat the thermostat exchanges, while
+    H_mix + heat (heat = minus the kinetic energy the two O half steps add)
+    is conserved to the integrator's own NVE level (Sec. "System I", PILE)."""
+    s = synth.water_box(8, 8.4, 8, 2, seed=3)
+    run = orc.Runner(s, orc.make_params(T=T, dt=0.25, tau=20.0, lam=1.0, seed=7))
+    h, hc = [], []
+    for _ in range(3000):
+        run.step(1)
+        e = run.estimators()
+        h.append(e["H_mix"])
+        hc.append(e["H_conserved"])
+    h, hc = np.array(h), np.array(hc)
+    nve = orc.Runner(s, orc.make_params(T=T, dt=0.25, tau=0.0, lam=0.0, seed=7))
+    h0 = []
+    for _ in range(3000):
+        nve.step(1)
+        h0.append(nve.estimators()["H_mix"])
+    h0 = np.array(h0)
+    assert np.std(h - h[0]) > 1.0                          # the thermostat does exchange heat
+    assert np.std(hc - hc[0]) < 2e-3 * np.std(h - h[0])
+    assert abs(hc[-1] - hc[0]) < 1e-2 * abs(h[-1] - h[0]) + 0.1
+    assert np.std(hc - hc[0]) < 2.0 * np.std(h0 - h0[0])   # no worse than plain NVE

@@ -239,34 +239,33 @@ def test_neighbour_list_complete(orc):
     s = _small_mixed_system(8, 2, 16, seed=13)
     tl, dmax, R = orc.nlist(s)
     assert R == pytest.approx(RC + 2 * dmax)
+    # canonical form: lower atom first, each (pair, image) once
+    assert np.all(tl[:, 0] < tl[:, 1])
+    assert len(set(map(tuple, tl.tolist()))) == len(tl)
     have = set(map(tuple, tl.tolist()))
     L = s.box
     P = s.P_type[s.type_of_atom]
     nonp = s.pseudo_type[s.type_of_atom] == 0
+    ref = lambda a: s.q[s.bead_rows(a)[0]] - L * np.floor(s.q[s.bead_rows(a)[0]] / L)
     for a in range(s.n_atoms):
-        for c in range(s.n_atoms):
-            if a == c or not (nonp[a] and nonp[c]):
+        for c in range(a + 1, s.n_atoms):
+            if not (nonp[a] and nonp[c]):
                 continue
-            if P[a] < P[c]:
-                continue
-            for ba in range(P[a]):
-                x = s.q[s.bead_rows(a)[ba]]
-                y = s.q[s.bead_rows(c)[ba * P[c] // P[a]]]
+            fine, coarse = (a, c) if P[a] >= P[c] else (c, a)
+            Pf, Pc = P[fine], P[coarse]
+            for bf in range(Pf):
+                # displacement from a's bead to c's bead on the pair's fine grid
+                xa = s.q[s.bead_rows(a)[bf if a == fine else bf * Pc // Pf]]
+                xc = s.q[s.bead_rows(c)[bf if c == fine else bf * Pc // Pf]]
                 for nx in range(-3, 4):
                     for ny in range(-3, 4):
                         for nz in range(-3, 4):
                             n = np.array([nx, ny, nz])
                             if s.mol_of_atom[a] == s.mol_of_atom[c] and not n.any():
                                 continue
-                            if np.linalg.norm(y - x + n * L) >= RC:
+                            if np.linalg.norm(xc - xa + n * L) >= RC:
                                 continue
                             # the same image in the wrapped-reference frame
-                            ra = s.q[s.bead_rows(a)[0]] - L * np.floor(s.q[s.bead_rows(a)[0]] / L)
-                            rc_ = s.q[s.bead_rows(c)[0]] - L * np.floor(s.q[s.bead_rows(c)[0]] / L)
-                            m = n + np.round(((y - x + n * L) - (rc_ - ra)) / L - n).astype(int)
-                            fwd = (a, c, int((m[0] + 2) * 25 + (m[1] + 2) * 5 + m[2] + 2))
-                            bwd = (c, a, int((-m[0] + 2) * 25 + (-m[1] + 2) * 5 - m[2] + 2))
-                            assert fwd in have or bwd in have
-    # owners are never coarser than their partners
-    Pt = s.P_type[s.type_of_atom]
-    assert np.all(Pt[tl[:, 0]] >= Pt[tl[:, 1]])
+                            m = n + np.round(((xc - xa + n * L) - (ref(c) - ref(a))) / L - n).astype(int)
+                            key = (a, c, int((m[0] + 2) * 25 + (m[1] + 2) * 5 + m[2] + 2))
+                            assert key in have, key
