@@ -55,6 +55,36 @@ GRAD = dict(workload="512 waters + ion(+3) + electron P=1024, 24.83 A box, H16/O
             n_waters=512, box_A=24.83, P_H=16, P_O=2, P_e=1024)
 
 
+def measured_alu_peaks(torch, stream, clocks_idx):
+    """FP64 and FP32 FMA-chain throughput of this GPU (the library's probe,
+    CUDA events), with the SM clocks sampled while it runs. Each is the best of
+    three timed launches (~5-10 ms each)."""
+    from paper_2411_11988_gb300 import alu_peak_tflops
+    clk = Clocks(clocks_idx)
+    clk.__enter__()
+    with torch.cuda.stream(stream):
+        f64 = max(alu_peak_tflops(True, 6000, stream)[0] for _ in range(3))
+        f32 = max(alu_peak_tflops(False, 120000, stream)[0] for _ in range(3))
+    clk.__exit__()
+    return {"fp64_tflops": f64, "fp32_tflops": f32, "clocks": clk.summary(),
+            "method": "mixts_alu_probe: SM-filling grid of 16 independent FMA chains per thread, best of 3"}
+
+
+def ncu_pipe_pct(kernel):
+    """The pipe utilisation ncu recorded for `kernel` in its committed profile
+    summary (profiles/<kernel>_*.md), with the file it came from."""
+    import glob
+    import re
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
+        for line in open(f):
+            m = re.match(r"\|\s*sm__(?:pipe_fp64_cycles_active|pipe_fma_cycles_active|inst_executed_pipe_fma)"
+                         r"[^|]*\|\s*([\d.]+)\s*%", line)
+            if m:
+                return {"pipe_pct": float(m.group(1)), "metric": line.split("|")[1].strip(),
+                        "source": os.path.relpath(f, ROOT)}
+    return None
+
+
 def ns_per_day(ms_per_step, dt=DT):
     return (1000.0 / ms_per_step) * dt * 86400.0 * 1e-6
 
@@ -170,7 +200,7 @@ def single_call_ms(m, torch, stream, steps, flush):
     return sum(a.elapsed_time(b) for a, b in ev) / steps
 
 
-def variant(torch, stream, flush, dev, sysm, dt, precision, steps, seed):
+def variant(torch, stream, flush, dev, sysm, dt, precision, steps, seed, peaks=None):
     from paper_2411_11988_gb300 import MixTS
     m = MixTS(sysm, T=300.0, dt=dt, tau=100.0, seed=seed, device=str(dev), stream=stream, precision=precision)
     ms, ph, calls, _, _ = timed_run(m, torch, stream, steps, 3, flush)
@@ -183,8 +213,11 @@ def variant(torch, stream, flush, dev, sysm, dt, precision, steps, seed):
     if precision == 1:
         flops = (e["n_evals"] - e["n_lj_evals"]) * FLOPS32_PAIR + e["n_lj_evals"] * (FLOPS32_PAIR + FLOPS32_LJ_EXTRA)
         ach = flops / (pair_ms * 1e-3) / 1e12
-        out["roofline_pair"] = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                "frac": ach / FP32_PEAK_TFLOPS, "note": "algorithmic flops count each term once"}
+        pk = peaks["fp32_tflops"] if peaks else FP32_PEAK_TFLOPS
+        out["roofline_pair"] = {"bound": "alu", "kernel": "k_pair32", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                                "frac": ach / pk, "peak_source": "measured FP32 FMA chains" if peaks else "nominal",
+                                "frac_of_nominal": ach / FP32_PEAK_TFLOPS, "ncu": ncu_pipe_pct("k_pair32"),
+                                "note": "algorithmic flops count each term once"}
     return out
 
 
@@ -369,20 +402,66 @@ def e2e_run(m, torch, stream, steps):
     return (t1 - t0) * 1000.0 / steps, 2 * nb, 2 * nb + 8 * 21
 
 
-def cpu_baseline(steps, warmup=0):
-    """The FP64 oracle, as it stands, on the host: `steps` full steps of the workload."""
+def _cpu_model():
+    """CPU model string of this host (/proc/cpuinfo, else lscpu)."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def _oracle_steps(args):
+    """One host process: `steps` timed oracle steps of the workload (after
+    `warmup` untimed ones); returns ms per step. Runs in a spawned child."""
+    steps, warmup, seed = args
+    sys.path.insert(0, ROOT)
     import oracle
-    s = build_system(WORKLOAD["P_H"], WORKLOAD["P_O"], 0)
-    prm = oracle.make_params(T=300.0, dt=DT, tau=100.0, lam=1.0, seed=0)
-    run = oracle.Runner(s, prm)
+    s = build_system(WORKLOAD["P_H"], WORKLOAD["P_O"], seed)
+    run = oracle.Runner(s, oracle.make_params(T=300.0, dt=DT, tau=100.0, lam=1.0, seed=seed))
     run.step(warmup)
     t0 = time.perf_counter()
     run.step(steps)
-    t1 = time.perf_counter()
-    ms = (t1 - t0) * 1000.0 / steps
-    return ms, {"value": ns_per_day(ms), "unit": "ns/day", "cores": 1, "kind": "oracle",
-                "sample": f"{steps} full steps of the workload (single-threaded C oracle)",
-                "ms_per_step": ms}
+    return (time.perf_counter() - t0) * 1000.0 / steps
+
+
+def cpu_baseline(steps, warmup=0, all_cores=True):
+    """The FP64 oracle, as it stands, on this host's cores: once single-threaded
+    (`steps` full steps of the workload), then as one independent oracle
+    process per core (replicas, `steps` steps each, started together), whose
+    aggregate throughput is the all-core figure. Processes are spawned, never
+    forked, so a CUDA context in the parent is not inherited."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    ncores = os.cpu_count() or 1
+    ms1 = _oracle_steps((steps, warmup, 0))
+    single = {"value": ns_per_day(ms1), "unit": "ns/day", "cores": 1, "ms_per_step": ms1,
+              "sample": f"{steps} full steps of the workload after {warmup} untimed, one process"}
+    out = {"value": single["value"], "unit": "ns/day", "cores": 1, "kind": "oracle", "cpu_model": _cpu_model(),
+           "nproc": ncores, "ms_per_step": ms1, "sample": single["sample"], "single_thread": single}
+    if all_cores and ncores > 1:
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(ncores) as pool:
+            per = pool.map(_oracle_steps, [(steps, warmup, i) for i in range(ncores)])
+        wall = time.perf_counter() - t0
+        agg = sum(ns_per_day(ms) for ms in per)
+        out.update(value=agg, cores=ncores, ms_per_step=statistics.mean(per),
+                   sample=f"{ncores} concurrent single-threaded oracle processes (one per core), each {steps} "
+                          f"full steps of the workload after {warmup} untimed; value = summed ns/day",
+                   all_cores={"value": agg, "unit": "ns/day", "cores": ncores, "wall_s": wall,
+                              "ms_per_step_per_process": per})
+    return out["ms_per_step"], out
 
 
 def replica_reduce(step_ms, world, device=None, dt=DT):
@@ -411,7 +490,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--cpu-steps", type=int, default=6)
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -429,12 +508,14 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # bounded sample: each step is one full oracle step of the workload
-        # (~2 s); warm-up steps untimed, at most 60 timed steps
-        k = max(1, min(args.steps, 60))
-        ms, cb = cpu_baseline(k, warmup=min(args.warmup, 3))
+        # bounded sample: every host core runs its own oracle replica of the
+        # workload (~1-2 s per full step), warm-up steps untimed, at most 30
+        # timed steps each
+        k = max(1, min(args.steps, 30))
+        w = min(args.warmup, 3)
+        ms, cb = cpu_baseline(k, warmup=w)
         line = {"metric": METRIC, "value": cb["value"], "unit": "ns/day", "n_gpus": args.gpus,
-                "steps": k, "warmup": min(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "steps": k, "warmup": w, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
                 "config": dict(WORKLOAD, l2="n/a (host)"), "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -466,6 +547,7 @@ def main():
     m = MixTS(s, T=300.0, dt=dt_main, tau=100.0, seed=rank, device=str(dev), stream=stream, precision=prec)
     step_ms, ph_ms, ph_calls, kernels, clk = timed_run(m, torch, stream, args.steps, args.warmup, flush,
                                                        clocks_idx=local)
+    peaks = measured_alu_peaks(torch, stream, local)
     est = m.estimators()
     single_ms = single_call_ms(m, torch, stream, max(3, args.steps // 2), flush)
     step_ms, value = replica_reduce(step_ms, world, dev, dt_main)
@@ -473,12 +555,12 @@ def main():
     pair_ms = ph_ms["pair"] / max(1, ph_calls["pair"])
     if prec == 1:
         flops = (evals - est["n_lj_evals"]) * FLOPS32_PAIR + est["n_lj_evals"] * (FLOPS32_PAIR + FLOPS32_LJ_EXTRA)
-        peak, kname = FP32_PEAK_TFLOPS, "k_pair32"
-        peak_src = "FP32 ALU: 152 SM x 128 FMA/clk x 2 x 2.07 GHz"
+        peak, peak_nom, kname = peaks["fp32_tflops"], FP32_PEAK_TFLOPS, "k_pair32"
+        peak_src = "measured FP32 FMA-chain throughput (mixts_alu_probe), this run"
     else:
         flops = (evals - est["n_lj_evals"]) * FLOPS_PAIR + est["n_lj_evals"] * (FLOPS_PAIR + FLOPS_LJ_EXTRA)
-        peak, kname = FP64_PEAK_TFLOPS, "k_pair64"
-        peak_src = "FP64 ALU: 152 SM x 2 FMA/clk x 2 x 2.07 GHz (nominal 1.25 TFLOP/s)"
+        peak, peak_nom, kname = peaks["fp64_tflops"], FP64_PEAK_TFLOPS, "k_pair64"
+        peak_src = "measured FP64 FMA-chain throughput (mixts_alu_probe), this run"
     achieved = flops / (pair_ms * 1e-3) / 1e12
     e2e_ms, h2d, d2h = e2e_run(m, torch, stream, max(3, args.steps // 2))
 
@@ -500,13 +582,13 @@ def main():
         vs = max(10, args.steps)
         variants = {
             "fp32_forces_water512_H32O4": variant(torch, stream, flush, dev, build_system(32, 4, rank), DT, 1, vs,
-                                                  rank),
+                                                  rank, peaks),
         }
         ie = ION_ELECTRON
         for prec, key in [(1, "fp32_forces_ion_electron"), (0, "fp64_ion_electron")]:
             sie = synth.water_box(ie["n_waters"], ie["box_A"], ie["P_H"], ie["P_O"], seed=rank,
                                   ion=dict(synth.systems.ION3), electron_P=ie["P_e"])
-            variants[key] = variant(torch, stream, flush, dev, sie, ie["dt_fs"], prec, vs, rank)
+            variants[key] = variant(torch, stream, flush, dev, sie, ie["dt_fs"], prec, vs, rank, peaks)
             variants[key]["workload"] = ie["workload"]
         variants["batched_64_fp32"] = batch_variant(torch, stream, flush, dev, vs)
         variants["grad_ion_electron512"] = grad_variant(torch, stream, dev, 10)
@@ -516,7 +598,7 @@ def main():
 
     cb = None
     if rank == 0 and not args.no_cpu:
-        _, cb = cpu_baseline(args.cpu_steps)
+        _, cb = cpu_baseline(args.cpu_steps, warmup=1)
 
     if rank == 0:
         per_phase = {k: ph_ms[k] / max(1, ph_calls[k]) for k in ph_ms if ph_calls[k]}
@@ -536,7 +618,10 @@ def main():
             "mixts_speedup_vs_uniform": (uni["ms_per_step"] / step_ms) if uni else None,
             "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": peak_src, "flops_per_launch": flops, "launch_ms": pair_ms},
+                         "peak_source": peak_src, "peak_nominal": peak_nom,
+                         "frac_of_nominal": achieved / peak_nom, "flops_per_launch": flops, "launch_ms": pair_ms,
+                         "ncu": ncu_pipe_pct(kname)},
+            "alu_peaks_measured": peaks,
             "phase_ms_per_call": per_phase,
             "cpu_baseline": cb,
             "e2e": {"value": ns_per_day(e2e_ms, dt_main) * world, "unit": "ns/day", "h2d_bytes_per_step": h2d,

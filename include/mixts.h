@@ -154,13 +154,25 @@ MIXTS_API size_t mixts_workspace_size(const mixts_system* sys, int n_sys, const 
 MIXTS_API mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* prm, void* workspace,
                         size_t ws_bytes, void* stream, mixts_handle* out);
 
-/* F <- -dV_mix/dq at the current q (neighbour list rebuilt from q), written
- * to sys.f. If energy_host is not NULL it receives V (one per system) and
- * the call synchronises; otherwise it is asynchronous. Reads the caller's q
- * afresh; the next mixts_step restarts from the caller's q and p. */
+/* Bead forces of the mixTS potential, Eq. (mts-hamiltonian): F <- -dV_mix/dq
+ * at the current q, every pair, bond and angle term on its finer
+ * participant's bead grid (Fig. 1 and its discussion give the bead maps) with
+ * weight 1/N_max, plus the pseudopotential of Sec. "System II". The
+ * neighbour list is rebuilt from q. F is written to sys.f ([n_beads][3]
+ * FP64, the bead layout above, caller-owned device memory). If energy_host
+ * (host, n_sys doubles) is not NULL it receives V_mix per system and the
+ * call synchronises and reports device-side errors; otherwise it is
+ * asynchronous and such errors surface at the next synchronising call.
+ * Reads the caller's q afresh; the next mixts_step restarts from the
+ * caller's q and p. */
 MIXTS_API mixts_status mixts_forces(mixts_handle h, double* energy_host);
 
-/* Advance n_steps OBABO steps (asynchronous). On return (in stream order)
+/* Advance n_steps steps of the split propagator of Sec. "Evaluation"
+ * (e^{-dt L} = e^{-dt/2 L_mix} e^{-dt L0_RP} e^{-dt/2 L_mix}: half kicks of
+ * V_mix around the exact normal-mode evolution of the free ring polymers of
+ * Eq. (mts-hamiltonian-b), each type with its own bead count), inside the
+ * two PILE thermostat half steps of Sec. "System I" (OBABO). Asynchronous;
+ * n_steps >= 0 (MIXTS_ERR_ARG otherwise). On return (in stream order)
  * sys.q, sys.p and sys.f hold the state after the last step. With timing off
  * and n_steps >= the handle's steps per graph launch (default 10, see
  * mixts_set_graph), whole multiples of it run as replays of one captured
@@ -173,7 +185,12 @@ MIXTS_API mixts_status mixts_step(mixts_handle h, int n_steps);
  * batched handle needs >= 1). Drops any graph captured so far. */
 MIXTS_API mixts_status mixts_set_graph(mixts_handle h, int steps_per_launch);
 
-/* Synchronise and return the estimates of the last completed step. */
+/* Synchronise and return the estimates of the last completed step (the
+ * per-step output of Sec. "Output and Analysis": potential parts, bead
+ * kinetic and spring energy of Eq. (mts-hamiltonian-b), temperature, the
+ * primitive and centroid-virial kinetic estimators per type, R_g^2, and the
+ * conserved H_mix + thermostat heat). out_host: host, n_sys records.
+ * Reports latched device-side errors as its status. */
 MIXTS_API mixts_status mixts_estimators(mixts_handle h, mixts_estimates* out_host);
 
 /* Synchronise and copy the neighbour list of the last force evaluation:
@@ -183,9 +200,13 @@ MIXTS_API mixts_status mixts_estimators(mixts_handle h, mixts_estimates* out_hos
  * kind 0: nonbonded list, 1: pseudo-particle site list. */
 MIXTS_API mixts_status mixts_nlist(mixts_handle h, int kind, int* out3_host, long cap, long* n_out, double* thresh_host);
 
-/* Opaque checkpoint of the whole dynamical state (normal-mode coordinates,
- * step counter, thermostat heat): size, save (synchronises), restore. A
- * restore followed by n steps reproduces the saved run bit for bit. */
+/* Opaque checkpoint of the whole dynamical state (normal-mode coordinates
+ * and momenta of the free ring polymers of Eq. (mts-hamiltonian-b), step
+ * counter, thermostat heat): size, save (synchronises; blob_host is host
+ * memory of at least mixts_state_size bytes; MIXTS_ERR_STATE before the
+ * first step), restore (MIXTS_ERR_STATE for a blob of another system). The
+ * thermostat noise is counter-based on the step index, so a restore
+ * followed by n steps reproduces the saved run bit for bit. */
 MIXTS_API size_t mixts_state_size(mixts_handle h);
 MIXTS_API mixts_status mixts_get_state(mixts_handle h, void* blob_host, size_t bytes);
 MIXTS_API mixts_status mixts_set_state(mixts_handle h, const void* blob_host, size_t bytes);
@@ -262,19 +283,35 @@ MIXTS_API mixts_status mixts_batch_tune(mixts_handle h, int steps_per_launch, mi
  * cudaMalloc fails or fragments it), and drivers that forbid device
  * allocation after start-up. It computes F <- -dV_mix/dq at sys->q into
  * sys->f (both caller-owned device arrays) and, if energy_host is not NULL,
- * V. All device scratch (tables, neighbour lists, accumulators) lives in one
- * static device array of MIXTS_NOALLOC_MAX_BYTES that every GPU loading the
- * library holds until exit; systems needing more return
+ * V. sys->p is not used (a force evaluation touches no momenta) and may be
+ * NULL. All device scratch (tables, neighbour lists, accumulators) lives in
+ * one static device array of MIXTS_NOALLOC_MAX_BYTES that every GPU loading
+ * the library holds until exit; systems needing more return
  * MIXTS_ERR_WORKSPACE. It calls no cudaMalloc or cudaFree. The first call on
  * each device looks up that device's address of the array
- * (cudaGetSymbolAddress), so make it once before any stream capture.
- * Every call reuses the same array and clears what must start at zero;
- * calls that overlap on the GPU (other streams, other host threads) race
- * on it and must be serialised by the caller. The call returns after its
- * work on `stream` has finished. */
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make
+ * that first call before any stream capture; a device reset
+ * (cudaDeviceReset) invalidates the kept address, so the entry point must
+ * not be called in a process after a reset of that device. Every call
+ * reuses the same array and clears what must start at zero; calls that
+ * overlap on the GPU (other streams, other host threads) race on it and
+ * must be serialised by the caller. The call returns after its work on
+ * `stream` has finished, with or without energy_host, and reports device-side
+ * failures (MIXTS_ERR_NLIST_OVERFLOW with a nlist_cap too small for the
+ * system, MIXTS_ERR_NONFINITE, MIXTS_ERR_BOX) as its status, with the reason
+ * on stderr. */
 #define MIXTS_NOALLOC_MAX_BYTES (32u << 20)
 MIXTS_API mixts_status mixts_forces_noalloc(const mixts_system* sys, const mixts_params* prm, void* stream,
                                             double* energy_host);
+
+/* ALU peak probe for roofline denominators (no counterpart in the paper; it
+ * measures the pipe the pair sweeps are bound by). Launches one SM-filling
+ * grid of independent fused multiply-add chains, binary64 if fp64 != 0 else
+ * binary32, `iters` FMAs per chain, once untimed and once timed with CUDA
+ * events on `stream` (a cudaStream_t; synchronises it). flop_out (host) gets
+ * the timed launch's flop count (2 per FMA), ms_out (host) its device time.
+ * Allocates nothing. */
+MIXTS_API mixts_status mixts_alu_probe(int fp64, int iters, void* stream, double* flop_out, double* ms_out);
 
 MIXTS_API void mixts_destroy(mixts_handle h);
 MIXTS_API const char* mixts_last_error(mixts_handle h);

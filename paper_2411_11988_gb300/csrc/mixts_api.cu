@@ -695,6 +695,15 @@ static mixts_status cuda_check(mixts_handle h, cudaError_t e, const char* what) 
   return set_err(h, MIXTS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// device -> host copy ordered on the handle's stream, then wait for it: the
+// caller's stream may be non-blocking, so a legacy-stream cudaMemcpy would not
+// be ordered after the kernels that wrote src
+static mixts_status d2h(mixts_handle h, void* dst, const void* src, size_t bytes, const char* what) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return cuda_check(h, e, what);
+}
+
 static mixts_status device_error(mixts_handle h) {
   int e = 0;
   cudaError_t ce = cudaMemcpyAsync(&e, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
@@ -773,7 +782,10 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   put(img, p.o_slot_type, p.slot_type);
   put(img, p.o_dsf, p.dsf);
   if (!p.ps_tab.empty()) put(img, p.o_pstab, p.ps_tab);
-  mixts_status st = cuda_check(h, cudaMemcpy(h->ws, img.data(), p.tab_bytes, cudaMemcpyHostToDevice), "upload tables");
+  // upload on the caller's stream (the kernels that read the tables follow it
+  // there); the host image stays alive until the synchronisation below
+  mixts_status st =
+      cuda_check(h, cudaMemcpyAsync(h->ws, img.data(), p.tab_bytes, cudaMemcpyHostToDevice, h->stream), "upload tables");
   if (st == MIXTS_OK)
     st = cuda_check(h, cudaMemsetAsync(h->ws + p.tab_bytes, 0, p.ar.size - p.tab_bytes, h->stream), "clear state");
   if (st == MIXTS_OK) st = cuda_check(h, cudaStreamSynchronize(h->stream), "init sync");
@@ -952,7 +964,7 @@ mixts_status mixts_forces(mixts_handle h, double* energy_host) {
   if (energy_host) {
     st = device_error(h);
     if (st != MIXTS_OK) return st;
-    st = cuda_check(h, cudaMemcpy(energy_host, h->d.est, sizeof(double), cudaMemcpyDeviceToHost), "energy");
+    st = d2h(h, energy_host, h->d.est, sizeof(double), "energy");
   }
   return st;
 }
@@ -1018,7 +1030,7 @@ mixts_status mixts_estimators(mixts_handle h, mixts_estimates* out) {
   mixts_status st = device_error(h);
   if (st != MIXTS_OK) return st;
   double e[EST_N];
-  st = cuda_check(h, cudaMemcpy(e, h->d.est, sizeof(e), cudaMemcpyDeviceToHost), "estimates");
+  st = d2h(h, e, h->d.est, sizeof(e), "estimates");
   if (st != MIXTS_OK) return st;
   memset(out, 0, sizeof(*out));
   out->V = e[0];
@@ -1055,7 +1067,7 @@ mixts_status mixts_nlist(mixts_handle h, int kind, int* out3, long cap, long* n_
   const Plan& p = h->plan;
   if (thresh) {
     double t4[4];
-    cudaMemcpy(t4, h->d.thresh, sizeof(t4), cudaMemcpyDeviceToHost);
+    if ((st = d2h(h, t4, h->d.thresh, sizeof(t4), "thresholds")) != MIXTS_OK) return st;
     thresh[0] = kind == 0 ? t4[0] : t4[2];
     thresh[1] = kind == 0 ? t4[1] : t4[3];
     thresh[2] = t4[3];
@@ -1064,11 +1076,9 @@ mixts_status mixts_nlist(mixts_handle h, int kind, int* out3, long cap, long* n_
   const int rcap = kind == 0 ? p.nl_cap : p.pl_cap;
   std::vector<int> cnt(std::max(1, rows)), ent((size_t)std::max(1, rows) * rcap);
   if (rows > 0) {
-    cudaMemcpy(cnt.data(), kind == 0 ? h->d.nl_cnt : h->d.pl_cnt, sizeof(int) * rows, cudaMemcpyDeviceToHost);
-    st = cuda_check(h,
-                    cudaMemcpy(ent.data(), kind == 0 ? h->d.nl : h->d.pl, sizeof(int) * (size_t)rows * rcap,
-                               cudaMemcpyDeviceToHost),
-                    "list copy");
+    st = d2h(h, cnt.data(), kind == 0 ? h->d.nl_cnt : h->d.pl_cnt, sizeof(int) * rows, "list counts");
+    if (st == MIXTS_OK)
+      st = d2h(h, ent.data(), kind == 0 ? h->d.nl : h->d.pl, sizeof(int) * (size_t)rows * rcap, "list copy");
     if (st != MIXTS_OK) return st;
   }
   long n = 0;
@@ -1127,11 +1137,11 @@ mixts_status mixts_get_state(mixts_handle h, void* blob, size_t bytes) {
   const uint64_t nb = (uint64_t)h->d.n_beads;
   memcpy(b, &magic, 8);
   memcpy(b + 8, &nb, 8);
-  cudaMemcpy(b + 16, h->d.step_ctr, 8, cudaMemcpyDeviceToHost);
-  cudaMemcpy(b + 24, h->d.heat, 8, cudaMemcpyDeviceToHost);
   const size_t n3 = sizeof(double) * 3 * nb;
-  cudaMemcpy(b + 64, h->d.q_nm, n3, cudaMemcpyDeviceToHost);
-  return cuda_check(h, cudaMemcpy(b + 64 + n3, h->d.p_nm, n3, cudaMemcpyDeviceToHost), "get state");
+  cudaMemcpyAsync(b + 16, h->d.step_ctr, 8, cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(b + 24, h->d.heat, 8, cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(b + 64, h->d.q_nm, n3, cudaMemcpyDeviceToHost, h->stream);
+  return d2h(h, b + 64 + n3, h->d.p_nm, n3, "get state");
 }
 
 mixts_status mixts_set_state(mixts_handle h, const void* blob, size_t bytes) {
@@ -1740,10 +1750,10 @@ extern "C" MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int ta, i
   h->f_valid = false;
   mixts_status st = device_error(h);
   if (st != MIXTS_OK) return st;
-  if (V_host) cudaMemcpy(V_host, h->d.est, sizeof(double), cudaMemcpyDeviceToHost);
+  if (V_host && (st = d2h(h, V_host, h->d.est, sizeof(double), "potential")) != MIXTS_OK) return st;
   if (dVdtheta_host) {
     std::vector<long long> g(2 * MT * MT + 8);
-    st = cuda_check(h, cudaMemcpy(g.data(), gacc, sizeof(long long) * g.size(), cudaMemcpyDeviceToHost), "grad");
+    st = d2h(h, g.data(), gacc, sizeof(long long) * g.size(), "grad");
     if (st != MIXTS_OK) return st;
     auto SG = [&](int a, int b) { return (double)g[2 * (a * MT + b)] * EINV; };
     auto SL = [&](int a, int b) { return (double)g[2 * (a * MT + b) + 1] * EINV; };
@@ -1813,10 +1823,15 @@ mixts_status noalloc_base(void** out) {
 }
 }  // namespace
 
-extern "C" MIXTS_API mixts_status mixts_forces_noalloc(const mixts_system* sys, const mixts_params* prm,
+extern "C" MIXTS_API mixts_status mixts_forces_noalloc(const mixts_system* sys_in, const mixts_params* prm,
                                                        void* stream, double* energy_host) {
-  if (!sys || !prm) return MIXTS_ERR_ARG;
-  const size_t need = mixts_workspace_size(sys, 1, prm);
+  if (!sys_in || !prm) return MIXTS_ERR_ARG;
+  // A force evaluation neither reads nor writes momenta, so a caller without
+  // a momentum array may pass p = NULL; the handle then points p at f, which
+  // no kernel of this path touches through p.
+  mixts_system sys = *sys_in;
+  if (!sys.p) sys.p = sys.f;
+  const size_t need = mixts_workspace_size(&sys, 1, prm);
   if (need == 0) return MIXTS_ERR_ARG;
   if (need > (size_t)MIXTS_NOALLOC_MAX_BYTES) {
     fprintf(stderr, "mixts_forces_noalloc: system needs %zu bytes of scratch, the static maximum is %zu\n", need,
@@ -1829,10 +1844,14 @@ extern "C" MIXTS_API mixts_status mixts_forces_noalloc(const mixts_system* sys, 
   // mixts_init uploads the tables and clears every accumulator, list counter
   // and flag in the scratch, so nothing carries over from the previous call
   mixts_handle h = nullptr;
-  st = mixts_init(sys, 1, prm, base, (size_t)MIXTS_NOALLOC_MAX_BYTES, stream, &h);
+  st = mixts_init(&sys, 1, prm, base, (size_t)MIXTS_NOALLOC_MAX_BYTES, stream, &h);
   if (st != MIXTS_OK) return st;
   st = mixts_forces(h, energy_host);
-  if (st == MIXTS_OK && !energy_host) st = cuda_check(h, cudaStreamSynchronize(h->stream), "noalloc sync");
+  // without an energy pointer mixts_forces does not synchronise: wait here and
+  // read the device error word (list overflow, non-finite forces, box too
+  // small) before the handle that locates it goes away
+  if (st == MIXTS_OK && !energy_host) st = device_error(h);
+  if (st != MIXTS_OK) fprintf(stderr, "mixts_forces_noalloc: %s\n", h->err.c_str());
   mixts_destroy(h);
   return st;
 }

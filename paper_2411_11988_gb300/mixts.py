@@ -102,6 +102,7 @@ def lib():
         L.mixts_batch_tune.argtypes = [C.c_void_p, C.c_int, C.POINTER(_Tuning)]
         L.mixts_potential_grad.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_double,
                                            C.POINTER(C.c_double), C.c_void_p, C.POINTER(C.c_double)]
+        L.mixts_alu_probe.argtypes = [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.mixts_destroy.argtypes = [C.c_void_p]
         L.mixts_last_error.argtypes = [C.c_void_p]
         L.mixts_last_error.restype = C.c_char_p
@@ -114,7 +115,8 @@ EXPORTED = ["mixts_workspace_size", "mixts_init", "mixts_forces", "mixts_step", 
             "mixts_nlist", "mixts_state_size", "mixts_get_state", "mixts_set_state", "mixts_gaussians",
             "mixts_destroy", "mixts_last_error", "mixts_version", "mixts_reload", "mixts_set_timing",
             "mixts_get_timing", "mixts_forces_noalloc", "mixts_potential_grad", "mixts_batch_member",
-            "mixts_batch_tune", "mixts_set_graph", "mixts_rdf_accumulate", "mixts_rdf_normalise"]
+            "mixts_batch_tune", "mixts_set_graph", "mixts_rdf_accumulate", "mixts_rdf_normalise",
+            "mixts_alu_probe"]
 # force-field parameters of the differentiation variant, in mixts_potential_grad's order
 THETA_NAMES = ["sigma_a", "A_a_eV", "b_a", "sigma_b", "A_b_eV", "b_b", "q_a", "eps_aa"]
 PHASES = ["nlist", "pair", "bonded", "pseudo", "prop", "final", "other"]
@@ -301,6 +303,19 @@ class MixTS:
             self.close()
         except Exception:
             pass
+
+
+def alu_peak_tflops(fp64, iters=None, stream=None):
+    """Measured FMA-chain throughput of this GPU in TFLOP/s (binary64 or binary32)."""
+    import torch
+    if iters is None:
+        iters = 2000 if fp64 else 60000
+    st = stream if stream is not None else torch.cuda.current_stream()
+    flop, ms = C.c_double(0.0), C.c_double(0.0)
+    rc = lib().mixts_alu_probe(1 if fp64 else 0, int(iters), C.c_void_p(st.cuda_stream), C.byref(flop), C.byref(ms))
+    if rc != 0:
+        raise MixtsError(rc, "mixts_alu_probe failed")
+    return flop.value / (ms.value * 1e-3) / 1e12, ms.value
 
 
 def _potential_fn():

@@ -123,3 +123,23 @@ def test_batch_member_queries(gpu):
         view.nlist()
     single.close()
     b.close()
+
+
+# members of the 64-system batch workload (water count, P_H, P_O, seed index):
+# the largest (512 waters at P_H = 64), the smallest box at P_H = 64, and
+# classical-oxygen members at both ends of the size range
+C4_MEMBERS = [2, 11, 3, 19, 0, 15]
+
+
+def test_batch_workload_members_match_oracle(gpu):
+    draws = synth.batched_draws(64, 1000)
+    systems = [synth.water_box(draws[i][0], synth.density_box_length(draws[i][0]), draws[i][1], draws[i][2], seed=i)
+               for i in C4_MEMBERS]
+    assert (draws[2][0], draws[2][1]) == (512, 64)
+    b = gpu.MixTSBatch(systems, precision=1, seeds=C4_MEMBERS)
+    E = b.forces()
+    for k, s in enumerate(systems):
+        F_or, parts = oracle.forces(s)
+        assert _force_err(b.f[k].cpu().numpy(), F_or) < 1e-5, C4_MEMBERS[k]
+        assert abs(E[k] - parts[0]) <= 1e-5 * abs(parts[0])
+    b.close()

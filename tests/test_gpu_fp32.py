@@ -38,6 +38,11 @@ def _case(name):
         s = synth.water_box(8, 8.4, 8, 2, seed=3, ion=dict(synth.systems.ION3), electron_P=128)
         s.q = s.q + np.random.default_rng(103).normal(0, 0.08, s.q.shape)
         return s
+    if name in ("h1_o4", "h4_o8"):  # H coarser than O: O owns the O-H terms
+        ph, po = (1, 4) if name == "h1_o4" else (4, 8)
+        s = synth.water_box(27, 9.3, ph, po, seed=12)
+        s.q = s.q + np.random.default_rng(17).normal(0, 0.06, s.q.shape)
+        return s
     if name == "c2":
         return synth.water_box(512, 24.83, 32, 4, seed=0)
     if name == "c3":
@@ -45,7 +50,7 @@ def _case(name):
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("name", ["c1", "c1_spread", "mixed", "c2", "c3"])
+@pytest.mark.parametrize("name", ["c1", "c1_spread", "mixed", "h1_o4", "h4_o8", "c2", "c3"])
 def test_fp32_forces(gpu, name):
     s = _case(name)
     m = gpu.MixTS(s, precision=gpu.FP32_FORCES)

@@ -47,7 +47,16 @@ def _force_err(F, F_or):
     return np.abs(F - F_or).max() / rms
 
 
-@pytest.mark.parametrize("case", ["c1", "c1_spread", "mixed16", "mixed128", "uniform4"])
+def _h_coarser(P_H, P_O, seed=12):
+    """Water with the lighter species on the coarser grid: O owns every O-H
+    term (Fig. 1's N1 = 4, N2 = 1 and N1 = 4, N2 = 2 maps, read with O as the
+    finer particle)."""
+    s = synth.water_box(27, 9.3, P_H, P_O, seed=seed)
+    s.q = s.q + np.random.default_rng(seed + 5).normal(0, 0.06, s.q.shape)
+    return s
+
+
+@pytest.mark.parametrize("case", ["c1", "c1_spread", "mixed16", "mixed128", "uniform4", "h1_o4", "h4_o8"])
 def test_forces_match_oracle(gpu, case):
     if case == "c1":
         s = _c1()
@@ -57,6 +66,10 @@ def test_forces_match_oracle(gpu, case):
         s = _mixed(16)
     elif case == "mixed128":
         s = _mixed(128)
+    elif case == "h1_o4":
+        s = _h_coarser(1, 4)
+    elif case == "h4_o8":
+        s = _h_coarser(4, 8)
     else:
         s = synth.water_box(27, 9.3, 4, 4, seed=4)
     m = gpu.MixTS(s)
@@ -74,9 +87,12 @@ def test_forces_match_oracle(gpu, case):
     m.close()
 
 
-@pytest.mark.parametrize("case", ["c1_spread", "mixed16", "mixed128"])
+@pytest.mark.parametrize("case", ["c1_spread", "mixed16", "mixed128", "h1_o4"])
 def test_neighbour_lists_bit_exact(gpu, case):
-    s = _c1(seed=5, spread=0.15) if case == "c1_spread" else _mixed(16 if case == "mixed16" else 128)
+    if case == "h1_o4":
+        s = _h_coarser(1, 4, seed=14)
+    else:
+        s = _c1(seed=5, spread=0.15) if case == "c1_spread" else _mixed(16 if case == "mixed16" else 128)
     m = gpu.MixTS(s)
     m.forces()
     tl, th = m.nlist(0)
@@ -115,15 +131,19 @@ def _run_both(s, nsteps, **kw):
     return m, run
 
 
-@pytest.mark.parametrize("case", ["c1", "mixed16", "mixed128", "h64"])
+@pytest.mark.parametrize("case", ["c1", "mixed16", "mixed128", "h64", "h1_o4", "h4_o8", "electron1024"])
 def test_one_step_matches_oracle(gpu, case):
     if case == "c1":
         s = _c1(seed=1)
+    elif case in ("h1_o4", "h4_o8"):
+        s = _h_coarser(*((1, 4) if case == "h1_o4" else (4, 8)), seed=13)
+    elif case == "electron1024":  # 256 waters H8/O1 + ion + 1024-bead electron, the large-P transforms
+        s = synth.water_box(256, 18.6, 8, 1, seed=2, ion=dict(synth.systems.ION3), electron_P=1024)
     elif case == "h64":  # the largest bead count of the fused small-P propagation tile
         s = synth.water_box(8, synth.density_box_length(8), 64, 16, seed=11)
     else:
         s = _mixed(16 if case == "mixed16" else 128, seed=9)
-    m, run = _run_both(s, 1, dt=0.25 if case in ("c1", "h64") else 0.1)
+    m, run = _run_both(s, 1, dt=0.1 if case in ("mixed16", "mixed128", "electron1024") else 0.25)
     q, p, f = (x.cpu().numpy() for x in (m.q, m.p, m.f))
     assert np.abs(q - run.q).max() < 1e-11 * np.abs(run.q).max()
     assert np.abs(p - run.p).max() < FTOL * 10 * np.sqrt(np.mean(run.p ** 2))

@@ -30,19 +30,19 @@ def P():
     return pkg
 
 
-def _noalloc_forces(P, sysm, q):
+def _noalloc_forces(P, sysm, q, energy=True, with_p=True, nlist_cap=0, expect=0):
     import torch
     L = P.lib()
     qd = torch.from_numpy(np.ascontiguousarray(q)).cuda()
     pd = torch.zeros_like(qd)
     fd = torch.full_like(qd, float("nan"))
-    st, keep = P.mixts.pack_system(sysm, qd.data_ptr(), pd.data_ptr(), fd.data_ptr(), 0)
-    prm = P.mixts._Params(300.0, 0.25, 100.0, 1.0, 9.0, 0.2, 0, 0)
+    st, keep = P.mixts.pack_system(sysm, qd.data_ptr(), pd.data_ptr() if with_p else 0, fd.data_ptr(), 0)
+    prm = P.mixts._Params(300.0, 0.25, 100.0, 1.0, 9.0, 0.2, 0, nlist_cap)
     e = C.c_double(0.0)
     stream = torch.cuda.current_stream().cuda_stream
-    rc = L.mixts_forces_noalloc(C.byref(st), C.byref(prm), C.c_void_p(stream), C.byref(e))
-    assert rc == 0, P.mixts.STATUS.get(rc, rc)
-    return fd.cpu().numpy(), e.value
+    rc = L.mixts_forces_noalloc(C.byref(st), C.byref(prm), C.c_void_p(stream), C.byref(e) if energy else None)
+    assert rc == expect, P.mixts.STATUS.get(rc, rc)
+    return fd.cpu().numpy(), (e.value if energy else None)
 
 
 @pytest.mark.parametrize("case", ["water32_H8_O2", "ion_electron"])
@@ -73,3 +73,28 @@ def test_noalloc_rejects_oversized(P):
     assert L.mixts_workspace_size(C.byref(st), 1, C.byref(prm)) > (32 << 20)
     rc = L.mixts_forces_noalloc(C.byref(st), C.byref(prm), None, None)
     assert rc == 4
+
+
+def test_noalloc_without_energy_or_momenta(P):
+    """No energy pointer: the call still waits for its work and checks the
+    device error word; no momentum array: p = NULL is accepted."""
+    s = synth.water_box(32, 9.865, 8, 2, seed=1)
+    m = P.MixTS(s)
+    f_ref, _ = m.forces()
+    f_ref = f_ref.cpu().numpy()
+    m.close()
+    rms = np.sqrt(np.mean(f_ref ** 2))
+    for energy, with_p in [(False, True), (True, False), (False, False)]:
+        f, _ = _noalloc_forces(P, s, s.q, energy=energy, with_p=with_p)
+        assert np.abs(f - f_ref).max() / rms <= FTOL
+
+
+def test_noalloc_reports_list_overflow(P):
+    """A neighbour-list capacity far below what the system needs is reported
+    as MIXTS_ERR_NLIST_OVERFLOW on both the energy and the no-energy path, and
+    the next regular call succeeds (the scratch is fully reset)."""
+    s = synth.water_box(32, 9.865, 8, 2, seed=0)
+    for energy in (True, False):
+        _noalloc_forces(P, s, s.q, energy=energy, nlist_cap=32, expect=5)
+    f, v = _noalloc_forces(P, s, s.q)
+    assert np.isfinite(f).all() and np.isfinite(v)
