@@ -69,7 +69,7 @@ typedef struct {
   const int* type_of_atom;    /* [n_atoms] */
   const int* mol_of_atom;     /* [n_atoms]; same molecule, zero image: no nonbonded term */
   const int* P_type;          /* [n_types] bead counts, powers of two, <= 1024 */
-  const double* mass_type;    /* [n_types] amu; the bead mass equals the physical mass */
+  const double* mass_type;    /* [n_types] amu, physical mass (sets the spring constant N m/(beta hbar)^2) */
   const double* charge_type;  /* [n_types] e */
   const double* lj_eps;       /* [n_types*n_types] kcal/mol, symmetric */
   const double* lj_sig;       /* [n_types*n_types] A */
@@ -90,6 +90,10 @@ typedef struct {
   double* p;                  /* DEVICE [n_beads][3] momenta */
   double* f;                  /* DEVICE [n_beads][3] forces, written by the library */
   uint64_t seed;              /* Philox key of the thermostat noise */
+  const double* bead_mass_type; /* [n_types] amu, fictitious bead mass m_f of the kinetic term p^2/2m_f
+                                   (Sec. "Theory" after Eq. rpham: statics do not depend on it);
+                                   NULL: m_f = m. m_f = m/P_t gives ring-polymer molecular dynamics
+                                   in the beta H convention of Eq. (mts-hamiltonian) */
 } mixts_system;
 
 typedef struct {
@@ -101,6 +105,8 @@ typedef struct {
   double dsf_alpha;    /* 1/A, damping of the damped-shifted-force Coulomb */
   int precision;       /* mixts_precision */
   int nlist_cap;       /* entries per owner row of the neighbour list; 0: automatic */
+  int free_ring_substeps; /* free ring polymer evolution (Sec. "Evaluation"): 0 exact in normal modes;
+                             n >= 1 velocity Verlet on the springs with n sub-steps of dt/n */
 } mixts_params;
 
 /* Estimates of the state after the last completed step (or of the current

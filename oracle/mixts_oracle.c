@@ -71,6 +71,11 @@ static void lay_init(const or_system* s, lay_t* L) {
 }
 static void lay_free(lay_t* L) { free(L->rank); }
 
+/* fictitious bead mass of type t (the kinetic term p^2/2m_f of Eq. rpham) */
+static double bead_mass(const or_system* s, int t) {
+  return s->bead_mass_type ? s->bead_mass_type[t] : s->mass_type[t];
+}
+
 static long row_of(const or_system* s, const lay_t* L, int a, int b) {
   int t = s->type_of_atom[a];
   return L->off[t] + (long)b * L->N[t] + L->rank[a];
@@ -746,13 +751,15 @@ static void thermostat(const or_system* s, const lay_t* L, const cst_t* c, const
   for (int t = 0; t < s->n_types; ++t) {
     int P = s->P_type[t], N = L->N[t];
     if (N == 0) continue;
-    double m = s->mass_type[t];
+    double m = bead_mass(s, t);
     double* C = (double*)malloc(sizeof(double) * (size_t)P * P);
     double* om = (double*)malloc(sizeof(double) * (size_t)P);
     double* v = (double*)malloc(sizeof(double) * (size_t)P);
     double* vn = (double*)malloc(sizeof(double) * (size_t)P);
     or_nm_matrix(P, C);
     or_nm_freqs(P, bh, om);
+    /* the modes' frequencies with bead mass m_f: omega_k sqrt(m / m_f) */
+    for (int k = 0; k < P; ++k) om[k] *= sqrt(s->mass_type[t] / m);
     for (int k = 0; k < N; ++k)
       for (int d = 0; d < 3; ++d) {
         for (int j = 0; j < P; ++j) v[j] = p[3 * (L->off[t] + (long)j * N + k) + d];
@@ -791,6 +798,29 @@ static void kick(const or_system* s, const lay_t* L, const cst_t* c, double h, d
       for (int d = 0; d < 3; ++d) p[3 * r + d] += h * F[3 * r + d] * c->kcal;
 }
 
+/* velocity Verlet on the ring-polymer springs of Eq. (mts-hamiltonian-b),
+ * the alternative to the exact normal-mode evolution in Sec. "Evaluation":
+ * n sub-steps of h = dt/n, each p += (h/2) f(q), q += h p/m_f,
+ * p += (h/2) f(q), with f_b = -kappa (2 q_b - q_{b+1} - q_{b-1}) and
+ * kappa = P m/(beta hbar)^2 (ring closure q_P = q_0). One atom, one
+ * Cartesian component: P beads in q[], p[]. */
+static void free_ring_vv(int P, double kap, double mf, double dt, int n, double* q, double* p, double* f) {
+  double h = dt / n;
+  for (int j = 0; j < P; ++j) {
+    int jp = (j + 1) % P, jm = (j + P - 1) % P;
+    f[j] = -kap * (2.0 * q[j] - q[jp] - q[jm]);
+  }
+  for (int sub = 0; sub < n; ++sub) {
+    for (int j = 0; j < P; ++j) p[j] += 0.5 * h * f[j];
+    for (int j = 0; j < P; ++j) q[j] += h * p[j] / mf;
+    for (int j = 0; j < P; ++j) {
+      int jp = (j + 1) % P, jm = (j + P - 1) % P;
+      f[j] = -kap * (2.0 * q[j] - q[jp] - q[jm]);
+    }
+    for (int j = 0; j < P; ++j) p[j] += 0.5 * h * f[j];
+  }
+}
+
 static void free_ring(const or_system* s, const lay_t* L, const cst_t* c, const or_params* prm, double* q,
                       double* p) {
   double kT = c->kB * prm->T;
@@ -799,7 +829,7 @@ static void free_ring(const or_system* s, const lay_t* L, const cst_t* c, const 
   for (int t = 0; t < s->n_types; ++t) {
     int P = s->P_type[t], N = L->N[t];
     if (N == 0) continue;
-    double m = s->mass_type[t];
+    double m = bead_mass(s, t);
     double* C = (double*)malloc(sizeof(double) * (size_t)P * P);
     double* om = (double*)malloc(sizeof(double) * (size_t)P);
     double* qv = (double*)malloc(sizeof(double) * (size_t)P);
@@ -808,11 +838,21 @@ static void free_ring(const or_system* s, const lay_t* L, const cst_t* c, const 
     double* pn = (double*)malloc(sizeof(double) * (size_t)P);
     or_nm_matrix(P, C);
     or_nm_freqs(P, bh, om);
+    for (int k = 0; k < P; ++k) om[k] *= sqrt(s->mass_type[t] / m);
+    double kap = P * s->mass_type[t] / (bh * bh);
     for (int k = 0; k < N; ++k)
       for (int d = 0; d < 3; ++d) {
         for (int j = 0; j < P; ++j) {
           qv[j] = q[3 * (L->off[t] + (long)j * N + k) + d];
           pv[j] = p[3 * (L->off[t] + (long)j * N + k) + d];
+        }
+        if (prm->vv_substeps > 0) {
+          free_ring_vv(P, kap, m, dt, prm->vv_substeps, qv, pv, qn);
+          for (int j = 0; j < P; ++j) {
+            q[3 * (L->off[t] + (long)j * N + k) + d] = qv[j];
+            p[3 * (L->off[t] + (long)j * N + k) + d] = pv[j];
+          }
+          continue;
         }
         for (int mm = 0; mm < P; ++mm) {
           double aq = 0.0, ap = 0.0;
@@ -889,11 +929,11 @@ void or_estimators(const or_system* s, const or_params* prm, const double* q, co
   long nbeads = L.off[nt];
   for (int t = 0; t < nt; ++t) {
     int P = s->P_type[t], N = L.N[t];
-    double m = s->mass_type[t];
+    double m = s->mass_type[t], mf = bead_mass(s, t);
     double kspr = P * m / (bh * bh);
     double et = 0.0, cv = 0.0, rg = 0.0;
     for (long r = L.off[t]; r < L.off[t + 1]; ++r)
-      for (int d = 0; d < 3; ++d) ke += p[3 * r + d] * p[3 * r + d] / (2.0 * m);
+      for (int d = 0; d < 3; ++d) ke += p[3 * r + d] * p[3 * r + d] / (2.0 * mf);
     for (int k = 0; k < N; ++k) {
       double cen[3] = {0, 0, 0};
       for (int j = 0; j < P; ++j)

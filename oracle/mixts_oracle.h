@@ -53,6 +53,8 @@ typedef struct {
   const double* angle_k;     /* kcal/mol/rad^2, V = k/2 (theta-theta0)^2 */
   const double* angle_theta0;/* rad */
   double box, r_cut, dsf_alpha;
+  const double* bead_mass_type; /* [n_types] fictitious bead mass m_f (amu) of the kinetic term
+                                   p^2/2m_f (Sec. "Theory", Eq. rpham); NULL: m_f = m */
 } or_system;
 
 typedef struct {
@@ -61,6 +63,8 @@ typedef struct {
   double tau_centroid; /* fs; <= 0 switches the centroid friction off */
   double pile_lambda;  /* gamma_k = 2 lambda omega_k for k > 0; 0 switches it off */
   uint64_t seed;
+  int vv_substeps;     /* free ring polymer: 0 exact normal-mode evolution; n >= 1 velocity
+                          Verlet on the springs with n sub-steps of dt/n (Sec. "Evaluation") */
 } or_params;
 
 /* constants in internal units: [0]=kB amu A^2/fs^2/K, [1]=hbar amu A^2/fs,
@@ -93,13 +97,16 @@ long or_nlist(const or_system* s, const double* q, long cap, int* out3, double* 
  * out_thresh[0]=d_max sites, [1]=d_max pseudo, [2]=threshold */
 long or_pseudo_list(const or_system* s, const double* q, long cap, int* out3, double* out_thresh);
 
-/* orthonormal real normal-mode matrix C[j*P+k] and frequencies omega_k (1/fs) */
+/* orthonormal real normal-mode matrix C[j*P+k] and frequencies omega_k (1/fs)
+ * of the free ring polymer with bead mass equal to the physical mass; with a
+ * bead mass m_f they scale by sqrt(m / m_f) */
 void or_nm_matrix(int P, double* C);
 void or_nm_freqs(int P, double beta_hbar, double* omega);
 
 /* one O(dt/2) B(dt/2) A(dt) B(dt/2) O(dt/2) step in place; F holds the
  * forces at q on entry and at the new q on exit. heat accumulates minus the
- * kinetic-energy change made by the two thermostat half steps (kcal/mol). */
+ * kinetic-energy change made by the two thermostat half steps (kcal/mol).
+ * Momenta are p = m_f dq/dt with the bead mass m_f. */
 void or_step(const or_system* s, const or_params* prm, double* q, double* p, double* F,
              uint64_t step, double* heat, double* parts);
 

@@ -51,12 +51,13 @@ class OrSystem(C.Structure):
         ("n_angles", C.c_int), ("angles", C.POINTER(C.c_int)),
         ("angle_k", C.POINTER(C.c_double)), ("angle_theta0", C.POINTER(C.c_double)),
         ("box", C.c_double), ("r_cut", C.c_double), ("dsf_alpha", C.c_double),
+        ("bead_mass_type", C.POINTER(C.c_double)),
     ]
 
 
 class OrParams(C.Structure):
     _fields_ = [("T", C.c_double), ("dt", C.c_double), ("tau_centroid", C.c_double),
-                ("pile_lambda", C.c_double), ("seed", C.c_uint64)]
+                ("pile_lambda", C.c_double), ("seed", C.c_uint64), ("vv_substeps", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -110,6 +111,9 @@ class _Bound:
             angles=i32(sysm.angles).ravel(), angle_k=f64(sysm.angle_k),
             angle_theta0=f64(sysm.angle_theta0),
         )
+        bm = getattr(sysm, "bead_mass_type", None)
+        if bm is not None:
+            self.keep["bead_mass_type"] = f64(bm)
         k = self.keep
         self.s = OrSystem(
             sysm.n_atoms, sysm.n_types, _p(k["type_of_atom"], C.c_int), _p(k["mol_of_atom"], C.c_int),
@@ -119,7 +123,8 @@ class _Bound:
             int(sysm.bonds.shape[0]), _p(k["bonds"], C.c_int), _p(k["bond_k"], C.c_double),
             _p(k["bond_r0"], C.c_double), int(sysm.angles.shape[0]), _p(k["angles"], C.c_int),
             _p(k["angle_k"], C.c_double), _p(k["angle_theta0"], C.c_double),
-            float(sysm.box), float(r_cut), float(alpha))
+            float(sysm.box), float(r_cut), float(alpha),
+            _p(k["bead_mass_type"], C.c_double) if bm is not None else None)
         self.nt = sysm.n_types
         self.nbeads = sysm.n_beads
 
@@ -270,8 +275,10 @@ def nm_freqs(P, beta_hbar):
     return w
 
 
-def make_params(T=300.0, dt=0.25, tau=100.0, lam=1.0, seed=0):
-    return OrParams(float(T), float(dt), float(tau), float(lam), int(seed))
+def make_params(T=300.0, dt=0.25, tau=100.0, lam=1.0, seed=0, vv=0):
+    """Integrator parameters; vv > 0 evolves the free ring polymer by velocity
+    Verlet on the springs with vv sub-steps instead of exactly."""
+    return OrParams(float(T), float(dt), float(tau), float(lam), int(seed), int(vv))
 
 
 class Runner:

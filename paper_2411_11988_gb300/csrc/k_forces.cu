@@ -347,6 +347,63 @@ __device__ __forceinline__ void dsf_direct(const Dev& d, double s, double* g, do
 // binary64 quadratics with binary32 tails, forces rounded once into the fixed
 // point; the partner's bead gets the reaction.
 // ---------------------------------------------------------------------------
+// Work items of the FP64 sweep for the current list: every owner row gets
+// (slice blocks) x (chunks of P32_CH entries per lane group) items, only as
+// many chunks as its row holds, written in row order (finest owners first,
+// so the heaviest items are handed out first). One CTA; also resets the
+// counter the sweep's warps take items from.
+constexpr int ITEM_THREADS = 1024;
+__global__ void __launch_bounds__(ITEM_THREADS) k_pair_items(Dev d) {
+  __shared__ int wsum[ITEM_THREADS / 32];
+  __shared__ int carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < d.n_nonp; base += ITEM_THREADS) {
+    const int i = base + tid;
+    int n = 0, nch = 0, lgsb = 0;
+    if (i < d.n_nonp) {
+      const int cnt = min(d.nl_cnt[i], d.nl_cap);
+      const int lgP = d.ainfo[i].log2P;
+      const int lgPp = lgP < 5 ? lgP : 5;
+      const int per = P32_CH << (5 - lgPp);
+      nch = (cnt + per - 1) / per;
+      lgsb = lgP - lgPp;
+      n = nch << lgsb;
+    }
+    int incl = n;  // inclusive scan over the block
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int v = lane < ITEM_THREADS / 32 ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      if (lane < ITEM_THREADS / 32) wsum[lane] = v;
+    }
+    __syncthreads();
+    const int off = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - n;
+    for (int k = 0; k < n; ++k) {
+      const int sb = k / nch, ch = k - sb * nch;
+      d.pitems[off + k] = make_int2(i, (sb << 16) | ch);
+    }
+    __syncthreads();
+    if (tid == 0) carry += wsum[ITEM_THREADS / 32 - 1];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    d.pctr[0] = carry;
+    d.pctr[1] = 0;
+  }
+}
+
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   extern __shared__ double dtab[];  // DSF interval table: 6 doubles, then 8 floats per interval
   __shared__ PairPar tab[MT * MT];
@@ -382,11 +439,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int lgM = d.lgPmax_nb;
-  const int nsbm = lgM > 5 ? 1 << (lgM - 5) : 1;
-  const int nch = d.p64_nch;
-  const int n_items = d.n_nonp * nsbm * nch;
+  const int n_items = d.pctr[0];
   const double rc = d.rc;
   // r_cut^2 in the 2^-96 A^2 units of the integer squared distances (exact)
   fm::u128 rc2q;
@@ -402,18 +455,21 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
       rc2q = fm::u128{0ull, sh > -53 ? m >> (-sh) : 0ull};
   }
   const int base = d.dsf_base;
-  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_items; w += nwarps) {
-    const int ch = w % nch;
-    const int rest = w / nch;
-    const int sb = rest % nsbm, pos = rest / nsbm;
+  // items are handed out one per warp from a counter (the fixed-point sums
+  // make the result independent of which warp takes which item)
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(d.pctr + 1, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= n_items) break;
+    const int2 it = d.pitems[w];
+    const int pos = it.x, sb = it.y >> 16, ch = it.y & 0xFFFF;
     const AtomInfo ai = d.ainfo[pos];
     const int lgPi = ai.log2P;
     const int lgPp = lgPi < 5 ? lgPi : 5;  // log2 of the lanes per group
     const int lgG = 5 - lgPp;
-    if (sb >= (1 << (lgPi - lgPp))) continue;
     const int cnt = min(d.nl_cnt[pos], d.nl_cap);
     const int e0 = ch * (P32_CH << lgG);
-    if (e0 >= cnt) continue;
     const int e1 = min(cnt, e0 + (P32_CH << lgG));
     const int sl = lane & ((1 << lgPp) - 1), grp = lane >> lgPp;
     const int b = (sb << lgPp) + sl;  // owner bead of this lane
@@ -426,8 +482,12 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
     long long fix = 0, fiy = 0, fiz = 0;
     double elj = 0.0, ec = 0.0, vir = 0.0;
     int nev = 0, nlj = 0, bad = 0;
-    for (int e = e0 + grp; e < e1; e += (1 << lgG)) {
-      const int ent = lst[e];
+    // every lane runs the same number of rounds (the reaction sums below
+    // are warp-collective); a group past the end of the chunk idles
+    for (int eb = e0; eb < e1; eb += (1 << lgG)) {
+      const int e = eb + grp;
+      const bool valid = e < e1;
+      const int ent = lst[valid ? e : e0];
       const int tj = (ent >> 7) & 15;
       const int lgPj = tLg[tj];
       const int row0j = ent >> 11, oj = tOff[tj];
@@ -436,44 +496,64 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
       const longlong4_32a sv = shi[ent & 127];
       const long long ix = (xj.x - xi.x) + sv.x, iy = (xj.y - xi.y) + sv.y, iz = (xj.z - xi.z) + sv.z;
       const fm::u128 q2 = fm::norm2(ix, iy, iz);
-      if (!fm::lt128(q2, rc2q)) continue;
-      const int pq = fm::msb128(q2);
-      const double r2 = pq >= 0 ? fm::u128_to_dbl(q2, pq, 96) : 0.0;
-      const int fl = flg[trow + tj];
-      const PairPar pp = tab[trow + tj];
-      double fr = 0.0;
-      if (fl & 1) {
-        double g, fg, x = 0.0;
-        const int key = pq >= 6 ? fm::dsf_key(q2, pq, &x) : 0;
-        if (key >= base)
-          dsf_poly_split(dtab + 6 * (key - base), ftab + 8 * (key - base), x, &g, &fg);
-        else
-          dsf_direct(d, r2, &g, &fg);
-        ec = fma(pp.qq, g, ec);
-        fr = pp.qq * fg;
+      long long kx = 0, ky = 0, kz = 0;
+      if (valid && fm::lt128(q2, rc2q)) {
+        const int pq = fm::msb128(q2);
+        const double r2 = pq >= 0 ? fm::u128_to_dbl(q2, pq, 96) : 0.0;
+        const int fl = flg[trow + tj];
+        const PairPar pp = tab[trow + tj];
+        double fr = 0.0;
+        if (fl & 1) {
+          double g, fg, x = 0.0;
+          const int key = pq >= 6 ? fm::dsf_key(q2, pq, &x) : 0;
+          if (key >= base)
+            dsf_poly_split(dtab + 6 * (key - base), ftab + 8 * (key - base), x, &g, &fg);
+          else
+            dsf_direct(d, r2, &g, &fg);
+          ec = fma(pp.qq, g, ec);
+          fr = pp.qq * fg;
+        }
+        if (fl & 2) {
+          const double rinv = rsqrt(r2);
+          const double r = r2 * rinv;
+          const double rinv2 = rinv * rinv;
+          const double sr2 = pp.s2 * rinv2;
+          const double sr6 = sr2 * sr2 * sr2;
+          const double sr12 = sr6 * sr6;
+          elj += pp.e4 * (sr12 - sr6) - pp.vrc - (r - rc) * pp.dvrc;
+          fr += (6.0 * pp.e4 * (2.0 * sr12 - sr6) * rinv + pp.dvrc) * rinv;
+          ++nlj;
+        }
+        kx = fm::mulfix(fr, ix, 4 + wsh, &bad);
+        ky = fm::mulfix(fr, iy, 4 + wsh, &bad);
+        kz = fm::mulfix(fr, iz, 4 + wsh, &bad);
+        fix -= kx;
+        fiy -= ky;
+        fiz -= kz;
+        vir = fma(fr, r2, vir);
+        ++nev;
       }
-      if (fl & 2) {
-        const double rinv = rsqrt(r2);
-        const double r = r2 * rinv;
-        const double rinv2 = rinv * rinv;
-        const double sr2 = pp.s2 * rinv2;
-        const double sr6 = sr2 * sr2 * sr2;
-        const double sr12 = sr6 * sr6;
-        elj += pp.e4 * (sr12 - sr6) - pp.vrc - (r - rc) * pp.dvrc;
-        fr += (6.0 * pp.e4 * (2.0 * sr12 - sr6) * rinv + pp.dvrc) * rinv;
-        ++nlj;
+      // A coarser partner's bead is shared by 2^lgR consecutive lanes of the
+      // group: sum their reactions exactly in registers first, so one lane
+      // issues the atomics instead of 2^lgR lanes on the same address.
+      const int lgR = min(lgPi - lgPj, lgPp);
+      const int lgRmax = __reduce_max_sync(0xffffffffu, (unsigned)lgR);
+      for (int o = 0; o < lgRmax; ++o) {
+        const long long vx = __shfl_xor_sync(0xffffffffu, kx, 1 << o);
+        const long long vy = __shfl_xor_sync(0xffffffffu, ky, 1 << o);
+        const long long vz = __shfl_xor_sync(0xffffffffu, kz, 1 << o);
+        if (o < lgR) {
+          kx += vx;
+          ky += vy;
+          kz += vz;
+        }
       }
-      const long long kx = fm::mulfix(fr, ix, 4 + wsh, &bad), ky = fm::mulfix(fr, iy, 4 + wsh, &bad),
-                      kz = fm::mulfix(fr, iz, 4 + wsh, &bad);
-      fix -= kx;
-      fiy -= ky;
-      fiz -= kz;
-      vir = fma(fr, r2, vir);
-      ++nev;
-      unsigned long long* fj = d.F_fix + 3 * (size_t)(row0j + bj * tN[tj]);
-      atomicAdd(fj + 0, (unsigned long long)kx);
-      atomicAdd(fj + 1, (unsigned long long)ky);
-      atomicAdd(fj + 2, (unsigned long long)kz);
+      if ((sl & ((1 << lgR) - 1)) == 0 && (kx | ky | kz) != 0) {
+        unsigned long long* fj = d.F_fix + 3 * (size_t)(row0j + bj * tN[tj]);
+        atomicAdd(fj + 0, (unsigned long long)kx);
+        atomicAdd(fj + 1, (unsigned long long)ky);
+        atomicAdd(fj + 2, (unsigned long long)kz);
+      }
     }
     // the owner's force: lanes of the same bead (one per group) summed exactly
     for (int o = 1 << lgPp; o < 32; o <<= 1) {
@@ -510,29 +590,204 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
 }
 
 // ---------------------------------------------------------------------------
-// nonbonded pair sweep, FP32 forces (precision MIXTS_FP32_FORCES), the terms
-// of Eq. (mts-hamiltonian) regrouped by slice of the finest grid.
+// nonbonded pair sweep, FP32 forces (precision MIXTS_FP32_FORCES).
 //
-// Full neighbour lists (every row lists all partners): only the owner's bead
-// is written, so there are no reaction atomics; every term is evaluated from
-// both sides and the energies carry a factor 1/2.
+// Full neighbour lists (every row lists all partners): only the owner's beads
+// are written, so there are no per-term reaction atomics; every term is
+// evaluated from both of its atoms and energies and counts carry a factor 1/2.
 //
-// One warp per (owner atom, block of slices, chunk of its full list). The
-// lanes are slices s of the finest grid: P' = min(P_max, 32) lanes per group
-// and G = 32 / P' groups taking different list entries, so an entry is decoded
-// once per group and every lane evaluates the same atom pair on its own slice
-// (owner bead s >> (lgP_max - lgP_i), partner bead s >> (lgP_max - lgP_j));
-// the pair is active at s iff s is a multiple of P_max / P*. Displacements are
-// the bead-0 displacement (exact grid part plus remainder, binary32) plus the
-// two beads' offsets from their bead 0, so the result carries no large
-// cancellation. The damped-shifted-force Coulomb uses the erfc approximation
-// of Abramowitz & Stegun, Handbook of Mathematical Functions, eq. 7.1.26
-// (|error| <= 1.5e-7), with the exact Gaussian in the force.
+// Before the sweep, k_list_seg32 regroups each row by partner type (a
+// counting sort, one warp per row) and folds the pair's bead-0 displacement
+// (r_j0 + n L) - r_i0 into each entry once, in binary32 from the exact
+// 2^-12 A grid parts plus their remainders. An item is then (owner atom i,
+// partner type t, block of 32 owner beads, chunk of entries) with one fine
+// grid P* = max(P_i, P_t), one weight 1/P* and one parameter set: lanes are
+// the owner's beads (groups of min(P_i, 32) lanes take different entries) and
+// each lane walks the P* / P_i fine slices of its bead, s = b (P*/P_i) + k,
+// meeting partner bead s >> log2(P* / P_t). The displacement of a term is
+// the entry's bead-0 displacement plus the two beads' binary32 offsets from
+// their bead 0, so no large cancellation enters. Items hold ~2^10 terms
+// whatever the bead counts and are handed out from a counter.
+//
+// The damped-shifted-force Coulomb uses the erfc approximation of Abramowitz
+// & Stegun, Handbook of Mathematical Functions, eq. 7.1.26 (|error| <=
+// 1.5e-7), with the exact Gaussian in the force.
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NL_THREADS) k_list_seg32(Dev d) {
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= d.n_nonp) return;
+  const int nt = d.n_types;
+  const int cnt = min(d.nl_cnt[i], d.nl_cap);
+  const int* row = d.nl + (size_t)i * d.nl_cap;
+  // lane u counts the entries whose partner is of type u (n_types <= 16)
+  int c_mine = 0;
+  for (int e0 = 0; e0 < cnt; e0 += 32) {
+    const int e = e0 + lane;
+    const int t = e < cnt ? (row[e] >> 7) & 15 : -1;
+    for (int u = 0; u < nt; ++u) {
+      const unsigned m = __ballot_sync(0xffffffffu, t == u);
+      if (lane == u) c_mine += __popc(m);
+    }
+  }
+  int incl = c_mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  int next = incl - c_mine;  // lane u: next slot of type u
+  if (lane <= nt) d.nlseg[(size_t)i * (nt + 1) + lane] = lane < nt ? next : cnt;
+  const int r0i = d.ainfo[i].row0;
+  const float4 hi = d.Xf[r0i], lo = d.Xl[r0i];
+  const float bh = d.box_hi, bl = d.box_lo;
+  float4* out = d.nlB + (size_t)i * d.nl_cap;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int e0 = 0; e0 < cnt; e0 += 32) {
+    const int e = e0 + lane;
+    const int ent = e < cnt ? row[e] : 0;
+    const int t = e < cnt ? (ent >> 7) & 15 : -1;
+    int dest = 0;
+    for (int u = 0; u < nt; ++u) {
+      const unsigned m = __ballot_sync(0xffffffffu, t == u);
+      const int bse = __shfl_sync(0xffffffffu, next, u);
+      if (t == u) dest = bse + __popc(m & lt_mask);
+      if (lane == u) next += __popc(m);
+    }
+    if (e < cnt) {
+      const int row0j = ent >> 11, code = ent & 127;
+      const float nx = (float)(code / 25 - 2), ny = (float)((code / 5) % 5 - 2), nz = (float)(code % 5 - 2);
+      const float4 hj = d.Xf[row0j], lj = d.Xl[row0j];
+      const float bx = ((hj.x - hi.x) + nx * bh) + ((lj.x - lo.x) + nx * bl);
+      const float by = ((hj.y - hi.y) + ny * bh) + ((lj.y - lo.y) + ny * bl);
+      const float bz = ((hj.z - hi.z) + nz * bh) + ((lj.z - lo.z) + nz * bl);
+      const int abase = d.off[t] + ((row0j - d.off[t]) << d.log2P[t]);  // atom-major bead 0 of j
+      out[dest] = make_float4(bx, by, bz, __int_as_float((abase << 4) | t));
+    }
+  }
+}
+
+// log2 of the entries of one FP32 item: 2^LG_P32_TERMS terms = entries x
+// (owner beads of the block) x (fine slices per owner bead)
+__device__ __forceinline__ int p32_lg_entries(int lgPi, int lgPt) {
+  const int lgPp = lgPi < 5 ? lgPi : 5;
+  const int lgS = lgPi > lgPt ? lgPi : lgPt;
+  const int lgE = LG_P32_TERMS - lgPp - (lgS - lgPi);
+  return lgE > 0 ? lgE : 0;
+}
+
+// Items of the FP32 sweep for the current list: (row, partner type, slice
+// block, chunk), rows in order (finest owners first). One CTA; also resets
+// the hand-out counter.
+__global__ void __launch_bounds__(ITEM_THREADS) k_pair_items32(Dev d) {
+  __shared__ int wsum[ITEM_THREADS / 32];
+  __shared__ int carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nt = d.n_types;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < d.n_nonp; base += ITEM_THREADS) {
+    const int i = base + tid;
+    int n = 0, lgP = 0, lgsb = 0;
+    const int* seg = d.nlseg + (size_t)i * (nt + 1);
+    if (i < d.n_nonp) {
+      lgP = d.ainfo[i].log2P;
+      lgsb = lgP > 5 ? lgP - 5 : 0;
+      for (int t = 0; t < nt; ++t) {
+        const int c = seg[t + 1] - seg[t];
+        const int E = 1 << p32_lg_entries(lgP, d.log2P[t]);
+        n += ((c + E - 1) / E) << lgsb;
+      }
+    }
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int v = lane < ITEM_THREADS / 32 ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      if (lane < ITEM_THREADS / 32) wsum[lane] = v;
+    }
+    __syncthreads();
+    int off = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - n;
+    if (i < d.n_nonp) {
+      for (int t = 0; t < nt; ++t) {
+        const int c = seg[t + 1] - seg[t];
+        const int E = 1 << p32_lg_entries(lgP, d.log2P[t]);
+        const int nch = (c + E - 1) / E;
+        for (int sb = 0; sb < (1 << lgsb); ++sb)
+          for (int ch = 0; ch < nch; ++ch) d.pitems[off++] = make_int2(i, (t << 27) | (sb << 20) | ch);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) carry += wsum[ITEM_THREADS / 32 - 1];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    d.pctr[0] = carry;
+    d.pctr[1] = 0;
+  }
+}
+
+template <bool LJ>
+__device__ __forceinline__ void pair32_entries(const float4* __restrict__ lst, int e_begin, int e_end, int estep,
+                                               int lgr, int sh_t, const float4* __restrict__ Xd, int b, float4 di,
+                                               float qq, float e4, float s2, float vrc, float dvrc, float rc,
+                                               float rc2, float alpha, float alpha2, float g2a, float cf, float c0,
+                                               float& fx, float& fy, float& fz, float& ec, float& elj, float& vir,
+                                               int& nev) {
+  // erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x)
+  const float ap = 0.3275911f, a1 = 0.254829592f, a2 = -0.284496736f, a3 = 1.421413741f, a4 = -1.453152027f,
+              a5 = 1.061405429f;
+  const float nl2e = -alpha2 * 1.4426950408889634f;
+  const float pa = ap * alpha;
+  for (int e = e_begin; e < e_end; e += estep) {
+    const float4 B = lst[e];
+    const int abase = __float_as_int(B.w) >> 4;
+    const float bx = B.x - di.x, by = B.y - di.y, bz = B.z - di.z;
+    for (int k = 0; k < (1 << lgr); ++k) {
+      const int s = (b << lgr) + k;  // fine slice of the pair's grid
+      const float4 dj = Xd[abase + (s >> sh_t)];
+      const float dx = bx + dj.x, dy = by + dj.y, dz = bz + dj.z;
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      if (r2 < rc2) {
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float t = __fdividef(1.0f, fmaf(pa, r, 1.0f));
+        float ex;  // exp(-a^2 r^2), argument in [-a^2 rc^2, 0]
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(nl2e * r2));
+        const float pl = fmaf(fmaf(fmaf(fmaf(a5, t, a4), t, a3), t, a2), t, a1) * t;
+        const float erc = pl * ex;
+        ec = fmaf(qq, fmaf(erc, rinv, fmaf(cf, r - rc, -c0)), ec);
+        float fr = qq * (fmaf(erc * rinv, rinv, fmaf(g2a * ex, rinv, -cf)) * rinv);
+        if (LJ) {
+          const float rinv2 = rinv * rinv;
+          const float sr2 = s2 * rinv2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
+          elj += e4 * (sr12 - sr6) - vrc - (r - rc) * dvrc;
+          fr += (6.0f * e4 * (2.0f * sr12 - sr6) * rinv + dvrc) * rinv;
+        }
+        // force on i is minus the force on j along d = x_j - x_i
+        fx = fmaf(-fr, dx, fx);
+        fy = fmaf(-fr, dy, fy);
+        fz = fmaf(-fr, dz, fz);
+        vir = fmaf(fr, r2, vir);
+        ++nev;
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
   __shared__ float qqt[MT * MT], e4t[MT * MT], s2t[MT * MT], vrct[MT * MT], dvrct[MT * MT];
-  __shared__ float4 shh[125], shl[125];
-  __shared__ int tN[MT], tLg[MT], tOff[MT];
+  __shared__ int tLg[MT], tOff[MT];
   const int nt = d.n_types;
   for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
     const PairPar pp = d.pairpar[(e / nt) * MT + (e % nt)];
@@ -543,120 +798,66 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
     dvrct[e] = (float)pp.dvrc;
   }
   for (int e = threadIdx.x; e < nt; e += blockDim.x) {
-    tN[e] = d.N[e];
     tLg[e] = d.log2P[e];
     tOff[e] = d.off[e];
   }
-  for (int e = threadIdx.x; e < 125; e += blockDim.x) {
-    const int nx = e / 25 - 2, ny = (e / 5) % 5 - 2, nz = e % 5 - 2;
-    const double lo = d.box - (double)d.box_hi;
-    shh[e] = make_float4(nx * d.box_hi, ny * d.box_hi, nz * d.box_hi, 0.0f);
-    shl[e] = make_float4((float)(nx * lo), (float)(ny * lo), (float)(nz * lo), 0.0f);
-  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int lgM = d.lgPmax_nb;
-  const int lgPp = lgM < 5 ? lgM : 5;  // log2 P'
-  const int lgG = 5 - lgPp;
-  const int sl = lane & ((1 << lgPp) - 1), grp = lane >> lgPp;
-  const int nsb = 1 << (lgM - lgPp), nch = d.p32_nch;
-  const int n_items = d.n_nonp * nsb * nch;
+  const int n_items = d.pctr[0];
   const float rc = (float)d.rc, rc2 = (float)d.rc2;
   const float alpha = (float)d.alpha, alpha2 = (float)(d.alpha * d.alpha);
   const float g2a = (float)d.dsf_g, cf = (float)d.dsf_cf, c0 = (float)d.dsf_erfc_rc_over_rc;
-  // erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x)
-  const float ap = 0.3275911f, a1 = 0.254829592f, a2 = -0.284496736f, a3 = 1.421413741f, a4 = -1.453152027f,
-              a5 = 1.061405429f;
-  const float log2e = 1.4426950408889634f;
-  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_items; w += nwarps) {
-    const int ch = w % nch;
-    const int rest = w / nch;
-    const int sb = rest % nsb, pos = rest / nsb;
-    const int cnt = min(d.nl_cnt[pos], d.nl_cap);
-    const int e0 = ch * (P32_CH << lgG);
-    if (e0 >= cnt) continue;
-    const int e1 = min(cnt, e0 + (P32_CH << lgG));
-    const AtomInfo ai = d.ainfo[pos];
-    const int s = (sb << lgPp) + sl;  // slice of the finest grid
-    const int row_i = ai.row0 + (s >> (lgM - ai.log2P)) * ai.stride;
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(d.pctr + 1, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= n_items) break;
+    const int2 it = d.pitems[w];
+    const int i = it.x, t = it.y >> 27, sb = (it.y >> 20) & 127, ch = it.y & 0xFFFFF;
+    const AtomInfo ai = d.ainfo[i];
+    const int lgPi = ai.log2P, lgPt = tLg[t];
+    const int lgPp = lgPi < 5 ? lgPi : 5;  // log2 of the lanes per group
+    const int lgG = 5 - lgPp;
+    const int lgS = lgPi > lgPt ? lgPi : lgPt;
+    const int lgr = lgS - lgPi;  // fine slices per owner bead
+    const int sl = lane & ((1 << lgPp) - 1), grp = lane >> lgPp;
+    const int b = (sb << lgPp) + sl;  // owner bead of this lane
+    const int* seg = d.nlseg + (size_t)i * (nt + 1);
+    const int E = 1 << p32_lg_entries(lgPi, lgPt);
+    const int e0 = seg[t] + ch * E, e1 = min(seg[t + 1], e0 + E);
     const int oi = tOff[ai.type];
-    const float4 di = d.Xd[oi + ((ai.row0 - oi) << ai.log2P) + (s >> (lgM - ai.log2P))];
-    const float4 hi0 = d.Xf[ai.row0], lo0 = d.Xl[ai.row0];
-    const int* lst = d.nl + (size_t)pos * d.nl_cap;
-    const int trow = ai.type * nt;
-    float fx = 0.f, fy = 0.f, fz = 0.f, elj = 0.f, ec = 0.f, vir = 0.f;
-    int nev = 0, nlj = 0;
-    int ent_next = e0 + grp < e1 ? lst[e0 + grp] : 0;
-    for (int e = e0 + grp; e < e1; e += (1 << lgG)) {
-      const int ent = ent_next;  // the next entry's load overlaps this one's work
-      ent_next = e + (1 << lgG) < e1 ? lst[e + (1 << lgG)] : 0;
-      const int tj = (ent >> 7) & 15;
-      const int lgPj = tLg[tj];
-      const int lgS = ai.log2P > lgPj ? ai.log2P : lgPj;  // log2 P*
-      const int row0j = ent >> 11;
-      const float4 hj = d.Xf[row0j], lj = d.Xl[row0j];
-      const int oj = tOff[tj];
-      const float4 dj = d.Xd[oj + ((row0j - oj) << lgPj) + (s >> (lgM - lgPj))];
-      const float4 sh = shh[ent & 127], sm = shl[ent & 127];
-      const float dx = (((hj.x - hi0.x) + sh.x) + ((lj.x - lo0.x) + sm.x)) + (dj.x - di.x);
-      const float dy = (((hj.y - hi0.y) + sh.y) + ((lj.y - lo0.y) + sm.y)) + (dj.y - di.y);
-      const float dz = (((hj.z - hi0.z) + sh.z) + ((lj.z - lo0.z) + sm.z)) + (dj.z - di.z);
-      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-      const bool act = (s & ((1 << (lgM - lgS)) - 1)) == 0;
-      if (!(act && r2 < rc2)) continue;
-      const int k = trow + tj;
-      const float wgt = __int_as_float((127 - lgS) << 23);  // 1/P*
-      const float rinv = rsqrtf(r2);
-      const float r = r2 * rinv;
-      float fr = 0.f, et = 0.f, lt = 0.f;
-      const float qq = qqt[k];
-      if (qq != 0.f) {
-        const float t = __fdividef(1.0f, fmaf(ap, alpha * r, 1.0f));
-        float ex;  // exp(-a^2 r^2), argument in [-a^2 rc^2, 0]
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(-alpha2 * log2e * r2));
-        const float pl = fmaf(fmaf(fmaf(fmaf(a5, t, a4), t, a3), t, a2), t, a1) * t;
-        const float erc = pl * ex;
-        et = qq * (fmaf(erc, rinv, -c0) + cf * (r - rc));
-        fr = qq * (fmaf(erc * rinv, rinv, fmaf(g2a * ex, rinv, -cf)) * rinv);
-      }
-      const float e4 = e4t[k];
-      if (e4 != 0.f) {
-        const float rinv2 = rinv * rinv;
-        const float sr2 = s2t[k] * rinv2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
-        lt = e4 * (sr12 - sr6) - vrct[k] - (r - rc) * dvrct[k];
-        fr += (6.0f * e4 * (2.0f * sr12 - sr6) * rinv + dvrct[k]) * rinv;
-        ++nlj;
-      }
-      fr *= wgt;
-      // force on i is minus the force on j along d = x_j - x_i
-      fx = fmaf(-fr, dx, fx);
-      fy = fmaf(-fr, dy, fy);
-      fz = fmaf(-fr, dz, fz);
-      ec = fmaf(wgt, et, ec);
-      elj = fmaf(wgt, lt, elj);
-      vir = fmaf(fr, r2, vir);
-      ++nev;
-    }
-    // lane partials to fixed point by bit assembly, then exact integer sums
+    const float4 di = d.Xd[oi + ((ai.row0 - oi) << lgPi) + b];
+    const int k = ai.type * nt + t;
+    const float qq = qqt[k], e4 = e4t[k];
+    const float wgt = __int_as_float((127 - lgS) << 23);  // 1/P*
+    float fx = 0.f, fy = 0.f, fz = 0.f, ec = 0.f, elj = 0.f, vir = 0.f;
+    int nev = 0;
+    const float4* lst = d.nlB + (size_t)i * d.nl_cap;
+    if (e4 != 0.f)
+      pair32_entries<true>(lst, e0 + grp, e1, 1 << lgG, lgr, lgS - lgPt, d.Xd, b, di, qq, e4, s2t[k], vrct[k],
+                           dvrct[k], rc, rc2, alpha, alpha2, g2a, cf, c0, fx, fy, fz, ec, elj, vir, nev);
+    else
+      pair32_entries<false>(lst, e0 + grp, e1, 1 << lgG, lgr, lgS - lgPt, d.Xd, b, di, qq, 0.f, 1.f, 0.f, 0.f, rc,
+                            rc2, alpha, alpha2, g2a, cf, c0, fx, fy, fz, ec, elj, vir, nev);
+    // lane partials (times 1/P*) to fixed point by bit assembly, then exact
+    // integer sums over the groups, which hold the same owner beads
     int bad = 0;
-    long long kx = fixs(f2d_bits(fx), 44, &bad), ky = fixs(f2d_bits(fy), 44, &bad), kz = fixs(f2d_bits(fz), 44, &bad);
-    // over the groups (same slice) and over slices that share the owner's bead
-    const int lgShare = lgM - ai.log2P < lgPp ? lgM - ai.log2P : lgPp;
-    for (int o = 1; o < 32; o <<= 1) {
-      if (o < (1 << lgPp) && o >= (1 << lgShare)) continue;
+    long long kx = fixs(f2d_bits(fx * wgt), 44, &bad), ky = fixs(f2d_bits(fy * wgt), 44, &bad),
+              kz = fixs(f2d_bits(fz * wgt), 44, &bad);
+    for (int o = 1 << lgPp; o < 32; o <<= 1) {
       kx += __shfl_xor_sync(0xffffffffu, kx, o);
       ky += __shfl_xor_sync(0xffffffffu, ky, o);
       kz += __shfl_xor_sync(0xffffffffu, kz, o);
     }
-    if (grp == 0 && (sl & ((1 << lgShare) - 1)) == 0 && (kx | ky | kz) != 0) {
-      unsigned long long* fi = d.F_fix + 3 * (size_t)row_i;
+    if (grp == 0 && (kx | ky | kz) != 0) {
+      unsigned long long* fi = d.F_fix + 3 * (size_t)(ai.row0 + b * ai.stride);
       atomicAdd(fi + 0, (unsigned long long)kx);
       atomicAdd(fi + 1, (unsigned long long)ky);
       atomicAdd(fi + 2, (unsigned long long)kz);
     }
     // every term is seen from both of its atoms: energies carry a factor 1/2
-    long long kl = fixs(f2d_bits(elj), 39, &bad), kc = fixs(f2d_bits(ec), 39, &bad), kv = fixs(f2d_bits(vir), 39, &bad);
+    long long kl = fixs(f2d_bits(elj * wgt), 39, &bad), kc = fixs(f2d_bits(ec * wgt), 39, &bad),
+              kv = fixs(f2d_bits(vir * wgt), 39, &bad);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       kl += __shfl_xor_sync(0xffffffffu, kl, o);
@@ -664,14 +865,15 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
       kv += __shfl_xor_sync(0xffffffffu, kv, o);
     }
     nev = warp_sumi(nev);
-    nlj = warp_sumi(nlj);
     bad = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
       if (kl) atomicAdd(d.E_fix + E_LJ, (unsigned long long)kl);
       if (kc) atomicAdd(d.E_fix + E_COUL, (unsigned long long)kc);
       if (kv) atomicAdd(d.E_fix + E_VIRIAL, (unsigned long long)kv);
-      if (nev) atomicAdd(d.E_fix + E_NEVAL, (unsigned long long)nev);
-      if (nlj) atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nlj);
+      if (nev) {
+        atomicAdd(d.E_fix + E_NEVAL, (unsigned long long)nev);
+        if (e4 != 0.f) atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nev);
+      }
       if (bad) atomicOr(d.err, ERR_NONFINITE);
     }
   }
@@ -1025,10 +1227,10 @@ int launch_pair(const Dev& d, cudaStream_t s) {
   const int wpb = PAIR_THREADS / 32;
   if (d.precision == MIXTS_FP32_FORCES) {
     if (d.n_nonp == 0) return 0;
-    const int lgPp = d.lgPmax_nb < 5 ? d.lgPmax_nb : 5;
-    const long long items = (long long)d.n_nonp * (1 << (d.lgPmax_nb - lgPp)) * d.p32_nch;
-    k_pair32<<<(int)std::min<long long>((items + wpb - 1) / wpb, d.pair32_grid), PAIR_THREADS, 0, s>>>(d);
-    return 1;
+    k_list_seg32<<<(d.n_nonp + wpb - 1) / wpb, NL_THREADS, 0, s>>>(d);
+    k_pair_items32<<<1, ITEM_THREADS, 0, s>>>(d);
+    k_pair32<<<d.pair32_grid, PAIR_THREADS, 0, s>>>(d);
+    return 3;
   }
   if (d.n_pitems == 0) return 0;
   const size_t smem = PAIR64_SMEM_PER_INTERVAL * (size_t)d.dsf_nint;
@@ -1038,9 +1240,10 @@ int launch_pair(const Dev& d, cudaStream_t s) {
     attr = true;
   }
   const int nsbm = d.lgPmax_nb > 5 ? 1 << (d.lgPmax_nb - 5) : 1;
-  const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;
+  const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;  // bound on the list's items
+  k_pair_items<<<1, ITEM_THREADS, 0, s>>>(d);
   k_pair64<<<(int)std::min<long long>((items + wpb - 1) / wpb, d.pair_grid), PAIR_THREADS, smem, s>>>(d);
-  return 1;
+  return 2;
 }
 
 int launch_bonded(const Dev& d, cudaStream_t s, const AtomInfo* ainfo_atom) {

@@ -92,6 +92,7 @@ struct Plan {
       o_slot_type, o_dsf, o_pstab, o_pairpar_alt, o_pspar_alt, o_pc, o_gacc;
   size_t o_state = 0, state_bytes = 0;
   size_t o_xd = 0, o_xia = 0;
+  size_t o_pitems = 0, o_pctr = 0, o_nlb = 0, o_nlseg = 0;
   size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_xl, o_ref, o_refd, o_reff, o_spread, o_spread_big, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
       o_err, o_step, o_heat, o_est, o_parts;
 };
@@ -258,6 +259,10 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
     fail(p, MIXTS_ERR_ARG, "NULL per-type or per-atom array");
     return p;
   }
+  if (prm->free_ring_substeps < 0) {
+    fail(p, MIXTS_ERR_ARG, "free_ring_substeps must be >= 0");
+    return p;
+  }
   if (prm->precision != MIXTS_FP64 && prm->precision != MIXTS_FP32_FORCES) {
     fail(p, MIXTS_ERR_ARG, "unknown precision");
     return p;
@@ -272,7 +277,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
       fail(p, MIXTS_ERR_BEADS, "bead counts must be powers of two in 1..1024");
       return p;
     }
-    if (!(s->mass_type[t] > 0.0)) {
+    if (!(s->mass_type[t] > 0.0) || (s->bead_mass_type && !(s->bead_mass_type[t] > 0.0))) {
       fail(p, MIXTS_ERR_ARG, "masses must be positive");
       return p;
     }
@@ -444,6 +449,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   for (int t = 0; t < p.nt; ++t) {
     const int P = s->P_type[t];
     const double m = s->mass_type[t];
+    const double mf = s->bead_mass_type ? s->bead_mass_type[t] : m;  // fictitious bead mass
     std::vector<double> T(P);
     for (int k = 0; k < P; ++k) T[k] = cos(2.0 * PI * k / P);
     p.cm_off[t] = (int)p.cm.size();
@@ -467,23 +473,43 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
       for (int k = 0; k < P; ++k) p.cm.push_back(r2P * T[k]);
     }
     p.mc_off[t] = (int)p.mc.size();
+    const int nsub = prm->free_ring_substeps;
     for (int k = 0; k < P; ++k) {
-      const double w = 2.0 * sqrt((double)P) / bh * sin(PI * k / P);
+      // mode frequency with bead mass m_f: springs P m/(beta hbar)^2, kinetic p^2/2m_f
+      const double w = 2.0 * sqrt((double)P) / bh * sin(PI * k / P) * sqrt(m / mf);
       const double gam = (k == 0) ? (prm->tau_centroid > 0.0 ? 1.0 / prm->tau_centroid : 0.0)
                                   : 2.0 * prm->pile_lambda * w;
       ModeCoef c;
       c.c1 = exp(-0.5 * prm->dt * gam);
-      c.c2s = sqrt(1.0 - c.c1 * c.c1) * sqrt(m * kT);
-      if (k == 0) {
+      c.c2s = sqrt(1.0 - c.c1 * c.c1) * sqrt(mf * kT);
+      c.hmw2 = 0.5 * mf * w * w;
+      if (nsub > 0) {
+        // velocity Verlet on the springs, which act on mode k as the force
+        // -m_f w^2 q_k: one sub-step h maps (p, q) by [[a, -B], [C, a]] with
+        // a = 1 - h^2 w^2 / 2, B = m_f w^2 h (1 - h^2 w^2 / 4), C = h / m_f;
+        // the step is its n-th power (equal diagonals, determinant 1)
+        const double h = prm->dt / nsub, hw2 = h * h * w * w;
+        const double a = 1.0 - 0.5 * hw2, B = mf * w * w * h * (1.0 - 0.25 * hw2), Cq = h / mf;
+        double M00 = 1.0, M01 = 0.0, M10 = 0.0, M11 = 1.0;  // rows (p, q), columns (p, q)
+        for (int j = 0; j < nsub; ++j) {
+          const double n00 = a * M00 - B * M10, n01 = a * M01 - B * M11;
+          const double n10 = Cq * M00 + a * M10, n11 = Cq * M01 + a * M11;
+          M00 = n00;
+          M01 = n01;
+          M10 = n10;
+          M11 = n11;
+        }
+        c.cw = M00;
+        c.mws = -M01;
+        c.swm = M10;
+      } else if (k == 0) {
         c.cw = 1.0;
         c.mws = 0.0;
-        c.swm = prm->dt / m;
-        c.hmw2 = 0.0;
+        c.swm = prm->dt / mf;
       } else {
         c.cw = cos(w * prm->dt);
-        c.mws = m * w * sin(w * prm->dt);
-        c.swm = sin(w * prm->dt) / (m * w);
-        c.hmw2 = 0.5 * m * w * w;
+        c.mws = mf * w * sin(w * prm->dt);
+        c.swm = sin(w * prm->dt) / (mf * w);
       }
       p.mc.push_back(c);
     }
@@ -578,7 +604,9 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_xf = A.add(sizeof(float4) * p.n_beads);
   p.o_xl = A.add(sizeof(float4) * p.n_beads);
   if (prm->precision == MIXTS_FP32_FORCES) p.o_xd = A.add(sizeof(float4) * p.n_beads);
-  else p.o_xia = A.add(sizeof(longlong4_32a) * p.n_beads);
+  // the atom-major fixed-point copy feeds the FP64 sweep, which the
+  // parameter-gradient path runs whatever the handle's precision
+  p.o_xia = A.add(sizeof(longlong4_32a) * p.n_beads);
   p.o_ref = A.add(sizeof(double) * 3 * p.na);
   p.o_refd = A.add(sizeof(double4_32a) * std::max(1, p.n_nonp));
   p.o_reff = A.add(sizeof(float4) * std::max(1, p.n_nonp));
@@ -586,6 +614,20 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_spread_big = A.add(sizeof(double) * (size_t)std::max(1, p.n_spread_big));
   p.o_nl = A.add(sizeof(int) * (size_t)std::max(1, p.n_nonp) * p.nl_cap);
   p.o_nlcnt = A.add(sizeof(int) * std::max(1, p.n_nonp));
+  {  // FP64 pair items: at most every row's slice blocks times 32-entry chunks of a full row
+    const int lgM = p.n_classes > 0 ? p.cls_log2P[0] : 0;
+    const size_t nsbm = lgM > 5 ? (size_t)1 << (lgM - 5) : 1;
+    size_t nitems = (size_t)p.n_nonp * nsbm * ((p.nl_cap + P32_CH - 1) / P32_CH);
+    if (prm->precision == MIXTS_FP32_FORCES) {
+      // FP32 items: per row and partner type at most ceil(entries / 1) + 1 chunks of >= 1 entry per group...
+      // bounded by one item per entry and slice block plus one partial item per type
+      nitems = (size_t)p.n_nonp * nsbm * ((size_t)p.nl_cap + p.nt);
+      p.o_nlb = A.add(sizeof(float4) * (size_t)std::max(1, p.n_nonp) * p.nl_cap);
+      p.o_nlseg = A.add(sizeof(int) * (size_t)std::max(1, p.n_nonp) * (p.nt + 1));
+    }
+    p.o_pitems = A.add(sizeof(int2) * std::max<size_t>(1, nitems));
+    p.o_pctr = A.add(sizeof(int) * 4);
+  }
   p.o_pl = A.add(sizeof(int) * (size_t)std::max(1, p.n_pseudo) * p.pl_cap);
   p.o_plcnt = A.add(sizeof(int) * std::max(1, p.n_pseudo));
   p.o_thresh = A.add(sizeof(double) * 8);
@@ -850,7 +892,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
     d.mc_off[t] = p.mc_off[t];
     d.big_slot0[t] = p.big_slot0[t];
     d.sb_off[t] = p.sb_off[t];
-    d.mass[t] = sys->mass_type[t];
+    d.mass[t] = sys->bead_mass_type ? sys->bead_mass_type[t] : sys->mass_type[t];  // kinetic (bead) mass
   }
   for (int c = 0; c < p.n_classes; ++c) {
     d.cls_P[c] = p.cls_P[c];
@@ -909,6 +951,11 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   }
   d.nl = (int*)(w + p.o_nl);
   d.nl_cnt = (int*)(w + p.o_nlcnt);
+  d.pitems = (int2*)(w + p.o_pitems);
+  d.pctr = (int*)(w + p.o_pctr);
+  d.nlB = p.o_nlb ? (float4*)(w + p.o_nlb) : nullptr;
+  d.nlseg = p.o_nlseg ? (int*)(w + p.o_nlseg) : nullptr;
+  d.box_lo = (float)(sys->box - (double)d.box_hi);
   d.pl = (int*)(w + p.o_pl);
   d.pl_cnt = (int*)(w + p.o_plcnt);
   d.thresh = (double*)(w + p.o_thresh);

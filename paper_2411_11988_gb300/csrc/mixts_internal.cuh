@@ -14,7 +14,8 @@ constexpr int MAX_CLASSES = 12;
 constexpr int SMALL_P = 64;     // types with P <= SMALL_P propagate in one fused tile kernel
 constexpr int BIG_MB = 8;       // modes (or beads) per CTA of the large-P transforms
 constexpr int PROP_SMEM_MAX = 200 * 1024;
-constexpr int P32_CH = 32;      // list candidates per lane group of one FP32 pair item  // dynamic shared memory cap of the propagation kernels
+constexpr int P32_CH = 32;      // list entries per lane group of one FP64 pair item
+constexpr int LG_P32_TERMS = 10; // log2 of the bead-pair terms of one FP32 pair item
 // shared memory of one large-P transform CTA: the cos table and BIG_MB rows
 // of the 3N columns (forward: forces, q and p modes, plus the centroids)
 inline size_t big_prop_smem(int P, int N) { return sizeof(double) * ((size_t)P + (3 * (size_t)BIG_MB + 1) * 3 * N); }
@@ -121,7 +122,12 @@ struct Dev {
   int pair_grid, pair32_grid, pseudo_chunks;  // persistent grid sizes, site-list split
   int nl_cpl;                                 // list candidates per lane of one list warp
   int p32_nch;                                // FP32 pair items per owner row and slice block (list chunks)
-  int p64_nch;                                // FP64 slice-parallel items per owner row and slice block
+  int p64_nch;                                // FP64 slice-parallel items per owner row and slice block (bound)
+  int2* pitems;                               // FP64 pair items of the current list: (owner pos, sb << 16 | chunk)
+  int* pctr;                                  // [0] item count of the current list, [1] next item to hand out
+  float4* nlB;                 // FP32 path: list rows regrouped by partner type, (bead-0 displacement, tag)
+  int* nlseg;                  // FP32 path: [n_nonp][n_types + 1] first entry of each partner type in nlB
+  float box_lo;                // box - box_hi (binary32)
   double mass[MT];
   // sorted classes of non-pseudo atoms (P descending)
   int cls_P[MAX_CLASSES], cls_log2P[MAX_CLASSES], cls_pos0[MAX_CLASSES], cls_n[MAX_CLASSES],

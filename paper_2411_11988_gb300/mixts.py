@@ -44,14 +44,14 @@ class _System(C.Structure):
         ("angle_k", C.POINTER(C.c_double)), ("angle_theta0", C.POINTER(C.c_double)),
         ("box", C.c_double),
         ("q", C.c_void_p), ("p", C.c_void_p), ("f", C.c_void_p),
-        ("seed", C.c_uint64),
+        ("seed", C.c_uint64), ("bead_mass_type", C.POINTER(C.c_double)),
     ]
 
 
 class _Params(C.Structure):
     _fields_ = [("T", C.c_double), ("dt", C.c_double), ("tau_centroid", C.c_double),
                 ("pile_lambda", C.c_double), ("r_cut", C.c_double), ("dsf_alpha", C.c_double),
-                ("precision", C.c_int), ("nlist_cap", C.c_int)]
+                ("precision", C.c_int), ("nlist_cap", C.c_int), ("free_ring_substeps", C.c_int)]
 
 
 class _Tuning(C.Structure):
@@ -140,6 +140,9 @@ def pack_system(sysm, q_ptr=0, p_ptr=0, f_ptr=0, seed=0):
              pp_b=f64(sysm.pp_b), bonds=i32(sysm.bonds).ravel(), bond_k=f64(sysm.bond_k),
              bond_r0=f64(sysm.bond_r0), angles=i32(sysm.angles).ravel(), angle_k=f64(sysm.angle_k),
              angle_theta0=f64(sysm.angle_theta0))
+    bm = getattr(sysm, "bead_mass_type", None)
+    if bm is not None:
+        k["bead_mass_type"] = f64(bm)
     s = _System(len(k["type_of_atom"]), len(k["P_type"]),
                 _ptr(k["type_of_atom"], C.c_int), _ptr(k["mol_of_atom"], C.c_int), _ptr(k["P_type"], C.c_int),
                 _ptr(k["mass_type"], C.c_double), _ptr(k["charge_type"], C.c_double),
@@ -148,7 +151,8 @@ def pack_system(sysm, q_ptr=0, p_ptr=0, f_ptr=0, seed=0):
                 int(len(k["bond_k"])), _ptr(k["bonds"], C.c_int), _ptr(k["bond_k"], C.c_double),
                 _ptr(k["bond_r0"], C.c_double), int(len(k["angle_k"])), _ptr(k["angles"], C.c_int),
                 _ptr(k["angle_k"], C.c_double), _ptr(k["angle_theta0"], C.c_double),
-                float(sysm.box), q_ptr, p_ptr, f_ptr, int(seed))
+                float(sysm.box), q_ptr, p_ptr, f_ptr, int(seed),
+                _ptr(k["bead_mass_type"], C.c_double) if bm is not None else None)
     return s, k
 
 
@@ -160,7 +164,8 @@ class MixTS:
     """
 
     def __init__(self, sysm, T=300.0, dt=0.25, tau=100.0, pile_lambda=1.0, r_cut=9.0, alpha=0.2,
-                 precision=FP64, nlist_cap=0, seed=0, device="cuda:0", stream=None, q=None, p=None):
+                 precision=FP64, nlist_cap=0, seed=0, device="cuda:0", stream=None, q=None, p=None,
+                 free_ring_substeps=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("MixTS needs a CUDA device")
@@ -177,7 +182,7 @@ class MixTS:
             self.p = torch.from_numpy(p0.copy()).to(self.device)
             self.f = torch.zeros_like(self.q)
         self.params = _Params(float(T), float(dt), float(tau), float(pile_lambda), float(r_cut), float(alpha),
-                              int(precision), int(nlist_cap))
+                              int(precision), int(nlist_cap), int(free_ring_substeps))
         s, keep = pack_system(sysm, self.q.data_ptr(), self.p.data_ptr(), self.f.data_ptr(), seed)
         nbytes = L.mixts_workspace_size(C.byref(s), 1, C.byref(self.params))
         if nbytes == 0:
@@ -371,7 +376,7 @@ class MixTSBatch:
     """
 
     def __init__(self, systems, T=300.0, dt=0.25, tau=100.0, pile_lambda=1.0, r_cut=9.0, alpha=0.2,
-                 precision=FP64, nlist_cap=0, seeds=None, device="cuda:0", stream=None):
+                 precision=FP64, nlist_cap=0, seeds=None, device="cuda:0", stream=None, free_ring_substeps=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("MixTSBatch needs a CUDA device")
@@ -400,7 +405,7 @@ class MixTSBatch:
         arr = (_System * n)(*structs)
         self.n = n
         self.params = _Params(float(T), float(dt), float(tau), float(pile_lambda), float(r_cut), float(alpha),
-                              int(precision), int(nlist_cap))
+                              int(precision), int(nlist_cap), int(free_ring_substeps))
         nbytes = L.mixts_workspace_size(arr, n, C.byref(self.params))
         if nbytes == 0:
             raise MixtsError(1, "mixts_workspace_size rejected the batch")

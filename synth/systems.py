@@ -55,6 +55,8 @@ class System:
     angle_theta0: np.ndarray
     q: np.ndarray = field(default=None)
     p: np.ndarray = field(default=None)
+    # fictitious bead mass per type (kinetic term p^2/2m_f); None: the physical mass
+    bead_mass_type: np.ndarray = field(default=None)
 
     # ---- bookkeeping (layout only) ----
     @property

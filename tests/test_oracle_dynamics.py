@@ -2,7 +2,8 @@
 
 * P-bead harmonic oscillator: <x^2>_P = (1/(beta m)) sum_k [w^2 + 4P^2 sin^2(pi k/P)/(beta hbar)^2]^-1,
   exact at finite P for the ring-polymer Hamiltonian Eq. (rpham); the
-  primitive and centroid-virial kinetic estimators average to (3/2) m w^2 <x^2>_P.
+  primitive and centroid-virial kinetic estimators average to (3/2) m w^2 <x^2>_P,
+  whatever the fictitious bead mass and with the velocity-Verlet free ring.
 * Two harmonic particles with 8 and 2 beads coupled through the mixTS pair
   map: sampled bead covariance equals (beta K)^-1, K the Hessian of
   H0 + V_mix of Eq. (mts-hamiltonian).
@@ -34,15 +35,21 @@ def _ho_exact_x2(P, m, w, beta, bh):
     return (1.0 / (beta * m)) * np.sum(1.0 / (w ** 2 + 4 * P ** 2 * np.sin(np.pi * k / P) ** 2 / bh ** 2))
 
 
-@pytest.mark.parametrize("P", [1, 4, 32])
-def test_harmonic_oscillator_closed_form(orc, P):
+@pytest.mark.parametrize("P,mf_over_m,vv", [(1, 1.0, 0), (4, 1.0, 0), (32, 1.0, 0), (8, 0.125, 0), (8, 4.0, 0),
+                                         (8, 1.0, 6)])
+def test_harmonic_oscillator_closed_form(orc, P, mf_over_m, vv):
+    """The closed form holds for any fictitious bead mass m_f (statics do not
+    depend on it, Sec. "Theory" after Eq. rpham) and with the velocity-Verlet
+    free ring (sampling error of its O(dt^2) shadow Hamiltonian far below the
+    statistical error at dt = 1 fs, 6 sub-steps)."""
     c, kT, bh = _consts(orc)
     m = 1.0
     w = 4.0 / bh                      # beta hbar omega = 4
     k_md = m * w ** 2
     k_kcal = k_md / c["kcal"]
     s = synth.harmonic_tether([P, 1], [(0, 1, k_kcal)], masses=[m, 1.0], seed=P)
-    prm = orc.make_params(T=T, dt=1.0, tau=20.0, lam=1.0, seed=100 + P)
+    s.bead_mass_type = np.array([m * mf_over_m, 1.0])
+    prm = orc.make_params(T=T, dt=1.0, tau=20.0, lam=1.0, seed=100 + P, vv=vv)
     run = orc.Runner(s, prm)
     run.step(2000)
     x2, kp, kc, tb = [], [], [], []

@@ -85,6 +85,61 @@ def test_free_ring_step_is_exact_flow(orc, P):
         assert np.allclose(run.p[:, d], z[P:], rtol=0, atol=1e-11)
 
 
+def _free_ring_step(orc, P, dt, m, mf, vv, seed=1):
+    """One force-free, thermostat-free step of a P-bead ring; returns (q0, p0, q1, p1, kappa)."""
+    c = orc.constants()
+    T = 300.0
+    bh = c["hbar"] / (c["kB"] * T)
+    s = synth.harmonic_tether([P], [], masses=[m], seed=P)
+    s.bead_mass_type = np.array([mf])
+    rng = np.random.default_rng(seed)
+    s.q = s.q + rng.normal(0, 0.2, s.q.shape)
+    s.p = rng.normal(0, np.sqrt(mf * c["kB"] * T), s.q.shape)
+    run = orc.Runner(s, orc.make_params(T=T, dt=dt, tau=0.0, lam=0.0, seed=0, vv=vv))
+    q0, p0 = run.q.copy(), run.p.copy()
+    run.step(1)
+    return q0, p0, run.q.copy(), run.p.copy(), P * m / bh ** 2
+
+
+@pytest.mark.parametrize("P,mf_over_m", [(8, 1.0), (8, 0.125), (4, 3.0)])
+def test_free_ring_with_bead_mass_is_exact_flow(orc, P, mf_over_m):
+    """With a fictitious bead mass m_f the free ring polymer still evolves
+    exactly: dq/dt = p/m_f, dp/dt = -K q with the physical-mass springs."""
+    m = 1.008
+    mf = m * mf_over_m
+    q0, p0, q1, p1, kappa = _free_ring_step(orc, P, 0.7, m, mf, 0)
+    K = kappa * _ring_laplacian(P)
+    G = np.zeros((2 * P, 2 * P))
+    G[:P, P:] = np.eye(P) / mf
+    G[P:, :P] = -K
+    E = scipy.linalg.expm(0.7 * G)
+    for d in range(3):
+        z = E @ np.concatenate([q0[:, d], p0[:, d]])
+        assert np.allclose(q1[:, d], z[:P], rtol=0, atol=1e-11)
+        assert np.allclose(p1[:, d], z[P:], rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("P,mf_over_m", [(8, 1.0), (16, 0.0625)])
+def test_velocity_verlet_free_ring_converges_to_exact(orc, P, mf_over_m):
+    """Velocity Verlet on the springs (Sec. "Evaluation") is a second-order
+    integrator of the same free ring: doubling its sub-steps divides the
+    error against the exact evolution by ~4, and it conserves the centroid."""
+    m = 1.008
+    mf = m * mf_over_m
+    dt = 0.25
+    qe, pe = _free_ring_step(orc, P, dt, m, mf, 0)[2:4]
+    errs = []
+    for n in (4, 8, 16, 32):
+        q0, p0, q1, p1, _ = _free_ring_step(orc, P, dt, m, mf, n)
+        errs.append(np.abs(q1 - qe).max())
+        # the springs exert no net force: the centroid drifts freely
+        assert np.allclose(q1.mean(0), q0.mean(0) + p0.mean(0) * dt / mf, rtol=0, atol=1e-12)
+        assert np.allclose(p1.mean(0), p0.mean(0), rtol=0, atol=1e-12)
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(3.5 < r < 4.5 for r in ratios), (errs, ratios)
+    assert errs[-1] < 1e-3 * np.abs(qe - q0).max()
+
+
 def test_philox_matches_triton_interpreter(orc):
     pytest.importorskip("triton")
     code = r"""
