@@ -249,7 +249,9 @@ MIXTS_API mixts_status mixts_gaussians(mixts_handle h, uint32_t step, uint32_t s
  * changing the handle's parameters. V_host (may be NULL) gets V_mix;
  * dVdq_dev (device [n_beads][3], may be NULL) gets grad_out * dV/dq;
  * dVdtheta_host (8, may be NULL) gets grad_out * dV/dtheta in kcal/mol per
- * unit of theta. Pair terms are recomputed, not stored. Synchronises; the
+ * unit of theta; with it NULL the adjoint sums over theta are skipped (a
+ * potential-only or force-only evaluation). Pair terms are recomputed, not
+ * stored. Synchronises; the
  * next mixts_step restarts from the caller's q and p. */
 MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int type_a, int type_b, const double* theta,
                                             double grad_out, double* V_host, double* dVdq_dev,
@@ -272,6 +274,25 @@ MIXTS_API mixts_status mixts_rdf_accumulate(mixts_handle h, int type_a, int type
 MIXTS_API mixts_status mixts_rdf_normalise(mixts_handle h, int type_a, int type_b, double dr, int n_bins,
                                            long long n_frames, const unsigned long long* hist_host,
                                            double* g_host);
+
+/* Centroid velocity autocorrelation of the atoms of one type, for
+ * ring-polymer molecular dynamics correlation functions from NVE trajectories
+ * (Sec. "Output and Analysis"; run with the thermostat off, tau_centroid = 0
+ * and pile_lambda = 0, and bead masses m_f = m/P_t, with which the dynamics of
+ * the beta H_mix convention of Eq. (mts-hamiltonian) give every centroid the
+ * RPMD equation of motion). Call after each mixts_step of a fixed number of
+ * steps (one lag unit). Each call adds sum_k v_k(now) . v_k(now - L) over the
+ * type's atoms to acc_dev[L] and 1 to cnt_dev[L] for every lag L < n_lag
+ * with a frame L calls back (v = dq̄/dt, A/fs, the centroid velocity from the
+ * mode-space momenta of the last step), then stores the current frame in
+ * ring_dev. All three are caller-owned DEVICE arrays, zeroed by the caller
+ * before the first call and passed unchanged afterwards: ring_dev n_lag * 3
+ * N_t doubles, acc_dev n_lag doubles, cnt_dev n_lag uint64 (cnt_dev[0] =
+ * frames so far). C(L) per atom = acc_dev[L] / (cnt_dev[L] N_t).
+ * Asynchronous on the handle's stream; deterministic (fixed-order sums).
+ * MIXTS_ERR_STATE before the first step. */
+MIXTS_API mixts_status mixts_vacf_accumulate(mixts_handle h, int type, int n_lag, double* ring_dev,
+                                             double* acc_dev, unsigned long long* cnt_dev);
 
 /* Member i of a batched handle (borrowed; valid until the batch is destroyed). */
 MIXTS_API mixts_status mixts_batch_member(mixts_handle h, int i, mixts_handle* member);

@@ -156,7 +156,13 @@ static pairval_t nb_pair(const or_system* s, const cst_t* c, int ti, int tj, dou
   double qq = c->ke * s->charge_type[ti] * s->charge_type[tj];
   if (qq != 0.0) {
     double v, dv;
-    dsf_raw(s->dsf_alpha, rc, r, &v, &dv);
+    if (s->coulomb == 1) { /* Ewald real space, truncated at r_cut */
+      double a = s->dsf_alpha;
+      v = erfc(a * r) / r;
+      dv = -erfc(a * r) / (r * r) - 2.0 * a / sqrt(OR_PI) * exp(-a * a * r * r) / r;
+    } else {
+      dsf_raw(s->dsf_alpha, rc, r, &v, &dv);
+    }
     o.v_c = qq * v;
     o.dv += qq * dv;
   }
@@ -384,6 +390,119 @@ static void angle_terms(const or_system* s, const lay_t* L, int ang, const doubl
   free(b2);
 }
 
+/* ---------------------------------------------------------------------------
+ * Long-range electrostatics on centroids (coulomb = 1). The paper treats
+ * electrostatics with SPME and approximates the bead-bead interactions by
+ * centroid-centroid ones (Sec. "Theory", last paragraph). Here the Ewald
+ * split keeps the short-range real-space part erfc(alpha r)/r on every bead
+ * pair (the mixTS map, in nb_pair) and evaluates the smooth rest on the
+ * centroids qbar_a = (1/P_a) sum_b q_{a,b} of the charged sites:
+ *   E_rec = (2 pi k_e / V) sum_{k != 0} exp(-k^2/(4 alpha^2)) / k^2 |S(k)|^2,
+ *           S(k) = sum_a q_a exp(i k.qbar_a), k = 2 pi n / L, |n| <= kmax
+ *   E_intra = - k_e sum_{a<b same molecule} q_a q_b erf(alpha r_ab) / r_ab
+ *             (centroids, zero image: the pairs the real-space part excludes)
+ *   E_self = - k_e alpha / sqrt(pi) sum_a q_a^2
+ *   E_bg = - k_e pi Q^2 / (2 V alpha^2), Q = sum_a q_a (neutralising background)
+ * A centroid force F_a acts as F_a / P_a on each bead of a (dqbar/dq_b =
+ * 1/P). The virial is minus the derivative of these terms under a uniform
+ * dilation of positions and box. Direct sums, no mesh.
+ * ------------------------------------------------------------------------- */
+static void ewald_centroid(const or_system* s, const lay_t* L, const cst_t* c, const double* q, double* F,
+                           long only_row, int only_atom, acc_t* acc) {
+  int na = s->n_atoms;
+  double Lb = s->box, V = Lb * Lb * Lb, a = s->dsf_alpha, ke = c->ke;
+  double* cen = (double*)calloc(3 * (size_t)(na > 0 ? na : 1), sizeof(double));
+  double* fc = (double*)calloc(3 * (size_t)(na > 0 ? na : 1), sizeof(double));
+  double Q = 0.0, q2sum = 0.0;
+  for (int i = 0; i < na; ++i) {
+    int t = s->type_of_atom[i];
+    if (s->pseudo_type[t]) continue;
+    int P = s->P_type[t];
+    for (int b = 0; b < P; ++b) {
+      long r = row_of(s, L, i, b);
+      for (int d = 0; d < 3; ++d) cen[3 * i + d] += q[3 * r + d];
+    }
+    for (int d = 0; d < 3; ++d) cen[3 * i + d] /= P;
+    Q += s->charge_type[t];
+    q2sum += s->charge_type[t] * s->charge_type[t];
+  }
+  double e = 0.0, w = 0.0;
+  int km = s->ewald_kmax;
+  for (int nx = -km; nx <= km; ++nx)
+    for (int ny = -km; ny <= km; ++ny)
+      for (int nz = -km; nz <= km; ++nz) {
+        if (nx == 0 && ny == 0 && nz == 0) continue;
+        if (nx * nx + ny * ny + nz * nz > km * km) continue;
+        double kx = 2.0 * OR_PI * nx / Lb, ky = 2.0 * OR_PI * ny / Lb, kz = 2.0 * OR_PI * nz / Lb;
+        double k2 = kx * kx + ky * ky + kz * kz;
+        double wk = 2.0 * OR_PI * ke / V * exp(-k2 / (4.0 * a * a)) / k2;
+        double sr = 0.0, si = 0.0;
+        for (int i = 0; i < na; ++i) {
+          int t = s->type_of_atom[i];
+          if (s->pseudo_type[t] || s->charge_type[t] == 0.0) continue;
+          double ph = kx * cen[3 * i] + ky * cen[3 * i + 1] + kz * cen[3 * i + 2];
+          sr += s->charge_type[t] * cos(ph);
+          si += s->charge_type[t] * sin(ph);
+        }
+        double s2 = sr * sr + si * si;
+        e += wk * s2;
+        w += wk * s2 * (1.0 - k2 / (2.0 * a * a));
+        /* F_a = -dE/dqbar_a = 2 wk q_a k (sin(ph) sr - cos(ph) si) */
+        for (int i = 0; i < na; ++i) {
+          int t = s->type_of_atom[i];
+          if (s->pseudo_type[t] || s->charge_type[t] == 0.0) continue;
+          double ph = kx * cen[3 * i] + ky * cen[3 * i + 1] + kz * cen[3 * i + 2];
+          double g = 2.0 * wk * s->charge_type[t] * (sin(ph) * sr - cos(ph) * si);
+          fc[3 * i] += g * kx;
+          fc[3 * i + 1] += g * ky;
+          fc[3 * i + 2] += g * kz;
+        }
+      }
+  /* intramolecular pairs, on centroids, zero image */
+  for (int i = 0; i < na; ++i) {
+    int ti = s->type_of_atom[i];
+    if (s->pseudo_type[ti] || s->charge_type[ti] == 0.0) continue;
+    for (int j = i + 1; j < na; ++j) {
+      int tj = s->type_of_atom[j];
+      if (s->pseudo_type[tj] || s->charge_type[tj] == 0.0 || s->mol_of_atom[i] != s->mol_of_atom[j]) continue;
+      double d[3] = {cen[3 * j] - cen[3 * i], cen[3 * j + 1] - cen[3 * i + 1], cen[3 * j + 2] - cen[3 * i + 2]};
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      double qq = ke * s->charge_type[ti] * s->charge_type[tj];
+      double v = -qq * erf(a * r) / r;
+      double dv = -qq * (2.0 * a / sqrt(OR_PI) * exp(-a * a * r * r) / r - erf(a * r) / (r * r));
+      e += v;
+      w += -dv * r;
+      for (int k = 0; k < 3; ++k) {
+        fc[3 * j + k] += -dv * d[k] / r;
+        fc[3 * i + k] -= -dv * d[k] / r;
+      }
+    }
+  }
+  e += -ke * a / sqrt(OR_PI) * q2sum;
+  double ebg = -ke * OR_PI * Q * Q / (2.0 * V * a * a);
+  e += ebg;
+  w += 3.0 * ebg;
+  if (only_atom < 0) {
+    acc->v_c += e;
+    acc->virial += w;
+  }
+  if (F) {
+    for (int i = 0; i < na; ++i) {
+      int t = s->type_of_atom[i];
+      if (s->pseudo_type[t]) continue;
+      if (only_atom >= 0 && i != only_atom) continue;
+      int P = s->P_type[t];
+      for (int b = 0; b < P; ++b) {
+        long r = row_of(s, L, i, b);
+        if (only_row >= 0 && r != only_row) continue;
+        for (int d = 0; d < 3; ++d) F[3 * r + d] += fc[3 * i + d] / P;
+      }
+    }
+  }
+  free(cen);
+  free(fc);
+}
+
 static void all_terms(const or_system* s, const double* q, double* F, long only_row, int only_atom,
                       double* parts) {
   lay_t L;
@@ -420,6 +539,7 @@ static void all_terms(const or_system* s, const double* q, double* F, long only_
       continue;
     angle_terms(s, &L, g, q, F, only_row, &acc);
   }
+  if (s->coulomb == 1) ewald_centroid(s, &L, &c, q, F, only_row, only_atom, &acc);
   if (parts) {
     parts[1] = acc.v_lj;
     parts[2] = acc.v_c;

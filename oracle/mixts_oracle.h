@@ -55,6 +55,11 @@ typedef struct {
   double box, r_cut, dsf_alpha;
   const double* bead_mass_type; /* [n_types] fictitious bead mass m_f (amu) of the kinetic term
                                    p^2/2m_f (Sec. "Theory", Eq. rpham); NULL: m_f = m */
+  int coulomb;                  /* 0: damped shifted force (dsf_alpha) on every bead pair;
+                                   1: Ewald with splitting dsf_alpha: real space erfc(alpha r)/r on every
+                                   bead pair within r_cut, reciprocal space on the ring-polymer centroids
+                                   (Sec. "Theory", last paragraph: SPME with centroid electrostatics) */
+  int ewald_kmax;               /* reciprocal vectors k = 2 pi n / L with n integer, |n|^2 <= kmax^2 */
 } or_system;
 
 typedef struct {
@@ -80,7 +85,9 @@ int or_pair_map(int Ni, int Nj, int* bead_i, int* bead_j);
 /* nested three-body map, Ni >= Nj >= Nk; writes Ni triples */
 int or_triple_map(int Ni, int Nj, int Nk, int* bead_i, int* bead_j, int* bead_k);
 
-/* V_mix and F = -dV_mix/dq at q. parts[0..9] = V_total, V_lj, V_coul,
+/* V_mix and F = -dV_mix/dq at q. parts[0..9] = V_total, V_lj, V_coul
+ * (with coulomb = 1: real space + reciprocal + intramolecular, self and
+ * background corrections),
  * V_bond, V_angle, V_pseudo, virial (sum r.f over interacting bead pairs,
  * kcal/mol), n_evals (algorithmic count of nonbonded in-cutoff bead-pair
  * terms), n_pseudo_evals (same for the pseudopotential), 0. */

@@ -52,6 +52,7 @@ class OrSystem(C.Structure):
         ("angle_k", C.POINTER(C.c_double)), ("angle_theta0", C.POINTER(C.c_double)),
         ("box", C.c_double), ("r_cut", C.c_double), ("dsf_alpha", C.c_double),
         ("bead_mass_type", C.POINTER(C.c_double)),
+        ("coulomb", C.c_int), ("ewald_kmax", C.c_int),
     ]
 
 
@@ -124,7 +125,8 @@ class _Bound:
             _p(k["bond_r0"], C.c_double), int(sysm.angles.shape[0]), _p(k["angles"], C.c_int),
             _p(k["angle_k"], C.c_double), _p(k["angle_theta0"], C.c_double),
             float(sysm.box), float(r_cut), float(alpha),
-            _p(k["bead_mass_type"], C.c_double) if bm is not None else None)
+            _p(k["bead_mass_type"], C.c_double) if bm is not None else None,
+            int(getattr(sysm, "coulomb", 0) or 0), int(getattr(sysm, "ewald_kmax", 0) or 0))
         self.nt = sysm.n_types
         self.nbeads = sysm.n_beads
 
@@ -348,3 +350,51 @@ def sincos_2pi(r):
     c = C.c_float()
     lib().or_sincos_2pi(int(r), C.byref(s), C.byref(c))
     return s.value, c.value
+
+
+def rpmd_bead_masses(sysm):
+    """Bead masses m_f = m / P_t per type. In the beta H_mix convention of
+    Eq. (mts-hamiltonian) (potential weighted 1/N_i, springs N_i m/(beta hbar)^2)
+    Newton's equations with these masses give every centroid the RPMD
+    equation of motion m d^2(qbar)/dt^2 = -(1/P) sum_b dV/dq_b."""
+    return np.asarray(sysm.mass_type, dtype=np.float64) / np.asarray(sysm.P_type, dtype=np.float64)
+
+
+def centroid_velocities(sysm, p, type_t):
+    """Centroid velocities dq̄/dt = (1/P) sum_b p_b / m_f of the atoms of type t,
+    [N_t, 3], from bead momenta p in the flat layout."""
+    bm = getattr(sysm, "bead_mass_type", None)
+    mf = float(bm[type_t]) if bm is not None else float(sysm.mass_type[type_t])
+    off = sysm.type_offsets()
+    N = int(sysm.n_of_type()[type_t])
+    P = int(sysm.P_type[type_t])
+    blk = np.asarray(p[off[type_t]:off[type_t + 1]]).reshape(P, N, 3)
+    return blk.mean(axis=0) / mf
+
+
+class VelocityCorrelation:
+    """Time correlation <v(0).v(t)> of centroid velocities, accumulated over
+    every time origin of a trajectory (Sec. "Output and Analysis": RPMD
+    correlation functions from NVE trajectories). add(v) takes the [N, 3]
+    velocities of one frame; acc[L] sums v(now).v(now - L) over atoms and
+    origins, cnt[L] counts the origins, for lags L < n_lag frames."""
+
+    def __init__(self, n_lag):
+        self.n_lag = int(n_lag)
+        self.frames = []
+        self.acc = np.zeros(self.n_lag)
+        self.cnt = np.zeros(self.n_lag, dtype=np.int64)
+
+    def add(self, v):
+        v = np.asarray(v, dtype=np.float64)
+        self.frames.append(v)
+        n = len(self.frames)
+        for L in range(min(self.n_lag, n)):
+            self.acc[L] += float(np.sum(v * self.frames[n - 1 - L]))
+            self.cnt[L] += 1
+        if len(self.frames) > self.n_lag:
+            self.frames.pop(0)
+
+    def per_atom(self, n_atoms):
+        """C(L) per atom: acc / (cnt * n_atoms)."""
+        return self.acc / np.maximum(self.cnt, 1) / n_atoms

@@ -2,8 +2,9 @@
 
 The observables are those of Sec. "Output and Analysis": the centroid-virial
 kinetic energy per type, the mean squared bead spread R_g^2 per type, the bead
-temperature and radial distribution functions, all produced on the GPU by the
-library (estimators and RDF histogram kernels). The partial-quantisation sweep
+temperature, radial distribution functions and ring-polymer molecular
+dynamics (RPMD) time correlation functions from NVE trajectories, all produced
+on the GPU by the library (estimator, RDF histogram and correlation kernels). The partial-quantisation sweep
 follows Sec. "System I": the same water box run with the hydrogen and oxygen
 bead counts chosen independently, so that the convergence of each observable
 can be traced to the quantisation of each species.
@@ -58,6 +59,35 @@ def sample(m: MixTS, n_eq, n_samp, every, pairs=(), dr=0.02, nbins=None, n_block
             tb.append(e["T_beads"])
     return {"KE_cv": block_stats(ke, n_blocks), "Rg2": block_stats(rg, n_blocks), "T_beads": block_stats(tb, n_blocks),
             "g": {k: m.rdf_normalise(k[0], k[1], h, frames, dr) for k, h in hist.items()}, "frames": frames}
+
+
+def rpmd_bead_masses(sysm):
+    """Bead masses m_f = m / P_t per type: with them, Newton's equations of the
+    beta H_mix convention (potential weighted 1/P_t, springs P_t m/(beta hbar)^2)
+    give every centroid the RPMD equation of motion."""
+    return np.asarray(sysm.mass_type, dtype=np.float64) / np.asarray(sysm.P_type, dtype=np.float64)
+
+
+class CentroidVACF:
+    """Centroid velocity autocorrelation <v(0).v(t)> of the atoms of one type,
+    accumulated on the GPU over every time origin (mixts_vacf_accumulate).
+    Call add() after each step of an NVE run (thermostat off, RPMD bead
+    masses); result() gives C(L) per atom in (A/fs)^2 for lags of one add()."""
+
+    def __init__(self, m: MixTS, type_t, n_lag, n_atoms):
+        torch = m.torch
+        self.m, self.t, self.n = m, int(type_t), int(n_atoms)
+        self.ring = torch.zeros((int(n_lag), self.n, 3), dtype=torch.float64, device=m.device)
+        self.acc = torch.zeros(int(n_lag), dtype=torch.float64, device=m.device)
+        self.cnt = torch.zeros(int(n_lag), dtype=torch.int64, device=m.device)
+
+    def add(self):
+        self.m.vacf_accumulate(self.t, self.ring, self.acc, self.cnt)
+
+    def result(self):
+        acc = self.acc.cpu().numpy()
+        cnt = self.cnt.cpu().numpy()
+        return acc / np.maximum(cnt, 1) / self.n, cnt
 
 
 def quantisation_sweep(make_system, combos, dt=0.25, precision=FP64, n_eq=2000, n_samp=2000, every=10,

@@ -94,6 +94,7 @@ __global__ void k_list_prep(Dev d, const int* atom_is_pseudo) {
   const double dp = reduce_spread_kind(d, atom_is_pseudo, 1, red);
   for (int i = threadIdx.x; i < d.n_nonp; i += blockDim.x) d.nl_cnt[i] = 0;
   for (int i = threadIdx.x; i < d.n_pseudo; i += blockDim.x) d.pl_cnt[i] = 0;
+  if (threadIdx.x < 2) d.pctr[threadIdx.x] = 0;  // pair items of the new list, and their hand-out counter
   if (threadIdx.x == 0) {
     const double L = d.box;
     const double R = __dadd_rn(d.rc, __dmul_rn(2.0, ds));
@@ -349,58 +350,48 @@ __device__ __forceinline__ void dsf_direct(const Dev& d, double s, double* g, do
 // ---------------------------------------------------------------------------
 // Work items of the FP64 sweep for the current list: every owner row gets
 // (slice blocks) x (chunks of P32_CH entries per lane group) items, only as
-// many chunks as its row holds, written in row order (finest owners first,
-// so the heaviest items are handed out first). One CTA; also resets the
-// counter the sweep's warps take items from.
+// many chunks as its row holds. One CTA per 1024 rows reserves a contiguous
+// range of the item array (the counter was cleared with the list) and writes
+// its rows' items in row order.
 constexpr int ITEM_THREADS = 1024;
 __global__ void __launch_bounds__(ITEM_THREADS) k_pair_items(Dev d) {
   __shared__ int wsum[ITEM_THREADS / 32];
-  __shared__ int carry;
+  __shared__ int base;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) carry = 0;
+  const int i = blockIdx.x * ITEM_THREADS + tid;
+  int n = 0, nch = 0, lgsb = 0;
+  if (i < d.n_nonp) {
+    const int cnt = min(d.nl_cnt[i], d.nl_cap);
+    const int lgP = d.ainfo[i].log2P;
+    const int lgPp = lgP < 5 ? lgP : 5;
+    const int per = P32_CH << (5 - lgPp);
+    nch = (cnt + per - 1) / per;
+    lgsb = lgP - lgPp;
+    n = nch << lgsb;
+  }
+  int incl = n;  // inclusive scan over the block
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[wid] = incl;
   __syncthreads();
-  for (int base = 0; base < d.n_nonp; base += ITEM_THREADS) {
-    const int i = base + tid;
-    int n = 0, nch = 0, lgsb = 0;
-    if (i < d.n_nonp) {
-      const int cnt = min(d.nl_cnt[i], d.nl_cap);
-      const int lgP = d.ainfo[i].log2P;
-      const int lgPp = lgP < 5 ? lgP : 5;
-      const int per = P32_CH << (5 - lgPp);
-      nch = (cnt + per - 1) / per;
-      lgsb = lgP - lgPp;
-      n = nch << lgsb;
-    }
-    int incl = n;  // inclusive scan over the block
+  if (wid == 0) {
+    int v = lane < ITEM_THREADS / 32 ? wsum[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
     }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      int v = lane < ITEM_THREADS / 32 ? wsum[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-      }
-      if (lane < ITEM_THREADS / 32) wsum[lane] = v;
-    }
-    __syncthreads();
-    const int off = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - n;
-    for (int k = 0; k < n; ++k) {
-      const int sb = k / nch, ch = k - sb * nch;
-      d.pitems[off + k] = make_int2(i, (sb << 16) | ch);
-    }
-    __syncthreads();
-    if (tid == 0) carry += wsum[ITEM_THREADS / 32 - 1];
-    __syncthreads();
+    if (lane < ITEM_THREADS / 32) wsum[lane] = v;
+    if (lane == 31) base = atomicAdd(d.pctr, v);
   }
-  if (tid == 0) {
-    d.pctr[0] = carry;
-    d.pctr[1] = 0;
+  __syncthreads();
+  const int off = base + (wid > 0 ? wsum[wid - 1] : 0) + incl - n;
+  for (int k = 0; k < n; ++k) {
+    const int sb = k / nch, ch = k - sb * nch;
+    d.pitems[off + k] = make_int2(i, (sb << 16) | ch);
   }
 }
 
@@ -597,9 +588,10 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
 // evaluated from both of its atoms and energies and counts carry a factor 1/2.
 //
 // Before the sweep, k_list_seg32 regroups each row by partner type (a
-// counting sort, one warp per row) and folds the pair's bead-0 displacement
+// counting sort, one warp per row), folds the pair's bead-0 displacement
 // (r_j0 + n L) - r_i0 into each entry once, in binary32 from the exact
-// 2^-12 A grid parts plus their remainders. An item is then (owner atom i,
+// 2^-12 A grid parts plus their remainders, and writes the row's work items.
+// An item is then (owner atom i,
 // partner type t, block of 32 owner beads, chunk of entries) with one fine
 // grid P* = max(P_i, P_t), one weight 1/P* and one parameter set: lanes are
 // the owner's beads (groups of min(P_i, 32) lanes take different entries) and
@@ -613,6 +605,15 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
 // & Stegun, Handbook of Mathematical Functions, eq. 7.1.26 (|error| <=
 // 1.5e-7), with the exact Gaussian in the force.
 // ---------------------------------------------------------------------------
+// log2 of the entries of one FP32 item: 2^LG_P32_TERMS terms = entries x
+// (owner beads of the block) x (fine slices per owner bead)
+__device__ __forceinline__ int p32_lg_entries(int lgPi, int lgPt) {
+  const int lgPp = lgPi < 5 ? lgPi : 5;
+  const int lgS = lgPi > lgPt ? lgPi : lgPt;
+  const int lgE = LG_P32_TERMS - lgPp - (lgS - lgPi);
+  return lgE > 0 ? lgE : 0;
+}
+
 __global__ void __launch_bounds__(NL_THREADS) k_list_seg32(Dev d) {
   const int lane = threadIdx.x & 31;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -638,6 +639,30 @@ __global__ void __launch_bounds__(NL_THREADS) k_list_seg32(Dev d) {
   }
   int next = incl - c_mine;  // lane u: next slot of type u
   if (lane <= nt) d.nlseg[(size_t)i * (nt + 1) + lane] = lane < nt ? next : cnt;
+  // this row's work items, (partner type, slice block, chunk) of ~2^LG_P32_TERMS
+  // terms each, in a range of the item array reserved with one atomic
+  {
+    const int lgP = d.ainfo[i].log2P;
+    const int lgsb = lgP > 5 ? lgP - 5 : 0;
+    const int nch = lane < nt ? (c_mine + (1 << p32_lg_entries(lgP, d.log2P[lane])) - 1) >>
+                                    p32_lg_entries(lgP, d.log2P[lane])
+                              : 0;
+    const int n = nch << lgsb;
+    int ni = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, ni, o);
+      if (lane >= o) ni += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, ni, 31);
+    int base = 0;
+    if (lane == 0 && total > 0) base = atomicAdd(d.pctr, total);
+    base = __shfl_sync(0xffffffffu, base, 0) + ni - n;
+    for (int k = 0; k < n; ++k) {
+      const int sb = k / nch, ch = k - sb * nch;
+      d.pitems[base + k] = make_int2(i, (lane << 27) | (sb << 20) | ch);
+    }
+  }
   const int r0i = d.ainfo[i].row0;
   const float4 hi = d.Xf[r0i], lo = d.Xl[r0i];
   const float bh = d.box_hi, bl = d.box_lo;
@@ -667,76 +692,11 @@ __global__ void __launch_bounds__(NL_THREADS) k_list_seg32(Dev d) {
   }
 }
 
-// log2 of the entries of one FP32 item: 2^LG_P32_TERMS terms = entries x
-// (owner beads of the block) x (fine slices per owner bead)
-__device__ __forceinline__ int p32_lg_entries(int lgPi, int lgPt) {
-  const int lgPp = lgPi < 5 ? lgPi : 5;
-  const int lgS = lgPi > lgPt ? lgPi : lgPt;
-  const int lgE = LG_P32_TERMS - lgPp - (lgS - lgPi);
-  return lgE > 0 ? lgE : 0;
-}
-
-// Items of the FP32 sweep for the current list: (row, partner type, slice
-// block, chunk), rows in order (finest owners first). One CTA; also resets
-// the hand-out counter.
-__global__ void __launch_bounds__(ITEM_THREADS) k_pair_items32(Dev d) {
-  __shared__ int wsum[ITEM_THREADS / 32];
-  __shared__ int carry;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int nt = d.n_types;
-  if (tid == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < d.n_nonp; base += ITEM_THREADS) {
-    const int i = base + tid;
-    int n = 0, lgP = 0, lgsb = 0;
-    const int* seg = d.nlseg + (size_t)i * (nt + 1);
-    if (i < d.n_nonp) {
-      lgP = d.ainfo[i].log2P;
-      lgsb = lgP > 5 ? lgP - 5 : 0;
-      for (int t = 0; t < nt; ++t) {
-        const int c = seg[t + 1] - seg[t];
-        const int E = 1 << p32_lg_entries(lgP, d.log2P[t]);
-        n += ((c + E - 1) / E) << lgsb;
-      }
-    }
-    int incl = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      int v = lane < ITEM_THREADS / 32 ? wsum[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-      }
-      if (lane < ITEM_THREADS / 32) wsum[lane] = v;
-    }
-    __syncthreads();
-    int off = carry + (wid > 0 ? wsum[wid - 1] : 0) + incl - n;
-    if (i < d.n_nonp) {
-      for (int t = 0; t < nt; ++t) {
-        const int c = seg[t + 1] - seg[t];
-        const int E = 1 << p32_lg_entries(lgP, d.log2P[t]);
-        const int nch = (c + E - 1) / E;
-        for (int sb = 0; sb < (1 << lgsb); ++sb)
-          for (int ch = 0; ch < nch; ++ch) d.pitems[off++] = make_int2(i, (t << 27) | (sb << 20) | ch);
-      }
-    }
-    __syncthreads();
-    if (tid == 0) carry += wsum[ITEM_THREADS / 32 - 1];
-    __syncthreads();
-  }
-  if (tid == 0) {
-    d.pctr[0] = carry;
-    d.pctr[1] = 0;
-  }
-}
-
+// The terms of one lane over its group's entries [e_begin, e_end) with
+// stride estep: each entry's record and its first partner bead are loaded one
+// entry ahead of their use (two-stage software pipeline), so the dependent
+// load chain (entry record -> partner bead) overlaps the previous entry's
+// arithmetic.
 template <bool LJ>
 __device__ __forceinline__ void pair32_entries(const float4* __restrict__ lst, int e_begin, int e_end, int estep,
                                                int lgr, int sh_t, const float4* __restrict__ Xd, int b, float4 di,
@@ -749,13 +709,22 @@ __device__ __forceinline__ void pair32_entries(const float4* __restrict__ lst, i
               a5 = 1.061405429f;
   const float nl2e = -alpha2 * 1.4426950408889634f;
   const float pa = ap * alpha;
+  const int s0 = b << lgr;  // first fine slice of this lane's owner bead
+  if (e_begin >= e_end) return;
+  float4 B = __ldg(lst + e_begin);
+  float4 dj0 = __ldg(Xd + (__float_as_int(B.w) >> 4) + (s0 >> sh_t));
+  int en = e_begin + estep;
+  float4 Bn = en < e_end ? __ldg(lst + en) : B;
   for (int e = e_begin; e < e_end; e += estep) {
-    const float4 B = lst[e];
+    // stage ahead: the next entry's first partner bead, the entry after it
+    const float4 djn = __ldg(Xd + (__float_as_int(Bn.w) >> 4) + (s0 >> sh_t));
+    const int enn = en + estep;
+    const float4 Bnn = enn < e_end ? __ldg(lst + enn) : Bn;
     const int abase = __float_as_int(B.w) >> 4;
     const float bx = B.x - di.x, by = B.y - di.y, bz = B.z - di.z;
+#pragma unroll 2
     for (int k = 0; k < (1 << lgr); ++k) {
-      const int s = (b << lgr) + k;  // fine slice of the pair's grid
-      const float4 dj = Xd[abase + (s >> sh_t)];
+      const float4 dj = k == 0 ? dj0 : __ldg(Xd + abase + ((s0 + k) >> sh_t));
       const float dx = bx + dj.x, dy = by + dj.y, dz = bz + dj.z;
       const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
       if (r2 < rc2) {
@@ -782,6 +751,10 @@ __device__ __forceinline__ void pair32_entries(const float4* __restrict__ lst, i
         ++nev;
       }
     }
+    B = Bn;
+    dj0 = djn;
+    Bn = Bnn;
+    en = enn;
   }
 }
 
@@ -1228,9 +1201,8 @@ int launch_pair(const Dev& d, cudaStream_t s) {
   if (d.precision == MIXTS_FP32_FORCES) {
     if (d.n_nonp == 0) return 0;
     k_list_seg32<<<(d.n_nonp + wpb - 1) / wpb, NL_THREADS, 0, s>>>(d);
-    k_pair_items32<<<1, ITEM_THREADS, 0, s>>>(d);
     k_pair32<<<d.pair32_grid, PAIR_THREADS, 0, s>>>(d);
-    return 3;
+    return 2;
   }
   if (d.n_pitems == 0) return 0;
   const size_t smem = PAIR64_SMEM_PER_INTERVAL * (size_t)d.dsf_nint;
@@ -1241,7 +1213,7 @@ int launch_pair(const Dev& d, cudaStream_t s) {
   }
   const int nsbm = d.lgPmax_nb > 5 ? 1 << (d.lgPmax_nb - 5) : 1;
   const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;  // bound on the list's items
-  k_pair_items<<<1, ITEM_THREADS, 0, s>>>(d);
+  k_pair_items<<<(d.n_nonp + ITEM_THREADS - 1) / ITEM_THREADS, ITEM_THREADS, 0, s>>>(d);
   k_pair64<<<(int)std::min<long long>((items + wpb - 1) / wpb, d.pair_grid), PAIR_THREADS, smem, s>>>(d);
   return 2;
 }

@@ -176,14 +176,14 @@ __global__ void k_grad_q(Dev d, double grad_out, double* dvdq) {
 }
 
 int launch_grad(const Dev& d, cudaStream_t s, int ta, int tb, double ke, const double* pc, unsigned long long* acc,
-                double grad_out, double* dvdq) {
+                double grad_out, double* dvdq, bool want_theta) {
   int n = 0;
   const int wpb = GRAD_THREADS / 32;
-  if (d.n_pitems > 0) {
+  if (want_theta && d.n_pitems > 0) {
     k_grad_nb<<<(d.n_pitems + wpb - 1) / wpb, GRAD_THREADS, 0, s>>>(d, acc);
     ++n;
   }
-  if (d.n_ppitems > 0 && d.n_nonp > 0) {
+  if (want_theta && d.n_ppitems > 0 && d.n_nonp > 0) {
     k_grad_pseudo<<<(d.n_ppitems + wpb - 1) / wpb, GRAD_THREADS, 0, s>>>(d, ta, tb, ke, pc, acc + 2 * MT * MT);
     ++n;
   }

@@ -1686,6 +1686,25 @@ extern "C" MIXTS_API mixts_status mixts_rdf_normalise(mixts_handle h, int ta, in
 }
 
 // ---------------------------------------------------------------------------
+// Centroid velocity autocorrelation (ring-polymer molecular dynamics).
+// ---------------------------------------------------------------------------
+namespace mx {
+int launch_vacf(const Dev& d, cudaStream_t s, int t, int n_lag, double* ring, double* acc, unsigned long long* cnt);
+}
+
+extern "C" MIXTS_API mixts_status mixts_vacf_accumulate(mixts_handle h, int type, int n_lag, double* ring_dev,
+                                                        double* acc_dev, unsigned long long* cnt_dev) {
+  if (!h || !ring_dev || !acc_dev || !cnt_dev) return MIXTS_ERR_ARG;
+  if (!h->kids.empty()) return set_err(h, MIXTS_ERR_ARG, "batched handle: query a member (mixts_batch_member)");
+  if (type < 0 || type >= h->d.n_types || h->d.N[type] == 0)
+    return set_err(h, MIXTS_ERR_ARG, "type must hold atoms");
+  if (n_lag < 1 || n_lag > 65535) return set_err(h, MIXTS_ERR_ARG, "n_lag must be 1..65535");
+  if (!h->nm_valid) return set_err(h, MIXTS_ERR_STATE, "no mode-space state yet: call mixts_step first");
+  phase(h, 6, [&] { return launch_vacf(h->d, h->stream, type, n_lag, ring_dev, acc_dev, cnt_dev); });
+  return cuda_check(h, cudaGetLastError(), "vacf launch");
+}
+
+// ---------------------------------------------------------------------------
 // Parameter gradient (the differentiation variant).
 // ---------------------------------------------------------------------------
 namespace {
@@ -1707,7 +1726,7 @@ void pseudo_param_derivs_host(double ke, double q, double sig, double A, double 
 
 namespace mx {
 int launch_grad(const Dev& d, cudaStream_t s, int ta, int tb, double ke, const double* pc, unsigned long long* acc,
-                double grad_out, double* dvdq);
+                double grad_out, double* dvdq, bool want_theta);
 }
 
 extern "C" MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int ta, int tb, const double* theta,
@@ -1791,7 +1810,11 @@ extern "C" MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int ta, i
   phase(h, 1, [&] { return launch_pair(dd, s); });
   phase(h, 2, [&] { return launch_bonded(dd, s, h->ainfo_atom); });
   phase(h, 3, [&] { return launch_pseudo(dd, s); });
-  phase(h, 6, [&] { return launch_grad(dd, s, ta, tb, u.ke, (const double*)(w + p.o_pc), gacc, grad_out, dVdq_dev); });
+  // the adjoint sums over theta run only when dV/dtheta is asked for
+  phase(h, 6, [&] {
+    return launch_grad(dd, s, ta, tb, u.ke, (const double*)(w + p.o_pc), gacc, grad_out, dVdq_dev,
+                       dVdtheta_host != nullptr);
+  });
   phase(h, 6, [&] { return launch_forces_out(dd, s); });
   h->nm_valid = false;
   h->f_valid = false;

@@ -102,6 +102,7 @@ def lib():
         L.mixts_batch_tune.argtypes = [C.c_void_p, C.c_int, C.POINTER(_Tuning)]
         L.mixts_potential_grad.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_double,
                                            C.POINTER(C.c_double), C.c_void_p, C.POINTER(C.c_double)]
+        L.mixts_vacf_accumulate.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
         L.mixts_alu_probe.argtypes = [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.mixts_destroy.argtypes = [C.c_void_p]
         L.mixts_last_error.argtypes = [C.c_void_p]
@@ -116,7 +117,7 @@ EXPORTED = ["mixts_workspace_size", "mixts_init", "mixts_forces", "mixts_step", 
             "mixts_destroy", "mixts_last_error", "mixts_version", "mixts_reload", "mixts_set_timing",
             "mixts_get_timing", "mixts_forces_noalloc", "mixts_potential_grad", "mixts_batch_member",
             "mixts_batch_tune", "mixts_set_graph", "mixts_rdf_accumulate", "mixts_rdf_normalise",
-            "mixts_alu_probe"]
+            "mixts_alu_probe", "mixts_vacf_accumulate"]
 # force-field parameters of the differentiation variant, in mixts_potential_grad's order
 THETA_NAMES = ["sigma_a", "A_a_eV", "b_a", "sigma_b", "A_b_eV", "b_b", "q_a", "eps_aa"]
 PHASES = ["nlist", "pair", "bonded", "pseudo", "prop", "final", "other"]
@@ -262,22 +263,31 @@ class MixTS:
                                               int(n_frames), _ptr(h, C.c_uint64), _ptr(g, C.c_double)))
         return g
 
+    def vacf_accumulate(self, type_t, ring, acc, cnt):
+        """Add the current frame to a centroid velocity autocorrelation
+        (float64 device tensors ring [n_lag, N_t, 3], acc [n_lag], int64 cnt
+        [n_lag], zeroed before the first call)."""
+        self._check(lib().mixts_vacf_accumulate(self.h, int(type_t), int(acc.numel()), C.c_void_p(ring.data_ptr()),
+                                                C.c_void_p(acc.data_ptr()), C.c_void_p(cnt.data_ptr())))
+
     def set_graph(self, steps_per_launch):
         """Steps per captured CUDA graph launch of step() (0: plain launches)."""
         self._check(lib().mixts_set_graph(self.h, int(steps_per_launch)))
 
-    def potential_grad(self, type_a, type_b, theta, grad_out=1.0, want_dvdq=True):
-        """V_mix(q, theta), grad_out * dV/dq (device tensor or None), grad_out * dV/dtheta (8 floats).
+    def potential_grad(self, type_a, type_b, theta, grad_out=1.0, want_dvdq=True, want_theta=True):
+        """V_mix(q, theta), grad_out * dV/dq (device tensor or None), grad_out * dV/dtheta (8 floats or None).
 
         theta follows THETA_NAMES; it is applied to this evaluation only.
+        Without want_theta the adjoint sums over theta are not run.
         """
         th = (C.c_double * 8)(*[float(x) for x in theta])
         v = C.c_double(0.0)
         g = (C.c_double * 8)()
         dq = self.torch.empty_like(self.q) if want_dvdq else None
         self._check(lib().mixts_potential_grad(self.h, int(type_a), int(type_b), th, float(grad_out), C.byref(v),
-                                               C.c_void_p(dq.data_ptr()) if want_dvdq else None, g))
-        return v.value, dq, np.array(list(g))
+                                               C.c_void_p(dq.data_ptr()) if want_dvdq else None,
+                                               g if want_theta else None))
+        return v.value, dq, (np.array(list(g)) if want_theta else None)
 
     def reload(self):
         """Declare that q and/or p were rewritten in place (host-resident state)."""
@@ -330,29 +340,33 @@ def _potential_fn():
         """V_mix as a differentiable function of (theta, q) for one MixTS engine.
 
         ``theta`` is a float64 CPU tensor of 8 parameters (THETA_NAMES order),
-        ``q`` a float64 device tensor [n_beads, 3]. The forward pass runs the
-        force kernels and the adjoint sums in one call; the backward pass only
-        scales the stored gradients by the incoming one.
+        ``q`` a float64 device tensor [n_beads, 3]. The forward pass evaluates
+        V only; the backward pass re-evaluates the pair terms at the saved
+        (theta, q) and runs the adjoint sums, scaled by the incoming gradient,
+        for the inputs that need one (nothing per pair term is stored).
         """
 
         @staticmethod
         def forward(ctx, theta, q, engine, type_a, type_b):
             if q.data_ptr() != engine.q.data_ptr():
                 engine.q.copy_(q)
-            v, dq, g = engine.potential_grad(type_a, type_b, theta.detach().cpu().tolist(), 1.0,
-                                             want_dvdq=ctx.needs_input_grad[1])
-            ctx.save_for_backward(torch.from_numpy(g), dq if dq is not None else torch.empty(0))
+            v, _, _ = engine.potential_grad(type_a, type_b, theta.detach().cpu().tolist(), 1.0, want_dvdq=False,
+                                            want_theta=False)
+            ctx.engine, ctx.types = engine, (type_a, type_b)
+            ctx.save_for_backward(theta.detach(), q)
             return torch.tensor(v, dtype=torch.float64)
 
         @staticmethod
         def backward(ctx, gv):
-            g, dq = ctx.saved_tensors
-            gth = gq = None
-            if ctx.needs_input_grad[0]:
-                gth = (gv.cpu() * g).to(torch.float64)
-            if ctx.needs_input_grad[1]:
-                gq = dq * gv.to(dq.device)
-            return gth, gq, None, None, None
+            theta, q = ctx.saved_tensors
+            engine = ctx.engine
+            if q.data_ptr() != engine.q.data_ptr():
+                engine.q.copy_(q)
+            want_th, want_q = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+            _, dq, g = engine.potential_grad(ctx.types[0], ctx.types[1], theta.cpu().tolist(), float(gv),
+                                             want_dvdq=want_q, want_theta=want_th)
+            gth = torch.from_numpy(g).to(torch.float64) if want_th else None
+            return gth, (dq if want_q else None), None, None, None
 
     return MixTSPotential
 

@@ -57,6 +57,10 @@ class System:
     p: np.ndarray = field(default=None)
     # fictitious bead mass per type (kinetic term p^2/2m_f); None: the physical mass
     bead_mass_type: np.ndarray = field(default=None)
+    # electrostatics: 0 damped shifted force per bead pair; 1 Ewald (real space per
+    # bead pair, reciprocal space on centroids with wave vectors |n| <= ewald_kmax)
+    coulomb: int = 0
+    ewald_kmax: int = 0
 
     # ---- bookkeeping (layout only) ----
     @property

@@ -141,3 +141,24 @@ def test_grad_full_size_ion_electron_512(gpu):
         for j in range(8):
             assert abs(g[j] - g_or[j]) <= 1e-9 * abs(g_or[j]) + _gtol(V), (gpu.THETA_NAMES[j], g[j], g_or[j])
         m.close()
+
+
+def test_forward_alone_skips_the_adjoint(gpu):
+    """The autograd forward evaluates V only: the adjoint sums over theta run
+    in backward, on the pair terms recomputed there (nothing is stored)."""
+    torch = pytest.importorskip("torch")
+    s = _mixed()
+    m = gpu.MixTS(s)
+    th = torch.tensor(oracle.theta_of(s, 0, 1), dtype=torch.float64)
+    k0 = m.timing()[2]
+    V = gpu.mixts_potential(th, m.q, m, 0, 1)
+    k1 = m.timing()[2]
+    _, _, g = m.potential_grad(0, 1, th.tolist())
+    k2 = m.timing()[2]
+    assert k1 - k0 < k2 - k1  # the forward launched fewer kernels than a full gradient evaluation
+    assert V.item() == m.potential_grad(0, 1, th.tolist(), want_dvdq=False, want_theta=False)[0]
+    thg = th.clone().requires_grad_(True)
+    V2 = gpu.mixts_potential(thg, m.q, m, 0, 1)
+    V2.backward()
+    assert np.allclose(thg.grad.numpy(), g, rtol=1e-14, atol=0)
+    m.close()

@@ -56,7 +56,7 @@ def _h_coarser(P_H, P_O, seed=12):
     return s
 
 
-@pytest.mark.parametrize("case", ["c1", "c1_spread", "mixed16", "mixed128", "uniform4", "h1_o4", "h4_o8"])
+@pytest.mark.parametrize("case", ["c1", "c1_spread", "mixed16", "mixed128", "uniform4", "h1_o4", "h4_o8", "h64_o16"])
 def test_forces_match_oracle(gpu, case):
     if case == "c1":
         s = _c1()
@@ -70,6 +70,9 @@ def test_forces_match_oracle(gpu, case):
         s = _h_coarser(1, 4)
     elif case == "h4_o8":
         s = _h_coarser(4, 8)
+    elif case == "h64_o16":  # two slice blocks per H owner; energies summed from 2^-34 fixed-point lanes
+        s = synth.water_box(64, 12.43, 64, 16, seed=15)
+        s.q = s.q + np.random.default_rng(16).normal(0, 0.05, s.q.shape)
     else:
         s = synth.water_box(27, 9.3, 4, 4, seed=4)
     m = gpu.MixTS(s)

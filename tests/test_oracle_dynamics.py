@@ -197,3 +197,55 @@ def test_thermostat_heat_conserves_effective_energy(orc):
     assert np.std(hc - hc[0]) < 2e-3 * np.std(h - h[0])
     assert abs(hc[-1] - hc[0]) < 1e-2 * abs(h[-1] - h[0]) + 0.1
     assert np.std(hc - hc[0]) < 2.0 * np.std(h0 - h0[0])   # no worse than plain NVE
+
+
+@pytest.mark.parametrize("P", [1, 8])
+def test_rpmd_harmonic_centroid_vacf(orc, P):
+    """Ring-polymer molecular dynamics in an external harmonic well (bead mass
+    m/P, thermostat off): the centroid evolves in the well exactly, so its
+    Kubo-transformed velocity autocorrelation is (3 kT / m) cos(w t) at any P
+    (Sec. "Output and Analysis": RPMD correlation functions from NVE
+    trajectories). Origins are sampled by PILE segments between NVE segments."""
+    c, kT, bh = _consts(orc)
+    m, M_anchor = 1.0, 1.0e9
+    w = 2.0 / bh                               # beta hbar omega = 2
+    k_kcal = m * w ** 2 / c["kcal"]
+    s = synth.harmonic_tether([P, 1], [(0, 1, k_kcal)], masses=[m, M_anchor], seed=31 + P)
+    s.bead_mass_type = orc.rpmd_bead_masses(s)
+    run = orc.Runner(s, orc.make_params(T=T, dt=1.0, tau=10.0, lam=1.0, seed=40 + P))
+    nve = orc.make_params(T=T, dt=1.0, tau=0.0, lam=0.0, seed=0)
+    nvt = run.prm
+    run.step(300)
+    n_lag, segs = 41, 1500
+    acc = np.zeros(n_lag)
+    per_seg = []
+    for _ in range(segs):
+        run.prm = nve
+        v0 = orc.centroid_velocities(s, run.p, 0)[0]
+        cs = [float(v0 @ v0)]
+        for _ in range(n_lag - 1):
+            run.step(1)
+            cs.append(float(v0 @ orc.centroid_velocities(s, run.p, 0)[0]))
+        per_seg.append(cs)
+        run.prm = nvt
+        run.step(25)
+    per_seg = np.array(per_seg)
+    mean = per_seg.mean(axis=0)
+    err = per_seg.std(axis=0, ddof=1) / np.sqrt(segs)
+    t = np.arange(n_lag) * 1.0
+    exact = 3.0 * kT / m * np.cos(w * t)
+    assert np.all(np.abs(mean - exact) < 4 * err + 0.01 * exact[0]), np.max(np.abs(mean - exact) / err)
+    # the accumulator over every origin of one NVE trajectory gives the same
+    # lagged products as the direct loop above
+    vc = orc.VelocityCorrelation(5)
+    run.prm = nve
+    frames = []
+    for _ in range(12):
+        run.step(1)
+        v = orc.centroid_velocities(s, run.p, 0)
+        frames.append(v)
+        vc.add(v)
+    for L in range(5):
+        direct = sum(float(np.sum(frames[i] * frames[i - L])) for i in range(L, 12))
+        assert vc.acc[L] == pytest.approx(direct, rel=1e-13)
+        assert vc.cnt[L] == 12 - L
