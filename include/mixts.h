@@ -102,11 +102,20 @@ typedef struct {
   double tau_centroid; /* fs, centroid Langevin time; <= 0: off */
   double pile_lambda;  /* internal modes get friction 2*lambda*omega_k; 0: off */
   double r_cut;        /* A, cutoff of every nonbonded and pseudopotential term */
-  double dsf_alpha;    /* 1/A, damping of the damped-shifted-force Coulomb */
+  double dsf_alpha;    /* 1/A, damping of the damped-shifted-force Coulomb (coulomb = 0) or the
+                          Ewald splitting parameter (coulomb = 1) */
   int precision;       /* mixts_precision */
   int nlist_cap;       /* entries per owner row of the neighbour list; 0: automatic */
   int free_ring_substeps; /* free ring polymer evolution (Sec. "Evaluation"): 0 exact in normal modes;
                              n >= 1 velocity Verlet on the springs with n sub-steps of dt/n */
+  int coulomb;         /* 0: damped-shifted-force Coulomb on every bead pair of the mixTS map;
+                          1: Ewald, the paper's treatment (Sec. "Theory", last paragraph: SPME with
+                          centroid electrostatics): real space k_e q q erfc(alpha r)/r on every bead
+                          pair within r_cut, reciprocal space on the ring-polymer centroids (direct
+                          sum over wave vectors 2 pi n / L with |n| <= ewald_kmax, each centroid's force
+                          shared equally by its beads), minus the same-molecule erf(alpha r)/r terms
+                          of the centroids, the self energy and a neutralising background */
+  int ewald_kmax;      /* coulomb = 1: largest |n| of the reciprocal sum, 1..64 */
 } mixts_params;
 
 /* Estimates of the state after the last completed step (or of the current
@@ -240,7 +249,8 @@ MIXTS_API mixts_status mixts_gaussians(mixts_handle h, uint32_t step, uint32_t s
                              float* out_dev);
 
 /* Potential and gradients for the differentiation variant (Eq.
- * mts-hamiltonian with force-field parameters theta). theta (8 doubles, host)
+ * mts-hamiltonian with force-field parameters theta; damped-shifted-force
+ * Coulomb only: MIXTS_ERR_ARG for a handle made with coulomb = 1). theta (8 doubles, host)
  * = (sigma_a, A_a [eV], b_a, sigma_b, A_b [eV], b_b, q_a, eps_aa) for the
  * site types a = type_a and b = type_b: the pseudopotential parameters of
  * both, the charge of a, and the a-a Lennard-Jones epsilon; every other

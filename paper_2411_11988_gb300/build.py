@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmixts.so")
-SOURCES = ["mixts_api.cu", "k_prop.cu", "k_forces.cu", "k_grad.cu", "k_rdf.cu", "k_probe.cu", "k_corr.cu"]
+SOURCES = ["mixts_api.cu", "k_prop.cu", "k_forces.cu", "k_grad.cu", "k_rdf.cu", "k_probe.cu", "k_corr.cu", "k_ewald.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]

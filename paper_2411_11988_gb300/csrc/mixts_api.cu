@@ -72,6 +72,14 @@ struct Plan {
   std::vector<double> charge, eps, sig, pp_sig, pp_A, pp_b;  // raw force-field parameters (theta variant)
   int dsf_nint = 0, dsf_elo = -2;
   std::vector<double> ps_tab;  // pseudopotential tables (electron systems)
+  // centroid Ewald (coulomb == 1)
+  std::vector<double> kvec;    // 4 per wave vector
+  std::vector<int> kn, qinfo, intra;
+  std::vector<double> qcharge;
+  int n_kvec = 0, n_qatoms = 0, n_intra = 0;
+  double ew_const = 0.0, ew_bg = 0.0;
+  size_t o_kvec = 0, o_kn = 0, o_qinfo = 0, o_qcharge = 0, o_intra = 0, o_ewphase = 0, o_ewcen = 0, o_ews = 0,
+         o_ewek = 0;
   int ps_nint = 0, ps_elo = -6;
   std::vector<int> cm_off, mc_off, big_slot0, sb_off;
   int n_spread_big = 0;
@@ -204,13 +212,15 @@ static std::vector<double> pseudo_table(double kq, double sig, double A, double 
                         [&](LD s) { const LD r = sqrtl(s); return -(dV(r) - dvr) / r; }, rc, elo, nint_out);
 }
 
-std::vector<double> dsf_table(double alpha, double rc, int elo, int* nint_out) {
+// shifted: the damped-shifted-force form; otherwise the Ewald real-space
+// kernel erfc(a r)/r (value and slope not shifted at rc)
+std::vector<double> dsf_table(double alpha, double rc, int elo, int* nint_out, bool shifted = true) {
   typedef long double LD;
   const LD a = alpha, R = rc;
   const LD pil = 3.141592653589793238462643383279502884L;
-  const LD erc = erfcl(a * R);
+  const LD erc = shifted ? erfcl(a * R) : 0.0L;
   const LD gg = 2.0L * a / sqrtl(pil);
-  const LD cf = erc / (R * R) + gg * expl(-a * a * R * R) / R;
+  const LD cf = shifted ? erc / (R * R) + gg * expl(-a * a * R * R) / R : 0.0L;
   auto G = [&](LD sv) {
     const LD r = sqrtl(sv);
     return erfcl(a * r) / r - erc / R + cf * (r - R);
@@ -433,7 +443,49 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
     p.ang_par.push_back(s->angle_theta0[g]);
     for (int sl = 0; sl < Ps; ++sl) p.bitems.push_back(BondItem{1, g, sl, 0});
   }
-  p.dsf = dsf_table(prm->dsf_alpha, prm->r_cut, p.dsf_elo, &p.dsf_nint);
+  p.dsf = dsf_table(prm->dsf_alpha, prm->r_cut, p.dsf_elo, &p.dsf_nint, prm->coulomb != 1);
+  if (prm->coulomb != 0 && prm->coulomb != 1) {
+    fail(p, MIXTS_ERR_ARG, "coulomb must be 0 (damped shifted force) or 1 (Ewald)");
+    return p;
+  }
+  if (prm->coulomb == 1) {  // reciprocal sum on centroids: wave vectors, charged sites, same-molecule pairs
+    if (prm->ewald_kmax < 1 || prm->ewald_kmax > 64 || !(prm->dsf_alpha > 0.0)) {
+      fail(p, MIXTS_ERR_ARG, "Ewald needs ewald_kmax in 1..64 and a positive splitting parameter");
+      return p;
+    }
+    const double L = s->box, V = L * L * L, a = prm->dsf_alpha;
+    const int km = prm->ewald_kmax;
+    for (int nx = 0; nx <= km; ++nx)
+      for (int ny = -km; ny <= km; ++ny)
+        for (int nz = -km; nz <= km; ++nz) {
+          if (nx * nx + ny * ny + nz * nz > km * km) continue;
+          if (!(nx > 0 || (nx == 0 && (ny > 0 || (ny == 0 && nz > 0))))) continue;  // one of k, -k
+          const double kx = 2.0 * PI * nx / L, ky = 2.0 * PI * ny / L, kz = 2.0 * PI * nz / L;
+          const double k2 = kx * kx + ky * ky + kz * kz;
+          const double W = 2.0 * (2.0 * PI * u.ke / V) * exp(-k2 / (4.0 * a * a)) / k2;
+          p.kvec.insert(p.kvec.end(), {kx, ky, kz, W});
+          p.kn.insert(p.kn.end(), {nx, ny, nz, 0});
+        }
+    p.n_kvec = (int)(p.kvec.size() / 4);
+    std::vector<int> qidx(p.na, -1);
+    double Q = 0.0, q2 = 0.0;
+    for (int i = 0; i < p.na; ++i) {
+      const int t = s->type_of_atom[i];
+      if (s->pseudo_type[t] || s->charge_type[t] == 0.0) continue;
+      qidx[i] = p.n_qatoms++;
+      p.qinfo.insert(p.qinfo.end(), {p.off[t] + p.rank[i], p.N[t], s->P_type[t], i});
+      p.qcharge.push_back(s->charge_type[t]);
+      Q += s->charge_type[t];
+      q2 += s->charge_type[t] * s->charge_type[t];
+    }
+    for (int i = 0; i < p.na; ++i)
+      for (int j = i + 1; j < p.na; ++j)
+        if (qidx[i] >= 0 && qidx[j] >= 0 && s->mol_of_atom[i] == s->mol_of_atom[j])
+          p.intra.insert(p.intra.end(), {qidx[i], qidx[j]});
+    p.n_intra = (int)(p.intra.size() / 2);
+    p.ew_bg = -u.ke * PI * Q * Q / (2.0 * V * a * a);
+    p.ew_const = -u.ke * a / sqrt(PI) * q2 + p.ew_bg;
+  }
   // normal modes, thermostat, rotation
   const double kT = u.kB * prm->T;
   const double bh = u.hbar / kT;
@@ -594,6 +646,13 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_pspar_alt = A.add(sizeof(PseudoPar) * MT);
   p.o_pc = A.add(sizeof(double) * 8 * MT);
   p.o_gacc = A.add(sizeof(unsigned long long) * (2 * MT * MT + 8));
+  if (p.n_kvec > 0) {
+    p.o_kvec = A.add(sizeof(double) * p.kvec.size());
+    p.o_kn = A.add(sizeof(int) * p.kn.size());
+    p.o_qinfo = A.add(sizeof(int) * std::max<size_t>(4, p.qinfo.size()));
+    p.o_qcharge = A.add(sizeof(double) * std::max<size_t>(1, p.qcharge.size()));
+    p.o_intra = A.add(sizeof(int) * std::max<size_t>(2, p.intra.size()));
+  }
   p.tab_bytes = A.size;
   const size_t nb3 = (size_t)p.n_beads * 3;
   p.o_qnm = A.add(sizeof(double) * nb3);
@@ -637,6 +696,12 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_heat = A.add(sizeof(double));
   p.o_est = A.add(sizeof(double) * EST_N);
   p.o_parts = A.add(sizeof(double) * 6 * std::max<size_t>(1, p.slot_type.size()));
+  if (p.n_kvec > 0) {
+    p.o_ewphase = A.add(sizeof(double2) * (size_t)std::max(1, p.n_qatoms) * 3 * (prm->ewald_kmax + 1));
+    p.o_ewcen = A.add(sizeof(double) * 4 * (size_t)std::max(1, p.n_qatoms));
+    p.o_ews = A.add(sizeof(double2) * (size_t)p.n_kvec);
+    p.o_ewek = A.add(sizeof(double) * 2 * (size_t)p.n_kvec);
+  }
   p.state_bytes = A.size - p.tab_bytes;
   return p;
 }
@@ -824,6 +889,13 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   put(img, p.o_slot_type, p.slot_type);
   put(img, p.o_dsf, p.dsf);
   if (!p.ps_tab.empty()) put(img, p.o_pstab, p.ps_tab);
+  if (p.n_kvec > 0) {
+    put(img, p.o_kvec, p.kvec);
+    put(img, p.o_kn, p.kn);
+    put(img, p.o_qinfo, p.qinfo);
+    put(img, p.o_qcharge, p.qcharge);
+    put(img, p.o_intra, p.intra);
+  }
   // upload on the caller's stream (the kernels that read the tables follow it
   // there); the host image stays alive until the synchronisation below
   mixts_status st =
@@ -863,6 +935,30 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.dsf_cf = erfc(prm->dsf_alpha * prm->r_cut) / (prm->r_cut * prm->r_cut) +
              d.dsf_g * exp(-prm->dsf_alpha * prm->dsf_alpha * prm->r_cut * prm->r_cut) / prm->r_cut;
   d.dsf_tab = (const double*)(h->ws + p.o_dsf);
+  if (prm->coulomb == 1) {  // Ewald real space: erfc(a r)/r, no shift at r_cut
+    d.dsf_erfc_rc_over_rc = 0.0;
+    d.dsf_cf = 0.0;
+  }
+  d.coulomb = prm->coulomb;
+  d.ew_kmax = prm->ewald_kmax;
+  d.n_kvec = p.n_kvec;
+  d.n_qatoms = p.n_kvec > 0 ? p.n_qatoms : 0;
+  d.n_intra = p.n_intra;
+  d.ew_ke = u.ke;
+  d.ew_const = p.ew_const;
+  d.ew_bg = p.ew_bg;
+  d.ew_inv2a2 = prm->coulomb == 1 ? 1.0 / (2.0 * prm->dsf_alpha * prm->dsf_alpha) : 0.0;
+  if (p.n_kvec > 0) {
+    d.kvec = (const double4_32a*)(h->ws + p.o_kvec);
+    d.kn = (const int4*)(h->ws + p.o_kn);
+    d.qinfo = (const int4*)(h->ws + p.o_qinfo);
+    d.qcharge = (const double*)(h->ws + p.o_qcharge);
+    d.intra = (const int2*)(h->ws + p.o_intra);
+    d.ew_phase = (double2*)(h->ws + p.o_ewphase);
+    d.ew_cen = (double4_32a*)(h->ws + p.o_ewcen);
+    d.ew_S = (double2*)(h->ws + p.o_ews);
+    d.ew_ek = (double*)(h->ws + p.o_ewek);
+  }
   d.full_list = prm->precision == MIXTS_FP32_FORCES ? 1 : 0;
   d.lgPmax_nb = p.n_classes > 0 ? p.cls_log2P[0] : 0;
   d.n_items32 = p.n_nonp << d.lgPmax_nb;
@@ -974,7 +1070,7 @@ static mixts_status eval_forces(mixts_handle h) {
   cudaStream_t s = h->stream;
   h->list_valid = true;
   phase(h, 0, [&] { return launch_nlist(d, s, h->atom_is_pseudo); });
-  phase(h, 1, [&] { return launch_pair(d, s); });
+  phase(h, 1, [&] { return launch_pair(d, s) + launch_ewald(d, s); });
   phase(h, 2, [&] { return launch_bonded(d, s, h->ainfo_atom); });
   phase(h, 3, [&] { return launch_pseudo(d, s); });
   return cuda_check(h, cudaGetLastError(), "force launch");
@@ -1738,6 +1834,7 @@ extern "C" MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int ta, i
   const int nt = p.nt;
   if (ta < 0 || ta >= nt || tb < 0 || tb >= nt || ta == tb || h->d.pseudo[ta] || h->d.pseudo[tb])
     return set_err(h, MIXTS_ERR_ARG, "theta types must be two distinct site types");
+  if (h->d.coulomb != 0) return set_err(h, MIXTS_ERR_ARG, "parameter gradients need the damped-shifted-force Coulomb");
   const double e0 = p.eps[ta * nt + ta];
   if (!(theta[0] > 0.0) || !(theta[2] > 0.0) || !(theta[3] > 0.0) || !(theta[5] > 0.0) ||
       !(e0 > 0.0 ? theta[7] > 0.0 : theta[7] >= 0.0))

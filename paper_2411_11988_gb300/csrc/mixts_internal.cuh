@@ -128,6 +128,18 @@ struct Dev {
   float4* nlB;                 // FP32 path: list rows regrouped by partner type, (bead-0 displacement, tag)
   int* nlseg;                  // FP32 path: [n_nonp][n_types + 1] first entry of each partner type in nlB
   float box_lo;                // box - box_hi (binary32)
+  // long-range electrostatics on centroids (coulomb == 1, see k_ewald.cu)
+  int coulomb, ew_kmax, n_kvec, n_qatoms, n_intra;
+  double ew_ke, ew_const, ew_bg, ew_inv2a2;  // k_e; self + background energy; background; 1/(2 alpha^2)
+  const double4_32a* kvec;     // [n_kvec] half-space wave vectors (kx, ky, kz, W_k)
+  const int4* kn;              // [n_kvec] (nx, ny, nz, 0)
+  const int4* qinfo;           // [n_qatoms] charged sites: (bead-0 row, row stride, P, atom)
+  const double* qcharge;       // [n_qatoms]
+  const int2* intra;           // [n_intra] same-molecule pairs of charged sites (indices into qinfo)
+  double2* ew_phase;           // [n_qatoms][3][ew_kmax + 1] exp(i 2 pi n x / L)
+  double4_32a* ew_cen;         // [n_qatoms] centroids
+  double2* ew_S;               // [n_kvec] structure factors
+  double* ew_ek;               // [n_kvec][2] energy and virial per wave vector
   double mass[MT];
   // sorted classes of non-pseudo atoms (P descending)
   int cls_P[MAX_CLASSES], cls_log2P[MAX_CLASSES], cls_pos0[MAX_CLASSES], cls_n[MAX_CLASSES],
@@ -397,6 +409,7 @@ int launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type);
 int launch_forces_out(const Dev& d, cudaStream_t s);
 void pair_grids(int nt, int nint, int* g64, int* g32);
 int launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out);
+int launch_ewald(const Dev& d, cudaStream_t s);
 
 // propagation modes
 enum : int {

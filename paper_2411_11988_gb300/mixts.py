@@ -51,7 +51,8 @@ class _System(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("T", C.c_double), ("dt", C.c_double), ("tau_centroid", C.c_double),
                 ("pile_lambda", C.c_double), ("r_cut", C.c_double), ("dsf_alpha", C.c_double),
-                ("precision", C.c_int), ("nlist_cap", C.c_int), ("free_ring_substeps", C.c_int)]
+                ("precision", C.c_int), ("nlist_cap", C.c_int), ("free_ring_substeps", C.c_int),
+                ("coulomb", C.c_int), ("ewald_kmax", C.c_int)]
 
 
 class _Tuning(C.Structure):
@@ -166,7 +167,7 @@ class MixTS:
 
     def __init__(self, sysm, T=300.0, dt=0.25, tau=100.0, pile_lambda=1.0, r_cut=9.0, alpha=0.2,
                  precision=FP64, nlist_cap=0, seed=0, device="cuda:0", stream=None, q=None, p=None,
-                 free_ring_substeps=0):
+                 free_ring_substeps=0, coulomb=0, ewald_kmax=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("MixTS needs a CUDA device")
@@ -183,7 +184,7 @@ class MixTS:
             self.p = torch.from_numpy(p0.copy()).to(self.device)
             self.f = torch.zeros_like(self.q)
         self.params = _Params(float(T), float(dt), float(tau), float(pile_lambda), float(r_cut), float(alpha),
-                              int(precision), int(nlist_cap), int(free_ring_substeps))
+                              int(precision), int(nlist_cap), int(free_ring_substeps), int(coulomb), int(ewald_kmax))
         s, keep = pack_system(sysm, self.q.data_ptr(), self.p.data_ptr(), self.f.data_ptr(), seed)
         nbytes = L.mixts_workspace_size(C.byref(s), 1, C.byref(self.params))
         if nbytes == 0:
@@ -390,7 +391,8 @@ class MixTSBatch:
     """
 
     def __init__(self, systems, T=300.0, dt=0.25, tau=100.0, pile_lambda=1.0, r_cut=9.0, alpha=0.2,
-                 precision=FP64, nlist_cap=0, seeds=None, device="cuda:0", stream=None, free_ring_substeps=0):
+                 precision=FP64, nlist_cap=0, seeds=None, device="cuda:0", stream=None, free_ring_substeps=0,
+                 coulomb=0, ewald_kmax=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("MixTSBatch needs a CUDA device")
@@ -419,7 +421,7 @@ class MixTSBatch:
         arr = (_System * n)(*structs)
         self.n = n
         self.params = _Params(float(T), float(dt), float(tau), float(pile_lambda), float(r_cut), float(alpha),
-                              int(precision), int(nlist_cap), int(free_ring_substeps))
+                              int(precision), int(nlist_cap), int(free_ring_substeps), int(coulomb), int(ewald_kmax))
         nbytes = L.mixts_workspace_size(arr, n, C.byref(self.params))
         if nbytes == 0:
             raise MixtsError(1, "mixts_workspace_size rejected the batch")
