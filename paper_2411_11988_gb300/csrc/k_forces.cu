@@ -605,13 +605,15 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
 // & Stegun, Handbook of Mathematical Functions, eq. 7.1.26 (|error| <=
 // 1.5e-7), with the exact Gaussian in the force.
 // ---------------------------------------------------------------------------
+constexpr int LG_P32_ENTRIES = 8;  // at most 256 entries per item (staged in shared memory)
+
 // log2 of the entries of one FP32 item: 2^LG_P32_TERMS terms = entries x
 // (owner beads of the block) x (fine slices per owner bead)
 __device__ __forceinline__ int p32_lg_entries(int lgPi, int lgPt) {
   const int lgPp = lgPi < 5 ? lgPi : 5;
   const int lgS = lgPi > lgPt ? lgPi : lgPt;
   const int lgE = LG_P32_TERMS - lgPp - (lgS - lgPi);
-  return lgE > 0 ? lgE : 0;
+  return lgE > 0 ? (lgE < LG_P32_ENTRIES ? lgE : LG_P32_ENTRIES) : 0;
 }
 
 __global__ void __launch_bounds__(NL_THREADS) k_list_seg32(Dev d) {
@@ -692,74 +694,106 @@ __global__ void __launch_bounds__(NL_THREADS) k_list_seg32(Dev d) {
   }
 }
 
-// The terms of one lane over its group's entries [e_begin, e_end) with
-// stride estep: each entry's record and its first partner bead are loaded one
-// entry ahead of their use (two-stage software pipeline), so the dependent
-// load chain (entry record -> partner bead) overlaps the previous entry's
-// arithmetic.
+// Parameters of one FP32 item (one owner type x partner type pair).
+struct P32Par {
+  float qq, e4, s2, vrc, dvrc, rc, rc2, pa, nl2e, g2a, cf, c0;
+};
+
+// One term: displacement d = (x_j - x_i), weight applied later. Skipped as a
+// whole when no lane of the warp is inside the cut-off (entries listed
+// within r_cut + 2 d_max but beyond r_cut); otherwise evaluated without
+// branches and masked.
 template <bool LJ>
-__device__ __forceinline__ void pair32_entries(const float4* __restrict__ lst, int e_begin, int e_end, int estep,
-                                               int lgr, int sh_t, const float4* __restrict__ Xd, int b, float4 di,
-                                               float qq, float e4, float s2, float vrc, float dvrc, float rc,
-                                               float rc2, float alpha, float alpha2, float g2a, float cf, float c0,
+__device__ __forceinline__ void pair32_term(const P32Par& c, float dx, float dy, float dz, float& fx, float& fy,
+                                            float& fz, float& ec, float& elj, float& vir, int& nev) {
+  // erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x)
+  const float a1 = 0.254829592f, a2 = -0.284496736f, a3 = 1.421413741f, a4 = -1.453152027f, a5 = 1.061405429f;
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  const bool in = r2 < c.rc2;
+  if (!__any_sync(0xffffffffu, in)) return;
+  const float rs = in ? r2 : c.rc2;  // finite arithmetic on masked lanes
+  const float rinv = rsqrtf(rs);
+  const float r = rs * rinv;
+  const float t = __fdividef(1.0f, fmaf(c.pa, r, 1.0f));
+  float ex;  // exp(-a^2 r^2), argument in [-a^2 rc^2, 0]
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(c.nl2e * rs));
+  const float pl = fmaf(fmaf(fmaf(fmaf(a5, t, a4), t, a3), t, a2), t, a1) * t;
+  const float erc = pl * ex;
+  float et = c.qq * fmaf(erc, rinv, fmaf(c.cf, r - c.rc, -c.c0));
+  float fr = c.qq * (fmaf(erc * rinv, rinv, fmaf(c.g2a * ex, rinv, -c.cf)) * rinv);
+  float lt = 0.0f;
+  if (LJ) {
+    const float rinv2 = rinv * rinv;
+    const float sr2 = c.s2 * rinv2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
+    lt = c.e4 * (sr12 - sr6) - c.vrc - (r - c.rc) * c.dvrc;
+    fr += (6.0f * c.e4 * (2.0f * sr12 - sr6) * rinv + c.dvrc) * rinv;
+  }
+  fr = in ? fr : 0.0f;
+  // force on i is minus the force on j along d = x_j - x_i
+  fx = fmaf(-fr, dx, fx);
+  fy = fmaf(-fr, dy, fy);
+  fz = fmaf(-fr, dz, fz);
+  vir = fmaf(fr, r2, vir);
+  ec += in ? et : 0.0f;
+  if (LJ) elj += in ? lt : 0.0f;
+  nev += in ? 1 : 0;
+}
+
+// The terms of one lane over its group's entries: local indices grp, grp +
+// G, ... below n of the item's entries staged in shared memory (buf), all
+// groups running the same number of rounds (the skip test is warp-wide).
+// R1: one fine slice per owner bead (partner not finer); the next round's
+// partner bead is loaded before this round's arithmetic. Otherwise each
+// entry's 2^lgr slices of the lane's bead.
+template <bool LJ, bool R1>
+__device__ __forceinline__ void pair32_entries(const float4* buf, int n, int grp, int G, int lgr, int sh_t,
+                                               const float4* __restrict__ Xd, int b, float4 di, const P32Par& c,
                                                float& fx, float& fy, float& fz, float& ec, float& elj, float& vir,
                                                int& nev) {
-  // erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x)
-  const float ap = 0.3275911f, a1 = 0.254829592f, a2 = -0.284496736f, a3 = 1.421413741f, a4 = -1.453152027f,
-              a5 = 1.061405429f;
-  const float nl2e = -alpha2 * 1.4426950408889634f;
-  const float pa = ap * alpha;
   const int s0 = b << lgr;  // first fine slice of this lane's owner bead
-  if (e_begin >= e_end) return;
-  float4 B = __ldg(lst + e_begin);
-  float4 dj0 = __ldg(Xd + (__float_as_int(B.w) >> 4) + (s0 >> sh_t));
-  int en = e_begin + estep;
-  float4 Bn = en < e_end ? __ldg(lst + en) : B;
-  for (int e = e_begin; e < e_end; e += estep) {
-    // stage ahead: the next entry's first partner bead, the entry after it
-    const float4 djn = __ldg(Xd + (__float_as_int(Bn.w) >> 4) + (s0 >> sh_t));
-    const int enn = en + estep;
-    const float4 Bnn = enn < e_end ? __ldg(lst + enn) : Bn;
-    const int abase = __float_as_int(B.w) >> 4;
-    const float bx = B.x - di.x, by = B.y - di.y, bz = B.z - di.z;
-#pragma unroll 2
-    for (int k = 0; k < (1 << lgr); ++k) {
-      const float4 dj = k == 0 ? dj0 : __ldg(Xd + abase + ((s0 + k) >> sh_t));
-      const float dx = bx + dj.x, dy = by + dj.y, dz = bz + dj.z;
-      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-      if (r2 < rc2) {
-        const float rinv = rsqrtf(r2);
-        const float r = r2 * rinv;
-        const float t = __fdividef(1.0f, fmaf(pa, r, 1.0f));
-        float ex;  // exp(-a^2 r^2), argument in [-a^2 rc^2, 0]
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(nl2e * r2));
-        const float pl = fmaf(fmaf(fmaf(fmaf(a5, t, a4), t, a3), t, a2), t, a1) * t;
-        const float erc = pl * ex;
-        ec = fmaf(qq, fmaf(erc, rinv, fmaf(cf, r - rc, -c0)), ec);
-        float fr = qq * (fmaf(erc * rinv, rinv, fmaf(g2a * ex, rinv, -cf)) * rinv);
-        if (LJ) {
-          const float rinv2 = rinv * rinv;
-          const float sr2 = s2 * rinv2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
-          elj += e4 * (sr12 - sr6) - vrc - (r - rc) * dvrc;
-          fr += (6.0f * e4 * (2.0f * sr12 - sr6) * rinv + dvrc) * rinv;
-        }
-        // force on i is minus the force on j along d = x_j - x_i
-        fx = fmaf(-fr, dx, fx);
-        fy = fmaf(-fr, dy, fy);
-        fz = fmaf(-fr, dz, fz);
-        vir = fmaf(fr, r2, vir);
-        ++nev;
+  const float4 far = make_float4(0.f, 0.f, 1e4f, 0.f);  // a partner far outside the cut-off
+  const int rounds = (n + G - 1) / G;
+  if (R1) {
+    // two entries per round (l, l + G), the next round's two loaded ahead
+    const int sj = s0 >> sh_t;
+    const int G2 = 2 * G;
+    int l = grp;
+    float4 Ba = l < n ? buf[l] : far, Bb = l + G < n ? buf[l + G] : far;
+    float4 da = l < n ? __ldg(Xd + (__float_as_int(Ba.w) >> 4) + sj) : far;
+    float4 db = l + G < n ? __ldg(Xd + (__float_as_int(Bb.w) >> 4) + sj) : far;
+    for (int r = 0; r < rounds; r += 2) {
+      const int ln = l + G2;
+      const float4 Bna = ln < n ? buf[ln] : far, Bnb = ln + G < n ? buf[ln + G] : far;
+      const float4 dna = ln < n ? __ldg(Xd + (__float_as_int(Bna.w) >> 4) + sj) : far;
+      const float4 dnb = ln + G < n ? __ldg(Xd + (__float_as_int(Bnb.w) >> 4) + sj) : far;
+      pair32_term<LJ>(c, (Ba.x - di.x) + da.x, (Ba.y - di.y) + da.y, (Ba.z - di.z) + da.z, fx, fy, fz, ec, elj, vir,
+                      nev);
+      pair32_term<LJ>(c, (Bb.x - di.x) + db.x, (Bb.y - di.y) + db.y, (Bb.z - di.z) + db.z, fx, fy, fz, ec, elj, vir,
+                      nev);
+      Ba = Bna;
+      Bb = Bnb;
+      da = dna;
+      db = dnb;
+      l = ln;
+    }
+  } else {
+    for (int r = 0, l = grp; r < rounds; ++r, l += G) {
+      const bool v = l < n;
+      const float4 B = v ? buf[l] : far;
+      const int abase = __float_as_int(B.w) >> 4;
+      const float bx = B.x - di.x, by = B.y - di.y, bz = B.z - di.z;
+#pragma unroll 4
+      for (int k = 0; k < (1 << lgr); ++k) {
+        const float4 dj = v ? __ldg(Xd + abase + ((s0 + k) >> sh_t)) : far;
+        pair32_term<LJ>(c, bx + dj.x, by + dj.y, bz + dj.z, fx, fy, fz, ec, elj, vir, nev);
       }
     }
-    B = Bn;
-    dj0 = djn;
-    Bn = Bnn;
-    en = enn;
   }
 }
 
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
   __shared__ float qqt[MT * MT], e4t[MT * MT], s2t[MT * MT], vrct[MT * MT], dvrct[MT * MT];
+  __shared__ float4 stage[PAIR_THREADS / 32][1 << LG_P32_ENTRIES];  // each warp's current item entries
   __shared__ int tLg[MT], tOff[MT];
   const int nt = d.n_types;
   for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
@@ -801,17 +835,43 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
     const int oi = tOff[ai.type];
     const float4 di = d.Xd[oi + ((ai.row0 - oi) << lgPi) + b];
     const int k = ai.type * nt + t;
-    const float qq = qqt[k], e4 = e4t[k];
+    P32Par c;
+    c.qq = qqt[k];
+    c.e4 = e4t[k];
+    c.s2 = s2t[k];
+    c.vrc = vrct[k];
+    c.dvrc = dvrct[k];
+    c.rc = rc;
+    c.rc2 = rc2;
+    c.pa = 0.3275911f * alpha;
+    c.nl2e = -alpha2 * 1.4426950408889634f;
+    c.g2a = g2a;
+    c.cf = cf;
+    c.c0 = c0;
     const float wgt = __int_as_float((127 - lgS) << 23);  // 1/P*
     float fx = 0.f, fy = 0.f, fz = 0.f, ec = 0.f, elj = 0.f, vir = 0.f;
     int nev = 0;
-    const float4* lst = d.nlB + (size_t)i * d.nl_cap;
-    if (e4 != 0.f)
-      pair32_entries<true>(lst, e0 + grp, e1, 1 << lgG, lgr, lgS - lgPt, d.Xd, b, di, qq, e4, s2t[k], vrct[k],
-                           dvrct[k], rc, rc2, alpha, alpha2, g2a, cf, c0, fx, fy, fz, ec, elj, vir, nev);
-    else
-      pair32_entries<false>(lst, e0 + grp, e1, 1 << lgG, lgr, lgS - lgPt, d.Xd, b, di, qq, 0.f, 1.f, 0.f, 0.f, rc,
-                            rc2, alpha, alpha2, g2a, cf, c0, fx, fy, fz, ec, elj, vir, nev);
+    const int sh_t = lgS - lgPt;
+    // stage the item's entries (<= 256, one coalesced copy), then walk them
+    float4* buf = stage[threadIdx.x >> 5];
+    const float4* lst = d.nlB + (size_t)i * d.nl_cap + e0;
+    const int n = e1 - e0;
+    for (int x = lane; x < n; x += 32) buf[x] = __ldg(lst + x);
+    __syncwarp();
+    const int G = 1 << lgG;
+    if (c.e4 != 0.f) {
+      if (lgr == 0)
+        pair32_entries<true, true>(buf, n, grp, G, 0, sh_t, d.Xd, b, di, c, fx, fy, fz, ec, elj, vir, nev);
+      else
+        pair32_entries<true, false>(buf, n, grp, G, lgr, sh_t, d.Xd, b, di, c, fx, fy, fz, ec, elj, vir, nev);
+    } else {
+      if (lgr == 0)
+        pair32_entries<false, true>(buf, n, grp, G, 0, sh_t, d.Xd, b, di, c, fx, fy, fz, ec, elj, vir, nev);
+      else
+        pair32_entries<false, false>(buf, n, grp, G, lgr, sh_t, d.Xd, b, di, c, fx, fy, fz, ec, elj, vir, nev);
+    }
+    __syncwarp();  // the buffer is refilled by the next item
+    const float e4 = c.e4;
     // lane partials (times 1/P*) to fixed point by bit assembly, then exact
     // integer sums over the groups, which hold the same owner beads
     int bad = 0;
