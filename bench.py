@@ -261,6 +261,7 @@ def batch_variant(torch, stream, flush, dev, steps):
     flops = sum((e["n_evals"] - e["n_lj_evals"]) * FLOPS32_PAIR + e["n_lj_evals"] * (FLOPS32_PAIR + FLOPS32_LJ_EXTRA)
                 for e in est)
     return {"workload": BATCH["workload"], "draws": [list(d) for d in draws],
+            "gpu_launches_per_step": (k1 - k0) / steps,
             "total_beads": int(sum(x.n_beads for x in systems)),
             "ns_per_day_aggregate": len(systems) * ns_per_day(ms), "ms_per_step": ms, "steps": steps,
             "bead_pair_evals_per_step": evals, "bead_pair_evals_per_s": evals * 1000.0 / ms,

@@ -143,11 +143,15 @@ typedef struct {
 typedef struct {
   double grid_scale;    /* persistent force-kernel CTAs of all members together, in SM-filling grids,
                            shared out by each member's share of the force work */
-  int streams;          /* parallel branches of the captured step graph */
+  int streams;          /* parallel branches of the captured step graph (per-member launches only) */
   int nl_cpl;           /* neighbour-list candidates per lane of one list warp */
   int steps_per_launch; /* steps captured in one graph launch */
   double ms_per_step;   /* measured for this shape (whole batch, one step) */
   int candidates;       /* shapes the tuner timed */
+  int persistent;       /* 1: every kernel of a step serves all members in one launch (one launch per
+                           phase); 0: per-member kernels on parallel graph branches. Systems with a
+                           pseudo particle, a type of more than 64 beads or coulomb = 1 always use 0 */
+  int item_lg_terms;    /* FP32 pair sweep: log2 of the bead-pair terms of one work item (tile size) */
 } mixts_batch_tuning;
 
 /* Bytes of device workspace mixts_init needs for these systems. */
@@ -164,8 +168,14 @@ MIXTS_API size_t mixts_workspace_size(const mixts_system* sys, int n_sys, const 
  * per-system queries (mixts_nlist, mixts_gaussians, mixts_potential_grad)
  * take a member handle from mixts_batch_member. A batched mixts_step of at
  * least steps_per_launch steps runs as CUDA graph launches, each advancing
- * every member by steps_per_launch steps; trajectories are bit-identical to
- * stepping each system alone. */
+ * every member by steps_per_launch steps. When every member allows it (no
+ * pseudo particle, no type of more than 64 beads, coulomb = 0) each kernel of
+ * a step is launched once for all members (a block finds its member from a
+ * prefix of the members' block counts); otherwise the members' own kernels
+ * run on parallel graph branches. Trajectories are bit-identical to stepping
+ * each system alone (with FP32 forces, while the work-item size is the
+ * single-system default of 2^10 terms: another size regroups the binary32
+ * partial sums). */
 MIXTS_API mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* prm, void* workspace,
                         size_t ws_bytes, void* stream, mixts_handle* out);
 
@@ -308,9 +318,10 @@ MIXTS_API mixts_status mixts_vacf_accumulate(mixts_handle h, int type, int n_lag
 MIXTS_API mixts_status mixts_batch_member(mixts_handle h, int i, mixts_handle* member);
 
 /* Autotune the launch shapes of a batched handle: time captured graphs of
- * candidate shapes (branch count x force-grid scale, then list candidates
- * per warp) on the live systems, keep the fastest, capture steps_per_launch
- * steps with it. The trial steps are undone (state saved and restored), so
+ * candidate shapes on the live systems (one launch per phase: force-grid
+ * scale x FP32 work-item size, then list candidates per warp; per-member
+ * launches: branch count x force-grid scale), keep the fastest, capture
+ * steps_per_launch steps with it. The trial steps are undone (state saved and restored), so
  * the trajectory is unchanged. Synchronises. out (may be NULL) gets the shape. */
 MIXTS_API mixts_status mixts_batch_tune(mixts_handle h, int steps_per_launch, mixts_batch_tuning* out);
 

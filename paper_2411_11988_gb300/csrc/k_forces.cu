@@ -88,10 +88,11 @@ constexpr int NL_THREADS = 256;
 // Once per list build: d_max of sites and of pseudo particles, the two list
 // radii (binary64, in the order the definition states), and cleared row
 // counters. thresh: [0] d_max, [1] R, [2] d_max pseudo, [3] R pseudo.
-__global__ void k_list_prep(Dev d, const int* atom_is_pseudo) {
+__device__ __forceinline__ void b_k_list_prep(const Dev& d, int bx) {
+  (void)bx;
   __shared__ long long red[32];
-  const double ds = reduce_spread_kind(d, atom_is_pseudo, 0, red);
-  const double dp = reduce_spread_kind(d, atom_is_pseudo, 1, red);
+  const double ds = reduce_spread_kind(d, d.atom_is_pseudo, 0, red);
+  const double dp = reduce_spread_kind(d, d.atom_is_pseudo, 1, red);
   for (int i = threadIdx.x; i < d.n_nonp; i += blockDim.x) d.nl_cnt[i] = 0;
   for (int i = threadIdx.x; i < d.n_pseudo; i += blockDim.x) d.pl_cnt[i] = 0;
   if (threadIdx.x < 2) d.pctr[threadIdx.x] = 0;  // pair items of the new list, and their hand-out counter
@@ -118,11 +119,19 @@ __global__ void k_list_prep(Dev d, const int* atom_is_pseudo) {
   }
 }
 
+__global__ void k_list_prep(const __grid_constant__ Dev d) { b_k_list_prep(d, blockIdx.x); }
+
+__global__ void k_list_prep_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
+  MX_BATCH_ENTER();
+  b_k_list_prep(d, bx);
+}
+
 // One warp per (owner row, chunk of 32 * nl_cpl candidates); entries are
 // appended with a per-row counter, so the row order is arbitrary.
-__global__ void __launch_bounds__(NL_THREADS) k_nlist(Dev d, int nchunk) {
+__device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
   const int lane = threadIdx.x & 31;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int w = (bx * blockDim.x + threadIdx.x) >> 5;
+  const int nchunk = (d.n_nonp + 32 * d.nl_cpl - 1) / (32 * d.nl_cpl);
   const int i = w / nchunk;
   const int chunk = w - i * nchunk;
   if (i >= d.n_nonp) return;
@@ -223,6 +232,13 @@ __global__ void __launch_bounds__(NL_THREADS) k_nlist(Dev d, int nchunk) {
         atomicOr(d.err, ERR_NLIST);
     }
   }
+}
+
+__global__ void __launch_bounds__(NL_THREADS) k_nlist(const __grid_constant__ Dev d) { b_k_nlist(d, blockIdx.x); }
+
+__global__ void __launch_bounds__(NL_THREADS) k_nlist_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
+  MX_BATCH_ENTER();
+  b_k_nlist(d, bx);
 }
 
 // pseudo-particle site list: one thread per (pseudo atom, site position)
@@ -354,11 +370,11 @@ __device__ __forceinline__ void dsf_direct(const Dev& d, double s, double* g, do
 // range of the item array (the counter was cleared with the list) and writes
 // its rows' items in row order.
 constexpr int ITEM_THREADS = 1024;
-__global__ void __launch_bounds__(ITEM_THREADS) k_pair_items(Dev d) {
+__device__ __forceinline__ void b_k_pair_items(const Dev& d, int bx) {
   __shared__ int wsum[ITEM_THREADS / 32];
   __shared__ int base;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int i = blockIdx.x * ITEM_THREADS + tid;
+  const int i = bx * ITEM_THREADS + tid;
   int n = 0, nch = 0, lgsb = 0;
   if (i < d.n_nonp) {
     const int cnt = min(d.nl_cnt[i], d.nl_cap);
@@ -395,7 +411,15 @@ __global__ void __launch_bounds__(ITEM_THREADS) k_pair_items(Dev d) {
   }
 }
 
-__global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
+__global__ void __launch_bounds__(ITEM_THREADS) k_pair_items(const __grid_constant__ Dev d) { b_k_pair_items(d, blockIdx.x); }
+
+__global__ void __launch_bounds__(ITEM_THREADS) k_pair_items_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
+  MX_BATCH_ENTER();
+  b_k_pair_items(d, bx);
+}
+
+__device__ __forceinline__ void b_k_pair64(const Dev& d, int bx) {
+  (void)bx;
   extern __shared__ double dtab[];  // DSF interval table: 6 doubles, then 8 floats per interval
   __shared__ PairPar tab[MT * MT];
   __shared__ int flg[MT * MT];      // bit 0: Coulomb, bit 1: Lennard-Jones
@@ -580,6 +604,13 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
   }
 }
 
+__global__ void __launch_bounds__(PAIR_THREADS) k_pair64(const __grid_constant__ Dev d) { b_k_pair64(d, blockIdx.x); }
+
+__global__ void __launch_bounds__(PAIR_THREADS) k_pair64_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
+  MX_BATCH_ENTER();
+  b_k_pair64(d, bx);
+}
+
 // ---------------------------------------------------------------------------
 // nonbonded pair sweep, FP32 forces (precision MIXTS_FP32_FORCES).
 //
@@ -607,18 +638,18 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair64(Dev d) {
 // ---------------------------------------------------------------------------
 constexpr int LG_P32_ENTRIES = 8;  // at most 256 entries per item (staged in shared memory)
 
-// log2 of the entries of one FP32 item: 2^LG_P32_TERMS terms = entries x
+// log2 of the entries of one FP32 item: 2^lgt terms = entries x
 // (owner beads of the block) x (fine slices per owner bead)
-__device__ __forceinline__ int p32_lg_entries(int lgPi, int lgPt) {
+__device__ __forceinline__ int p32_lg_entries(int lgPi, int lgPt, int lgt) {
   const int lgPp = lgPi < 5 ? lgPi : 5;
   const int lgS = lgPi > lgPt ? lgPi : lgPt;
-  const int lgE = LG_P32_TERMS - lgPp - (lgS - lgPi);
+  const int lgE = lgt - lgPp - (lgS - lgPi);
   return lgE > 0 ? (lgE < LG_P32_ENTRIES ? lgE : LG_P32_ENTRIES) : 0;
 }
 
-__global__ void __launch_bounds__(NL_THREADS) k_list_seg32(Dev d) {
+__device__ __forceinline__ void b_k_list_seg32(const Dev& d, int bx) {
   const int lane = threadIdx.x & 31;
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int i = (bx * blockDim.x + threadIdx.x) >> 5;
   if (i >= d.n_nonp) return;
   const int nt = d.n_types;
   const int cnt = min(d.nl_cnt[i], d.nl_cap);
@@ -641,13 +672,13 @@ __global__ void __launch_bounds__(NL_THREADS) k_list_seg32(Dev d) {
   }
   int next = incl - c_mine;  // lane u: next slot of type u
   if (lane <= nt) d.nlseg[(size_t)i * (nt + 1) + lane] = lane < nt ? next : cnt;
-  // this row's work items, (partner type, slice block, chunk) of ~2^LG_P32_TERMS
+  // this row's work items, (partner type, slice block, chunk) of ~2^p32_lgt
   // terms each, in a range of the item array reserved with one atomic
   {
     const int lgP = d.ainfo[i].log2P;
     const int lgsb = lgP > 5 ? lgP - 5 : 0;
-    const int nch = lane < nt ? (c_mine + (1 << p32_lg_entries(lgP, d.log2P[lane])) - 1) >>
-                                    p32_lg_entries(lgP, d.log2P[lane])
+    const int nch = lane < nt ? (c_mine + (1 << p32_lg_entries(lgP, d.log2P[lane], d.p32_lgt)) - 1) >>
+                                    p32_lg_entries(lgP, d.log2P[lane], d.p32_lgt)
                               : 0;
     const int n = nch << lgsb;
     int ni = n;
@@ -692,6 +723,13 @@ __global__ void __launch_bounds__(NL_THREADS) k_list_seg32(Dev d) {
       out[dest] = make_float4(bx, by, bz, __int_as_float((abase << 4) | t));
     }
   }
+}
+
+__global__ void __launch_bounds__(NL_THREADS) k_list_seg32(const __grid_constant__ Dev d) { b_k_list_seg32(d, blockIdx.x); }
+
+__global__ void __launch_bounds__(NL_THREADS) k_list_seg32_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
+  MX_BATCH_ENTER();
+  b_k_list_seg32(d, bx);
 }
 
 // Parameters of one FP32 item (one owner type x partner type pair).
@@ -791,7 +829,8 @@ __device__ __forceinline__ void pair32_entries(const float4* buf, int n, int grp
   }
 }
 
-__global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
+__device__ __forceinline__ void b_k_pair32(const Dev& d, int bx) {
+  (void)bx;
   __shared__ float qqt[MT * MT], e4t[MT * MT], s2t[MT * MT], vrct[MT * MT], dvrct[MT * MT];
   __shared__ float4 stage[PAIR_THREADS / 32][1 << LG_P32_ENTRIES];  // each warp's current item entries
   __shared__ int tLg[MT], tOff[MT];
@@ -830,7 +869,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
     const int sl = lane & ((1 << lgPp) - 1), grp = lane >> lgPp;
     const int b = (sb << lgPp) + sl;  // owner bead of this lane
     const int* seg = d.nlseg + (size_t)i * (nt + 1);
-    const int E = 1 << p32_lg_entries(lgPi, lgPt);
+    const int E = 1 << p32_lg_entries(lgPi, lgPt, d.p32_lgt);
     const int e0 = seg[t] + ch * E, e1 = min(seg[t + 1], e0 + E);
     const int oi = tOff[ai.type];
     const float4 di = d.Xd[oi + ((ai.row0 - oi) << lgPi) + b];
@@ -912,6 +951,13 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(Dev d) {
   }
 }
 
+__global__ void __launch_bounds__(PAIR_THREADS) k_pair32(const __grid_constant__ Dev d) { b_k_pair32(d, blockIdx.x); }
+
+__global__ void __launch_bounds__(PAIR_THREADS) k_pair32_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
+  MX_BATCH_ENTER();
+  b_k_pair32(d, bx);
+}
+
 // ---------------------------------------------------------------------------
 // bonded terms: one thread per (term, fine slice)
 // ---------------------------------------------------------------------------
@@ -922,8 +968,8 @@ __device__ __forceinline__ void fadd3w(unsigned long long* F, int row, double fx
   atomicAdd(r + 2, (unsigned long long)fix44(fz, 0, bad));
 }
 
-__global__ void __launch_bounds__(64) k_bonded(Dev d, const AtomInfo* ainfo_atom) {
-  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_k_bonded(const Dev& d, int bx) {
+  const int it = bx * blockDim.x + threadIdx.x;
   double eb = 0.0, ea = 0.0, vir = 0.0;
   int bad = 0;
   if (it < d.n_bitems) {
@@ -931,7 +977,7 @@ __global__ void __launch_bounds__(64) k_bonded(Dev d, const AtomInfo* ainfo_atom
     const int s = bi.slice;
     if (bi.kind == 0) {
       const int a = d.bond_atoms[2 * bi.term], c = d.bond_atoms[2 * bi.term + 1];
-      const AtomInfo A = ainfo_atom[a], Cc = ainfo_atom[c];
+      const AtomInfo A = d.ainfo_atom[a], Cc = d.ainfo_atom[c];
       const int lmax = A.log2P > Cc.log2P ? A.log2P : Cc.log2P;
       const double w = 1.0 / (double)(1 << lmax);
       const int ra = A.row0 + (s >> (lmax - A.log2P)) * A.stride;
@@ -951,7 +997,7 @@ __global__ void __launch_bounds__(64) k_bonded(Dev d, const AtomInfo* ainfo_atom
       fadd3w(d.F_fix, ra, -f * dx, -f * dy, -f * dz, &bad);
     } else {
       const int a1 = d.ang_atoms[3 * bi.term], o = d.ang_atoms[3 * bi.term + 1], a2 = d.ang_atoms[3 * bi.term + 2];
-      const AtomInfo A1 = ainfo_atom[a1], O = ainfo_atom[o], A2 = ainfo_atom[a2];
+      const AtomInfo A1 = d.ainfo_atom[a1], O = d.ainfo_atom[o], A2 = d.ainfo_atom[a2];
       int lmax = A1.log2P > O.log2P ? A1.log2P : O.log2P;
       lmax = lmax > A2.log2P ? lmax : A2.log2P;
       const double w = 1.0 / (double)(1 << lmax);
@@ -996,6 +1042,13 @@ __global__ void __launch_bounds__(64) k_bonded(Dev d, const AtomInfo* ainfo_atom
     eadd(d.E_fix, E_ANGLE, ea);
     eadd(d.E_fix, E_VIRIAL, vir);
   }
+}
+
+__global__ void __launch_bounds__(64) k_bonded(const __grid_constant__ Dev d) { b_k_bonded(d, blockIdx.x); }
+
+__global__ void __launch_bounds__(64) k_bonded_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
+  MX_BATCH_ENTER();
+  b_k_bonded(d, bx);
 }
 
 // ---------------------------------------------------------------------------
@@ -1227,12 +1280,13 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo32(Dev d) {
 // ---------------------------------------------------------------------------
 int launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo) {
   int n = 1;
-  k_list_prep<<<1, 1024, 0, s>>>(d, atom_is_pseudo);
+  (void)atom_is_pseudo;  // carried in d
+  k_list_prep<<<1, 1024, 0, s>>>(d);
   if (d.n_nonp > 0) {
     const int nchunk = (d.n_nonp + 32 * d.nl_cpl - 1) / (32 * d.nl_cpl);
     const long long warps = (long long)d.n_nonp * nchunk;
     const int wpb = NL_THREADS / 32;
-    k_nlist<<<(int)((warps + wpb - 1) / wpb), NL_THREADS, 0, s>>>(d, nchunk);
+    k_nlist<<<(int)((warps + wpb - 1) / wpb), NL_THREADS, 0, s>>>(d);
     ++n;
   }
   if (d.n_pseudo > 0 && d.n_nonp > 0) {
@@ -1280,8 +1334,66 @@ int launch_pair(const Dev& d, cudaStream_t s) {
 
 int launch_bonded(const Dev& d, cudaStream_t s, const AtomInfo* ainfo_atom) {
   if (d.n_bitems == 0) return 0;
-  k_bonded<<<(d.n_bitems + 63) / 64, 64, 0, s>>>(d, ainfo_atom);
+  (void)ainfo_atom;  // carried in d
+  k_bonded<<<(d.n_bitems + 63) / 64, 64, 0, s>>>(d);
   return 1;
+}
+
+// blocks of each batched kernel for one member: the single-system launch shapes
+void batch_block_counts(const Dev& d, int* c) {
+  for (int k = 0; k < BK_KINDS; ++k) c[k] = 0;
+  const int wpb = PAIR_THREADS / 32;
+  c[BK_PREP] = 1;
+  if (d.n_nonp > 0) {
+    const int nchunk = (d.n_nonp + 32 * d.nl_cpl - 1) / (32 * d.nl_cpl);
+    c[BK_NLIST] = (int)(((long long)d.n_nonp * nchunk + NL_THREADS / 32 - 1) / (NL_THREADS / 32));
+    if (d.precision == MIXTS_FP32_FORCES) {
+      c[BK_PAIRA] = (d.n_nonp + wpb - 1) / wpb;
+      c[BK_PAIRB] = d.pair32_grid;
+    } else {
+      const int nsbm = d.lgPmax_nb > 5 ? 1 << (d.lgPmax_nb - 5) : 1;
+      const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;
+      c[BK_PAIRA] = (d.n_nonp + ITEM_THREADS - 1) / ITEM_THREADS;
+      c[BK_PAIRB] = (int)std::min<long long>((items + wpb - 1) / wpb, d.pair_grid);
+    }
+  }
+  c[BK_BONDED] = (d.n_bitems + 63) / 64;
+  c[BK_PROP] = d.n_tiles;
+  c[BK_FINAL] = 1;
+}
+
+// neighbour lists, pair sweep and bonded terms of every member of a batch,
+// one launch per kernel
+int launch_forces_batched(const BatchGeom& g, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_pair64_b, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
+  const int r = g.nm + 1;
+  int n = 0;
+  auto pf = [&](int k) { return g.pfx + k * r; };
+  k_list_prep_b<<<g.blocks[BK_PREP], 1024, 0, s>>>(g.devs, pf(BK_PREP), g.nm);
+  ++n;
+  if (g.blocks[BK_NLIST] > 0) {
+    k_nlist_b<<<g.blocks[BK_NLIST], NL_THREADS, 0, s>>>(g.devs, pf(BK_NLIST), g.nm);
+    ++n;
+  }
+  if (g.blocks[BK_PAIRA] > 0) {
+    if (g.precision == MIXTS_FP32_FORCES) {
+      k_list_seg32_b<<<g.blocks[BK_PAIRA], NL_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
+      k_pair32_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, 0, s>>>(g.devs, pf(BK_PAIRB), g.nm);
+    } else {
+      k_pair_items_b<<<g.blocks[BK_PAIRA], ITEM_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
+      k_pair64_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
+    }
+    n += 2;
+  }
+  if (g.blocks[BK_BONDED] > 0) {
+    k_bonded_b<<<g.blocks[BK_BONDED], 64, 0, s>>>(g.devs, pf(BK_BONDED), g.nm);
+    ++n;
+  }
+  return n;
 }
 
 int launch_pseudo(const Dev& d, cudaStream_t s) {

@@ -91,12 +91,12 @@ __device__ __forceinline__ double bead_dist(double dx, double dy, double dz) { r
 // ---------------------------------------------------------------------------
 // small-P fused tile kernel
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(PROP_THREADS) k_prop_small(Dev d, int mode) {
+__device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
   extern __shared__ double sm[];
   __shared__ double red[(PROP_THREADS / 32) * NPART];
   __shared__ long long s_step;
   __shared__ long long s_d2[128];
-  const PropTile tl = d.tiles[blockIdx.x];
+  const PropTile tl = d.tiles[bx];
   const int t = tl.type, P = d.P[t], N = d.N[t], k0 = tl.k0, na = tl.na;
   const int C = 3 * na;
   const int PC = P * C;
@@ -259,6 +259,13 @@ __global__ void __launch_bounds__(PROP_THREADS) k_prop_small(Dev d, int mode) {
     if (tid == 0)
       for (int i = 0; i < NPART; ++i) d.parts[(size_t)tl.slot * NPART + i] = red[i];
   }
+}
+
+__global__ void __launch_bounds__(PROP_THREADS) k_prop_small(const __grid_constant__ Dev d, int mode) { b_k_prop_small(d, blockIdx.x, mode); }
+
+__global__ void __launch_bounds__(PROP_THREADS) k_prop_small_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm, int mode) {
+  MX_BATCH_ENTER();
+  b_k_prop_small(d, bx, mode);
 }
 
 // ---------------------------------------------------------------------------
@@ -585,7 +592,8 @@ __global__ void __launch_bounds__(INV_THREADS) k_big_inv(Dev d, int t, int mode)
 // step finalisation: reduce estimator partials in a fixed order, advance the
 // step counter, clear the energy accumulators
 // ---------------------------------------------------------------------------
-__global__ void k_final(Dev d, int mode, const int* slot_type) {
+__device__ __forceinline__ void b_k_final(const Dev& d, int bx, int mode) {
+  (void)bx;
   __shared__ double acc[MT * 4 + 2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int nq = d.n_types * 4 + 2;
@@ -596,7 +604,7 @@ __global__ void k_final(Dev d, int mode, const int* slot_type) {
       if (x < d.n_types * 4) {
         const int t = x / 4, qi = x % 4;
         for (int s = lane; s < d.n_part_slots; s += 32)
-          if (slot_type[s] == t) a += d.parts[(size_t)s * NPART + qi];
+          if (d.slot_type[s] == t) a += d.parts[(size_t)s * NPART + qi];
       } else {
         const int qi = 4 + (x - d.n_types * 4);
         for (int s = lane; s < d.n_part_slots; s += 32) a += d.parts[(size_t)s * NPART + qi];
@@ -655,6 +663,13 @@ __global__ void k_final(Dev d, int mode, const int* slot_type) {
   if (have) heat += acc[d.n_types * 4 + 1] / kc;  // start-of-step thermostat half
   *d.heat = heat;
   for (int i = 0; i < E_NSLOTS; ++i) d.E_fix[i] = 0ull;
+}
+
+__global__ void k_final(const __grid_constant__ Dev d, int mode) { b_k_final(d, blockIdx.x, mode); }
+
+__global__ void k_final_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm, int mode) {
+  MX_BATCH_ENTER();
+  b_k_final(d, bx, mode);
 }
 
 // caller forces and the energy record after a bare force evaluation
@@ -739,8 +754,34 @@ int launch_prop(const Dev& d, cudaStream_t s, int mode) {
   return n;
 }
 
+size_t batch_prop_smem(const Dev& d) {
+  size_t smem = 0;
+  for (int t = 0; t < d.n_types; ++t)
+    if (d.P[t] <= SMALL_P && d.N[t] > 0) smem = small_smem(d.P[t]) > smem ? small_smem(d.P[t]) : smem;
+  return smem;
+}
+
+// propagation (types with P <= SMALL_P) and step finalisation of every
+// member of a batch, one launch per kernel
+int launch_step_batched(const BatchGeom& g, cudaStream_t s, int mode) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_prop_small_b, cudaFuncAttributeMaxDynamicSharedMemorySize, PROP_SMEM_MAX);
+    attr = true;
+  }
+  const int r = g.nm + 1;
+  int n = 0;
+  if (g.blocks[BK_PROP] > 0) {
+    k_prop_small_b<<<g.blocks[BK_PROP], PROP_THREADS, g.prop_smem, s>>>(g.devs, g.pfx + BK_PROP * r, g.nm, mode);
+    ++n;
+  }
+  k_final_b<<<g.blocks[BK_FINAL], 1024, 0, s>>>(g.devs, g.pfx + BK_FINAL * r, g.nm, mode);
+  return n + 1;
+}
+
 int launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type) {
-  k_final<<<1, 1024, 0, s>>>(d, mode, slot_type);
+  (void)slot_type;  // carried in d
+  k_final<<<1, 1024, 0, s>>>(d, mode);
   return 1;
 }
 

@@ -748,6 +748,11 @@ struct mixts_ctx {
   int g_steps = 0;
   long long g_kernels = 0;
   mixts_batch_tuning tune{};
+  // one launch per phase for all members: member Dev records and per-kernel
+  // block prefixes in the batch's own slice of the workspace
+  unsigned char* bdev = nullptr;
+  int* bpfx = nullptr;
+  BatchGeom geom{};
   // single handle: steps per captured graph launch (0: eager launches)
   int graph_steps = 10;
   bool capturing = false;
@@ -1017,6 +1022,9 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.mc = (const ModeCoef*)(w + p.o_mc);
   d.tiles = (const PropTile*)(w + p.o_tiles);
   h->slot_type = (const int*)(w + p.o_slot_type);
+  d.slot_type = h->slot_type;
+  d.ainfo_atom = h->ainfo_atom;
+  d.atom_is_pseudo = h->atom_is_pseudo;
   d.q = sys->q;
   d.p = sys->p;
   d.f = sys->f;
@@ -1040,6 +1048,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   h->full_grid32 = d.pair32_grid;
   d.pseudo_chunks = prm->precision == MIXTS_FP32_FORCES ? 8 : 4;  // site-list slices per pseudo bead (measured)
   d.nl_cpl = 4;
+  d.p32_lgt = LG_P32_TERMS;
   d.p64_nch = (p.nl_cap + P32_CH - 1) / P32_CH;  // at most: one lane group, P32_CH entries per item
   {  // FP32 pair items: P32_CH candidates for each of the 32 / min(P_max, 32) lane groups
     const int lgG = 5 - std::min(d.lgPmax_nb, 5);
@@ -1433,6 +1442,7 @@ void apply_tuning(mixts_handle h, const mixts_batch_tuning& t) {
     k->d.pair_grid = std::max(1, std::min(k->full_grid64, g64));
     k->d.pair32_grid = std::max(1, std::min(k->full_grid32, g32));
     k->d.nl_cpl = t.nl_cpl;
+    k->d.p32_lgt = t.item_lg_terms > 0 ? t.item_lg_terms : LG_P32_TERMS;
   }
   h->tune = t;
 }
@@ -1445,6 +1455,11 @@ void drop_graph(mixts_handle h) {
 }
 }  // namespace
 
+// the batch's own region after the members: Dev records and block prefixes
+static size_t batch_region_bytes(int n_sys) {
+  return round_up(sizeof(Dev) * (size_t)n_sys, BATCH_ALIGN) + round_up(sizeof(int) * BK_KINDS * (size_t)(n_sys + 1), BATCH_ALIGN);
+}
+
 static size_t batch_workspace_size(const mixts_system* sys, int n_sys, const mixts_params* prm) {
   size_t total = 0;
   for (int i = 0; i < n_sys; ++i) {
@@ -1452,7 +1467,46 @@ static size_t batch_workspace_size(const mixts_system* sys, int n_sys, const mix
     if (n == 0) return 0;
     total += round_up(n, BATCH_ALIGN);
   }
-  return total + BATCH_ALIGN;
+  return total + batch_region_bytes(n_sys) + BATCH_ALIGN;
+}
+
+// every member can run the one-launch-per-phase step: no pseudo particle, no
+// type beyond the fused small-P propagation, damped-shifted-force Coulomb
+static bool batch_persistent_ok(mixts_handle h) {
+  for (auto k : h->kids) {
+    const Dev& d = k->d;
+    if (d.n_pseudo > 0 || d.coulomb != 0) return false;
+    for (int t = 0; t < d.n_types; ++t)
+      if (d.P[t] > SMALL_P && d.N[t] > 0) return false;
+  }
+  return true;
+}
+
+// upload the members' Dev records (after the current tuning) and the block
+// prefixes of every batched kernel
+static mixts_status batch_upload(mixts_handle h) {
+  const int nm = (int)h->kids.size();
+  std::vector<Dev> devs(nm);
+  std::vector<int> pfx((size_t)BK_KINDS * (nm + 1), 0);
+  BatchGeom& g = h->geom;
+  g = BatchGeom{};
+  g.nm = nm;
+  g.precision = h->kids[0]->d.precision;
+  for (int m = 0; m < nm; ++m) {
+    devs[m] = h->kids[m]->d;
+    int c[BK_KINDS];
+    batch_block_counts(devs[m], c);
+    for (int k = 0; k < BK_KINDS; ++k) pfx[(size_t)k * (nm + 1) + m + 1] = pfx[(size_t)k * (nm + 1) + m] + c[k];
+    g.prop_smem = std::max(g.prop_smem, batch_prop_smem(devs[m]));
+    g.pair_smem = std::max(g.pair_smem, (size_t)(6 * sizeof(double) + 8 * sizeof(float)) * (size_t)devs[m].dsf_nint);
+  }
+  for (int k = 0; k < BK_KINDS; ++k) g.blocks[k] = pfx[(size_t)k * (nm + 1) + nm];
+  g.devs = (const Dev*)h->bdev;
+  g.pfx = h->bpfx;
+  cudaError_t e = cudaMemcpyAsync(h->bdev, devs.data(), sizeof(Dev) * nm, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->bpfx, pfx.data(), sizeof(int) * pfx.size(), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // the host copies die here
+  return cuda_check(h, e, "batch upload");
 }
 
 static mixts_status batch_init(const mixts_system* sys, int n_sys, const mixts_params* prm, void* workspace,
@@ -1481,19 +1535,59 @@ static mixts_status batch_init(const mixts_system* sys, int n_sys, const mixts_p
     h->kids.push_back(k);
     off += round_up(n, BATCH_ALIGN);
   }
+  if (off + batch_region_bytes(n_sys) > ws_bytes) {
+    mixts_destroy(h);
+    return MIXTS_ERR_WORKSPACE;
+  }
+  h->bdev = h->ws + off;
+  h->bpfx = (int*)(h->ws + off + round_up(sizeof(Dev) * (size_t)n_sys, BATCH_ALIGN));
   mixts_batch_tuning t{};
   t.grid_scale = 2.0;
   t.streams = std::min(n_sys, 16);
   t.nl_cpl = 4;
   t.steps_per_launch = 10;
+  t.persistent = batch_persistent_ok(h) ? 1 : 0;
+  t.item_lg_terms = LG_P32_TERMS;
   apply_tuning(h, t);
   *out = h;
+  return MIXTS_OK;
+}
+
+// one launch per phase for all members: steps_per_launch steps of the
+// member step sequence (mixts_step), every kernel serving all members
+static mixts_status batch_capture_persistent(mixts_handle h) {
+  mixts_status st = batch_upload(h);
+  if (st != MIXTS_OK) return st;
+  const int K = std::max(1, h->tune.steps_per_launch);
+  if (!h->cap) {
+    st = cuda_check(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "capture stream");
+    if (st != MIXTS_OK) return st;
+  }
+  st = cuda_check(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (st != MIXTS_OK) return st;
+  const BatchGeom& g = h->geom;
+  long long nk = launch_step_batched(g, h->cap, PM_START);
+  for (int i = 0; i < K; ++i) {
+    nk += launch_forces_batched(g, h->cap);
+    nk += launch_step_batched(g, h->cap, i + 1 < K ? (PM_END | PM_EST | PM_START) : (PM_END | PM_EST | PM_PCART));
+  }
+  cudaGraph_t gr = nullptr;
+  st = cuda_check(h, cudaStreamEndCapture(h->cap, &gr), "end capture");
+  if (st == MIXTS_OK) st = cuda_check(h, cudaGraphInstantiate(&h->gexec, gr, 0), "graph instantiate");
+  if (gr) cudaGraphDestroy(gr);
+  if (st != MIXTS_OK) {
+    drop_graph(h);
+    return st;
+  }
+  h->g_steps = K;
+  h->g_kernels = nk;
   return MIXTS_OK;
 }
 
 // capture steps_per_launch steps of every member into one executable graph
 static mixts_status batch_capture(mixts_handle h) {
   drop_graph(h);
+  if (h->tune.persistent && batch_persistent_ok(h)) return batch_capture_persistent(h);
   const mixts_batch_tuning& t = h->tune;
   const int S = std::max(1, std::min(t.streams, (int)h->kids.size()));
   const int K = std::max(1, t.steps_per_launch);
@@ -1690,19 +1784,43 @@ extern "C" MIXTS_API mixts_status mixts_batch_tune(mixts_handle h, int steps_per
   int cands = 0;
   const double scales[] = {0.5, 1.0, 2.0, 4.0, 1e9};
   const int branches[] = {4, 8, 16, 32, 64};
-  for (int S : branches) {
-    if (S > n && S != branches[0]) continue;
-    for (double sc : scales) {
-      mixts_batch_tuning t{};
-      t.grid_scale = sc;
-      t.streams = std::min(S, n);
-      t.nl_cpl = 4;
-      double ms = 0.0;
-      if ((st = time_shape(t, &ms)) != MIXTS_OK) goto done_tuning;
-      ++cands;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = t;
+  if (batch_persistent_ok(h)) {
+    // one launch per phase: force-grid scale x FP32 work-item size (2^lgt terms)
+    const bool fp32 = h->kids[0]->d.precision == MIXTS_FP32_FORCES;
+    for (double sc : {0.5, 1.0, 2.0, 4.0})
+      for (int lgt : {9, 10, 11}) {
+        if (!fp32 && lgt != LG_P32_TERMS) continue;
+        mixts_batch_tuning t{};
+        t.grid_scale = sc;
+        t.streams = 1;
+        t.nl_cpl = 4;
+        t.persistent = 1;
+        t.item_lg_terms = lgt;
+        double ms = 0.0;
+        if ((st = time_shape(t, &ms)) != MIXTS_OK) goto done_tuning;
+        ++cands;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
+      }
+  } else {
+    for (int S : branches) {
+      if (S > n && S != branches[0]) continue;
+      for (double sc : scales) {
+        mixts_batch_tuning t{};
+        t.grid_scale = sc;
+        t.streams = std::min(S, n);
+        t.nl_cpl = 4;
+        t.persistent = 0;
+        t.item_lg_terms = LG_P32_TERMS;
+        double ms = 0.0;
+        if ((st = time_shape(t, &ms)) != MIXTS_OK) goto done_tuning;
+        ++cands;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
       }
     }
   }

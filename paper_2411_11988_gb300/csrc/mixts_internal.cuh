@@ -15,7 +15,7 @@ constexpr int SMALL_P = 64;     // types with P <= SMALL_P propagate in one fuse
 constexpr int BIG_MB = 8;       // modes (or beads) per CTA of the large-P transforms
 constexpr int PROP_SMEM_MAX = 200 * 1024;
 constexpr int P32_CH = 32;      // list entries per lane group of one FP64 pair item
-constexpr int LG_P32_TERMS = 10; // log2 of the bead-pair terms of one FP32 pair item
+constexpr int LG_P32_TERMS = 10; // default log2 of the bead-pair terms of one FP32 pair item (Dev::p32_lgt)
 // shared memory of one large-P transform CTA: the cos table and BIG_MB rows
 // of the 3N columns (forward: forces, q and p modes, plus the centroids)
 inline size_t big_prop_smem(int P, int N) { return sizeof(double) * ((size_t)P + (3 * (size_t)BIG_MB + 1) * 3 * N); }
@@ -122,12 +122,16 @@ struct Dev {
   int pair_grid, pair32_grid, pseudo_chunks;  // persistent grid sizes, site-list split
   int nl_cpl;                                 // list candidates per lane of one list warp
   int p32_nch;                                // FP32 pair items per owner row and slice block (list chunks)
+  int p32_lgt;                                // log2 of the bead-pair terms of one FP32 pair item (tunable)
   int p64_nch;                                // FP64 slice-parallel items per owner row and slice block (bound)
   int2* pitems;                               // FP64 pair items of the current list: (owner pos, sb << 16 | chunk)
   int* pctr;                                  // [0] item count of the current list, [1] next item to hand out
   float4* nlB;                 // FP32 path: list rows regrouped by partner type, (bead-0 displacement, tag)
   int* nlseg;                  // FP32 path: [n_nonp][n_types + 1] first entry of each partner type in nlB
   float box_lo;                // box - box_hi (binary32)
+  const int* atom_is_pseudo;   // [n_atoms]
+  const AtomInfo* ainfo_atom;  // [n_atoms] by atom index
+  const int* slot_type;        // [n_part_slots] type of each estimator partial slot
   // long-range electrostatics on centroids (coulomb == 1, see k_ewald.cu)
   int coulomb, ew_kmax, n_kvec, n_qatoms, n_intra;
   double ew_ke, ew_const, ew_bg, ew_inv2a2;  // k_e; self + background energy; background; 1/(2 alpha^2)
@@ -410,6 +414,59 @@ int launch_forces_out(const Dev& d, cudaStream_t s);
 void pair_grids(int nt, int nint, int* g64, int* g32);
 int launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out);
 int launch_ewald(const Dev& d, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Batched launches: one kernel launch serves the blocks of many systems. The
+// host stores the members' Dev records in device memory and, per kernel, the
+// prefix of the members' block counts; a block finds its member by binary
+// search, copies that member's Dev into shared memory and runs the same
+// kernel body as a single-system launch with its block index inside the
+// member's grid.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int batch_member(const int* pfx, int nm, int b) {
+  int lo = 0, hi = nm - 1;  // largest m with pfx[m] <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pfx[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+#define MX_BATCH_ENTER()                                                                   \
+  __shared__ __align__(16) int bdev_raw_[sizeof(Dev) / sizeof(int)];                       \
+  __shared__ int bdev_m_, bdev_bx_;                                                        \
+  if (threadIdx.x == 0) {                                                                  \
+    const int m_ = batch_member(pfx, nm, (int)blockIdx.x);                                 \
+    bdev_m_ = m_;                                                                          \
+    bdev_bx_ = (int)blockIdx.x - pfx[m_];                                                  \
+  }                                                                                        \
+  __syncthreads();                                                                         \
+  {                                                                                        \
+    const int* src_ = (const int*)(devs + bdev_m_);                                        \
+    for (int x_ = threadIdx.x; x_ < (int)(sizeof(Dev) / sizeof(int)); x_ += blockDim.x)    \
+      bdev_raw_[x_] = src_[x_];                                                            \
+  }                                                                                        \
+  __syncthreads();                                                                         \
+  const Dev& d = *(const Dev*)bdev_raw_;                                                   \
+  const int bx = bdev_bx_
+
+// per-kernel block-count prefixes of a batched launch (rows of nm + 1 ints)
+enum : int { BK_PREP = 0, BK_NLIST, BK_PAIRA, BK_PAIRB, BK_BONDED, BK_PROP, BK_FINAL, BK_KINDS };
+
+struct BatchGeom {
+  const Dev* devs;   // device [nm]
+  const int* pfx;    // device [BK_KINDS][nm + 1]
+  int nm;
+  int blocks[BK_KINDS];  // total blocks per kind
+  size_t prop_smem, pair_smem;
+  int precision;
+};
+
+int launch_step_batched(const BatchGeom& g, cudaStream_t s, int mode);  // propagation + finalisation
+int launch_forces_batched(const BatchGeom& g, cudaStream_t s);           // list, pair sweep, bonded
+void batch_block_counts(const Dev& d, int* counts);                       // BK_KINDS blocks of one member
+size_t batch_prop_smem(const Dev& d);
 
 // propagation modes
 enum : int {

@@ -57,7 +57,8 @@ class _Params(C.Structure):
 
 class _Tuning(C.Structure):
     _fields_ = [("grid_scale", C.c_double), ("streams", C.c_int), ("nl_cpl", C.c_int),
-                ("steps_per_launch", C.c_int), ("ms_per_step", C.c_double), ("candidates", C.c_int)]
+                ("steps_per_launch", C.c_int), ("ms_per_step", C.c_double), ("candidates", C.c_int),
+                ("persistent", C.c_int), ("item_lg_terms", C.c_int)]
 
 
 class _Estimates(C.Structure):

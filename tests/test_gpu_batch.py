@@ -143,3 +143,38 @@ def test_batch_workload_members_match_oracle(gpu):
         assert _force_err(b.f[k].cpu().numpy(), F_or) < 1e-5, C4_MEMBERS[k]
         assert abs(E[k] - parts[0]) <= 1e-5 * abs(parts[0])
     b.close()
+
+
+def test_batch_one_launch_per_phase(gpu):
+    """Water systems of uneven sizes and bead counts: a batched step launches
+    each kernel once for all members (<= 10 kernels per step), and every member
+    still matches its own single-system run bit for bit (FP64 and FP32)."""
+    systems = _systems()
+    for precision in (0, 1):
+        b = gpu.MixTSBatch(systems, precision=precision)
+        b.step(3)  # below steps_per_launch: plain per-member launches
+        _, _, k0 = b.timing()
+        b.step(10)  # one graph launch
+        _, _, k1 = b.timing()
+        assert (k1 - k0) / 10.0 <= 10.0, k1 - k0
+        for i, s in enumerate(systems):
+            m = gpu.MixTS(s, seed=i, precision=precision)
+            m.step(13)
+            assert np.array_equal(b.q[i].cpu().numpy(), m.q.cpu().numpy())
+            assert np.array_equal(b.p[i].cpu().numpy(), m.p.cpu().numpy())
+            m.close()
+        b.close()
+
+
+def test_batch_with_electron_member_falls_back(gpu):
+    """A member with a pseudo particle keeps the per-member kernels on
+    parallel graph branches; the trajectory is still the single-system one."""
+    systems = _systems()[:2] + [synth.water_box(8, 8.4, 8, 2, seed=3, ion=dict(synth.systems.ION3), electron_P=64)]
+    b = gpu.MixTSBatch(systems, dt=0.1)
+    b.step(12)
+    for i, s in enumerate(systems):
+        m = gpu.MixTS(s, seed=i, dt=0.1)
+        m.step(12)
+        assert np.array_equal(b.q[i].cpu().numpy(), m.q.cpu().numpy())
+        m.close()
+    b.close()
