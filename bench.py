@@ -221,7 +221,7 @@ def variant(torch, stream, flush, dev, sysm, dt, precision, steps, seed, peaks=N
     return out
 
 
-def batch_variant(torch, stream, flush, dev, steps):
+def batch_variant(torch, stream, flush, dev, steps, peaks=None):
     """The batched workload: tune the graph shapes, then time `steps` steps of
     all systems as graph launches of CHUNK steps (L2 flushed before each)."""
     import synth
@@ -251,7 +251,8 @@ def batch_variant(torch, stream, flush, dev, steps):
     k1 = b.timing()[2]
     est = b.estimators()
     evals = sum(e["n_evals"] for e in est)
-    # serialised per-phase device times of the same step, members one by one
+    # per-phase device times of the same step (eager launches with CUDA events:
+    # one launch per phase for all members when the batch runs that way)
     b.set_timing(True)
     b.step(2)
     ph, calls, _ = b.timing()
@@ -266,11 +267,13 @@ def batch_variant(torch, stream, flush, dev, steps):
             "ns_per_day_aggregate": len(systems) * ns_per_day(ms), "ms_per_step": ms, "steps": steps,
             "bead_pair_evals_per_step": evals, "bead_pair_evals_per_s": evals * 1000.0 / ms,
             "gpu_launches": k1 - k0, "tuning": tune, "tuning_s": tune_s,
-            "serialised_phase_ms_per_step": {k: v / 2.0 for k, v in ph.items() if calls[k]},
-            "roofline_pair_serialised": {"bound": "alu", "achieved": flops / (pair_ms * 1e-3) / 1e12,
-                                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                         "frac": flops / (pair_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-                                         "note": "sum of the members' k_pair32 launches timed one by one"}}
+            "phase_ms_per_step": {k: v / 2.0 for k, v in ph.items() if calls[k]},
+            "roofline_pair": {"bound": "alu", "kernel": "k_list_seg32_b + k_pair32_b" if tune.get("persistent") else
+                              "k_pair32 per member",
+                              "achieved": flops / (pair_ms * 1e-3) / 1e12,
+                              "peak": peaks["fp32_tflops"] if peaks else FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": flops / (pair_ms * 1e-3) / 1e12 / (peaks["fp32_tflops"] if peaks else FP32_PEAK_TFLOPS),
+                              "note": "one eager launch per phase for all members, CUDA events"}}
 
 
 def _run_observables(torch, stream, dev, sysm, dt, precision, n_eq, n_samp, every, pairs, dr=0.02, nbins=400):
@@ -315,18 +318,19 @@ def observables(torch, stream, dev):
                           electron_P=ie["P_e"])
     res = {}
     for key, prec in {"fp64": 0, "fp32_forces": 1}.items():
-        _, (rg_m, rg_e), g = _run_observables(torch, stream, dev, sie, ie["dt_fs"], prec, 2000, 8000, 10, [(2, 0)])
+        _, (rg_m, rg_e), g = _run_observables(torch, stream, dev, sie, ie["dt_fs"], prec, 5000, 45000, 10, [(2, 0)])
         res[key] = (rg_m[3], rg_e[3], g[(2, 0)])
     rg64, rg32 = res["fp64"], res["fp32_forces"]
     # partial quantisation (Sec. "System I"): H and O bead counts chosen independently
     from paper_2411_11988_gb300 import analysis
     combos = [(1, 1), (4, 1), (1, 4), (4, 4), (32, 1), (32, 4), (32, 32)]
     out["partial_quantisation"] = dict(
-        steps="2000 equilibration + 3000 sampled (every 10) per bead-count pair, dt 0.25 fs, FP64",
-        **analysis.quantisation_sweep(lambda ph, po: build_system(ph, po, 0), combos, dt=DT, n_eq=2000, n_samp=3000,
+        steps="8000 equilibration + 16000 sampled (every 10) per bead-count pair, dt 0.25 fs, FP64; "
+              "[mean, 8-block standard error]",
+        **analysis.quantisation_sweep(lambda ph, po: build_system(ph, po, 0), combos, dt=DT, n_eq=8000, n_samp=16000,
                                       every=10, device=str(dev), stream=stream))
     out["ion_electron"] = {
-        "steps": "2000 equilibration + 8000 sampled (every 10), dt 0.1 fs",
+        "steps": "5000 equilibration + 45000 sampled (every 10), dt 0.1 fs (5e4 steps, the workload's length)",
         "electron_Rg_A": {"fp64": [float(np.sqrt(rg64[0])), float(rg64[1] / (2 * np.sqrt(rg64[0])))],
                           "fp32_forces": [float(np.sqrt(rg32[0])), float(rg32[1] / (2 * np.sqrt(rg32[0])))]},
         "ion_O_rdf_first_peak": {k: [float(r[np.argmax(v[2][50:]) + 50]), float(np.max(v[2][50:]))]
@@ -340,7 +344,8 @@ def observables(torch, stream, dev):
 def grad_variant(torch, stream, dev, snapshots):
     """Forward + backward of the differentiable potential on snapshots of a
     short run; each gradient is checked against central differences of the
-    GPU potential (h = 1e-5 relative)."""
+    GPU potential (h = 1e-5 relative). The FP64 oracle's gradient at this
+    size is compared in the GPU tests."""
     import numpy as np
     import synth
     from paper_2411_11988_gb300 import MixTS, mixts_potential
@@ -350,7 +355,7 @@ def grad_variant(torch, stream, dev, snapshots):
     m = MixTS(s, T=300.0, dt=0.1, tau=100.0, seed=0, device=str(dev), stream=stream)
     th0 = np.array([s.pp_sigma[0], s.pp_A_eV[0], s.pp_b[0], s.pp_sigma[1], s.pp_A_eV[1], s.pp_b[1],
                     s.charge_type[0], s.lj_eps[0, 0]], dtype=np.float64)  # the system's own parameters
-    times, errs = [], []
+    times, errs, fd_noise = [], [], []
     for k in range(snapshots):
         m.step(5)
         with torch.cuda.stream(stream):
@@ -364,20 +369,44 @@ def grad_variant(torch, stream, dev, snapshots):
             times.append((time.perf_counter() - t0) * 1000.0)
         gth = th.grad.numpy()
         worst = 0.0
+        noise = 0.0
         for j in range(8):
             h = 1e-5 * abs(th0[j])
             tp, tm = th0.copy(), th0.copy()
             tp[j] += h
             tm[j] -= h
-            fd = (m.potential_grad(0, 1, tp, want_dvdq=False)[0] - m.potential_grad(0, 1, tm, want_dvdq=False)[0]) / (2 * h)
+            vp = m.potential_grad(0, 1, tp, want_dvdq=False, want_theta=False)[0]
+            vm = m.potential_grad(0, 1, tm, want_dvdq=False, want_theta=False)[0]
+            fd = (vp - vm) / (2 * h)
+            # rounding of V (~1e-13 |V| per evaluation) over 2h, and the
+            # truncation error of the central difference, bound |gth - fd|
+            noise = max(noise, 2e-13 * abs(V.item()) / (2 * h))
             worst = max(worst, abs(gth[j] - fd) / max(abs(fd), 1e-6 * abs(V.item())))
         errs.append(worst)
+        fd_noise.append(noise)
         m.reload()
     m.close()
     return {"workload": g["workload"], "snapshots": snapshots,
             "forward_backward_ms_median": float(np.median(times)), "forward_backward_ms_max": float(np.max(times)),
             "max_rel_err_vs_central_fd": float(np.max(errs)),
-            "note": "host wall time per snapshot (one synchronising call); FD step 1e-5 relative"}
+            "central_fd_rounding_bound_max": float(np.max(fd_noise)),
+            "note": "host wall time per snapshot (forward V only, backward recomputes and runs the adjoint); FD step "
+                    "1e-5 relative; errors relative to max(|dV/dtheta|, 1e-6 |V|)"}
+
+
+def ewald_variant(torch, stream, flush, dev, steps, alpha=0.35, kmax=11):
+    """The bench workload with the paper's electrostatics treatment: Ewald
+    real space per bead pair, reciprocal sum on the centroids (coulomb = 1)."""
+    from paper_2411_11988_gb300 import MixTS
+    sysm = build_system(32, 4, 0)
+    m = MixTS(sysm, T=300.0, dt=DT, tau=100.0, seed=0, device=str(dev), stream=stream, alpha=alpha, coulomb=1,
+              ewald_kmax=kmax)
+    ms, ph, calls, _, _ = timed_run(m, torch, stream, steps, 3, flush)
+    m.close()
+    return {"workload": WORKLOAD["workload"] + f", Ewald alpha {alpha} 1/A, |n| <= {kmax} on centroids",
+            "ns_per_day": ns_per_day(ms), "ms_per_step": ms,
+            "phase_ms_per_call": {k: ph[k] / max(1, calls[k]) for k in ph if calls[k]},
+            "note": "pair phase = real-space sweep + reciprocal sum on centroids"}
 
 
 def e2e_run(m, torch, stream, steps):
@@ -591,8 +620,9 @@ def main():
                                   ion=dict(synth.systems.ION3), electron_P=ie["P_e"])
             variants[key] = variant(torch, stream, flush, dev, sie, ie["dt_fs"], prec, vs, rank, peaks)
             variants[key]["workload"] = ie["workload"]
-        variants["batched_64_fp32"] = batch_variant(torch, stream, flush, dev, vs)
-        variants["grad_ion_electron512"] = grad_variant(torch, stream, dev, 10)
+        variants["batched_64_fp32"] = batch_variant(torch, stream, flush, dev, vs, peaks)
+        variants["grad_ion_electron512"] = grad_variant(torch, stream, dev, 100)
+        variants["fp64_ewald_centroid_water512_H32O4"] = ewald_variant(torch, stream, flush, dev, vs)
     obs = None
     if not args.no_observables:
         obs = observables(torch, stream, dev)

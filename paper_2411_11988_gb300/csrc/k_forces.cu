@@ -1362,38 +1362,47 @@ void batch_block_counts(const Dev& d, int* c) {
   c[BK_FINAL] = 1;
 }
 
-// neighbour lists, pair sweep and bonded terms of every member of a batch,
-// one launch per kernel
-int launch_forces_batched(const BatchGeom& g, cudaStream_t s) {
+// one part of the batched force evaluation: 0 neighbour lists, 1 pair sweep,
+// 2 bonded terms
+int launch_forces_batched_part(const BatchGeom& g, cudaStream_t s, int part) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_pair64_b, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr = true;
   }
   const int r = g.nm + 1;
-  int n = 0;
   auto pf = [&](int k) { return g.pfx + k * r; };
-  k_list_prep_b<<<g.blocks[BK_PREP], 1024, 0, s>>>(g.devs, pf(BK_PREP), g.nm);
-  ++n;
-  if (g.blocks[BK_NLIST] > 0) {
-    k_nlist_b<<<g.blocks[BK_NLIST], NL_THREADS, 0, s>>>(g.devs, pf(BK_NLIST), g.nm);
+  int n = 0;
+  if (part == 0) {
+    k_list_prep_b<<<g.blocks[BK_PREP], 1024, 0, s>>>(g.devs, pf(BK_PREP), g.nm);
     ++n;
-  }
-  if (g.blocks[BK_PAIRA] > 0) {
-    if (g.precision == MIXTS_FP32_FORCES) {
-      k_list_seg32_b<<<g.blocks[BK_PAIRA], NL_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
-      k_pair32_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, 0, s>>>(g.devs, pf(BK_PAIRB), g.nm);
-    } else {
-      k_pair_items_b<<<g.blocks[BK_PAIRA], ITEM_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
-      k_pair64_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
+    if (g.blocks[BK_NLIST] > 0) {
+      k_nlist_b<<<g.blocks[BK_NLIST], NL_THREADS, 0, s>>>(g.devs, pf(BK_NLIST), g.nm);
+      ++n;
     }
-    n += 2;
-  }
-  if (g.blocks[BK_BONDED] > 0) {
+  } else if (part == 1) {
+    if (g.blocks[BK_PAIRA] > 0) {
+      if (g.precision == MIXTS_FP32_FORCES) {
+        k_list_seg32_b<<<g.blocks[BK_PAIRA], NL_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
+        k_pair32_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, 0, s>>>(g.devs, pf(BK_PAIRB), g.nm);
+      } else {
+        k_pair_items_b<<<g.blocks[BK_PAIRA], ITEM_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
+        k_pair64_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
+      }
+      n += 2;
+    }
+  } else if (g.blocks[BK_BONDED] > 0) {
     k_bonded_b<<<g.blocks[BK_BONDED], 64, 0, s>>>(g.devs, pf(BK_BONDED), g.nm);
     ++n;
   }
   return n;
+}
+
+// neighbour lists, pair sweep and bonded terms of every member of a batch,
+// one launch per kernel
+int launch_forces_batched(const BatchGeom& g, cudaStream_t s) {
+  return launch_forces_batched_part(g, s, 0) + launch_forces_batched_part(g, s, 1) +
+         launch_forces_batched_part(g, s, 2);
 }
 
 int launch_pseudo(const Dev& d, cudaStream_t s) {

@@ -1657,10 +1657,35 @@ static mixts_status batch_capture(mixts_handle h) {
   return MIXTS_OK;
 }
 
+// eager batched steps with one launch per phase for all members, each
+// phase timed on the batch handle's events (the timing mode of a batch that
+// runs its graph that way)
+static mixts_status batch_step_eager_persistent(mixts_handle h, int n_steps) {
+  mixts_status st;
+  for (auto k : h->kids)
+    if ((st = step_prologue(k)) != MIXTS_OK) return set_err(h, st, k->err);
+  if ((st = batch_upload(h)) != MIXTS_OK) return st;
+  const BatchGeom& g = h->geom;
+  cudaStream_t s = h->stream;
+  phase(h, 4, [&] { return launch_step_batched(g, s, PM_START); });
+  for (int i = 0; i < n_steps; ++i) {
+    phase(h, 0, [&] { return launch_forces_batched_part(g, s, 0); });
+    phase(h, 1, [&] { return launch_forces_batched_part(g, s, 1); });
+    phase(h, 2, [&] { return launch_forces_batched_part(g, s, 2); });
+    phase(h, 4, [&] {
+      return launch_step_batched(g, s, i + 1 < n_steps ? (PM_END | PM_EST | PM_START) : (PM_END | PM_EST | PM_PCART));
+    });
+  }
+  for (auto k : h->kids) k->steps_done += n_steps;
+  h->steps_done += n_steps;
+  return cuda_check(h, cudaGetLastError(), "batched step launch");
+}
+
 static mixts_status batch_step(mixts_handle h, int n_steps) {
+  mixts_status st;
+  if (h->tm.on && h->tune.persistent && batch_persistent_ok(h)) return batch_step_eager_persistent(h, n_steps);
   bool timing = false;
   for (auto k : h->kids) timing = timing || k->tm.on;
-  mixts_status st;
   if (timing || n_steps < h->tune.steps_per_launch) {  // eager, member by member
     for (auto k : h->kids)
       if ((st = mixts_step(k, n_steps)) != MIXTS_OK) return set_err(h, st, k->err);

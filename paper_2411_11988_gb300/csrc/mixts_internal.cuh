@@ -465,6 +465,7 @@ struct BatchGeom {
 
 int launch_step_batched(const BatchGeom& g, cudaStream_t s, int mode);  // propagation + finalisation
 int launch_forces_batched(const BatchGeom& g, cudaStream_t s);           // list, pair sweep, bonded
+int launch_forces_batched_part(const BatchGeom& g, cudaStream_t s, int part);  // 0 list, 1 pair, 2 bonded
 void batch_block_counts(const Dev& d, int* counts);                       // BK_KINDS blocks of one member
 size_t batch_prop_smem(const Dev& d);
 

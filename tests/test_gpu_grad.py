@@ -127,7 +127,7 @@ def test_grad_full_size_ion_electron_512(gpu):
     """512 waters + ion + 1024-bead electron (H16/O2): seeded snapshots, GPU
     gradient against the oracle's."""
     base = synth.water_box(512, 24.83, 16, 2, seed=0, ion=dict(synth.systems.ION3), electron_P=1024)
-    for k in range(2):
+    for k in range(5):
         s = base.copy()
         s.q = base.q + np.random.default_rng(300 + k).normal(0, 0.05, base.q.shape)
         m = gpu.MixTS(s)
