@@ -584,13 +584,15 @@ void or_bead_force(const or_system* s, const double* q, int atom, int bead, doub
  *   d_max = max over non-pseudo beads of |q_{a,b} - q_{a,0}|
  *   R = r_cut + 2 d_max; the list is the set of unordered atom pairs with a
  *   lattice image, written canonically as (i, j, n) with i < j, for which
- *   |(r_j - r_i) + n L|^2 < R^2, n in [-2,2]^3, skipping same-molecule
- *   n = 0. Which atom of a pair a force kernel makes the owner of the entry
+ *   |(r_j - r_i) + n L|^2 < R^2, n in [-2,2]^3, skipping for a same-molecule
+ *   pair the image n = w_j - w_i, w_a = floor(q_{a,0}/L): the zero image of
+ *   the unwrapped coordinates, where the intramolecular terms (bonded, not
+ *   nonbonded) act. Which atom of a pair a force kernel makes the owner of the entry
  *   is the kernel's business; the set does not depend on it, because every
  *   operation below is odd under swapping i and j with n -> -n.
  * Every product and sum below is one IEEE operation in the order written.
  * ------------------------------------------------------------------------- */
-static void wrapped_refs(const or_system* s, const lay_t* L, const double* q, double* ref) {
+static void wrapped_refs(const or_system* s, const lay_t* L, const double* q, double* ref, int* wrap) {
   double Lb = s->box;
   for (int a = 0; a < s->n_atoms; ++a) {
     long r0 = row_of(s, L, a, 0);
@@ -598,6 +600,7 @@ static void wrapped_refs(const or_system* s, const lay_t* L, const double* q, do
       double x = q[3 * r0 + d];
       double fl = floor(x / Lb);
       ref[3 * a + d] = x - Lb * fl;
+      if (wrap) wrap[3 * a + d] = (int)fl;
     }
   }
 }
@@ -641,7 +644,8 @@ long or_nlist(const or_system* s, const double* q, long cap, int* out3, double* 
   lay_init(s, &L);
   int na = s->n_atoms;
   double* ref = (double*)malloc(sizeof(double) * 3 * (size_t)na);
-  wrapped_refs(s, &L, q, ref);
+  int* wrap = (int*)malloc(sizeof(int) * 3 * (size_t)na);
+  wrapped_refs(s, &L, q, ref, wrap);
   double dm = max_spread(s, &L, q, 0);
   double R = s->r_cut + 2.0 * dm;
   double R2 = R * R;
@@ -658,7 +662,9 @@ long or_nlist(const or_system* s, const double* q, long cap, int* out3, double* 
       for (int nx = -2; nx <= 2; ++nx)
         for (int ny = -2; ny <= 2; ++ny)
           for (int nz = -2; nz <= 2; ++nz) {
-            if (same && nx == 0 && ny == 0 && nz == 0) continue;
+            if (same && nx == wrap[3 * j] - wrap[3 * i] && ny == wrap[3 * j + 1] - wrap[3 * i + 1] &&
+                nz == wrap[3 * j + 2] - wrap[3 * i + 2])
+              continue;
             double d2 = disp2(ref + 3 * j, ref + 3 * i, nx, ny, nz, s->box);
             if (d2 < R2) {
               if (n < cap) {
@@ -672,6 +678,7 @@ long or_nlist(const or_system* s, const double* q, long cap, int* out3, double* 
     }
   }
   free(ref);
+  free(wrap);
   lay_free(&L);
   return n <= cap ? n : -n;
 }
@@ -681,7 +688,7 @@ long or_pseudo_list(const or_system* s, const double* q, long cap, int* out3, do
   lay_init(s, &L);
   int na = s->n_atoms;
   double* ref = (double*)malloc(sizeof(double) * 3 * (size_t)na);
-  wrapped_refs(s, &L, q, ref);
+  wrapped_refs(s, &L, q, ref, NULL);
   double ds = max_spread(s, &L, q, 0);
   double dp = max_spread(s, &L, q, 1);
   double R = (s->r_cut + ds) + dp;

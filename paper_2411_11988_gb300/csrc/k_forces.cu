@@ -24,7 +24,9 @@ namespace mx {
 //   R    = r_cut + 2 dmax
 //   keep (owner, other, n), n in [-2,2]^3, if
 //        ((r_o - r_w) + n L)^2 summed x, y, z left to right  <  R * R
-//   except same-molecule n = 0. Owner = finer atom; between equal bead
+//   except, for a same-molecule pair, the image n = w_other - w_owner with
+//   q_0 = r + w L (the zero image of the caller's unwrapped coordinates,
+//   where the intramolecular terms live). Owner = finer atom; between equal bead
 //   counts the lower sorted position when the positions sum to an even
 //   number, the higher one otherwise (balances the rows).
 // A binary32 screen with a rigorous error margin settles all but the
@@ -174,6 +176,13 @@ __device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
       const unsigned mz = my ? img_mask(dfz, Lf, Rlin) : 0u;
       if (mz) {
         const bool same = d.pos_mol[c] == moli;
+        // the image code of the same-molecule zero image in the wrapped frame
+        int xcode = -1;
+        if (same) {
+          const int4 wc = d.wrapn[c], wi = d.wrapn[i];
+          const int ex = wc.x - wi.x, ey = wc.y - wi.y, ez = wc.z - wi.z;
+          if (abs(ex) <= 2 && abs(ey) <= 2 && abs(ez) <= 2) xcode = (ex + 2) * 25 + (ey + 2) * 5 + (ez + 2);
+        }
         const int tag = (d.ainfo[c].row0 << 11) | (d.ainfo[c].type << 7);
         for (unsigned bx = mx; bx; bx &= bx - 1) {
           const int kx = __ffs(bx) - 1;
@@ -183,7 +192,7 @@ __device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
             const float ey = dfy + img_of(ky) * Lf;
             for (unsigned bz = mz; bz; bz &= bz - 1) {
               const int kz = __ffs(bz) - 1;
-              if (same && kx == 2 && ky == 2 && kz == 2) continue;
+              if (kx * 25 + ky * 5 + kz == xcode) continue;
               const float ez = dfz + img_of(kz) * Lf;
               const float d2f = ex * ex + ey * ey + ez * ez;
               bool keep;
@@ -296,6 +305,9 @@ __global__ void k_plist(Dev d) {
 // nonbonded pair sweep, FP64
 // ---------------------------------------------------------------------------
 constexpr int PAIR_THREADS = 256;
+// k_pair64 blocks of 14 warps: its ~72 registers then fit two blocks (28
+// warps) per SM, each with one copy of the interval table in shared memory
+constexpr int PAIR64_THREADS = 448;
 
 // Unit-charge DSF potential G(s), s = r^2, and -2 dG/ds from the interval
 // table: each is a quintic in x = s - s0 on each of 64 geometric
@@ -604,9 +616,9 @@ __device__ __forceinline__ void b_k_pair64(const Dev& d, int bx) {
   }
 }
 
-__global__ void __launch_bounds__(PAIR_THREADS) k_pair64(const __grid_constant__ Dev d) { b_k_pair64(d, blockIdx.x); }
+__global__ void __launch_bounds__(PAIR64_THREADS) k_pair64(const __grid_constant__ Dev d) { b_k_pair64(d, blockIdx.x); }
 
-__global__ void __launch_bounds__(PAIR_THREADS) k_pair64_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
+__global__ void __launch_bounds__(PAIR64_THREADS) k_pair64_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
   MX_BATCH_ENTER();
   b_k_pair64(d, bx);
 }
@@ -1304,7 +1316,7 @@ void pair_grids(int nt, int nint, int* g64, int* g32) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   (void)nt;
   cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_pair64, PAIR_THREADS, PAIR64_SMEM_PER_INTERVAL * (size_t)nint);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_pair64, PAIR64_THREADS, PAIR64_SMEM_PER_INTERVAL * (size_t)nint);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_pair32, PAIR_THREADS, 0);
   *g64 = std::max(1, b64) * std::max(1, sms);
   *g32 = std::max(1, b32) * std::max(1, sms);
@@ -1328,7 +1340,8 @@ int launch_pair(const Dev& d, cudaStream_t s) {
   const int nsbm = d.lgPmax_nb > 5 ? 1 << (d.lgPmax_nb - 5) : 1;
   const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;  // bound on the list's items
   k_pair_items<<<(d.n_nonp + ITEM_THREADS - 1) / ITEM_THREADS, ITEM_THREADS, 0, s>>>(d);
-  k_pair64<<<(int)std::min<long long>((items + wpb - 1) / wpb, d.pair_grid), PAIR_THREADS, smem, s>>>(d);
+  const int wpb64 = PAIR64_THREADS / 32;
+  k_pair64<<<(int)std::min<long long>((items + wpb64 - 1) / wpb64, d.pair_grid), PAIR64_THREADS, smem, s>>>(d);
   return 2;
 }
 
@@ -1354,7 +1367,7 @@ void batch_block_counts(const Dev& d, int* c) {
       const int nsbm = d.lgPmax_nb > 5 ? 1 << (d.lgPmax_nb - 5) : 1;
       const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;
       c[BK_PAIRA] = (d.n_nonp + ITEM_THREADS - 1) / ITEM_THREADS;
-      c[BK_PAIRB] = (int)std::min<long long>((items + wpb - 1) / wpb, d.pair_grid);
+      c[BK_PAIRB] = (int)std::min<long long>((items + PAIR64_THREADS / 32 - 1) / (PAIR64_THREADS / 32), d.pair_grid);
     }
   }
   c[BK_BONDED] = (d.n_bitems + 63) / 64;
@@ -1387,7 +1400,7 @@ int launch_forces_batched_part(const BatchGeom& g, cudaStream_t s, int part) {
         k_pair32_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, 0, s>>>(g.devs, pf(BK_PAIRB), g.nm);
       } else {
         k_pair_items_b<<<g.blocks[BK_PAIRA], ITEM_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
-        k_pair64_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
+        k_pair64_b<<<g.blocks[BK_PAIRB], PAIR64_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
       }
       n += 2;
     }

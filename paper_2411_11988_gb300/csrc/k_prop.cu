@@ -69,13 +69,16 @@ __device__ __forceinline__ void write_mirror(const Dev& d, int row, double x, do
 }
 
 // wrapped bead-0 reference of one atom, by atom index and (for non-pseudo
-// atoms) by sorted position for the neighbour search
-__device__ __forceinline__ void write_ref(const Dev& d, int atom, const double* rf) {
+// atoms) by sorted position for the neighbour search, with the lattice
+// vector fl that wrapped it (q_0 = r + fl L), which locates the zero image
+// of the caller's unwrapped coordinates for same-molecule pairs
+__device__ __forceinline__ void write_ref(const Dev& d, int atom, const double* rf, const double* fl) {
   for (int x = 0; x < 3; ++x) d.ref[3 * atom + x] = rf[x];
   const int pos = d.pos_of_atom[atom];
   if (pos >= 0) {
     d.refd[pos] = make_double4_32a(rf[0], rf[1], rf[2], 0.0);
     d.reff[pos] = make_float4((float)rf[0], (float)rf[1], (float)rf[2], __int_as_float(d.ainfo[pos].log2P));
+    d.wrapn[pos] = make_int4((int)fl[0], (int)fl[1], (int)fl[2], 0);
   }
 }
 
@@ -87,6 +90,73 @@ __device__ __forceinline__ double bead_d2(double dx, double dy, double dz) {
 }
 
 __device__ __forceinline__ double bead_dist(double dx, double dy, double dz) { return __dsqrt_rn(bead_d2(dx, dy, dz)); }
+
+// ---------------------------------------------------------------------------
+// Folded normal-mode transforms of a P x C tile in shared memory. The real
+// orthonormal basis is even or odd under bead j -> P - j: the cosine-like
+// modes k <= P/2 (centroid and alternating mode included) have
+// C[P-j][k] = C[j][k], the sine-like modes C[P-j][k] = -C[j][k]. With the
+// folded beads s_j = x_j + x_{P-j} and d_j = x_j - x_{P-j} (0 < j < P/2) each
+// sum runs over half the beads; the inverse computes the even part A_j and
+// the odd part B_j for j <= P/2 and writes x_j = A_j + B_j, x_{P-j} = A_j - B_j.
+// Half the multiply-adds of the dense products, in another rounding order.
+// ---------------------------------------------------------------------------
+// in place: row j <- s_j, row P - j <- d_j (0 < j < P/2)
+__device__ __forceinline__ void nm_fold(double* x, int P, int C, int tid, int nt) {
+  const int h = P / 2;
+  for (int e = tid; e < (h - 1) * C; e += nt) {
+    const int j = 1 + e / C, c = e - (e / C) * C;
+    const double a = x[j * C + c], b = x[(P - j) * C + c];
+    x[j * C + c] = a + b;
+    x[(P - j) * C + c] = a - b;
+  }
+}
+
+// out[k][c] = sum_j C[j][k] x_j from the folded rows f (nm_fold)
+__device__ __forceinline__ void nm_forward_folded(const double* Cm, int P, int C, const double* f, double* out,
+                                                  int tid, int nt) {
+  const int h = P / 2;
+  for (int e = tid; e < P * C; e += nt) {
+    const int k = e / C, c = e - (e / C) * C;
+    double a = 0.0;
+    if (k <= h) {
+      for (int j = 0; j <= h; ++j) a = fma(Cm[j * P + k], f[j * C + c], a);
+    } else {
+      for (int j = 1; j < h; ++j) a = fma(Cm[j * P + k], f[(P - j) * C + c], a);
+    }
+    out[e] = a;
+  }
+}
+
+// even and odd parts of x_j = sum_k C[j][k] q_k for j <= P/2: A in rows
+// 0..P/2 of ev, B in rows 1..P/2-1 of od (two passes' worth of threads)
+__device__ __forceinline__ void nm_inverse_parts(const double* Cm, int P, int C, const double* q, double* ev,
+                                                 double* od, int tid, int nt) {
+  const int h = P / 2;
+  const int ne = (h + 1) * C;
+  for (int e = tid; e < ne + (h > 1 ? (h - 1) * C : 0); e += nt) {
+    if (e < ne) {
+      const int j = e / C, c = e - (e / C) * C;
+      double a = 0.0;
+      for (int k = 0; k <= h; ++k) a = fma(Cm[j * P + k], q[k * C + c], a);
+      ev[j * C + c] = a;
+    } else {
+      const int e2 = e - ne;
+      const int j = 1 + e2 / C, c = e2 - (e2 / C) * C;
+      double b = 0.0;
+      for (int k = h + 1; k < P; ++k) b = fma(Cm[j * P + k], q[k * C + c], b);
+      od[j * C + c] = b;
+    }
+  }
+}
+
+// value of bead j from the parts (after nm_inverse_parts and a barrier)
+__device__ __forceinline__ double nm_inverse_value(const double* ev, const double* od, int P, int C, int j, int c) {
+  const int h = P / 2;
+  if (j == 0 || j == h) return ev[j * C + c];
+  if (j < h) return ev[j * C + c] + od[j * C + c];
+  return ev[(P - j) * C + c] - od[(P - j) * C + c];
+}
 
 // ---------------------------------------------------------------------------
 // small-P fused tile kernel
@@ -128,16 +198,11 @@ __device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
   }
   __syncthreads();
   if (mode & PM_IMPORT) {
-    for (int e = tid; e < PC; e += nt) {
-      const int k = e / C, c = e - (e / C) * C;
-      double aq = 0.0, ap = 0.0;
-      for (int j = 0; j < P; ++j) {
-        aq = fma(Cm[j * P + k], Xc[j * C + c], aq);
-        ap = fma(Cm[j * P + k], Fb[j * C + c], ap);
-      }
-      Qn[e] = aq;
-      Pn[e] = ap;
-    }
+    nm_fold(Xc, P, C, tid, nt);
+    nm_fold(Fb, P, C, tid, nt);
+    __syncthreads();
+    nm_forward_folded(Cm, P, C, Xc, Qn, tid, nt);
+    nm_forward_folded(Cm, P, C, Fb, Pn, tid, nt);
     __syncthreads();
   }
   double part[NPART] = {0, 0, 0, 0, 0, 0};
@@ -156,12 +221,9 @@ __device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
       }
     }
     __syncthreads();
-    for (int e = tid; e < PC; e += nt) {
-      const int k = e / C, c = e - (e / C) * C;
-      double a = 0.0;
-      for (int j = 0; j < P; ++j) a = fma(Cm[j * P + k], Fb[j * C + c], a);
-      Fn[e] = a;
-    }
+    nm_fold(Fb, P, C, tid, nt);
+    __syncthreads();
+    nm_forward_folded(Cm, P, C, Fb, Fn, tid, nt);
     __syncthreads();
     const double hk = 0.5 * d.dt * d.kcal;  // F in kcal/mol/A -> amu A/fs^2
     const uint32_t s_end = (uint32_t)s_step;
@@ -212,10 +274,12 @@ __device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
   }
   // Cartesian positions and mirrors
   if (mode & (PM_START | PM_QCART)) {
+    // Fb and Fn are free here: they hold the even and odd parts
+    nm_inverse_parts(Cm, P, C, Qn, Fb, Fn, tid, nt);
+    __syncthreads();
     for (int e = tid; e < PC; e += nt) {
       const int j = e / C, c = e - (e / C) * C;
-      double a = 0.0;
-      for (int k = 0; k < P; ++k) a = fma(Cm[j * P + k], Qn[k * C + c], a);
+      const double a = nm_inverse_value(Fb, Fn, P, C, j, c);
       Xc[e] = a;
       d.q[gidx(j, c)] = a;
     }
@@ -233,7 +297,7 @@ __device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
       write_mirror(d, row, Xc[j * C + 3 * a], Xc[j * C + 3 * a + 1], Xc[j * C + 3 * a + 2], fl[0], fl[1], fl[2],
                    Xc + 3 * a, d.off[t] + (k0 + a) * P + j);
       if (j == 0) {
-        write_ref(d, atom, rf);
+        write_ref(d, atom, rf, fl);
       } else {
         const double d2 = bead_d2(Xc[j * C + 3 * a] - Xc[3 * a], Xc[j * C + 3 * a + 1] - Xc[3 * a + 1],
                                   Xc[j * C + 3 * a + 2] - Xc[3 * a + 2]);
@@ -247,11 +311,12 @@ __device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
     }
   }
   if (mode & PM_PCART) {
+    __syncthreads();  // the position pass is done with Fb and Fn
+    nm_inverse_parts(Cm, P, C, Pn, Fb, Fn, tid, nt);
+    __syncthreads();
     for (int e = tid; e < PC; e += nt) {
       const int j = e / C, c = e - (e / C) * C;
-      double a = 0.0;
-      for (int k = 0; k < P; ++k) a = fma(Cm[j * P + k], Pn[k * C + c], a);
-      d.p[gidx(j, c)] = a;
+      d.p[gidx(j, c)] = nm_inverse_value(Fb, Fn, P, C, j, c);
     }
   }
   if (mode & (PM_END | PM_START)) {
@@ -286,7 +351,7 @@ __global__ void k_mirror_from_q(Dev d) {
     q0[x] = d.q[3 * (size_t)r0 + x];
     MirrorOut::wrap_ref(q0[x], d.box, &fl[x], &rf[x]);
   }
-  write_ref(d, atom, rf);
+  write_ref(d, atom, rf, fl);
   double sp = 0.0;
   for (int j = 0; j < P; ++j) {
     const size_t row = (size_t)r0 + (size_t)j * N;
@@ -560,7 +625,7 @@ __global__ void __launch_bounds__(INV_THREADS) k_big_inv(Dev d, int t, int mode)
       for (int x = 0; x < 3; ++x) MirrorOut::wrap_ref(Qc[3 * a + x], d.box, &fl[x], &rf[x]);
       const double* xb = Qc + (size_t)(jj + 1) * C + 3 * a;
       write_mirror(d, d.off[t] + j * N + a, xb[0], xb[1], xb[2], fl[0], fl[1], fl[2], Qc + 3 * a, d.off[t] + a * P + j);
-      if (jj == 0 && blockIdx.x == 0) write_ref(d, atom, rf);
+      if (jj == 0 && blockIdx.x == 0) write_ref(d, atom, rf, fl);
     }
     // spread partial of this bead block, per atom
     for (int a = warp; a < N; a += nw) {

@@ -100,7 +100,7 @@ struct Plan {
       o_slot_type, o_dsf, o_pstab, o_pairpar_alt, o_pspar_alt, o_pc, o_gacc;
   size_t o_state = 0, state_bytes = 0;
   size_t o_xd = 0, o_xia = 0;
-  size_t o_pitems = 0, o_pctr = 0, o_nlb = 0, o_nlseg = 0;
+  size_t o_pitems = 0, o_pctr = 0, o_nlb = 0, o_nlseg = 0, o_wrapn = 0;
   size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_xl, o_ref, o_refd, o_reff, o_spread, o_spread_big, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
       o_err, o_step, o_heat, o_est, o_parts;
 };
@@ -593,14 +593,13 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   } else {
     const double Rest = rc + 2.5;
     const double full = rho * 4.0 / 3.0 * PI * Rest * Rest * Rest;
-    p.nl_cap = (int)(1.3 * full) + 64;
+    p.nl_cap = (int)(1.5 * full) + 96;
     p.nl_cap = (p.nl_cap + 31) & ~31;
   }
-  {
-    const double Rp = rc + 12.0;
-    const double full = rho * 4.0 / 3.0 * PI * Rp * Rp * Rp;
-    p.pl_cap = std::max(64, std::min((int)(1.3 * full) + 128, 125 * std::max(1, p.n_nonp)));
-  }
+  // a pseudo particle's site list holds at most every site in each of the 125
+  // images of [-2,2]^3: that bound, so the list cannot overflow however far
+  // the ring polymer spreads (one row per pseudo particle)
+  p.pl_cap = std::max(64, 125 * std::max(1, p.n_nonp));
   if (p.n_pseudo > 0) {  // pseudopotential tables of the site types
     for (int t = 0; t < p.nt; ++t) {
       const PseudoPar& pp = p.pspar[t];
@@ -669,6 +668,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_ref = A.add(sizeof(double) * 3 * p.na);
   p.o_refd = A.add(sizeof(double4_32a) * std::max(1, p.n_nonp));
   p.o_reff = A.add(sizeof(float4) * std::max(1, p.n_nonp));
+  p.o_wrapn = A.add(sizeof(int4) * std::max(1, p.n_nonp));
   p.o_spread = A.add(sizeof(double) * (size_t)p.na);
   p.o_spread_big = A.add(sizeof(double) * (size_t)std::max(1, p.n_spread_big));
   p.o_nl = A.add(sizeof(int) * (size_t)std::max(1, p.n_nonp) * p.nl_cap);
@@ -824,8 +824,10 @@ static mixts_status device_error(mixts_handle h) {
   if (e == 0) return MIXTS_OK;
   cudaMemsetAsync(h->d.err, 0, sizeof(int), h->stream);
   if (e & ERR_BOX) return set_err(h, MIXTS_ERR_BOX, "list radius reached twice the box edge");
-  if (e & (ERR_NLIST | ERR_PLIST))
-    return set_err(h, MIXTS_ERR_NLIST_OVERFLOW, "a neighbour-list row outgrew its capacity");
+  if (e & ERR_NLIST)
+    return set_err(h, MIXTS_ERR_NLIST_OVERFLOW, "a nonbonded neighbour-list row outgrew nlist_cap");
+  if (e & ERR_PLIST)
+    return set_err(h, MIXTS_ERR_NLIST_OVERFLOW, "a pseudo-particle site list outgrew its capacity");
   if (e & ERR_NONFINITE) return set_err(h, MIXTS_ERR_NONFINITE, "non-finite or out-of-range force");
   if (e & ERR_TIMEOUT) return set_err(h, MIXTS_ERR_TIMEOUT, "bounded device wait expired");
   return set_err(h, MIXTS_ERR_CUDA, "unknown device error bits");
@@ -1040,6 +1042,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.ref = (double*)(w + p.o_ref);
   d.refd = (double4_32a*)(w + p.o_refd);
   d.reff = (float4*)(w + p.o_reff);
+  d.wrapn = (int4*)(w + p.o_wrapn);
   d.pos_of_atom = (const int*)(w + p.o_pos_of_atom);
   d.spread = (double*)(w + p.o_spread);
   d.spread_big = (double*)(w + p.o_spread_big);

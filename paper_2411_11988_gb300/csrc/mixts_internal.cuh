@@ -183,6 +183,7 @@ struct Dev {
   double* ref;                 // [n_atoms*3] wrapped bead-0 reference positions
   double4_32a* refd;           // [n_nonp] the same by sorted position
   float4* reff;                // [n_nonp] binary32 copy, .w = log2 P (int bits)
+  int4* wrapn;                 // [n_nonp] lattice vector that wrapped bead 0 (q_0 = ref + wrapn L)
   const int* pos_of_atom;      // [n_atoms] sorted position, -1 for pseudo particles
   double* spread;              // [n_atoms] max |q_b - q_0| (0 for large-P atoms)
   double* spread_big;          // large-P atoms: one partial per bead block, at sb_off[t] + rank * (P/BIG_MB)

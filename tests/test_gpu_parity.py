@@ -253,3 +253,27 @@ def test_graph_steps_equal_plain_launches(gpu):
     assert a.timing()[2] == d.timing()[2]
     for x in (a, b, c, d):
         x.close()
+
+
+@pytest.mark.parametrize("shift", [(1.9, -0.7, 3.3), (-4.2, 2.6, -0.35), (9.5, 0.2, 0.0)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_molecules_across_box_faces(gpu, shift, precision):
+    """A rigid translation leaves molecules across the box faces (each atom's
+    bead 0 wrapped into the box on its own): forces, energy and the list stay
+    those of the oracle, whose image sums work on the unwrapped coordinates."""
+    s = _mixed(16, seed=21)
+    s.q = s.q + np.asarray(shift)
+    L = s.box
+    w = np.array([np.floor(s.q[s.bead_rows(a)[0]] / L) for a in range(s.n_atoms)])
+    assert any(len({tuple(w[a]) for a in np.where(s.mol_of_atom == m)[0]}) > 1 for m in set(s.mol_of_atom.tolist()))
+    m = gpu.MixTS(s, precision=precision)
+    f, V = m.forces()
+    F_or, parts = oracle.forces(s)
+    tol = FTOL if precision == 0 else 1e-5
+    assert _force_err(f.cpu().numpy(), F_or) < tol
+    assert abs(V - parts[0]) <= tol * abs(parts[0])
+    tl, _ = m.nlist(0)
+    ol, _, _ = oracle.nlist(s)
+    if precision == 0:
+        assert np.array_equal(canonical(tl), ol)
+    m.close()

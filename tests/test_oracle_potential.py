@@ -235,8 +235,22 @@ def test_translation_and_periodicity(orc):
     assert np.abs(F3 - F).max() < 1e-10
 
 
-def test_neighbour_list_complete(orc):
-    s = _small_mixed_system(8, 2, 16, seed=13)
+def _straddling(s, shift):
+    """Rigid translation that leaves some molecules across the box faces:
+    each atom's bead 0 is wrapped into the box on its own, so atoms of one
+    molecule end up in different images of the wrapped frame."""
+    t = s.copy()
+    t.q = s.q + np.asarray(shift)
+    L = s.box
+    w = np.array([np.floor(t.q[t.bead_rows(a)[0]] / L) for a in range(t.n_atoms)])
+    split = any(len({tuple(w[a]) for a in np.where(t.mol_of_atom == m)[0]}) > 1 for m in set(t.mol_of_atom.tolist()))
+    return t, split
+
+
+@pytest.mark.parametrize("shift", [(0.0, 0.0, 0.0), (1.9, -0.7, 3.3), (-4.2, 2.6, -0.35)])
+def test_neighbour_list_complete(orc, shift):
+    s, split = _straddling(_small_mixed_system(8, 2, 16, seed=13), shift)
+    assert split or not any(shift)
     tl, dmax, R = orc.nlist(s)
     assert R == pytest.approx(RC + 2 * dmax)
     # canonical form: lower atom first, each (pair, image) once
@@ -269,3 +283,11 @@ def test_neighbour_list_complete(orc):
                             m = n + np.round(((xc - xa + n * L) - (ref(c) - ref(a))) / L - n).astype(int)
                             key = (a, c, int((m[0] + 2) * 25 + (m[1] + 2) * 5 + m[2] + 2))
                             assert key in have, key
+    # a same-molecule pair is never listed at the zero image of the unwrapped
+    # coordinates (its bonded terms act there), whatever frame wrapping put it in
+    for a in range(s.n_atoms):
+        for c in range(a + 1, s.n_atoms):
+            if s.mol_of_atom[a] != s.mol_of_atom[c] or not (nonp[a] and nonp[c]):
+                continue
+            m = np.round(((s.q[s.bead_rows(c)[0]] - s.q[s.bead_rows(a)[0]]) - (ref(c) - ref(a))) / L).astype(int)
+            assert (a, c, int((m[0] + 2) * 25 + (m[1] + 2) * 5 + m[2] + 2)) not in have
