@@ -70,12 +70,6 @@ __device__ double reduce_spread_kind(const Dev& d, const int* atom_is_pseudo, in
   long long m = 0;
   for (int a = threadIdx.x; a < d.n_atoms; a += blockDim.x)
     if (atom_is_pseudo[a] == want) m = max(m, __double_as_longlong(d.spread[a]));
-  for (int t = 0; t < d.n_types; ++t) {
-    if (d.P[t] <= SMALL_P || d.pseudo[t] != want) continue;
-    const int n = d.N[t] * (d.P[t] / BIG_MB);
-    for (int a = threadIdx.x; a < n; a += blockDim.x)
-      m = max(m, __double_as_longlong(d.spread_big[d.sb_off[t] + a]));
-  }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();

@@ -5,10 +5,12 @@
 //
 // Types with P <= SMALL_P: one CTA owns all P beads of a few atoms (a P x C
 // column tile, C = 3 * atoms) in shared memory and runs transform ->
-// elementwise update -> inverse transform in one pass. Types with larger P
-// (the 1024-bead electron) split the transforms over many CTAs by mode/bead
-// blocks, with the cosine table in shared memory.
+// elementwise update -> inverse transform in one pass, by the dense (folded)
+// mode matrix. Larger P (up to the 1024-bead electron): the same pass by one
+// thread-block cluster per tile, with four-step FFTs split over its CTAs.
 #include <math.h>
+
+#include <algorithm>
 
 #include "mixts_internal.cuh"
 
@@ -363,156 +365,285 @@ __global__ void k_mirror_from_q(Dev d) {
     }
   }
   d.spread[atom] = sp;
-  if (P > SMALL_P) {  // a large-P atom: its block partials must not keep older values
-    const int nb = P / BIG_MB;
-    for (int s = 0; s < nb; ++s) d.spread_big[d.sb_off[t] + k * nb + s] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// large-P path: one thread-block cluster of CL CTAs owns all P beads of a
+// few atoms and computes the orthonormal transforms by a four-step FFT
+// (P log P work instead of P^2), split over the cluster's SMs because a
+// single SM's FP64 pipe is far too slow for the 1024-bead electron.
+//
+// Real columns in pairs: two real columns a, b travel as one complex column
+// z = a + i b. With Y = DFT(z) (e^{-2 pi i jm/P}, unscaled) the columns'
+// real DFTs are (Y_m + conj Y_{P-m})/2 and (Y_m - conj Y_{P-m})/2i, and the
+// modes of the basis (1/sqrt P; sqrt(2/P) cos 2 pi jk/P for k < P/2;
+// (-1)^j/sqrt P; sqrt(2/P) sin 2 pi jk/P for k > P/2) are their scaled real
+// and imaginary parts. The inverse builds both columns' Hermitian spectra,
+// packs them the same way and runs the conjugate transform.
+//
+// Four steps, P = R S, bead j = S j1 + j2, frequency m = m1 + R m2:
+//   Y[m1 + R m2] = sum_j2 W_S^{j2 m2} W^{j2 m1} sum_j1 W_R^{j1 m1} x[S j1 + j2].
+// CTA r of the cluster owns the bead columns j2 in [r S/CL, (r+1) S/CL)
+// (length-R transforms over j1) and the frequencies m1 in [r R/CL, (r+1) R/CL)
+// (length-S transforms over m2, the modes k = m1 + R m2); the exchange in
+// between reads the other CTAs' shared memory (distributed shared memory).
+// ---------------------------------------------------------------------------
+constexpr int BIG_THREADS = 256;
+
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// barrier over every thread of every CTA of the cluster, with release /
+// acquire ordering of shared-memory writes across the cluster
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// generic address of the same shared-memory location in CTA `rank` of the cluster
+template <class T>
+__device__ __forceinline__ T* dsmem(T* p, unsigned rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"((uint64_t)p), "r"(rank));
+  return reinterpret_cast<T*>(out);
+}
+
+// w * u with w = (wx, sg wy)
+__device__ __forceinline__ double2 cmul(double2 w, double sg, double2 u) {
+  const double wi = sg * w.y;
+  return make_double2(fma(w.x, u.x, -wi * u.y), fma(w.x, u.y, wi * u.x));
+}
+
+// W^k = (cos, sin)(2 pi k / P), k in [0, P), from the half table tw[k < P/2]
+__device__ __forceinline__ double2 tw_full(const double2* tw, int k, int lgP) {
+  const int h = 1 << (lgP - 1);
+  const double2 w = tw[k & (h - 1)];
+  return k < h ? w : make_double2(-w.x, -w.y);
+}
+
+// In-place decimation-in-time FFTs of nrow rows of length L = 2^lgL (row i at
+// B + i L): input in bit-reversed order, output in natural order, exponent
+// sign sg (-1 forward, +1 inverse), no scaling; W_L^e = W^{e P/L}. Ends with
+// a block barrier.
+__device__ void fft_rows(double2* B, int nrow, int lgL, const double2* tw, int lgP, double sg, int tid, int nt) {
+  const int hL = 1 << (lgL - 1);
+  for (int s = 0; s < lgL; ++s) {
+    const int h = 1 << s;
+    for (int b = tid; b < nrow * hL; b += nt) {
+      const int row = b >> (lgL - 1), bb = b & (hL - 1);
+      const int pos = bb & (h - 1);
+      const int i0 = ((bb >> s) << (s + 1)) + pos;
+      double2* c = B + ((size_t)row << lgL);
+      const double2 a = c[i0];
+      const double2 t = cmul(tw[(pos << (lgL - 1 - s)) << (lgP - lgL)], sg, c[i0 + h]);
+      c[i0] = make_double2(a.x + t.x, a.y + t.y);
+      c[i0 + h] = make_double2(a.x - t.x, a.y - t.y);
+    }
+    __syncthreads();
   }
 }
 
-// ---------------------------------------------------------------------------
-// large-P path
-// ---------------------------------------------------------------------------
-// element (j, k) of the orthonormal normal-mode matrix; T holds
-// sqrt(2/P) cos(2 pi m / P), so the cos and sin modes need no multiply
-__device__ __forceinline__ double cjk(const double* T, int P, int j, int k, double rP) {
-  if (k == 0) return rP;
-  if (2 * k < P) return T[(j * k) & (P - 1)];
-  if (2 * k == P) return (j & 1) ? -rP : rP;
-  return T[(j * k - P / 4) & (P - 1)];  // sin(2 pi jk / P) = cos(2 pi (jk - P/4) / P)
+__device__ __forceinline__ int brev_n(int v, int lg) { return lg ? (int)(__brev((unsigned)v) >> (32 - lg)) : 0; }
+
+struct BigGeom {   // one CTA's share of a large-P tile
+  int P, lgP, R, lgR, S, lgS, CL, JL, ML, C, nz;
+  unsigned rank;
+  double2* tw;     // [P/2]
+  double2* Ab;     // [nz][JL][R]  bead-column rows
+  double2* Yb;     // [nz][ML][S]  frequency rows
+  double* Qm;      // [ML][S][C]  owned q modes
+  double* Pm;      // [ML][S][C]  owned p modes
+};
+
+// forward transform of a real array: Ab <- its owned bead columns (loaded by
+// the caller, bit-reversed over j1), then Yb <- Y[m1 + R m2] for the owned m1.
+// Ends after a cluster barrier, with every CTA's Yb complete.
+__device__ void big_forward(const BigGeom& g, int tid, int nt) {
+  __syncthreads();
+  fft_rows(g.Ab, g.nz * g.JL, g.lgR, g.tw, g.lgP, -1.0, tid, nt);
+  for (int e = tid; e < g.nz * g.JL * g.R; e += nt) {  // times e^{-2 pi i j2 m1 / P}
+    const int m1 = e & (g.R - 1), jl = (e >> g.lgR) % g.JL;
+    const int j2 = (int)g.rank * g.JL + jl;
+    g.Ab[e] = cmul(tw_full(g.tw, j2 * m1, g.lgP), -1.0, g.Ab[e]);
+  }
+  cluster_barrier();
+  for (int e = tid; e < g.nz * g.ML * g.S; e += nt) {
+    const int j2 = e & (g.S - 1), row = e >> g.lgS;  // row = z ML + ml
+    const int z = row / g.ML, ml = row - z * g.ML;
+    const int m1 = (int)g.rank * g.ML + ml;
+    const double2* src = dsmem(g.Ab, (unsigned)(j2 / g.JL));
+    g.Yb[((size_t)row << g.lgS) + brev_n(j2, g.lgS)] = src[((size_t)(z * g.JL + j2 % g.JL) << g.lgR) + m1];
+  }
+  __syncthreads();
+  fft_rows(g.Yb, g.nz * g.ML, g.lgS, g.tw, g.lgP, -1.0, tid, nt);
+  cluster_barrier();
 }
 
-constexpr int BIG_CC = 3;  // columns (one atom's x, y, z) per warp of the large-P transforms
+// mode k = m1 + R m2 (m1 owned: local index ml) of real column c after big_forward
+__device__ __forceinline__ double big_mode(const BigGeom& g, int ml, int m2, int c, double rP, double r2P) {
+  const int P = g.P;
+  const int m1 = (int)g.rank * g.ML + ml, k = m1 + g.R * m2;
+  const int z = c >> 1;
+  const double2 a = g.Yb[((size_t)(z * g.ML + ml) << g.lgS) + m2];
+  const int kk = (P - k) & (P - 1), n1 = kk & (g.R - 1), n2 = kk >> g.lgR;
+  const double2* yo = dsmem(g.Yb, (unsigned)(n1 / g.ML));
+  const double2 b = yo[((size_t)(z * g.ML + n1 % g.ML) << g.lgS) + n2];
+  const bool odd = c & 1;
+  if (k == 0 || 2 * k == P) return (odd ? a.y : a.x) * rP;
+  if (2 * k < P) return (odd ? a.y + b.y : a.x + b.x) * r2P;
+  return odd ? (a.x - b.x) * r2P : (b.y - a.y) * r2P;
+}
 
-// launch shapes of the large-P transforms, and the number of warps that
-// share one output group's sum (measured: the forward pass is fastest with 8
-// warps and no split, the inverse with 32 warps and a 4-way split)
-constexpr int FWD_THREADS = 256, FWD_SPLIT = 1;
-constexpr int INV_THREADS = 1024, INV_SPLIT = 4;
+// inverse transform of the owned modes X (Qm or Pm, every CTA's complete
+// and visible): Ab <- the bead values x[S j1 + j2] of the owned columns j2,
+// natural order over j1 (pair z: real part column 2z, imaginary part 2z+1).
+// Other CTAs may still read this CTA's Yb on return: the caller's next
+// cluster barrier orders that before Yb is written again.
+__device__ void big_inverse(const BigGeom& g, const double* X, int tid, int nt, double rP, double r2P) {
+  const int P = g.P, C = g.C;
+  for (int e = tid; e < g.nz * g.ML * g.S; e += nt) {
+    const int m2 = e & (g.S - 1), row = e >> g.lgS;
+    const int z = row / g.ML, ml = row - z * g.ML;
+    const int m = (int)g.rank * g.ML + ml + g.R * m2;
+    const int ca = 2 * z, cb = ca + 1;
+    const bool hb = cb < C;
+    const double* xl = X + ((size_t)ml * g.S + m2) * C;  // local modes at m
+    const double am = xl[ca], bm = hb ? xl[cb] : 0.0;
+    double2 v;
+    if (m == 0 || 2 * m == P) {
+      v = make_double2(am * rP, bm * rP);
+    } else {
+      const int mm = P - m, n1 = mm & (g.R - 1), n2 = mm >> g.lgR;
+      const double* xr = dsmem(X, (unsigned)(n1 / g.ML)) + ((size_t)(n1 % g.ML) * g.S + n2) * C;
+      const double amm = xr[ca], bmm = hb ? xr[cb] : 0.0;
+      v = 2 * m < P ? make_double2((am - bmm) * r2P, (amm + bm) * r2P)
+                    : make_double2((amm + bm) * r2P, (bmm - am) * r2P);
+    }
+    g.Yb[((size_t)row << g.lgS) + brev_n(m2, g.lgS)] = v;
+  }
+  __syncthreads();
+  fft_rows(g.Yb, g.nz * g.ML, g.lgS, g.tw, g.lgP, 1.0, tid, nt);
+  for (int e = tid; e < g.nz * g.ML * g.S; e += nt) {  // times e^{+2 pi i j2 m1 / P}
+    const int j2 = e & (g.S - 1), ml = (e >> g.lgS) % g.ML;
+    const int m1 = (int)g.rank * g.ML + ml;
+    g.Yb[e] = cmul(tw_full(g.tw, j2 * m1, g.lgP), 1.0, g.Yb[e]);
+  }
+  cluster_barrier();
+  for (int e = tid; e < g.nz * g.JL * g.R; e += nt) {
+    const int m1 = e & (g.R - 1), row = e >> g.lgR;  // row = z JL + jl
+    const int z = row / g.JL, jl = row - z * g.JL;
+    const int j2 = (int)g.rank * g.JL + jl;
+    const double2* src = dsmem(g.Yb, (unsigned)(m1 / g.ML));
+    g.Ab[((size_t)row << g.lgR) + brev_n(m1, g.lgR)] = src[((size_t)(z * g.ML + m1 % g.ML) << g.lgS) + j2];
+  }
+  __syncthreads();
+  fft_rows(g.Ab, g.nz * g.JL, g.lgR, g.tw, g.lgP, 1.0, tid, nt);
+}
 
-// forward transforms (C^T x) of this block's BIG_MB modes and the elementwise
-// step on them
-__global__ void __launch_bounds__(FWD_THREADS) k_big_fwd(Dev d, int t, int mode) {
+__device__ __forceinline__ void b_k_prop_big(const Dev& d, int mode) {
   extern __shared__ double sm[];
-  const int P = d.P[t], N = d.N[t], C = 3 * N;
-  double* T = sm;                       // [P]
-  double* Fn = T + P;                   // [BIG_MB*C]
-  double* Qi = Fn + BIG_MB * C;         // [BIG_MB*C] imported q modes
-  double* Pi = Qi + BIG_MB * C;         // [BIG_MB*C]
-  double* qbar = Pi + BIG_MB * C;       // [C]
-  __shared__ double red[(FWD_THREADS / 32) * NPART];
+  __shared__ double red[(BIG_THREADS / 32) * NPART];
   __shared__ long long s_step;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int kb = blockIdx.x * BIG_MB;
-  const double rP = rsqrt((double)P);
+  __shared__ long long s_d2[BIG_MAXA];
+  __shared__ double qb[3 * BIG_MAXA];
+  BigGeom g;
+  g.CL = d.big_cl;
+  g.rank = cluster_ctarank();
+  const PropTile tl = d.tiles[d.n_tiles + blockIdx.x / g.CL];
+  const int t = tl.type, N = d.N[t], k0 = tl.k0, na = tl.na;
+  g.P = d.P[t];
+  g.lgP = __ffs(g.P) - 1;
+  g.lgR = g.lgP / 2;
+  g.lgS = g.lgP - g.lgR;
+  g.R = 1 << g.lgR;
+  g.S = 1 << g.lgS;
+  g.JL = g.S / g.CL;
+  g.ML = g.R / g.CL;
+  g.C = 3 * na;
+  g.nz = (g.C + 1) >> 1;
+  const int P = g.P, C = g.C, R = g.R, S = g.S;
+  const int nown = g.ML * S;  // owned modes (and owned beads: JL R of them)
+  g.tw = (double2*)sm;
+  g.Ab = g.tw + P / 2;
+  g.Yb = g.Ab + (size_t)g.nz * g.JL * R;
+  g.Qm = (double*)(g.Yb + (size_t)g.nz * g.ML * S);
+  g.Pm = g.Qm + (size_t)nown * C;
+  double* Abd = (double*)g.Ab;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double rP = rsqrt((double)P), r2P = rsqrt(2.0 * (double)P);
+  const double m = d.mass[t];
   const double* cmg = d.cm + d.cm_off[t];
   const ModeCoef* mcf = d.mc + d.mc_off[t];
-  const size_t base = (size_t)d.off[t] * 3;  // element (j, c) at base + j*C + c
+  const unsigned rank = g.rank;
+  auto gidx = [&](int j, int c) -> size_t { return (size_t)(d.off[t] + j * N + k0) * 3 + c; };
+  // owned bead (jl, j1) -> bead index; owned mode (ml, m2) -> mode index
+  auto bead_of = [&](int jl, int j1) { return S * j1 + (int)rank * g.JL + jl; };
+  auto mode_of = [&](int ml, int m2) { return (int)rank * g.ML + ml + R * m2; };
+  // loads column values of the owned beads into Ab (bit-reversed over j1)
+  auto load_cols = [&](const double* src) {
+    if (C & 1)
+      for (int e = tid; e < g.JL * R; e += nt) Abd[2 * ((size_t)(g.nz - 1) * g.JL * R + e) + 1] = 0.0;
+    for (int e = tid; e < g.JL * R * C; e += nt) {
+      const int c = e % C, o = e / C, j1 = o % R, jl = o / R;
+      Abd[2 * (((size_t)((c >> 1) * g.JL + jl) << g.lgR) + brev_n(j1, g.lgR)) + (c & 1)] = src[gidx(bead_of(jl, j1), c)];
+    }
+  };
+
   if (tid == 0) s_step = *d.step_ctr;
-  for (int e = tid; e < P; e += blockDim.x) T[e] = cmg[e];
-  __syncthreads();
+  for (int e = tid; e < P / 2; e += nt) g.tw[e] = make_double2(cmg[2 * e], cmg[2 * e + 1]);
+  for (int e = tid; e < na; e += nt) s_d2[e] = 0;
   const bool need_f = (mode & (PM_END | PM_START)) != 0;
-  const int nout = BIG_MB * C;
-  // FWD_SPLIT warps per (mode, group of BIG_CC columns), each over a share of
-  // the beads: every matrix element is looked up once and feeds BIG_CC
-  // independent FMA chains; the shares are added in a fixed order
-  __shared__ double pbuf[FWD_THREADS / 32][3 * BIG_CC];
-  const int ncg = (C + BIG_CC - 1) / BIG_CC;
-  const int items = BIG_MB * ncg, slots = nw / FWD_SPLIT;
-  const int qs = warp % FWD_SPLIT, slot = warp / FWD_SPLIT;
-  for (int b0 = 0; b0 < items; b0 += slots) {
-    const int o = b0 + slot;
-    double af[BIG_CC], aq[BIG_CC], ap[BIG_CC];
-#pragma unroll
-    for (int u = 0; u < BIG_CC; ++u) af[u] = aq[u] = ap[u] = 0.0;
-    const int kk = o / ncg, c0 = (o - kk * ncg) * BIG_CC;
-    const int k = kb + kk;
-    const int ncol = o < items ? min(BIG_CC, C - c0) : 0;
-    for (int j = lane + 32 * qs; ncol > 0 && j < P; j += 32 * FWD_SPLIT) {
-      const double cj = cjk(T, P, j, k, rP);
-      const size_t g = base + (size_t)j * C + c0;
-#pragma unroll
-      for (int u = 0; u < BIG_CC; ++u) {
-        if (u < ncol) {
-          if (need_f) af[u] = fma(cj, fix_to_double(d.F_fix[g + u], FINV), af[u]);
-          if (mode & PM_IMPORT) {
-            aq[u] = fma(cj, d.q[g + u], aq[u]);
-            ap[u] = fma(cj, d.p[g + u], ap[u]);
-          }
-        }
+  if (mode & PM_IMPORT) {
+    for (int pass = 0; pass < 2; ++pass) {
+      load_cols(pass == 0 ? d.q : d.p);
+      big_forward(g, tid, nt);
+      double* dst = pass == 0 ? g.Qm : g.Pm;
+      for (int e = tid; e < nown * C; e += nt) {
+        const int c = e % C, o = e / C, m2 = o % S, ml = o / S;
+        dst[e] = big_mode(g, ml, m2, c, rP, r2P);
       }
     }
-#pragma unroll
-    for (int u = 0; u < BIG_CC; ++u) {
-      if (need_f) af[u] = warp_sum(af[u]);
-      if (mode & PM_IMPORT) {
-        aq[u] = warp_sum(aq[u]);
-        ap[u] = warp_sum(ap[u]);
-      }
-      if (lane == 0) {
-        pbuf[warp][u] = af[u];
-        pbuf[warp][BIG_CC + u] = aq[u];
-        pbuf[warp][2 * BIG_CC + u] = ap[u];
-      }
-    }
-    __syncthreads();
-    if (tid < slots * 3 * BIG_CC) {
-      const int sl = tid / (3 * BIG_CC), v = tid - sl * (3 * BIG_CC);
-      const int kind = v / BIG_CC, u = v - kind * BIG_CC;
-      const int oo = b0 + sl;
-      const int kk2 = oo / ncg, c2 = (oo - kk2 * ncg) * BIG_CC;
-      if (oo < items && u < min(BIG_CC, C - c2)) {
-        double sum = 0.0;
-        for (int w = 0; w < FWD_SPLIT; ++w) sum += pbuf[sl * FWD_SPLIT + w][v];
-        double* dst = kind == 0 ? Fn : (kind == 1 ? Qi : Pi);
-        dst[kk2 * C + c2 + u] = sum;
-      }
-    }
-    __syncthreads();
-  }
-  double part[NPART] = {0, 0, 0, 0, 0, 0};
-  if ((mode & PM_END) && (mode & PM_EST)) {
-    for (int c = warp; c < C; c += nw) {
-      double a = 0.0;
-      for (int j = lane; j < P; j += 32) a += d.q[base + (size_t)j * C + c];
-      a = warp_sum(a);
-      if (lane == 0) qbar[c] = a / P;
+  } else {
+    for (int e = tid; e < nown * C; e += nt) {
+      const int c = e % C, o = e / C, m2 = o % S, ml = o / S;
+      const size_t gi = gidx(mode_of(ml, m2), c);
+      g.Qm[e] = d.q_nm[gi];
+      g.Pm[e] = d.p_nm[gi];
     }
   }
+  cluster_barrier();  // every CTA's modes in place (the centroid sits in CTA 0)
+  for (int c = tid; c < C; c += nt) qb[c] = dsmem(g.Qm, 0u)[c] * rP;
   __syncthreads();
+  double part[NPART] = {0, 0, 0, 0, 0, 0};
   if (need_f) {
-    // this block's bead range: caller forces and the centroid virial
-    for (int e = tid; e < nout; e += blockDim.x) {
-      const int j = kb + e / C, c = e - (e / C) * C;
-      const size_t g = base + (size_t)j * C + c;
-      const double f = fix_to_double(d.F_fix[g], FINV);
-      if (mode & PM_END) {
-        d.f[g] = f;
-        if (mode & PM_EST) part[2] += (d.q[g] - qbar[c]) * f;
-      }
+    if (C & 1)
+      for (int e = tid; e < g.JL * R; e += nt) Abd[2 * ((size_t)(g.nz - 1) * g.JL * R + e) + 1] = 0.0;
+    for (int e = tid; e < g.JL * R * C; e += nt) {
+      const int c = e % C, o = e / C, j1 = o % R, jl = o / R;
+      const size_t gi = gidx(bead_of(jl, j1), c);
+      const double f = fix_to_double(d.F_fix[gi], FINV);
+      Abd[2 * (((size_t)((c >> 1) * g.JL + jl) << g.lgR) + brev_n(j1, g.lgR)) + (c & 1)] = f;
+      if (mode & PM_END) d.f[gi] = f;
+      if (mode & PM_START) d.F_fix[gi] = 0ull;
+      if ((mode & PM_END) && (mode & PM_EST)) part[2] += (d.q[gi] - qb[c]) * f;
     }
-  }
-  const double m = d.mass[t];
-  const double inv2m = 0.5 / m;
-  const double hk = 0.5 * d.dt * d.kcal;
-  const uint32_t s_end = (uint32_t)s_step;
-  const uint32_t s_start = (uint32_t)(s_step + ((mode & PM_END) ? 1 : 0));
-  for (int e = tid; e < nout; e += blockDim.x) {
-    const int k = kb + e / C, c = e - (e / C) * C;
-    const size_t g = base + (size_t)k * C + c;
-    double p, q;
-    if (mode & PM_IMPORT) {
-      p = Pi[e];
-      q = Qi[e];
-    } else {
-      p = d.p_nm[g];
-      q = d.q_nm[g];
-    }
-    if (need_f) {
+    big_forward(g, tid, nt);
+    const double hk = 0.5 * d.dt * d.kcal;  // F in kcal/mol/A -> amu A/fs^2
+    const uint32_t s_end = (uint32_t)s_step;
+    const uint32_t s_start = (uint32_t)(s_step + ((mode & PM_END) ? 1 : 0));
+    const double inv2m = 0.5 / m;
+    for (int e = tid; e < nown * C; e += nt) {
+      const int c = e % C, o = e / C, m2 = o % S, ml = o / S;
+      const int k = mode_of(ml, m2);
       const ModeCoef mk = mcf[k];
-      const double fk = Fn[e];
+      const uint64_t dof = (uint64_t)gidx(k, c);
+      double p = g.Pm[e], q = g.Qm[e];
+      const double fk = big_mode(g, ml, m2, c, rP, r2P);
       if (mode & PM_END) {
         p = fma(hk, fk, p);
-        const double xi = f2d_bits(gauss_dof(d.seed, s_end, 1u, (uint64_t)g));
+        const double xi = f2d_bits(gauss_dof(d.seed, s_end, 1u, dof));
         const double pn = fma(mk.c1, p, mk.c2s * xi);
         part[4] += (p * p - pn * pn) * inv2m;
         p = pn;
@@ -523,7 +654,7 @@ __global__ void __launch_bounds__(FWD_THREADS) k_big_fwd(Dev d, int t, int mode)
         }
       }
       if (mode & PM_START) {
-        const double xi = f2d_bits(gauss_dof(d.seed, s_start, 0u, (uint64_t)g));
+        const double xi = f2d_bits(gauss_dof(d.seed, s_start, 0u, dof));
         const double pn = fma(mk.c1, p, mk.c2s * xi);
         part[5] += (p * p - pn * pn) * inv2m;
         p = fma(hk, fk, pn);
@@ -532,126 +663,75 @@ __global__ void __launch_bounds__(FWD_THREADS) k_big_fwd(Dev d, int t, int mode)
         p = pr;
         q = qr;
       }
-    }
-    if (mode & (PM_IMPORT | PM_END | PM_START)) {
-      d.p_nm[g] = p;
-      d.q_nm[g] = q;
+      g.Pm[e] = p;
+      g.Qm[e] = q;
     }
   }
-  if (need_f) {
+  if (mode & (PM_IMPORT | PM_END | PM_START)) {
+    for (int e = tid; e < nown * C; e += nt) {
+      const int c = e % C, o = e / C, m2 = o % S, ml = o / S;
+      const size_t gi = gidx(mode_of(ml, m2), c);
+      d.q_nm[gi] = g.Qm[e];
+      d.p_nm[gi] = g.Pm[e];
+    }
+  }
+  cluster_barrier();  // updated modes visible; every read of the forward pass's Yb done
+  // Cartesian value of column c at owned bead (jl, j1) after big_inverse
+  auto xc = [&](int jl, int j1, int c) -> double {
+    return Abd[2 * (((size_t)((c >> 1) * g.JL + jl) << g.lgR) + j1) + (c & 1)];
+  };
+  if (mode & (PM_START | PM_QCART)) {
+    big_inverse(g, g.Qm, tid, nt, rP, r2P);
+    for (int e = tid; e < g.JL * R * C; e += nt) {
+      const int c = e % C, o = e / C, j1 = o % R, jl = o / R;
+      d.q[gidx(bead_of(jl, j1), c)] = xc(jl, j1, c);
+    }
+    cluster_barrier();  // bead 0 (CTA 0, jl = j1 = 0) visible
+    const double* ab0 = (const double*)dsmem(g.Ab, 0u);
+    for (int e = tid; e < g.JL * R * na; e += nt) {
+      const int a = e % na, o = e / na, j1 = o % R, jl = o / R;
+      const int j = bead_of(jl, j1);
+      const int atom = d.atom_of_tk[d.atoff[t] + k0 + a];
+      double x0[3], fl[3], rf[3];
+      for (int x = 0; x < 3; ++x) {
+        const int c = 3 * a + x;
+        x0[x] = ab0[2 * ((size_t)((c >> 1) * g.JL) << g.lgR) + (c & 1)];
+        MirrorOut::wrap_ref(x0[x], d.box, &fl[x], &rf[x]);
+      }
+      const double bx_ = xc(jl, j1, 3 * a), by_ = xc(jl, j1, 3 * a + 1), bz_ = xc(jl, j1, 3 * a + 2);
+      write_mirror(d, d.off[t] + j * N + k0 + a, bx_, by_, bz_, fl[0], fl[1], fl[2], x0, d.off[t] + (k0 + a) * P + j);
+      if (j == 0) {
+        write_ref(d, atom, rf, fl);
+      } else {
+        const double d2 = bead_d2(bx_ - x0[0], by_ - x0[1], bz_ - x0[2]);
+        atomicMax(&s_d2[a], __double_as_longlong(d2));  // this CTA's beads
+      }
+    }
+    cluster_barrier();  // every CTA's maximum in place; every read of bead 0 done
+    if (rank == 0)
+      for (int a = tid; a < na; a += nt) {
+        long long mx = 0;
+        for (int r = 0; r < g.CL; ++r) mx = max(mx, dsmem(s_d2, (unsigned)r)[a]);
+        d.spread[d.atom_of_tk[d.atoff[t] + k0 + a]] = __dsqrt_rn(__longlong_as_double(mx));
+      }
+  }
+  if (mode & PM_PCART) {
+    cluster_barrier();  // every read of the position pass's Yb and Ab done
+    big_inverse(g, g.Pm, tid, nt, rP, r2P);
+    for (int e = tid; e < g.JL * R * C; e += nt) {
+      const int c = e % C, o = e / C, j1 = o % R, jl = o / R;
+      d.p[gidx(bead_of(jl, j1), c)] = xc(jl, j1, c);
+    }
+  }
+  if (mode & (PM_END | PM_START)) {
     block_sum6(part, red);
     if (tid == 0)
-      for (int i = 0; i < NPART; ++i) d.parts[(size_t)(d.big_slot0[t] + blockIdx.x) * NPART + i] = red[i];
+      for (int i = 0; i < NPART; ++i) d.parts[(size_t)(tl.slot + (int)rank) * NPART + i] = red[i];
   }
+  cluster_barrier();  // no CTA leaves while another may still read its shared memory
 }
 
-// inverse transforms (C x) of this block's BIG_MB beads, mirrors, spread
-__global__ void __launch_bounds__(INV_THREADS) k_big_inv(Dev d, int t, int mode) {
-  extern __shared__ double sm[];
-  const int P = d.P[t], N = d.N[t], C = 3 * N;
-  double* T = sm;
-  double* Qc = T + P;                 // [(BIG_MB+1)*C], row 0 = bead 0, rows 1.. = own beads
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int jb = blockIdx.x * BIG_MB;
-  const double rP = rsqrt((double)P);
-  const double* cmg = d.cm + d.cm_off[t];
-  const size_t base = (size_t)d.off[t] * 3;
-  for (int e = tid; e < P; e += blockDim.x) T[e] = cmg[e];
-  __syncthreads();
-  const bool qc = (mode & (PM_START | PM_QCART)) != 0;
-  const int nout = (BIG_MB + 1) * C;
-  if (qc || (mode & PM_PCART)) {
-    // INV_SPLIT warps per (bead, group of BIG_CC columns), as in the forward pass
-    __shared__ double pbuf[INV_THREADS / 32][2 * BIG_CC];
-    const int ncg = (C + BIG_CC - 1) / BIG_CC;
-    const int items = (BIG_MB + 1) * ncg, slots = nw / INV_SPLIT;
-    const int qs = warp % INV_SPLIT, slot = warp / INV_SPLIT;
-    for (int b0 = 0; b0 < items; b0 += slots) {
-      const int o = b0 + slot;
-      const int r = o / ncg, c0 = (o - r * ncg) * BIG_CC;
-      const int j = r == 0 ? 0 : jb + r - 1;
-      const int ncol = o < items ? min(BIG_CC, C - c0) : 0;
-      double aq[BIG_CC], ap[BIG_CC];
-#pragma unroll
-      for (int u = 0; u < BIG_CC; ++u) aq[u] = ap[u] = 0.0;
-      for (int k = lane + 32 * qs; ncol > 0 && k < P; k += 32 * INV_SPLIT) {
-        const double cj = cjk(T, P, j, k, rP);
-        const size_t g = base + (size_t)k * C + c0;
-#pragma unroll
-        for (int u = 0; u < BIG_CC; ++u) {
-          if (u < ncol) {
-            if (qc) aq[u] = fma(cj, d.q_nm[g + u], aq[u]);
-            if (mode & PM_PCART) ap[u] = fma(cj, d.p_nm[g + u], ap[u]);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < BIG_CC; ++u) {
-        if (qc) aq[u] = warp_sum(aq[u]);
-        if (mode & PM_PCART) ap[u] = warp_sum(ap[u]);
-        if (lane == 0) {
-          pbuf[warp][u] = aq[u];
-          pbuf[warp][BIG_CC + u] = ap[u];
-        }
-      }
-      __syncthreads();
-      if (tid < slots * 2 * BIG_CC) {
-        const int sl = tid / (2 * BIG_CC), v = tid - sl * (2 * BIG_CC);
-        const int kind = v / BIG_CC, u = v - kind * BIG_CC;
-        const int oo = b0 + sl;
-        const int r2 = oo / ncg, c2 = (oo - r2 * ncg) * BIG_CC;
-        const int j2 = r2 == 0 ? 0 : jb + r2 - 1;
-        if (oo < items && u < min(BIG_CC, C - c2)) {
-          double sum = 0.0;
-          for (int w = 0; w < INV_SPLIT; ++w) sum += pbuf[sl * INV_SPLIT + w][v];
-          if (kind == 0 && qc) Qc[r2 * C + c2 + u] = sum;
-          if (kind == 1 && (mode & PM_PCART) && r2 > 0) d.p[base + (size_t)j2 * C + c2 + u] = sum;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  __syncthreads();
-  if (qc) {
-    for (int e = tid; e < BIG_MB * C; e += blockDim.x) {
-      const int j = jb + e / C, c = e - (e / C) * C;
-      d.q[base + (size_t)j * C + c] = Qc[C + e];
-    }
-    for (int e = tid; e < BIG_MB * N; e += blockDim.x) {
-      const int jj = e / N, a = e - (e / N) * N;
-      const int j = jb + jj;
-      const int atom = d.atom_of_tk[d.atoff[t] + a];
-      double fl[3], rf[3];
-      for (int x = 0; x < 3; ++x) MirrorOut::wrap_ref(Qc[3 * a + x], d.box, &fl[x], &rf[x]);
-      const double* xb = Qc + (size_t)(jj + 1) * C + 3 * a;
-      write_mirror(d, d.off[t] + j * N + a, xb[0], xb[1], xb[2], fl[0], fl[1], fl[2], Qc + 3 * a, d.off[t] + a * P + j);
-      if (jj == 0 && blockIdx.x == 0) write_ref(d, atom, rf, fl);
-    }
-    // spread partial of this bead block, per atom
-    for (int a = warp; a < N; a += nw) {
-      double sp = 0.0;
-      for (int jj = lane; jj < BIG_MB; jj += 32) {
-        const int j = jb + jj;
-        if (j == 0) continue;
-        const double* xb = Qc + (size_t)(jj + 1) * C + 3 * a;
-        const double dd = bead_dist(xb[0] - Qc[3 * a], xb[1] - Qc[3 * a + 1], xb[2] - Qc[3 * a + 2]);
-        sp = dd > sp ? dd : sp;
-      }
-      for (int o = 16; o > 0; o >>= 1) sp = fmax(sp, __shfl_xor_sync(0xffffffffu, sp, o));
-      if (lane == 0) {
-        const int atom = d.atom_of_tk[d.atoff[t] + a];
-        d.spread_big[d.sb_off[t] + a * gridDim.x + blockIdx.x] = sp;
-        if (blockIdx.x == 0) d.spread[atom] = 0.0;
-      }
-    }
-  }
-  if (mode & PM_START) {
-    for (int e = tid; e < BIG_MB * C; e += blockDim.x) {
-      const int j = jb + e / C, c = e - (e / C) * C;
-      d.F_fix[base + (size_t)j * C + c] = 0ull;
-    }
-  }
-}
+__global__ void __launch_bounds__(BIG_THREADS) k_prop_big(const __grid_constant__ Dev d, int mode) { b_k_prop_big(d, mode); }
 
 // ---------------------------------------------------------------------------
 // step finalisation: reduce estimator partials in a fixed order, advance the
@@ -782,8 +862,8 @@ static void prop_smem_optin() {
   static bool done = false;
   if (done) return;
   cudaFuncSetAttribute(k_prop_small, cudaFuncAttributeMaxDynamicSharedMemorySize, PROP_SMEM_MAX);
-  cudaFuncSetAttribute(k_big_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, PROP_SMEM_MAX);
-  cudaFuncSetAttribute(k_big_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, PROP_SMEM_MAX);
+  cudaFuncSetAttribute(k_prop_big, cudaFuncAttributeMaxDynamicSharedMemorySize, PROP_SMEM_MAX);
+  cudaFuncSetAttribute(k_prop_big, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   done = true;
 }
 
@@ -801,22 +881,50 @@ int launch_prop(const Dev& d, cudaStream_t s, int mode) {
     k_prop_small<<<d.n_tiles, PROP_THREADS, smem, s>>>(d, mode);
     ++n;
   }
-  for (int t = 0; t < d.n_types; ++t) {
-    if (d.P[t] <= SMALL_P || d.N[t] == 0) continue;
-    const int C = 3 * d.N[t];
-    const int nb = d.P[t] / BIG_MB;
-    if (mode & (PM_IMPORT | PM_END | PM_START)) {
-      const size_t smem = sizeof(double) * ((size_t)d.P[t] + 3 * (size_t)BIG_MB * C + C);
-      k_big_fwd<<<nb, FWD_THREADS, smem, s>>>(d, t, mode);
-      ++n;
-    }
-    if (mode & (PM_START | PM_QCART | PM_PCART)) {
-      const size_t smem = sizeof(double) * ((size_t)d.P[t] + (size_t)(BIG_MB + 1) * C);
-      k_big_inv<<<nb, INV_THREADS, smem, s>>>(d, t, mode);
-      ++n;
-    }
+  if (d.n_big_tiles > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)d.big_cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(d.n_big_tiles * d.big_cl));
+    cfg.blockDim = dim3(BIG_THREADS);
+    cfg.dynamicSmemBytes = (size_t)d.big_smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_prop_big, d, mode);
+    ++n;
   }
   return n;
+}
+
+int big_cluster_pick(int cl_max, const int* P, const int* na, int n, int* smem) {
+  prop_smem_optin();
+  for (int cl = cl_max; cl >= 1; cl >>= 1) {
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) need = std::max(need, big_prop_smem(P[i], na[i], cl));
+    if (need > (size_t)PROP_SMEM_MAX) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)cl);
+    cfg.blockDim = dim3(BIG_THREADS);
+    cfg.dynamicSmemBytes = need;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k_prop_big, &cfg) == cudaSuccess && nc > 0) {
+      *smem = (int)need;
+      return cl;
+    }
+    cudaGetLastError();  // clear a refused query before trying a smaller cluster
+  }
+  return 0;
 }
 
 size_t batch_prop_smem(const Dev& d) {

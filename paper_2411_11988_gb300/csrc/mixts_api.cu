@@ -81,12 +81,11 @@ struct Plan {
   size_t o_kvec = 0, o_kn = 0, o_qinfo = 0, o_qcharge = 0, o_intra = 0, o_ewphase = 0, o_ewcen = 0, o_ews = 0,
          o_ewek = 0;
   int ps_nint = 0, ps_elo = -6;
-  std::vector<int> cm_off, mc_off, big_slot0, sb_off;
-  int n_spread_big = 0;
+  std::vector<int> cm_off, mc_off;
   std::vector<ModeCoef> mc;
-  std::vector<PropTile> tiles;
+  std::vector<PropTile> tiles;  // small-P tiles, then large-P tiles
+  int n_small_tiles = 0, big_cl = 1;
   std::vector<int> slot_type;
-  int spread_slots = 1;
   int nl_cap = 0, pl_cap = 0;
   int n_classes = 0;
   int cls_P[MAX_CLASSES], cls_log2P[MAX_CLASSES], cls_pos0[MAX_CLASSES], cls_n[MAX_CLASSES],
@@ -101,7 +100,7 @@ struct Plan {
   size_t o_state = 0, state_bytes = 0;
   size_t o_xd = 0, o_xia = 0;
   size_t o_pitems = 0, o_pctr = 0, o_nlb = 0, o_nlseg = 0, o_wrapn = 0;
-  size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_xl, o_ref, o_refd, o_reff, o_spread, o_spread_big, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
+  size_t o_qnm, o_pnm, o_ffix, o_xw, o_xi, o_xf, o_xl, o_ref, o_refd, o_reff, o_spread, o_nl, o_nlcnt, o_pl, o_plcnt, o_thresh, o_efix,
       o_err, o_step, o_heat, o_est, o_parts;
 };
 
@@ -491,13 +490,6 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   const double bh = u.hbar / kT;
   p.cm_off.assign(MT, 0);
   p.mc_off.assign(MT, 0);
-  p.big_slot0.assign(MT, 0);
-  p.sb_off.assign(MT, 0);
-  for (int t = 0; t < p.nt; ++t)
-    if (s->P_type[t] > SMALL_P && big_prop_smem(s->P_type[t], p.N[t]) > (size_t)PROP_SMEM_MAX) {
-      fail(p, MIXTS_ERR_ARG, "a type with more than 64 beads holds too many atoms for one transform block");
-      return p;
-    }
   for (int t = 0; t < p.nt; ++t) {
     const int P = s->P_type[t];
     const double m = s->mass_type[t];
@@ -520,9 +512,11 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
             v = r2P * T[(j * k - P / 4) & (P - 1)];
           p.cm.push_back(v);
         }
-    } else {  // cosine table pre-scaled by sqrt(2/P), the weight of the cos/sin modes
-      const double r2P = sqrt(2.0 / P);
-      for (int k = 0; k < P; ++k) p.cm.push_back(r2P * T[k]);
+    } else {  // FFT twiddles (cos, sin)(2 pi m / P), m < P/2
+      for (int k = 0; k < P / 2; ++k) {
+        p.cm.push_back(T[k]);
+        p.cm.push_back(sin(2.0 * PI * k / P));
+      }
     }
     p.mc_off[t] = (int)p.mc.size();
     const int nsub = prm->free_ring_substeps;
@@ -576,14 +570,22 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
       p.slot_type.push_back(t);
     }
   }
+  // large-P tiles: one cluster of big_cl CTAs each (big_cl <= the shorter
+  // four-step factor 2^floor(lg P / 2) of every large-P type), with about
+  // two waves of CTAs over the GPU and one estimator slot per CTA
+  p.n_small_tiles = (int)p.tiles.size();
+  p.big_cl = BIG_CL_MAX;
+  for (int t = 0; t < p.nt; ++t)
+    if (s->P_type[t] > SMALL_P && p.N[t] > 0) p.big_cl = std::min(p.big_cl, 1 << (ilog2(s->P_type[t]) / 2));
   for (int t = 0; t < p.nt; ++t) {
     const int P = s->P_type[t];
     if (P <= SMALL_P || p.N[t] == 0) continue;
-    p.big_slot0[t] = (int)p.slot_type.size();
-    for (int b = 0; b < P / BIG_MB; ++b) p.slot_type.push_back(t);
-    p.spread_slots = std::max(p.spread_slots, P / BIG_MB);
-    p.sb_off[t] = p.n_spread_big;
-    p.n_spread_big += p.N[t] * (P / BIG_MB);
+    int apt = std::max(1, std::min(BIG_MAXA, (p.N[t] * p.big_cl + 303) / 304));
+    while (apt > 1 && big_prop_smem(P, apt, p.big_cl) > (size_t)BIG_SMEM_TARGET) --apt;
+    for (int k0 = 0; k0 < p.N[t]; k0 += apt) {
+      p.tiles.push_back(PropTile{t, k0, std::min(apt, p.N[t] - k0), (int)p.slot_type.size()});
+      for (int r = 0; r < p.big_cl; ++r) p.slot_type.push_back(t);
+    }
   }
   // neighbour-list capacities
   const double vol = s->box * s->box * s->box;
@@ -670,7 +672,6 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_reff = A.add(sizeof(float4) * std::max(1, p.n_nonp));
   p.o_wrapn = A.add(sizeof(int4) * std::max(1, p.n_nonp));
   p.o_spread = A.add(sizeof(double) * (size_t)p.na);
-  p.o_spread_big = A.add(sizeof(double) * (size_t)std::max(1, p.n_spread_big));
   p.o_nl = A.add(sizeof(int) * (size_t)std::max(1, p.n_nonp) * p.nl_cap);
   p.o_nlcnt = A.add(sizeof(int) * std::max(1, p.n_nonp));
   {  // FP64 pair items: at most every row's slice blocks times 32-entry chunks of a full row
@@ -929,9 +930,24 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.nl_cap = p.nl_cap;
   d.pl_cap = p.pl_cap;
   d.n_classes = p.n_classes;
-  d.n_tiles = (int)p.tiles.size();
+  d.n_tiles = p.n_small_tiles;
+  d.n_big_tiles = (int)p.tiles.size() - p.n_small_tiles;
+  if (d.n_big_tiles > 0) {
+    // the cluster size the device co-schedules (the plan's, or smaller: the
+    // slots of CTAs that do not exist stay zero)
+    std::vector<int> bP, bna;
+    for (size_t i = p.n_small_tiles; i < p.tiles.size(); ++i) {
+      bP.push_back(sys->P_type[p.tiles[i].type]);
+      bna.push_back(p.tiles[i].na);
+    }
+    d.big_cl = big_cluster_pick(p.big_cl, bP.data(), bna.data(), (int)bP.size(), &d.big_smem);
+    if (d.big_cl == 0) {
+      fprintf(stderr, "mixts_init: the device runs no thread-block cluster of the large-P propagation\n");
+      delete h;
+      return MIXTS_ERR_CUDA;
+    }
+  }
   d.n_part_slots = (int)p.slot_type.size();
-  d.spread_slots = p.spread_slots;
   d.precision = prm->precision;
   d.box = sys->box;
   d.rc = prm->r_cut;
@@ -993,8 +1009,6 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
     d.pseudo[t] = sys->pseudo_type[t] ? 1 : 0;
     d.cm_off[t] = p.cm_off[t];
     d.mc_off[t] = p.mc_off[t];
-    d.big_slot0[t] = p.big_slot0[t];
-    d.sb_off[t] = p.sb_off[t];
     d.mass[t] = sys->bead_mass_type ? sys->bead_mass_type[t] : sys->mass_type[t];  // kinetic (bead) mass
   }
   for (int c = 0; c < p.n_classes; ++c) {
@@ -1045,7 +1059,6 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.wrapn = (int4*)(w + p.o_wrapn);
   d.pos_of_atom = (const int*)(w + p.o_pos_of_atom);
   d.spread = (double*)(w + p.o_spread);
-  d.spread_big = (double*)(w + p.o_spread_big);
   pair_grids(p.nt, p.dsf_nint, &d.pair_grid, &d.pair32_grid);
   h->full_grid64 = d.pair_grid;
   h->full_grid32 = d.pair32_grid;

@@ -12,13 +12,19 @@ namespace mx {
 constexpr int MT = MIXTS_MAX_TYPES;
 constexpr int MAX_CLASSES = 12;
 constexpr int SMALL_P = 64;     // types with P <= SMALL_P propagate in one fused tile kernel
-constexpr int BIG_MB = 8;       // modes (or beads) per CTA of the large-P transforms
+constexpr int BIG_MAXA = 64;    // atoms per large-P propagation tile at most
+constexpr int BIG_CL_MAX = 16;  // CTAs per large-P tile (one thread-block cluster) at most
+constexpr int BIG_SMEM_TARGET = 100 * 1024;  // per-CTA shared memory of a large-P tile at most
 constexpr int PROP_SMEM_MAX = 200 * 1024;
 constexpr int P32_CH = 32;      // list entries per lane group of one FP64 pair item
 constexpr int LG_P32_TERMS = 10; // default log2 of the bead-pair terms of one FP32 pair item (Dev::p32_lgt)
-// shared memory of one large-P transform CTA: the cos table and BIG_MB rows
-// of the 3N columns (forward: forces, q and p modes, plus the centroids)
-inline size_t big_prop_smem(int P, int N) { return sizeof(double) * ((size_t)P + (3 * (size_t)BIG_MB + 1) * 3 * N); }
+// shared memory of one CTA of a large-P propagation tile of na atoms split
+// over a cluster of cl CTAs: the twiddles, the bead-column and frequency
+// rows of the packed complex columns, and the owned q and p modes
+inline size_t big_prop_smem(int P, int na, int cl) {
+  const size_t C = 3 * (size_t)na, nz = (C + 1) / 2, own = (size_t)P / cl;
+  return 16 * ((size_t)P / 2) + 16 * 2 * nz * own + 8 * 2 * C * own;
+}
 
 // Forces and energies are accumulated in 64-bit fixed point, so that sums
 // are exact integers whatever order the atomics land in: the whole step is
@@ -73,7 +79,7 @@ struct ModeCoef {  // per (type, mode): thermostat and exact free-ring rotation
   double hmw2;     // m omega^2 / 2 (spring energy in mode space)
 };
 
-struct PropTile {  // one CTA of the fused small-P propagation
+struct PropTile {  // one CTA of the fused propagation
   int type, k0, na, slot;
 };
 
@@ -90,9 +96,11 @@ struct Dev {
   int n_bitems, n_pitems, n_ppitems;
   int nl_cap, pl_cap;
   int n_classes;
-  int n_tiles;          // small-P propagation tiles
+  int n_tiles;          // small-P propagation tiles (tiles[0, n_tiles))
+  int n_big_tiles;      // large-P propagation tiles (tiles[n_tiles, n_tiles + n_big_tiles))
+  int big_smem;         // dynamic shared memory of one CTA of the large-P tile kernel
+  int big_cl;           // CTAs per large-P tile (cluster size)
   int n_part_slots;     // estimator partial slots
-  int spread_slots;     // per atom
   int precision;
   double box, rc, rc2, alpha;
   double dsf_erfc_rc_over_rc, dsf_cf, dsf_g;
@@ -115,10 +123,8 @@ struct Dev {
   uint64_t seed;
   // per type
   int P[MT], log2P[MT], N[MT], off[MT], pseudo[MT], atoff[MT];
-  int cm_off[MT];       // offset of C (P <= SMALL_P) or the cos table (P > SMALL_P)
+  int cm_off[MT];       // offset of C (P <= SMALL_P) or the FFT twiddles (P > SMALL_P)
   int mc_off[MT];       // offset of the ModeCoef rows
-  int big_slot0[MT];    // first estimator partial slot of a large-P type
-  int sb_off[MT];       // offset of a large-P type's spread partials
   int pair_grid, pair32_grid, pseudo_chunks;  // persistent grid sizes, site-list split
   int nl_cpl;                                 // list candidates per lane of one list warp
   int p32_nch;                                // FP32 pair items per owner row and slice block (list chunks)
@@ -185,8 +191,7 @@ struct Dev {
   float4* reff;                // [n_nonp] binary32 copy, .w = log2 P (int bits)
   int4* wrapn;                 // [n_nonp] lattice vector that wrapped bead 0 (q_0 = ref + wrapn L)
   const int* pos_of_atom;      // [n_atoms] sorted position, -1 for pseudo particles
-  double* spread;              // [n_atoms] max |q_b - q_0| (0 for large-P atoms)
-  double* spread_big;          // large-P atoms: one partial per bead block, at sb_off[t] + rank * (P/BIG_MB)
+  double* spread;              // [n_atoms] max |q_b - q_0|
   int* nl;                     // [n_nonp*nl_cap] (partner position << 7) | image code
   int* nl_cnt;                 // [n_nonp]
   int* pl;                     // [n_pseudo*pl_cap]
@@ -469,6 +474,10 @@ int launch_forces_batched(const BatchGeom& g, cudaStream_t s);           // list
 int launch_forces_batched_part(const BatchGeom& g, cudaStream_t s, int part);  // 0 list, 1 pair, 2 bonded
 void batch_block_counts(const Dev& d, int* counts);                       // BK_KINDS blocks of one member
 size_t batch_prop_smem(const Dev& d);
+// largest cluster size <= cl_max that the device co-schedules for the
+// large-P tile kernel (tiles of the n (P, atoms) shapes given), with its
+// per-CTA shared memory in *smem; 0 when none does
+int big_cluster_pick(int cl_max, const int* P, const int* na, int n, int* smem);
 
 // propagation modes
 enum : int {

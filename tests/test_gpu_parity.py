@@ -113,6 +113,28 @@ def test_neighbour_lists_bit_exact(gpu, case):
     m.close()
 
 
+@pytest.mark.parametrize("P_e", [128, 256, 1024])
+def test_step_path_spread_and_lists(gpu, P_e):
+    """After a step, the lists built from the propagation kernel's bead
+    spreads (the large-P types' maximum gathered over a thread-block
+    cluster) equal the oracle's lists of the same positions, radii included."""
+    import copy
+    s = _mixed(P_e, seed=3)
+    m = gpu.MixTS(s, T=300.0, dt=0.1, tau=100.0, seed=11)
+    m.step(1)
+    s2 = copy.deepcopy(s)
+    s2.q = m.q.cpu().numpy().copy()
+    tl, th = m.nlist(0)
+    ol, dmax, R = oracle.nlist(s2)
+    assert th[0] == dmax and th[1] == R
+    assert np.array_equal(canonical(tl), ol)
+    pl, pth = m.nlist(1)
+    opl, oth = oracle.pseudo_list(s2)
+    assert pth[0] == oth[1] and pth[1] == oth[2]
+    assert np.array_equal(pl, opl)
+    m.close()
+
+
 def test_gaussians_bit_exact(gpu):
     s = _c1()
     m = gpu.MixTS(s, seed=987654321)
@@ -134,12 +156,17 @@ def _run_both(s, nsteps, **kw):
     return m, run
 
 
-@pytest.mark.parametrize("case", ["c1", "mixed16", "mixed128", "h64", "h1_o4", "h4_o8", "electron1024"])
+@pytest.mark.parametrize("case", ["c1", "mixed16", "mixed128", "h64", "h1_o4", "h4_o8", "electron1024", "h128_o256"])
 def test_one_step_matches_oracle(gpu, case):
     if case == "c1":
         s = _c1(seed=1)
     elif case in ("h1_o4", "h4_o8"):
         s = _h_coarser(*((1, 4) if case == "h1_o4" else (4, 8)), seed=13)
+    elif case == "h128_o256":
+        # many atoms of two FFT-propagated types: 54 H at P = 128 in tiles of
+        # ten atoms (even column counts), 27 O at P = 256 in tiles of five
+        # (odd column counts, a half-filled last complex column)
+        s = _h_coarser(128, 256, seed=17)
     elif case == "electron1024":  # 256 waters H8/O1 + ion + 1024-bead electron, the large-P transforms
         s = synth.water_box(256, 18.6, 8, 1, seed=2, ion=dict(synth.systems.ION3), electron_P=1024)
     elif case == "h64":  # the largest bead count of the fused small-P propagation tile
