@@ -867,19 +867,22 @@ static void prop_smem_optin() {
   done = true;
 }
 
-int launch_prop(const Dev& d, cudaStream_t s, int mode) {
+int launch_prop(const Dev& d, cudaStream_t s, int mode, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
   int n = 0;
   prop_smem_optin();
   if (mode & PM_MIRROR) {
     k_mirror_from_q<<<(d.n_atoms + 127) / 128, 128, 0, s>>>(d);
     return 1;
   }
-  if (d.n_tiles > 0) {
-    size_t smem = 0;
-    for (int t = 0; t < d.n_types; ++t)
-      if (d.P[t] <= SMALL_P && d.N[t] > 0) smem = small_smem(d.P[t]) > smem ? small_smem(d.P[t]) : smem;
-    k_prop_small<<<d.n_tiles, PROP_THREADS, smem, s>>>(d, mode);
-    ++n;
+  // the large-P clusters (few SMs, latency-bound) run beside the small-P
+  // tiles when a side stream is given: the two touch disjoint rows, atoms
+  // and estimator slots
+  const bool split = side && ev_fork && ev_join && d.n_tiles > 0 && d.n_big_tiles > 0;
+  cudaStream_t sb = s;
+  if (split) {
+    cudaEventRecord(ev_fork, s);
+    cudaStreamWaitEvent(side, ev_fork, 0);
+    sb = side;
   }
   if (d.n_big_tiles > 0) {
     cudaLaunchConfig_t cfg = {};
@@ -891,11 +894,22 @@ int launch_prop(const Dev& d, cudaStream_t s, int mode) {
     cfg.gridDim = dim3((unsigned)(d.n_big_tiles * d.big_cl));
     cfg.blockDim = dim3(BIG_THREADS);
     cfg.dynamicSmemBytes = (size_t)d.big_smem;
-    cfg.stream = s;
+    cfg.stream = sb;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k_prop_big, d, mode);
     ++n;
+  }
+  if (d.n_tiles > 0) {
+    size_t smem = 0;
+    for (int t = 0; t < d.n_types; ++t)
+      if (d.P[t] <= SMALL_P && d.N[t] > 0) smem = small_smem(d.P[t]) > smem ? small_smem(d.P[t]) : smem;
+    k_prop_small<<<d.n_tiles, PROP_THREADS, smem, s>>>(d, mode);
+    ++n;
+  }
+  if (split) {
+    cudaEventRecord(ev_join, side);
+    cudaStreamWaitEvent(s, ev_join, 0);
   }
   return n;
 }

@@ -758,6 +758,9 @@ struct mixts_ctx {
   int graph_steps = 10;
   bool capturing = false;
   bool list_valid = false;  // neighbour lists and position mirrors match the current q
+  // large-P propagation beside the small-P tiles (both kinds present)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static void timer_fold(mixts_handle h) {
@@ -1101,8 +1104,25 @@ static mixts_status eval_forces(mixts_handle h) {
   return cuda_check(h, cudaGetLastError(), "force launch");
 }
 
+// the side stream of the large-P clusters, made by the step prologue
+// (eager, before any capture; a bare force evaluation never needs it);
+// without it the two kinds of tiles run one after the other
+static void ensure_side(mixts_handle h) {
+  if (!h->side && h->d.n_tiles > 0 && h->d.n_big_tiles > 0) {
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (h->side) cudaStreamDestroy(h->side);
+      if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+      h->side = nullptr;
+      h->ev_fork = h->ev_join = nullptr;
+    }
+  }
+}
+
 static void prop(mixts_handle h, int mode) {
-  phase(h, 4, [&] { return launch_prop(h->d, h->stream, mode); });
+  phase(h, 4, [&] { return launch_prop(h->d, h->stream, mode, h->side, h->ev_fork, h->ev_join); });
 }
 
 static void fin(mixts_handle h, int mode) {
@@ -1141,6 +1161,7 @@ mixts_status mixts_forces(mixts_handle h, double* energy_host) {
 // the Cartesian state, forces at the current positions
 static mixts_status step_prologue(mixts_handle h) {
   cudaStream_t s = h->stream;
+  ensure_side(h);
   if (!h->nm_valid) {
     prop(h, PM_IMPORT);
     h->nm_valid = true;
@@ -1420,6 +1441,12 @@ void mixts_destroy(mixts_handle h) {
     cudaStreamSynchronize(h->stream);
     for (auto e : h->tm.pool) cudaEventDestroy(e);
   }
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 

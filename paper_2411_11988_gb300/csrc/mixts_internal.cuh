@@ -414,7 +414,10 @@ int launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo);
 int launch_pair(const Dev& d, cudaStream_t s);
 int launch_bonded(const Dev& d, cudaStream_t s, const AtomInfo* ainfo_atom);
 int launch_pseudo(const Dev& d, cudaStream_t s);
-int launch_prop(const Dev& d, cudaStream_t s, int mode);
+// side / ev_fork / ev_join (optional): a second stream for the large-P
+// clusters, forked from and joined back into s with the two events
+int launch_prop(const Dev& d, cudaStream_t s, int mode, cudaStream_t side = nullptr, cudaEvent_t ev_fork = nullptr,
+                cudaEvent_t ev_join = nullptr);
 int launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type);
 int launch_forces_out(const Dev& d, cudaStream_t s);
 void pair_grids(int nt, int nint, int* g64, int* g32);
