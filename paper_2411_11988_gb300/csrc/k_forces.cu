@@ -324,6 +324,7 @@ __device__ __forceinline__ void dsf_table(const double* tab, int hi, double s, d
 }
 
 constexpr size_t PAIR64_SMEM_PER_INTERVAL = 6 * sizeof(double) + 8 * sizeof(float);
+constexpr size_t PAIR32_SMEM_PER_INTERVAL = 8 * sizeof(float);
 
 // The same two quintics at a given offset x = s - s0 inside the interval,
 // split by order: c0 + c1 x + c2 x^2 in binary64 (c = the interval's
@@ -638,19 +639,23 @@ __global__ void __launch_bounds__(PAIR64_THREADS) k_pair64_b(const Dev* __restri
 // their bead 0, so no large cancellation enters. Items hold ~2^10 terms
 // whatever the bead counts and are handed out from a counter.
 //
-// The damped-shifted-force Coulomb uses the erfc approximation of Abramowitz
-// & Stegun, Handbook of Mathematical Functions, eq. 7.1.26 (|error| <=
-// 1.5e-7), with the exact Gaussian in the force.
+// The damped-shifted-force (or Ewald real-space) Coulomb comes from a
+// binary32 interval table of cubics in s = r^2 (the FP64 sweep's table, refit
+// as cubics); Lennard-Jones is analytic.
 // ---------------------------------------------------------------------------
-constexpr int LG_P32_ENTRIES = 8;  // at most 256 entries per item (staged in shared memory)
+constexpr int LG_P32_ENTRIES = 7;  // at most 128 entries per item (staged in shared memory)
 
 // log2 of the entries of one FP32 item: 2^lgt terms = entries x
 // (owner beads of the block) x (fine slices per owner bead)
+// (capped so that the entries plus the staging padding of 4 x 2^(5 - lgPp)
+// groups fit P32_STAGE: 128 entries for owners of 4 or more beads, 64 for
+// two-bead owners, 32 for classical ones)
 __device__ __forceinline__ int p32_lg_entries(int lgPi, int lgPt, int lgt) {
   const int lgPp = lgPi < 5 ? lgPi : 5;
   const int lgS = lgPi > lgPt ? lgPi : lgPt;
   const int lgE = lgt - lgPp - (lgS - lgPi);
-  return lgE > 0 ? (lgE < LG_P32_ENTRIES ? lgE : LG_P32_ENTRIES) : 0;
+  const int cap = lgPp >= 2 ? LG_P32_ENTRIES : LG_P32_ENTRIES - 2 + lgPp;
+  return lgE > 0 ? (lgE < cap ? lgE : cap) : 0;
 }
 
 __device__ __forceinline__ void b_k_list_seg32(const Dev& d, int bx) {
@@ -740,80 +745,82 @@ __global__ void __launch_bounds__(NL_THREADS) k_list_seg32_b(const Dev* __restri
 
 // Parameters of one FP32 item (one owner type x partner type pair).
 struct P32Par {
-  float qq, e4, s2, vrc, dvrc, rc, rc2, pa, nl2e, g2a, cf, c0;
+  float rc, rc2, smin, qq, e4, s2, vrc, dvrc;
+  int kbase;  // key of the table's first interval: (127 + e_lo) << 6
 };
 
-// One term: displacement d = (x_j - x_i), weight applied later. Skipped as a
-// whole when no lane of the warp is inside the cut-off (entries listed
-// within r_cut + 2 d_max but beyond r_cut); otherwise evaluated without
-// branches and masked.
+// One term of an item, displacement d = x_j - x_i. The Coulomb part per unit
+// charge product comes from the binary32 interval table: its value G and its
+// force over r F are cubics in x = s - s0 on 64 sub-intervals per octave of
+// s = r^2, keyed by the exponent and top six mantissa bits of s. LJ items
+// add Lennard-Jones analytically and carry the total force; otherwise the
+// force stays per unit charge product (the item scales it once). Skipped as
+// a whole when no lane of the warp is inside the cut-off; otherwise
+// branch-free and masked at r_cut. nev counts the warp's in-cut-off terms
+// (the same on every lane).
 template <bool LJ>
-__device__ __forceinline__ void pair32_term(const P32Par& c, float dx, float dy, float dz, float& fx, float& fy,
-                                            float& fz, float& ec, float& elj, float& vir, int& nev) {
-  // erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x)
-  const float a1 = 0.254829592f, a2 = -0.284496736f, a3 = 1.421413741f, a4 = -1.453152027f, a5 = 1.061405429f;
-  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-  const bool in = r2 < c.rc2;
-  if (!__any_sync(0xffffffffu, in)) return;
-  const float rs = in ? r2 : c.rc2;  // finite arithmetic on masked lanes
-  const float rinv = rsqrtf(rs);
-  const float r = rs * rinv;
-  const float t = __fdividef(1.0f, fmaf(c.pa, r, 1.0f));
-  float ex;  // exp(-a^2 r^2), argument in [-a^2 rc^2, 0]
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(c.nl2e * rs));
-  const float pl = fmaf(fmaf(fmaf(fmaf(a5, t, a4), t, a3), t, a2), t, a1) * t;
-  const float erc = pl * ex;
-  float et = c.qq * fmaf(erc, rinv, fmaf(c.cf, r - c.rc, -c.c0));
-  float fr = c.qq * (fmaf(erc * rinv, rinv, fmaf(c.g2a * ex, rinv, -c.cf)) * rinv);
-  float lt = 0.0f;
+__device__ __forceinline__ void pair32_term(const P32Par& c, const float4* tab, float dx, float dy, float dz,
+                                            float& fx, float& fy, float& fz, float& ec, float& elj, float& vir,
+                                            int& nev) {
+  const float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  const bool in = s < c.rc2;
+  const unsigned m = __ballot_sync(0xffffffffu, in);
+  if (m == 0u) return;
+  nev += __popc(m);
+  const float sc = fminf(fmaxf(s, c.smin), c.rc2);
+  const int bits = __float_as_int(sc);
+  const int key = (bits >> 17) - c.kbase;
+  const float x = sc - __int_as_float(bits & 0xFFFE0000);
+  const float4 gq = tab[2 * key], fq = tab[2 * key + 1];
+  float g = fmaf(fmaf(fmaf(gq.w, x, gq.z), x, gq.y), x, gq.x);
+  float f = fmaf(fmaf(fmaf(fq.w, x, fq.z), x, fq.y), x, fq.x);
   if (LJ) {
-    const float rinv2 = rinv * rinv;
+    const float rinv = rsqrtf(sc);
+    const float r = sc * rinv, rinv2 = rinv * rinv;
     const float sr2 = c.s2 * rinv2, sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
-    lt = c.e4 * (sr12 - sr6) - c.vrc - (r - c.rc) * c.dvrc;
-    fr += (6.0f * c.e4 * (2.0f * sr12 - sr6) * rinv + c.dvrc) * rinv;
+    const float lt = c.e4 * (sr12 - sr6) - c.vrc - (r - c.rc) * c.dvrc;
+    f = fmaf(c.qq, f, (6.0f * c.e4 * (2.0f * sr12 - sr6) * rinv + c.dvrc) * rinv);
+    elj += in ? lt : 0.0f;
   }
-  fr = in ? fr : 0.0f;
+  g = in ? g : 0.0f;
+  f = in ? f : 0.0f;
+  ec += g;
   // force on i is minus the force on j along d = x_j - x_i
-  fx = fmaf(-fr, dx, fx);
-  fy = fmaf(-fr, dy, fy);
-  fz = fmaf(-fr, dz, fz);
-  vir = fmaf(fr, r2, vir);
-  ec += in ? et : 0.0f;
-  if (LJ) elj += in ? lt : 0.0f;
-  nev += in ? 1 : 0;
+  fx = fmaf(-f, dx, fx);
+  fy = fmaf(-f, dy, fy);
+  fz = fmaf(-f, dz, fz);
+  vir = fmaf(f, s, vir);
 }
 
 // The terms of one lane over its group's entries: local indices grp, grp +
-// G, ... below n of the item's entries staged in shared memory (buf), all
-// groups running the same number of rounds (the skip test is warp-wide).
-// R1: one fine slice per owner bead (partner not finer); the next round's
-// partner bead is loaded before this round's arithmetic. Otherwise each
-// entry's 2^lgr slices of the lane's bead.
+// G, ... below n of the item's entries staged in shared memory (buf, padded
+// past n with far entries, so that every group runs the same rounds without
+// bounds tests). R1: one fine slice per owner bead (partner not finer), two
+// entries per round with the next round's two partner beads loaded ahead.
+// Otherwise each entry's 2^lgr slices of the lane's bead.
 template <bool LJ, bool R1>
 __device__ __forceinline__ void pair32_entries(const float4* buf, int n, int grp, int G, int lgr, int sh_t,
                                                const float4* __restrict__ Xd, int b, float4 di, const P32Par& c,
-                                               float& fx, float& fy, float& fz, float& ec, float& elj, float& vir,
-                                               int& nev) {
+                                               const float4* tab, float& fx, float& fy, float& fz, float& ec,
+                                               float& elj, float& vir, int& nev) {
   const int s0 = b << lgr;  // first fine slice of this lane's owner bead
-  const float4 far = make_float4(0.f, 0.f, 1e4f, 0.f);  // a partner far outside the cut-off
   const int rounds = (n + G - 1) / G;
   if (R1) {
-    // two entries per round (l, l + G), the next round's two loaded ahead
     const int sj = s0 >> sh_t;
     const int G2 = 2 * G;
     int l = grp;
-    float4 Ba = l < n ? buf[l] : far, Bb = l + G < n ? buf[l + G] : far;
-    float4 da = l < n ? __ldg(Xd + (__float_as_int(Ba.w) >> 4) + sj) : far;
-    float4 db = l + G < n ? __ldg(Xd + (__float_as_int(Bb.w) >> 4) + sj) : far;
+    float4 Ba = buf[l], Bb = buf[l + G];
+    float4 da = __ldg(Xd + (__float_as_int(Ba.w) >> 4) + sj);
+    float4 db = __ldg(Xd + (__float_as_int(Bb.w) >> 4) + sj);
     for (int r = 0; r < rounds; r += 2) {
       const int ln = l + G2;
-      const float4 Bna = ln < n ? buf[ln] : far, Bnb = ln + G < n ? buf[ln + G] : far;
-      const float4 dna = ln < n ? __ldg(Xd + (__float_as_int(Bna.w) >> 4) + sj) : far;
-      const float4 dnb = ln + G < n ? __ldg(Xd + (__float_as_int(Bnb.w) >> 4) + sj) : far;
-      pair32_term<LJ>(c, (Ba.x - di.x) + da.x, (Ba.y - di.y) + da.y, (Ba.z - di.z) + da.z, fx, fy, fz, ec, elj, vir,
-                      nev);
-      pair32_term<LJ>(c, (Bb.x - di.x) + db.x, (Bb.y - di.y) + db.y, (Bb.z - di.z) + db.z, fx, fy, fz, ec, elj, vir,
-                      nev);
+      const float4 Bna = buf[ln], Bnb = buf[ln + G];
+      const float4 dna = __ldg(Xd + (__float_as_int(Bna.w) >> 4) + sj);
+      const float4 dnb = __ldg(Xd + (__float_as_int(Bnb.w) >> 4) + sj);
+      pair32_term<LJ>(c, tab, (Ba.x - di.x) + da.x, (Ba.y - di.y) + da.y, (Ba.z - di.z) + da.z, fx, fy, fz, ec,
+                      elj, vir, nev);
+      pair32_term<LJ>(c, tab, (Bb.x - di.x) + db.x, (Bb.y - di.y) + db.y, (Bb.z - di.z) + db.z, fx, fy, fz, ec,
+                      elj, vir, nev);
       Ba = Bna;
       Bb = Bnb;
       da = dna;
@@ -822,23 +829,28 @@ __device__ __forceinline__ void pair32_entries(const float4* buf, int n, int grp
     }
   } else {
     for (int r = 0, l = grp; r < rounds; ++r, l += G) {
-      const bool v = l < n;
-      const float4 B = v ? buf[l] : far;
+      const float4 B = buf[l];
       const int abase = __float_as_int(B.w) >> 4;
       const float bx = B.x - di.x, by = B.y - di.y, bz = B.z - di.z;
 #pragma unroll 4
       for (int k = 0; k < (1 << lgr); ++k) {
-        const float4 dj = v ? __ldg(Xd + abase + ((s0 + k) >> sh_t)) : far;
-        pair32_term<LJ>(c, bx + dj.x, by + dj.y, bz + dj.z, fx, fy, fz, ec, elj, vir, nev);
+        const float4 dj = __ldg(Xd + abase + ((s0 + k) >> sh_t));
+        pair32_term<LJ>(c, tab, bx + dj.x, by + dj.y, bz + dj.z, fx, fy, fz, ec, elj, vir, nev);
       }
     }
   }
 }
 
+// per-warp staging capacity: an item's entries plus the padding that the
+// two-ahead loads of the R1 walk reach (< 4 G for G groups); p32_lg_entries
+// keeps entries + 4 G within it
+constexpr int P32_STAGE = (1 << LG_P32_ENTRIES) + 32;
+
 __device__ __forceinline__ void b_k_pair32(const Dev& d, int bx) {
   (void)bx;
+  extern __shared__ float4 tab32[];  // the binary32 DSF table, 2 float4 per interval
   __shared__ float qqt[MT * MT], e4t[MT * MT], s2t[MT * MT], vrct[MT * MT], dvrct[MT * MT];
-  __shared__ float4 stage[PAIR_THREADS / 32][1 << LG_P32_ENTRIES];  // each warp's current item entries
+  __shared__ float4 stage[PAIR_THREADS / 32][P32_STAGE];  // each warp's current item entries
   __shared__ int tLg[MT], tOff[MT];
   const int nt = d.n_types;
   for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
@@ -853,12 +865,12 @@ __device__ __forceinline__ void b_k_pair32(const Dev& d, int bx) {
     tLg[e] = d.log2P[e];
     tOff[e] = d.off[e];
   }
+  for (int e = threadIdx.x; e < 2 * d.dsf_nint; e += blockDim.x) tab32[e] = d.dsf32[e];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int n_items = d.pctr[0];
-  const float rc = (float)d.rc, rc2 = (float)d.rc2;
-  const float alpha = (float)d.alpha, alpha2 = (float)(d.alpha * d.alpha);
-  const float g2a = (float)d.dsf_g, cf = (float)d.dsf_cf, c0 = (float)d.dsf_erfc_rc_over_rc;
+  const float rc = (float)d.rc, rc2 = (float)d.rc2, smin = (float)d.dsf_smin;
+  const int kbase = d.dsf_base - ((1023 - 127) << 6);
   for (;;) {
     int w = 0;
     if (lane == 0) w = atomicAdd(d.pctr + 1, 1);
@@ -881,47 +893,49 @@ __device__ __forceinline__ void b_k_pair32(const Dev& d, int bx) {
     const float4 di = d.Xd[oi + ((ai.row0 - oi) << lgPi) + b];
     const int k = ai.type * nt + t;
     P32Par c;
+    c.rc = rc;
+    c.rc2 = rc2;
+    c.smin = smin;
+    c.kbase = kbase;
     c.qq = qqt[k];
     c.e4 = e4t[k];
     c.s2 = s2t[k];
     c.vrc = vrct[k];
     c.dvrc = dvrct[k];
-    c.rc = rc;
-    c.rc2 = rc2;
-    c.pa = 0.3275911f * alpha;
-    c.nl2e = -alpha2 * 1.4426950408889634f;
-    c.g2a = g2a;
-    c.cf = cf;
-    c.c0 = c0;
     const float wgt = __int_as_float((127 - lgS) << 23);  // 1/P*
     float fx = 0.f, fy = 0.f, fz = 0.f, ec = 0.f, elj = 0.f, vir = 0.f;
     int nev = 0;
     const int sh_t = lgS - lgPt;
-    // stage the item's entries (<= 256, one coalesced copy), then walk them
+    const int G = 1 << lgG;
+    // stage the item's entries (<= 2^LG_P32_ENTRIES, one coalesced copy),
+    // padded with far entries of partner type t whose bead offsets are read
+    // from atom-major row 0 (a valid address), then walk them
     float4* buf = stage[threadIdx.x >> 5];
     const float4* lst = d.nlB + (size_t)i * d.nl_cap + e0;
     const int n = e1 - e0;
-    for (int x = lane; x < n; x += 32) buf[x] = __ldg(lst + x);
+    const float4 far = make_float4(0.f, 0.f, 1e4f, __int_as_float(t));
+    for (int x = lane; x < n + 4 * G; x += 32) buf[x] = x < n ? __ldg(lst + x) : far;
     __syncwarp();
-    const int G = 1 << lgG;
     if (c.e4 != 0.f) {
       if (lgr == 0)
-        pair32_entries<true, true>(buf, n, grp, G, 0, sh_t, d.Xd, b, di, c, fx, fy, fz, ec, elj, vir, nev);
+        pair32_entries<true, true>(buf, n, grp, G, 0, sh_t, d.Xd, b, di, c, tab32, fx, fy, fz, ec, elj, vir, nev);
       else
-        pair32_entries<true, false>(buf, n, grp, G, lgr, sh_t, d.Xd, b, di, c, fx, fy, fz, ec, elj, vir, nev);
+        pair32_entries<true, false>(buf, n, grp, G, lgr, sh_t, d.Xd, b, di, c, tab32, fx, fy, fz, ec, elj, vir, nev);
     } else {
       if (lgr == 0)
-        pair32_entries<false, true>(buf, n, grp, G, 0, sh_t, d.Xd, b, di, c, fx, fy, fz, ec, elj, vir, nev);
+        pair32_entries<false, true>(buf, n, grp, G, 0, sh_t, d.Xd, b, di, c, tab32, fx, fy, fz, ec, elj, vir, nev);
       else
-        pair32_entries<false, false>(buf, n, grp, G, lgr, sh_t, d.Xd, b, di, c, fx, fy, fz, ec, elj, vir, nev);
+        pair32_entries<false, false>(buf, n, grp, G, lgr, sh_t, d.Xd, b, di, c, tab32, fx, fy, fz, ec, elj, vir,
+                                     nev);
     }
     __syncwarp();  // the buffer is refilled by the next item
-    const float e4 = c.e4;
-    // lane partials (times 1/P*) to fixed point by bit assembly, then exact
-    // integer sums over the groups, which hold the same owner beads
+    // LJ items carry the total force; the others the force per unit charge
+    // product. Lane partials (times 1/P*) to fixed point by bit assembly,
+    // then exact integer sums over the groups, which hold the same owner beads
+    const float fs = (c.e4 != 0.f ? 1.0f : c.qq) * wgt;
     int bad = 0;
-    long long kx = fixs(f2d_bits(fx * wgt), 44, &bad), ky = fixs(f2d_bits(fy * wgt), 44, &bad),
-              kz = fixs(f2d_bits(fz * wgt), 44, &bad);
+    long long kx = fixs(f2d_bits(fx * fs), 44, &bad), ky = fixs(f2d_bits(fy * fs), 44, &bad),
+              kz = fixs(f2d_bits(fz * fs), 44, &bad);
     for (int o = 1 << lgPp; o < 32; o <<= 1) {
       kx += __shfl_xor_sync(0xffffffffu, kx, o);
       ky += __shfl_xor_sync(0xffffffffu, ky, o);
@@ -934,15 +948,14 @@ __device__ __forceinline__ void b_k_pair32(const Dev& d, int bx) {
       atomicAdd(fi + 2, (unsigned long long)kz);
     }
     // every term is seen from both of its atoms: energies carry a factor 1/2
-    long long kl = fixs(f2d_bits(elj * wgt), 39, &bad), kc = fixs(f2d_bits(ec * wgt), 39, &bad),
-              kv = fixs(f2d_bits(vir * wgt), 39, &bad);
+    long long kl = fixs(f2d_bits(elj * wgt), 39, &bad), kc = fixs(f2d_bits(ec * (c.qq * wgt)), 39, &bad),
+              kv = fixs(f2d_bits(vir * fs), 39, &bad);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       kl += __shfl_xor_sync(0xffffffffu, kl, o);
       kc += __shfl_xor_sync(0xffffffffu, kc, o);
       kv += __shfl_xor_sync(0xffffffffu, kv, o);
     }
-    nev = warp_sumi(nev);
     bad = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
       if (kl) atomicAdd(d.E_fix + E_LJ, (unsigned long long)kl);
@@ -950,7 +963,7 @@ __device__ __forceinline__ void b_k_pair32(const Dev& d, int bx) {
       if (kv) atomicAdd(d.E_fix + E_VIRIAL, (unsigned long long)kv);
       if (nev) {
         atomicAdd(d.E_fix + E_NEVAL, (unsigned long long)nev);
-        if (e4 != 0.f) atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nev);
+        if (c.e4 != 0.f) atomicAdd(d.E_fix + E_NLJEVAL, (unsigned long long)nev);
       }
       if (bad) atomicOr(d.err, ERR_NONFINITE);
     }
@@ -1311,7 +1324,8 @@ void pair_grids(int nt, int nint, int* g64, int* g32) {
   (void)nt;
   cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_pair64, PAIR64_THREADS, PAIR64_SMEM_PER_INTERVAL * (size_t)nint);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_pair32, PAIR_THREADS, 0);
+  cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_pair32, PAIR_THREADS, PAIR32_SMEM_PER_INTERVAL * (size_t)nint);
   *g64 = std::max(1, b64) * std::max(1, sms);
   *g32 = std::max(1, b32) * std::max(1, sms);
 }
@@ -1320,8 +1334,13 @@ int launch_pair(const Dev& d, cudaStream_t s) {
   const int wpb = PAIR_THREADS / 32;
   if (d.precision == MIXTS_FP32_FORCES) {
     if (d.n_nonp == 0) return 0;
+    static bool attr32 = false;
+    if (!attr32) {
+      cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      attr32 = true;
+    }
     k_list_seg32<<<(d.n_nonp + wpb - 1) / wpb, NL_THREADS, 0, s>>>(d);
-    k_pair32<<<d.pair32_grid, PAIR_THREADS, 0, s>>>(d);
+    k_pair32<<<d.pair32_grid, PAIR_THREADS, PAIR32_SMEM_PER_INTERVAL * (size_t)d.dsf_nint, s>>>(d);
     return 2;
   }
   if (d.n_pitems == 0) return 0;
@@ -1375,6 +1394,7 @@ int launch_forces_batched_part(const BatchGeom& g, cudaStream_t s, int part) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_pair64_b, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_pair32_b, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr = true;
   }
   const int r = g.nm + 1;
@@ -1391,7 +1411,7 @@ int launch_forces_batched_part(const BatchGeom& g, cudaStream_t s, int part) {
     if (g.blocks[BK_PAIRA] > 0) {
       if (g.precision == MIXTS_FP32_FORCES) {
         k_list_seg32_b<<<g.blocks[BK_PAIRA], NL_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
-        k_pair32_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, 0, s>>>(g.devs, pf(BK_PAIRB), g.nm);
+        k_pair32_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
       } else {
         k_pair_items_b<<<g.blocks[BK_PAIRA], ITEM_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
         k_pair64_b<<<g.blocks[BK_PAIRB], PAIR64_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);

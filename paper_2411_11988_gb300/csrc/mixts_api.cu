@@ -69,6 +69,7 @@ struct Plan {
   std::vector<double> bond_par, ang_par;
   std::vector<double> cm;
   std::vector<double> dsf;     // DSF interval table
+  std::vector<float> dsf32;    // its binary32 cubic form (FP32 forces)
   std::vector<double> charge, eps, sig, pp_sig, pp_A, pp_b;  // raw force-field parameters (theta variant)
   int dsf_nint = 0, dsf_elo = -2;
   std::vector<double> ps_tab;  // pseudopotential tables (electron systems)
@@ -96,7 +97,7 @@ struct Plan {
   size_t o_tab = 0, tab_bytes = 0;
   size_t o_ainfo, o_pos_atom, o_pos_mol, o_atom_of_tk, o_ainfo_atom, o_pos_of_atom, o_is_pseudo, o_pseudo_atom, o_pinfo,
       o_pairpar, o_pspar, o_bitems, o_bond_atoms, o_bond_par, o_ang_atoms, o_ang_par, o_cm, o_mc, o_tiles,
-      o_slot_type, o_dsf, o_pstab, o_pairpar_alt, o_pspar_alt, o_pc, o_gacc;
+      o_slot_type, o_dsf, o_dsf32, o_pstab, o_pairpar_alt, o_pspar_alt, o_pc, o_gacc;
   size_t o_state = 0, state_bytes = 0;
   size_t o_xd = 0, o_xia = 0;
   size_t o_pitems = 0, o_pctr = 0, o_nlb = 0, o_nlseg = 0, o_wrapn = 0;
@@ -135,33 +136,38 @@ void pseudo_at(const PseudoPar& pp, double r, double* v, double* dv) {
 // rc^2. Each quintic interpolates its function at the six Chebyshev nodes of
 // the interval (values in long double). Row layout: c0..c5 of G, then
 // c0..c5 of -2 G'.
-static void fit_quintic(const long double* tn, const long double* val, long double h, double* out) {
+template <int N>
+static void fit_poly(const long double* tn, const long double* val, long double h, double* out) {
   typedef long double LD;
-  LD A[6][7];
-  for (int i = 0; i < 6; ++i) {
+  LD A[N][N + 1];
+  for (int i = 0; i < N; ++i) {
     LD tp = 1.0L;
-    for (int j = 0; j < 6; ++j) {
+    for (int j = 0; j < N; ++j) {
       A[i][j] = tp;
       tp *= tn[i];
     }
-    A[i][6] = val[i];
+    A[i][N] = val[i];
   }
-  for (int c = 0; c < 6; ++c) {  // Gauss-Jordan, partial pivoting
+  for (int c = 0; c < N; ++c) {  // Gauss-Jordan, partial pivoting
     int pv = c;
-    for (int r = c + 1; r < 6; ++r)
+    for (int r = c + 1; r < N; ++r)
       if (fabsl(A[r][c]) > fabsl(A[pv][c])) pv = r;
-    for (int j = 0; j < 7; ++j) std::swap(A[c][j], A[pv][j]);
-    for (int r = 0; r < 6; ++r) {
+    for (int j = 0; j < N + 1; ++j) std::swap(A[c][j], A[pv][j]);
+    for (int r = 0; r < N; ++r) {
       if (r == c) continue;
       const LD f = A[r][c] / A[c][c];
-      for (int j = c; j < 7; ++j) A[r][j] -= f * A[c][j];
+      for (int j = c; j < N + 1; ++j) A[r][j] -= f * A[c][j];
     }
   }
   LD hk = 1.0L;
-  for (int j = 0; j < 6; ++j) {
-    out[j] = (double)(A[j][6] / A[j][j] / hk);
+  for (int j = 0; j < N; ++j) {
+    out[j] = (double)(A[j][N] / A[j][j] / hk);
     hk *= h;
   }
+}
+
+static void fit_quintic(const long double* tn, const long double* val, long double h, double* out) {
+  fit_poly<6>(tn, val, h, out);
 }
 
 // Interval table of a function of s = r^2 and of a second one (the force
@@ -212,8 +218,12 @@ static std::vector<double> pseudo_table(double kq, double sig, double A, double 
 }
 
 // shifted: the damped-shifted-force form; otherwise the Ewald real-space
-// kernel erfc(a r)/r (value and slope not shifted at rc)
-std::vector<double> dsf_table(double alpha, double rc, int elo, int* nint_out, bool shifted = true) {
+// kernel erfc(a r)/r (value and slope not shifted at rc). With tab32 also
+// the binary32 table of the FP32 pair sweep: per interval the cubics
+// (interpolating at four Chebyshev nodes) of the same two functions,
+// coefficients c0..c3 of G then c0..c3 of -2 G'.
+std::vector<double> dsf_table(double alpha, double rc, int elo, int* nint_out, bool shifted = true,
+                              std::vector<float>* tab32 = nullptr) {
   typedef long double LD;
   const LD a = alpha, R = rc;
   const LD pil = 3.141592653589793238462643383279502884L;
@@ -232,8 +242,10 @@ std::vector<double> dsf_table(double alpha, double rc, int elo, int* nint_out, b
   while (ldexp(1.0, ehi) <= rc * rc) ++ehi;
   const int nint = (ehi - elo) * 64;
   std::vector<double> tab(12 * (size_t)nint);
-  LD tn[6];
+  LD tn[6], tc[4];
   for (int i = 0; i < 6; ++i) tn[i] = (1.0L - cosl((2 * i + 1) * pil / 12.0L)) / 2.0L;
+  for (int i = 0; i < 4; ++i) tc[i] = (1.0L - cosl((2 * i + 1) * pil / 8.0L)) / 2.0L;
+  if (tab32) tab32->assign(8 * (size_t)nint, 0.0f);
   for (int k = 0; k < nint; ++k) {
     const int oct = k / 64, sub = k % 64;
     const LD s0 = ldexpl(1.0L + sub / 64.0L, elo + oct);
@@ -245,6 +257,16 @@ std::vector<double> dsf_table(double alpha, double rc, int elo, int* nint_out, b
     }
     fit_quintic(tn, v, h, &tab[12 * (size_t)k]);
     fit_quintic(tn, dv, h, &tab[12 * (size_t)k + 6]);
+    if (tab32) {
+      double c[8];
+      for (int i = 0; i < 4; ++i) {
+        v[i] = G(s0 + tc[i] * h);
+        dv[i] = dG(s0 + tc[i] * h);
+      }
+      fit_poly<4>(tc, v, h, c);
+      fit_poly<4>(tc, dv, h, c + 4);
+      for (int j = 0; j < 8; ++j) (*tab32)[8 * (size_t)k + j] = (float)c[j];
+    }
   }
   *nint_out = nint;
   return tab;
@@ -442,7 +464,8 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
     p.ang_par.push_back(s->angle_theta0[g]);
     for (int sl = 0; sl < Ps; ++sl) p.bitems.push_back(BondItem{1, g, sl, 0});
   }
-  p.dsf = dsf_table(prm->dsf_alpha, prm->r_cut, p.dsf_elo, &p.dsf_nint, prm->coulomb != 1);
+  p.dsf = dsf_table(prm->dsf_alpha, prm->r_cut, p.dsf_elo, &p.dsf_nint, prm->coulomb != 1,
+                    prm->precision == MIXTS_FP32_FORCES ? &p.dsf32 : nullptr);
   if (prm->coulomb != 0 && prm->coulomb != 1) {
     fail(p, MIXTS_ERR_ARG, "coulomb must be 0 (damped shifted force) or 1 (Ewald)");
     return p;
@@ -642,6 +665,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_tiles = A.add(sizeof(PropTile) * std::max<size_t>(1, p.tiles.size()));
   p.o_slot_type = A.add(sizeof(int) * std::max<size_t>(1, p.slot_type.size()));
   p.o_dsf = A.add(sizeof(double) * p.dsf.size());
+  p.o_dsf32 = A.add(sizeof(float) * std::max<size_t>(8, p.dsf32.size()));
   p.o_pstab = A.add(sizeof(double) * std::max<size_t>(1, p.ps_tab.size()));
   p.o_pairpar_alt = A.add(sizeof(PairPar) * MT * MT);
   p.o_pspar_alt = A.add(sizeof(PseudoPar) * MT);
@@ -899,6 +923,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   put(img, p.o_tiles, p.tiles);
   put(img, p.o_slot_type, p.slot_type);
   put(img, p.o_dsf, p.dsf);
+  if (!p.dsf32.empty()) put(img, p.o_dsf32, p.dsf32);
   if (!p.ps_tab.empty()) put(img, p.o_pstab, p.ps_tab);
   if (p.n_kvec > 0) {
     put(img, p.o_kvec, p.kvec);
@@ -961,6 +986,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.dsf_cf = erfc(prm->dsf_alpha * prm->r_cut) / (prm->r_cut * prm->r_cut) +
              d.dsf_g * exp(-prm->dsf_alpha * prm->dsf_alpha * prm->r_cut * prm->r_cut) / prm->r_cut;
   d.dsf_tab = (const double*)(h->ws + p.o_dsf);
+  d.dsf32 = (const float4*)(h->ws + p.o_dsf32);
   if (prm->coulomb == 1) {  // Ewald real space: erfc(a r)/r, no shift at r_cut
     d.dsf_erfc_rc_over_rc = 0.0;
     d.dsf_cf = 0.0;
@@ -1541,7 +1567,9 @@ static mixts_status batch_upload(mixts_handle h) {
     batch_block_counts(devs[m], c);
     for (int k = 0; k < BK_KINDS; ++k) pfx[(size_t)k * (nm + 1) + m + 1] = pfx[(size_t)k * (nm + 1) + m] + c[k];
     g.prop_smem = std::max(g.prop_smem, batch_prop_smem(devs[m]));
-    g.pair_smem = std::max(g.pair_smem, (size_t)(6 * sizeof(double) + 8 * sizeof(float)) * (size_t)devs[m].dsf_nint);
+    g.pair_smem = std::max(g.pair_smem, (devs[m].precision == MIXTS_FP32_FORCES ? (size_t)8 * sizeof(float)
+                                                                                 : (size_t)(6 * sizeof(double) + 8 * sizeof(float))) *
+                                             (size_t)devs[m].dsf_nint);
   }
   for (int k = 0; k < BK_KINDS; ++k) g.blocks[k] = pfx[(size_t)k * (nm + 1) + nm];
   g.devs = (const Dev*)h->bdev;

@@ -106,6 +106,7 @@ struct Dev {
   double dsf_erfc_rc_over_rc, dsf_cf, dsf_g;
   // DSF interval table: s in [dsf_smin, 2^e_hi), 64 sub-intervals per octave
   const double* dsf_tab;
+  const float4* dsf32;      // binary32 cubics (FP32 forces): [G c0..c3][-2G' c0..c3] per interval
   int dsf_nint, dsf_base;   // interval count; (1023 + e_lo) << 6
   double dsf_smin;          // 2^e_lo
   // pseudopotential interval tables, one per site type (same layout as the
