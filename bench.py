@@ -85,6 +85,27 @@ def ncu_pipe_pct(kernel):
     return None
 
 
+def ncu_dram_bytes(kernel):
+    """DRAM bytes (read + write) per launch of `kernel` from the ncu capture in
+    its committed profile summary, with the file it came from."""
+    import glob
+    import re
+    units = {"B": 1.0, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
+        total, seen = 0.0, False
+        for line in open(f):
+            if not line.startswith("| dram__bytes_"):
+                continue
+            cells = line.split("|")
+            vals = re.findall(r"([\d.]+)\s*(GB|MB|KB|B)\b", cells[2])
+            for v, u in vals[:2]:
+                total += float(v) * units[u]
+            seen = seen or bool(vals)
+        if seen:
+            return total, os.path.relpath(f, ROOT)
+    return None, None
+
+
 def ns_per_day(ms_per_step, dt=DT):
     return (1000.0 / ms_per_step) * dt * 86400.0 * 1e-6
 
@@ -640,6 +661,9 @@ def main():
 
     if rank == 0:
         per_phase = {k: ph_ms[k] / max(1, ph_calls[k]) for k in ph_ms if ph_calls[k]}
+        # DRAM bytes per launch from the kernel's committed ncu summary
+        # (L2-resident working set: far below the bytes the kernel touches)
+        traffic, traffic_src = ncu_dram_bytes(kname)
         line = {
             "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -655,7 +679,8 @@ def main():
             "observables": obs,
             "mixts_speedup_vs_uniform": (uni["ms_per_step"] / step_ms) if uni else None,
             "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": traffic_src,
                          "peak_source": peak_src, "peak_nominal": peak_nom,
                          "frac_of_nominal": achieved / peak_nom, "flops_per_launch": flops, "launch_ms": pair_ms,
                          "ncu": ncu_pipe_pct(kname)},
