@@ -782,9 +782,10 @@ struct mixts_ctx {
   int graph_steps = 10;
   bool capturing = false;
   bool list_valid = false;  // neighbour lists and position mirrors match the current q
-  // large-P propagation beside the small-P tiles (both kinds present)
+  // bonded and pseudopotential terms beside the pair sweep, large-P
+  // propagation beside the small-P tiles
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_list = nullptr, ev_join = nullptr;
 };
 
 static void timer_fold(mixts_handle h) {
@@ -1119,30 +1120,54 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   return MIXTS_OK;
 }
 
+// Forces at the current positions. With the side stream (steps; not the
+// per-phase timing mode) the bonded terms run beside the neighbour search
+// and pair sweep, and the pseudopotential sweep beside the pair sweep once
+// its list exists: every kernel adds into the fixed-point accumulators with
+// integer atomics, so the sums are the same in any order.
 static mixts_status eval_forces(mixts_handle h) {
   const Dev& d = h->d;
   cudaStream_t s = h->stream;
   h->list_valid = true;
+  const bool par = h->side && h->ev_list && !h->tm.on;
+  if (par) {
+    cudaEventRecord(h->ev_fork, s);
+    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    h->kernels += launch_bonded(d, h->side, h->ainfo_atom);
+  }
   phase(h, 0, [&] { return launch_nlist(d, s, h->atom_is_pseudo); });
+  if (par) {
+    cudaEventRecord(h->ev_list, s);
+    cudaStreamWaitEvent(h->side, h->ev_list, 0);
+    h->kernels += launch_pseudo(d, h->side);
+  }
   phase(h, 1, [&] { return launch_pair(d, s) + launch_ewald(d, s); });
-  phase(h, 2, [&] { return launch_bonded(d, s, h->ainfo_atom); });
-  phase(h, 3, [&] { return launch_pseudo(d, s); });
+  if (par) {
+    cudaEventRecord(h->ev_join, h->side);
+    cudaStreamWaitEvent(s, h->ev_join, 0);
+  } else {
+    phase(h, 2, [&] { return launch_bonded(d, s, h->ainfo_atom); });
+    phase(h, 3, [&] { return launch_pseudo(d, s); });
+  }
   return cuda_check(h, cudaGetLastError(), "force launch");
 }
 
-// the side stream of the large-P clusters, made by the step prologue
-// (eager, before any capture; a bare force evaluation never needs it);
-// without it the two kinds of tiles run one after the other
+// the side stream (with its fork, list and join events) of the force terms
+// that run beside the pair sweep and of the large-P clusters, made by the
+// step prologue (eager, before any capture; a bare force evaluation never
+// makes it); without it everything runs in order on the handle's stream
 static void ensure_side(mixts_handle h) {
-  if (!h->side && h->d.n_tiles > 0 && h->d.n_big_tiles > 0) {
+  if (!h->side) {
     if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_list, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       if (h->side) cudaStreamDestroy(h->side);
       if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+      if (h->ev_list) cudaEventDestroy(h->ev_list);
       h->side = nullptr;
-      h->ev_fork = h->ev_join = nullptr;
+      h->ev_fork = h->ev_list = h->ev_join = nullptr;
     }
   }
 }
@@ -1472,6 +1497,7 @@ void mixts_destroy(mixts_handle h) {
     cudaStreamDestroy(h->side);
   }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_list) cudaEventDestroy(h->ev_list);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
