@@ -785,7 +785,8 @@ struct mixts_ctx {
   // bonded and pseudopotential terms beside the pair sweep, large-P
   // propagation beside the small-P tiles
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_list = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_list = nullptr, ev_join = nullptr, ev_post = nullptr, ev_fin = nullptr;
+  bool fin_pending = false;  // a finalisation on the side stream not yet joined
 };
 
 static void timer_fold(mixts_handle h) {
@@ -1129,7 +1130,7 @@ static mixts_status eval_forces(mixts_handle h) {
   const Dev& d = h->d;
   cudaStream_t s = h->stream;
   h->list_valid = true;
-  const bool par = h->side && h->ev_list && !h->tm.on;
+  const bool par = h->side && !h->tm.on;
   if (par) {
     cudaEventRecord(h->ev_fork, s);
     cudaStreamWaitEvent(h->side, h->ev_fork, 0);
@@ -1140,6 +1141,10 @@ static mixts_status eval_forces(mixts_handle h) {
     cudaEventRecord(h->ev_list, s);
     cudaStreamWaitEvent(h->side, h->ev_list, 0);
     h->kernels += launch_pseudo(d, h->side);
+  }
+  if (h->fin_pending) {  // the previous step's finalisation clears the energy accumulators
+    cudaStreamWaitEvent(s, h->ev_fin, 0);
+    h->fin_pending = false;
   }
   phase(h, 1, [&] { return launch_pair(d, s) + launch_ewald(d, s); });
   if (par) {
@@ -1161,13 +1166,15 @@ static void ensure_side(mixts_handle h) {
     if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_list, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_post, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fin, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       if (h->side) cudaStreamDestroy(h->side);
-      if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-      if (h->ev_list) cudaEventDestroy(h->ev_list);
+      for (cudaEvent_t e : {h->ev_fork, h->ev_list, h->ev_join, h->ev_post})
+        if (e) cudaEventDestroy(e);
       h->side = nullptr;
-      h->ev_fork = h->ev_list = h->ev_join = nullptr;
+      h->ev_fork = h->ev_list = h->ev_join = h->ev_post = h->ev_fin = nullptr;
     }
   }
 }
@@ -1176,8 +1183,27 @@ static void prop(mixts_handle h, int mode) {
   phase(h, 4, [&] { return launch_prop(h->d, h->stream, mode, h->side, h->ev_fork, h->ev_join); });
 }
 
+// step finalisation; with the side stream it runs there, beside the next
+// step's neighbour search, and the next pair sweep (the first kernel that
+// adds to the energy accumulators it clears) or the end of mixts_step waits
+// for it
 static void fin(mixts_handle h, int mode) {
+  if (h->side && !h->tm.on) {
+    cudaEventRecord(h->ev_post, h->stream);
+    cudaStreamWaitEvent(h->side, h->ev_post, 0);
+    h->kernels += launch_final(h->d, h->side, mode, h->slot_type);
+    cudaEventRecord(h->ev_fin, h->side);
+    h->fin_pending = true;
+    return;
+  }
   phase(h, 5, [&] { return launch_final(h->d, h->stream, mode, h->slot_type); });
+}
+
+static void fin_join(mixts_handle h) {
+  if (h->fin_pending) {
+    cudaStreamWaitEvent(h->stream, h->ev_fin, 0);
+    h->fin_pending = false;
+  }
 }
 
 mixts_status mixts_forces(mixts_handle h, double* energy_host) {
@@ -1254,6 +1280,7 @@ mixts_status mixts_step(mixts_handle h, int n_steps) {
   eval_forces(h);
   prop(h, PM_END | PM_EST | PM_PCART);
   fin(h, PM_END | PM_EST);
+  fin_join(h);
   h->steps_done += n_steps;
   return cuda_check(h, cudaGetLastError(), "step launch");
 }
@@ -1499,6 +1526,8 @@ void mixts_destroy(mixts_handle h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_list) cudaEventDestroy(h->ev_list);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_post) cudaEventDestroy(h->ev_post);
+  if (h->ev_fin) cudaEventDestroy(h->ev_fin);
   delete h;
 }
 
