@@ -81,14 +81,68 @@ __device__ double reduce_spread_kind(const Dev& d, const int* atom_is_pseudo, in
 
 constexpr int NL_THREADS = 256;
 
+// cell of a wrapped bead-0 reference (binary32 position in [0, L))
+__device__ __forceinline__ int cell_of(float4 r, float inv_side, int nc) {
+  const int cx = min(max((int)(r.x * inv_side), 0), nc - 1);
+  const int cy = min(max((int)(r.y * inv_side), 0), nc - 1);
+  const int cz = min(max((int)(r.z * inv_side), 0), nc - 1);
+  return (cx * nc + cy) * nc + cz;
+}
+
 // Once per list build: d_max of sites and of pseudo particles, the two list
 // radii (binary64, in the order the definition states), and cleared row
-// counters. thresh: [0] d_max, [1] R, [2] d_max pseudo, [3] R pseudo.
+// counters. thresh: [0] d_max, [1] R, [2] d_max pseudo, [3] R pseudo. With
+// a cell grid, also the atoms sorted by cell (a counting sort in shared
+// memory; the order inside a cell is arbitrary) and whether this step's
+// radius fits the cell side.
 __device__ __forceinline__ void b_k_list_prep(const Dev& d, int bx) {
   (void)bx;
   __shared__ long long red[32];
+  __shared__ int ccnt[NC_MAX * NC_MAX * NC_MAX];
+  __shared__ int wtot[32];
   const double ds = reduce_spread_kind(d, d.atom_is_pseudo, 0, red);
   const double dp = reduce_spread_kind(d, d.atom_is_pseudo, 1, red);
+  if (d.nc > 0) {
+    const int nc = d.nc, ncell = nc * nc * nc;
+    const float inv_side = (float)(nc / d.box);
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) ccnt[c] = 0;
+    __syncthreads();
+    for (int a = threadIdx.x; a < d.n_nonp; a += blockDim.x) atomicAdd(&ccnt[cell_of(d.reff[a], inv_side, nc)], 1);
+    __syncthreads();
+    // exclusive scan over the cells: each thread a contiguous run of cells
+    const int per = (ncell + blockDim.x - 1) / blockDim.x;
+    const int c0 = threadIdx.x * per, c1 = min(c0 + per, ncell);
+    int run = 0;
+    for (int c = c0; c < c1; ++c) run += ccnt[c];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = run;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wtot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int v = lane < (int)(blockDim.x >> 5) ? wtot[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      wtot[lane] = v;
+    }
+    __syncthreads();
+    int start = (wid > 0 ? wtot[wid - 1] : 0) + incl - run;
+    for (int c = c0; c < c1; ++c) {
+      const int n = ccnt[c];
+      d.cell_start[c] = start;
+      ccnt[c] = start;  // next free slot of the cell
+      start += n;
+    }
+    if (threadIdx.x == 0) d.cell_start[ncell] = d.n_nonp;
+    __syncthreads();
+    for (int a = threadIdx.x; a < d.n_nonp; a += blockDim.x)
+      d.cell_atoms[atomicAdd(&ccnt[cell_of(d.reff[a], inv_side, nc)], 1)] = a;
+  }
   for (int i = threadIdx.x; i < d.n_nonp; i += blockDim.x) d.nl_cnt[i] = 0;
   for (int i = threadIdx.x; i < d.n_pseudo; i += blockDim.x) d.pl_cnt[i] = 0;
   if (threadIdx.x < 2) d.pctr[threadIdx.x] = 0;  // pair items of the new list, and their hand-out counter
@@ -100,6 +154,9 @@ __device__ __forceinline__ void b_k_list_prep(const Dev& d, int bx) {
     d.thresh[1] = R;
     d.thresh[2] = dp;
     d.thresh[3] = Rp;
+    // cells: every pair within R lies in neighbouring cells when R fits the
+    // side (with room for the binary32 cell assignment)
+    if (d.nc > 0) *d.cell_ok = __dadd_rn(R, 1e-3) <= L / d.nc ? 1 : 0;
     // binary32 screen constants of both lists: R^2 -/+ margin, linear radius
     float* tf = (float*)(d.thresh + 4);
     const double RR[2] = {R, Rp};
@@ -122,12 +179,20 @@ __global__ void k_list_prep_b(const Dev* __restrict__ devs, const int* __restric
   b_k_list_prep(d, bx);
 }
 
-// One warp per (owner row, chunk of 32 * nl_cpl candidates); entries are
-// appended with a per-row counter, so the row order is arbitrary.
+// parts of one owner row's candidate search: the 27 neighbouring cells with
+// a cell grid, otherwise chunks of 32 * nl_cpl candidates
+__host__ __device__ __forceinline__ int nlist_parts(const Dev& d) {
+  return d.nc > 0 ? 27 : (d.n_nonp + 32 * d.nl_cpl - 1) / (32 * d.nl_cpl);
+}
+
+// One warp per (owner row, part of its candidates): a neighbouring cell of
+// the row's atom, or (all pairs, or a step whose radius exceeds the cell
+// side) a contiguous range of candidates. Entries are appended with a
+// per-row counter, so the row order is arbitrary.
 __device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
   const int lane = threadIdx.x & 31;
   const int w = (bx * blockDim.x + threadIdx.x) >> 5;
-  const int nchunk = (d.n_nonp + 32 * d.nl_cpl - 1) / (32 * d.nl_cpl);
+  const int nchunk = nlist_parts(d);
   const int i = w / nchunk;
   const int chunk = w - i * nchunk;
   if (i >= d.n_nonp) return;
@@ -144,15 +209,36 @@ __device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
   const int Pi = __float_as_int(ri.w);
   const int moli = d.pos_mol[i];
   int* row = d.nl + (size_t)i * d.nl_cap;
-  const int cpl = d.nl_cpl;
-  const int c0 = chunk * 32 * cpl;
+  // this warp's candidates: cand(k) for k < len
+  const bool cells = d.nc > 0 && *d.cell_ok;
+  int c0, len;
+  const int* cand = nullptr;
+  if (cells) {
+    const int nc = d.nc;
+    const int ci = cell_of(ri, (float)(nc / L), nc);
+    const int cx = ci / (nc * nc), cy = (ci / nc) % nc, cz = ci % nc;
+    const int nx = (cx + chunk / 9 - 1 + nc) % nc, ny = (cy + (chunk / 3) % 3 - 1 + nc) % nc,
+              nz = (cz + chunk % 3 - 1 + nc) % nc;
+    const int cell = (nx * nc + ny) * nc + nz;
+    c0 = d.cell_start[cell];
+    len = d.cell_start[cell + 1] - c0;
+    cand = d.cell_atoms + c0;
+  } else if (d.nc > 0) {  // cell grid, radius too large this step: 27 ranges of all pairs
+    const int per = (d.n_nonp + 26) / 27;
+    c0 = chunk * per;
+    len = max(0, min(per, d.n_nonp - c0));
+  } else {
+    c0 = chunk * 32 * d.nl_cpl;
+    len = max(0, min(32 * d.nl_cpl, d.n_nonp - c0));
+  }
   constexpr int MAXE = 8;  // entries one lane keeps per candidate (images)
 #pragma unroll 1
-  for (int t = 0; t < cpl; ++t) {
-    const int c = c0 + t * 32 + lane;
+  for (int t = 0; t < len; t += 32) {
+    const int k = t + lane;
+    const int c = k < len ? (cand ? cand[k] : c0 + k) : -1;
     int ne = 0;
     int ents[MAXE];
-    if (c < d.n_nonp && c != i) {
+    if (c >= 0 && c != i) {
       const float4 rc4 = d.reff[c];
       const int Pc = __float_as_int(rc4.w);
       bool own;
@@ -1302,8 +1388,7 @@ int launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo) {
   (void)atom_is_pseudo;  // carried in d
   k_list_prep<<<1, 1024, 0, s>>>(d);
   if (d.n_nonp > 0) {
-    const int nchunk = (d.n_nonp + 32 * d.nl_cpl - 1) / (32 * d.nl_cpl);
-    const long long warps = (long long)d.n_nonp * nchunk;
+    const long long warps = (long long)d.n_nonp * nlist_parts(d);
     const int wpb = NL_THREADS / 32;
     k_nlist<<<(int)((warps + wpb - 1) / wpb), NL_THREADS, 0, s>>>(d);
     ++n;
@@ -1371,8 +1456,7 @@ void batch_block_counts(const Dev& d, int* c) {
   const int wpb = PAIR_THREADS / 32;
   c[BK_PREP] = 1;
   if (d.n_nonp > 0) {
-    const int nchunk = (d.n_nonp + 32 * d.nl_cpl - 1) / (32 * d.nl_cpl);
-    c[BK_NLIST] = (int)(((long long)d.n_nonp * nchunk + NL_THREADS / 32 - 1) / (NL_THREADS / 32));
+    c[BK_NLIST] = (int)(((long long)d.n_nonp * nlist_parts(d) + NL_THREADS / 32 - 1) / (NL_THREADS / 32));
     if (d.precision == MIXTS_FP32_FORCES) {
       c[BK_PAIRA] = (d.n_nonp + wpb - 1) / wpb;
       c[BK_PAIRB] = d.pair32_grid;

@@ -88,6 +88,8 @@ struct Plan {
   int n_small_tiles = 0, big_cl = 1;
   std::vector<int> slot_type;
   int nl_cap = 0, pl_cap = 0;
+  int nc = 0;  // cells per side of the neighbour search (0: all pairs)
+  size_t o_cstart = 0, o_catoms = 0, o_cok = 0;
   int n_classes = 0;
   int cls_P[MAX_CLASSES], cls_log2P[MAX_CLASSES], cls_pos0[MAX_CLASSES], cls_n[MAX_CLASSES],
       cls_item0[MAX_CLASSES + 1];
@@ -610,6 +612,13 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
       for (int r = 0; r < p.big_cl; ++r) p.slot_type.push_back(t);
     }
   }
+  // cell list of the neighbour search: cells at least r_cut + 2 A wide (the
+  // list radius is r_cut + 2 d_max; a step whose radius exceeds the cell
+  // side searches all pairs instead), used when at least 3 fit per side
+  {
+    const int nc = (int)floor(s->box / (prm->r_cut + 2.0));
+    p.nc = nc >= 3 ? std::min(nc, NC_MAX) : 0;
+  }
   // neighbour-list capacities
   const double vol = s->box * s->box * s->box;
   const double rho = p.n_nonp / vol;
@@ -698,6 +707,9 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   p.o_spread = A.add(sizeof(double) * (size_t)p.na);
   p.o_nl = A.add(sizeof(int) * (size_t)std::max(1, p.n_nonp) * p.nl_cap);
   p.o_nlcnt = A.add(sizeof(int) * std::max(1, p.n_nonp));
+  p.o_cstart = A.add(sizeof(int) * ((size_t)p.nc * p.nc * p.nc + 1));
+  p.o_catoms = A.add(sizeof(int) * std::max(1, p.n_nonp));
+  p.o_cok = A.add(sizeof(int));
   {  // FP64 pair items: at most every row's slice blocks times 32-entry chunks of a full row
     const int lgM = p.n_classes > 0 ? p.cls_log2P[0] : 0;
     const size_t nsbm = lgM > 5 ? (size_t)1 << (lgM - 5) : 1;
@@ -1103,6 +1115,10 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   }
   d.nl = (int*)(w + p.o_nl);
   d.nl_cnt = (int*)(w + p.o_nlcnt);
+  d.nc = p.nc;
+  d.cell_start = (int*)(w + p.o_cstart);
+  d.cell_atoms = (int*)(w + p.o_catoms);
+  d.cell_ok = (int*)(w + p.o_cok);
   d.pitems = (int2*)(w + p.o_pitems);
   d.pctr = (int*)(w + p.o_pctr);
   d.nlB = p.o_nlb ? (float4*)(w + p.o_nlb) : nullptr;

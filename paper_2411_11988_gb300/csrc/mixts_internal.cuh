@@ -13,6 +13,7 @@ constexpr int MT = MIXTS_MAX_TYPES;
 constexpr int MAX_CLASSES = 12;
 constexpr int SMALL_P = 64;     // types with P <= SMALL_P propagate in one fused tile kernel
 constexpr int BIG_MAXA = 64;    // atoms per large-P propagation tile at most
+constexpr int NC_MAX = 16;      // cells per side of the neighbour search at most (NC_MAX^3 counted in shared memory)
 constexpr int BIG_CL_MAX = 16;  // CTAs per large-P tile (one thread-block cluster) at most
 constexpr int BIG_SMEM_TARGET = 100 * 1024;  // per-CTA shared memory of a large-P tile at most
 constexpr int PROP_SMEM_MAX = 200 * 1024;
@@ -195,6 +196,11 @@ struct Dev {
   double* spread;              // [n_atoms] max |q_b - q_0|
   int* nl;                     // [n_nonp*nl_cap] (partner position << 7) | image code
   int* nl_cnt;                 // [n_nonp]
+  // cell list of the neighbour search (nc >= 3 cells per side; 0: all pairs)
+  int nc;                      // cells per side, cell side L / nc
+  int* cell_start;             // [nc^3 + 1] first sorted slot of each cell
+  int* cell_atoms;             // [n_nonp] atom positions ordered by cell
+  int* cell_ok;                // 1 when this step's list radius fits the cell side
   int* pl;                     // [n_pseudo*pl_cap]
   int* pl_cnt;                 // [n_pseudo]
   double* thresh;              // [4] d_max, list radius, d_max pseudo, pseudo radius

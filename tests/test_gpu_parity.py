@@ -135,6 +135,36 @@ def test_step_path_spread_and_lists(gpu, P_e):
     m.close()
 
 
+@pytest.mark.parametrize("case", ["cells", "cells_fallback"])
+def test_cell_list_search(gpu, case):
+    """A box at least three list radii wide is searched through its 27
+    neighbouring cells (r_cut = 6 A in the 24.83 A box: 3 cells of 8.28 A);
+    a step whose list radius r_cut + 2 d_max exceeds the cell side (bead
+    spreads above 1.14 A) searches all pairs instead. Either way the lists
+    equal the oracle's bit for bit, the forces agree at 1e-11, and one step
+    (lists rebuilt from the propagation kernel's spreads) matches."""
+    rc = 6.0
+    s = synth.water_box(512, 24.83, 2, 1, seed=21)
+    if case == "cells_fallback":
+        s.q = s.q + np.random.default_rng(22).normal(0, 0.45, s.q.shape)
+    m = gpu.MixTS(s, r_cut=rc, T=300.0, dt=0.1, tau=100.0, seed=11)
+    m.forces()
+    tl, th = m.nlist(0)
+    ol, dmax, R = oracle.nlist(s, r_cut=rc)
+    assert th[0] == dmax and th[1] == R
+    assert (R + 1e-3 <= 24.83 / 3) == (case == "cells")
+    assert np.array_equal(canonical(tl), ol)
+    F_or = oracle.forces(s, r_cut=rc)[0]
+    assert _force_err(m.f.cpu().numpy(), F_or) < FTOL
+    m.step(1)
+    run = oracle.Runner(s, oracle.make_params(T=300.0, dt=0.1, tau=100.0, lam=1.0, seed=11), r_cut=rc)
+    run.step(1)
+    q = m.q.cpu().numpy()
+    assert np.abs(q - run.q).max() < 1e-11 * np.abs(run.q).max()
+    assert _force_err(m.f.cpu().numpy(), run.F) < 1e-10
+    m.close()
+
+
 def test_gaussians_bit_exact(gpu):
     s = _c1()
     m = gpu.MixTS(s, seed=987654321)
