@@ -55,6 +55,11 @@ __device__ __forceinline__ float screen_margin(double L, double R) {
 // 2^23 + k has k in its mantissa bits.
 __device__ __forceinline__ float img_of(int k) { return __int_as_float(0x4B000000 | k) - 8388610.0f; }
 
+// bit k of the result when |d + (k - 2) L| < Rlin for the one image k
+__device__ __forceinline__ unsigned img_bit(float dd, int k, float Lf, float Rlin) {
+  return fabsf(dd + img_of(k) * Lf) < Rlin ? 1u << k : 0u;
+}
+
 // bit k of the result is set when |d + (k - 2) L| < Rlin, k = 0..4
 __device__ __forceinline__ unsigned img_mask(float dd, float Lf, float Rlin) {
   unsigned m = 0;
@@ -81,11 +86,19 @@ __device__ double reduce_spread_kind(const Dev& d, const int* atom_is_pseudo, in
 
 constexpr int NL_THREADS = 256;
 
-// cell of a wrapped bead-0 reference (binary32 position in [0, L))
+// integer part of 0 <= v < 2^22 without a conversion instruction (those
+// share the slow FP64 unit): (v - 1/2) + 2^23 rounds to floor(v) in the
+// mantissa bits (a tie at an integer v may give v - 1, harmless for cells)
+__device__ __forceinline__ int floor_small(float v) {
+  return __float_as_int(__fadd_rn(__fadd_rn(v, -0.5f), 8388608.0f)) - 0x4B000000;
+}
+
+// cell of a wrapped bead-0 reference (binary32 position in [0, L)); the
+// list-prep sort and the search use this one function
 __device__ __forceinline__ int cell_of(float4 r, float inv_side, int nc) {
-  const int cx = min(max((int)(r.x * inv_side), 0), nc - 1);
-  const int cy = min(max((int)(r.y * inv_side), 0), nc - 1);
-  const int cz = min(max((int)(r.z * inv_side), 0), nc - 1);
+  const int cx = min(max(floor_small(r.x * inv_side), 0), nc - 1);
+  const int cy = min(max(floor_small(r.y * inv_side), 0), nc - 1);
+  const int cz = min(max(floor_small(r.z * inv_side), 0), nc - 1);
   return (cx * nc + cy) * nc + cz;
 }
 
@@ -104,7 +117,7 @@ __device__ __forceinline__ void b_k_list_prep(const Dev& d, int bx) {
   const double dp = reduce_spread_kind(d, d.atom_is_pseudo, 1, red);
   if (d.nc > 0) {
     const int nc = d.nc, ncell = nc * nc * nc;
-    const float inv_side = (float)(nc / d.box);
+    const float inv_side = d.cell_inv;
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) ccnt[c] = 0;
     __syncthreads();
     for (int a = threadIdx.x; a < d.n_nonp; a += blockDim.x) atomicAdd(&ccnt[cell_of(d.reff[a], inv_side, nc)], 1);
@@ -154,6 +167,8 @@ __device__ __forceinline__ void b_k_list_prep(const Dev& d, int bx) {
     d.thresh[1] = R;
     d.thresh[2] = dp;
     d.thresh[3] = Rp;
+    d.thresh[10] = __dmul_rn(R, R);
+    d.thresh[11] = __dmul_rn(Rp, Rp);
     // cells: every pair within R lies in neighbouring cells when R fits the
     // side (with room for the binary32 cell assignment)
     if (d.nc > 0) *d.cell_ok = __dadd_rn(R, 1e-3) <= L / d.nc ? 1 : 0;
@@ -179,6 +194,23 @@ __global__ void k_list_prep_b(const Dev* __restrict__ devs, const int* __restric
   b_k_list_prep(d, bx);
 }
 
+constexpr int NL_EBUF = 32 * 8;  // staged entries per warp of the search (one round's worst case)
+
+// appends a warp's staged entries to row i with one reservation
+__device__ __forceinline__ void nlist_flush(const Dev& d, int i, int* row, const int* eb, int nb, int lane) {
+  if (nb == 0) return;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(&d.nl_cnt[i], nb);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int k = lane; k < nb; k += 32) {
+    if (base + k < d.nl_cap)
+      row[base + k] = eb[k];
+    else
+      atomicOr(d.err, ERR_NLIST);
+  }
+  __syncwarp();
+}
+
 // parts of one owner row's candidate search: the 27 neighbouring cells with
 // a cell grid, otherwise chunks of 32 * nl_cpl candidates
 __host__ __device__ __forceinline__ int nlist_parts(const Dev& d) {
@@ -202,7 +234,7 @@ __device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
     return;
   }
   const double L = d.box;
-  const double R2 = __dmul_rn(d.thresh[1], d.thresh[1]);
+  const double R2 = d.thresh[10];
   const float R2lo = tf.x, R2hi = tf.y, Rlin = tf.z;
   const float Lf = ((const float*)(d.thresh + 4))[8];
   const float4 ri = d.reff[i];
@@ -213,12 +245,18 @@ __device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
   const bool cells = d.nc > 0 && *d.cell_ok;
   int c0, len;
   const int* cand = nullptr;
+  int kxc = 0, kyc = 0, kzc = 0;  // cells: the one image code per axis that can lie within R
   if (cells) {
     const int nc = d.nc;
-    const int ci = cell_of(ri, (float)(nc / L), nc);
+    const int ci = cell_of(ri, d.cell_inv, nc);
     const int cx = ci / (nc * nc), cy = (ci / nc) % nc, cz = ci % nc;
-    const int nx = (cx + chunk / 9 - 1 + nc) % nc, ny = (cy + (chunk / 3) % 3 - 1 + nc) % nc,
-              nz = (cz + chunk % 3 - 1 + nc) % nc;
+    const int ux = cx + chunk / 9 - 1, uy = cy + (chunk / 3) % 3 - 1, uz = cz + chunk % 3 - 1;
+    // a neighbouring cell across a box face holds its atoms' images one L
+    // away; with cells at least R wide no other image is within R
+    kxc = 2 + (ux < 0 ? -1 : (ux >= nc ? 1 : 0));
+    kyc = 2 + (uy < 0 ? -1 : (uy >= nc ? 1 : 0));
+    kzc = 2 + (uz < 0 ? -1 : (uz >= nc ? 1 : 0));
+    const int nx = (ux + nc) % nc, ny = (uy + nc) % nc, nz = (uz + nc) % nc;
     const int cell = (nx * nc + ny) * nc + nz;
     c0 = d.cell_start[cell];
     len = d.cell_start[cell + 1] - c0;
@@ -232,6 +270,9 @@ __device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
     len = max(0, min(32 * d.nl_cpl, d.n_nonp - c0));
   }
   constexpr int MAXE = 8;  // entries one lane keeps per candidate (images)
+  __shared__ int ebuf[NL_THREADS / 32][NL_EBUF];
+  int* eb = ebuf[(threadIdx.x >> 5) % (NL_THREADS / 32)];
+  int nb = 0;  // entries staged (the same on every lane)
 #pragma unroll 1
   for (int t = 0; t < len; t += 32) {
     const int k = t + lane;
@@ -251,9 +292,9 @@ __device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
         own = (((i + c) & 1) == 0) ? (i == lo) : (i != lo);
       }
       const float dfx = rc4.x - ri.x, dfy = rc4.y - ri.y, dfz = rc4.z - ri.z;
-      const unsigned mx = own ? img_mask(dfx, Lf, Rlin) : 0u;
-      const unsigned my = mx ? img_mask(dfy, Lf, Rlin) : 0u;
-      const unsigned mz = my ? img_mask(dfz, Lf, Rlin) : 0u;
+      const unsigned mx = own ? (cells ? img_bit(dfx, kxc, Lf, Rlin) : img_mask(dfx, Lf, Rlin)) : 0u;
+      const unsigned my = mx ? (cells ? img_bit(dfy, kyc, Lf, Rlin) : img_mask(dfy, Lf, Rlin)) : 0u;
+      const unsigned mz = my ? (cells ? img_bit(dfz, kzc, Lf, Rlin) : img_mask(dfz, Lf, Rlin)) : 0u;
       if (mz) {
         const bool same = d.pos_mol[c] == moli;
         // the image code of the same-molecule zero image in the wrapped frame
@@ -302,7 +343,8 @@ __device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
         }
       }
     }
-    // one reservation per warp: inclusive prefix of the lane counts
+    // the round's entries go to the warp's staging buffer at the inclusive
+    // prefix of the lane counts (flushed first when they would not fit)
     int incl = ne;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -310,17 +352,15 @@ __device__ __forceinline__ void b_k_nlist(const Dev& d, int bx) {
       if (lane >= o) incl += v;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    int base = 0;
-    if (lane == 31 && total > 0) base = atomicAdd(&d.nl_cnt[i], total);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    const int first = base + incl - ne;
-    for (int k = 0; k < ne; ++k) {
-      if (first + k < d.nl_cap)
-        row[first + k] = ents[k];
-      else
-        atomicOr(d.err, ERR_NLIST);
+    if (nb + total > NL_EBUF) {
+      nlist_flush(d, i, row, eb, nb, lane);
+      nb = 0;
     }
+    for (int k = 0; k < ne; ++k) eb[nb + incl - ne + k] = ents[k];
+    nb += total;
+    __syncwarp();
   }
+  nlist_flush(d, i, row, eb, nb, lane);
 }
 
 __global__ void __launch_bounds__(NL_THREADS) k_nlist(const __grid_constant__ Dev d) { b_k_nlist(d, blockIdx.x); }
@@ -333,7 +373,7 @@ __global__ void __launch_bounds__(NL_THREADS) k_nlist_b(const Dev* __restrict__ 
 // pseudo-particle site list: one thread per (pseudo atom, site position)
 __global__ void k_plist(Dev d) {
   const double L = d.box;
-  const double R2 = __dmul_rn(d.thresh[3], d.thresh[3]);
+  const double R2 = d.thresh[11];
   const int e = blockIdx.y;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= d.n_nonp) return;
@@ -1084,7 +1124,7 @@ __device__ __forceinline__ void b_k_bonded(const Dev& d, int bx) {
       const int a = d.bond_atoms[2 * bi.term], c = d.bond_atoms[2 * bi.term + 1];
       const AtomInfo A = d.ainfo_atom[a], Cc = d.ainfo_atom[c];
       const int lmax = A.log2P > Cc.log2P ? A.log2P : Cc.log2P;
-      const double w = 1.0 / (double)(1 << lmax);
+      const double w = pow2_neg(lmax);
       const int ra = A.row0 + (s >> (lmax - A.log2P)) * A.stride;
       const int rcw = Cc.row0 + (s >> (lmax - Cc.log2P)) * Cc.stride;
       const double k = d.bond_par[2 * bi.term], r0 = d.bond_par[2 * bi.term + 1];
@@ -1105,7 +1145,7 @@ __device__ __forceinline__ void b_k_bonded(const Dev& d, int bx) {
       const AtomInfo A1 = d.ainfo_atom[a1], O = d.ainfo_atom[o], A2 = d.ainfo_atom[a2];
       int lmax = A1.log2P > O.log2P ? A1.log2P : O.log2P;
       lmax = lmax > A2.log2P ? lmax : A2.log2P;
-      const double w = 1.0 / (double)(1 << lmax);
+      const double w = pow2_neg(lmax);
       const int r1 = A1.row0 + (s >> (lmax - A1.log2P)) * A1.stride;
       const int ro = O.row0 + (s >> (lmax - O.log2P)) * O.stride;
       const int r2i = A2.row0 + (s >> (lmax - A2.log2P)) * A2.stride;
@@ -1200,7 +1240,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
   const AtomInfo pe = d.pinfo[e];
   const int row_e = pe.row0 + s * pe.stride;
   const double4_32a xe = d.Xw[row_e];
-  const double wgt = 1.0 / (double)(1 << pe.log2P);
+  const double wgt = pow2_neg(pe.log2P);
   const int cnt = min(d.pl_cnt[e], d.pl_cap);
   const int* lst = d.pl + (size_t)e * d.pl_cap;
   const double rc = d.rc, rc2 = d.rc2;

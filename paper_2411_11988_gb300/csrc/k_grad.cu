@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(GRAD_THREADS) k_grad_nb(Dev d, unsigned long l
     const AtomInfo ai = d.ainfo[pos];
     const int row_i = ai.row0 + b * ai.stride;
     const double4_32a xi = d.Xw[row_i];
-    const double wgt = 1.0 / (double)(1 << ai.log2P);
+    const double wgt = pow2_neg(ai.log2P);
     const int cnt = min(d.nl_cnt[pos], d.nl_cap);
     const int* lst = d.nl + (size_t)pos * d.nl_cap;
     for (int e = lane; e < cnt; e += 32) {
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(GRAD_THREADS) k_grad_pseudo(Dev d, int ta, int
   const int s = w - base;
   const AtomInfo pe = d.pinfo[e];
   const double4_32a xe = d.Xw[pe.row0 + s * pe.stride];
-  const double wgt = 1.0 / (double)(1 << pe.log2P);
+  const double wgt = pow2_neg(pe.log2P);
   const int cnt = min(d.pl_cnt[e], d.pl_cap);
   const int* lst = d.pl + (size_t)e * d.pl_cap;
   double g[7] = {0, 0, 0, 0, 0, 0, 0};

@@ -726,7 +726,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   }
   p.o_pl = A.add(sizeof(int) * (size_t)std::max(1, p.n_pseudo) * p.pl_cap);
   p.o_plcnt = A.add(sizeof(int) * std::max(1, p.n_pseudo));
-  p.o_thresh = A.add(sizeof(double) * 8);
+  p.o_thresh = A.add(sizeof(double) * 12);  // 4 radii, 9 binary32 screen constants, R^2, R_pseudo^2
   p.o_efix = A.add(sizeof(unsigned long long) * E_NSLOTS);
   p.o_err = A.add(sizeof(int) * 4);
   p.o_step = A.add(sizeof(long long));
@@ -1116,6 +1116,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.nl = (int*)(w + p.o_nl);
   d.nl_cnt = (int*)(w + p.o_nlcnt);
   d.nc = p.nc;
+  d.cell_inv = p.nc > 0 ? (float)(p.nc / sys->box) : 0.0f;
   d.cell_start = (int*)(w + p.o_cstart);
   d.cell_atoms = (int*)(w + p.o_catoms);
   d.cell_ok = (int*)(w + p.o_cok);

@@ -198,12 +198,14 @@ struct Dev {
   int* nl_cnt;                 // [n_nonp]
   // cell list of the neighbour search (nc >= 3 cells per side; 0: all pairs)
   int nc;                      // cells per side, cell side L / nc
+  float cell_inv;              // nc / L
   int* cell_start;             // [nc^3 + 1] first sorted slot of each cell
   int* cell_atoms;             // [n_nonp] atom positions ordered by cell
   int* cell_ok;                // 1 when this step's list radius fits the cell side
   int* pl;                     // [n_pseudo*pl_cap]
   int* pl_cnt;                 // [n_pseudo]
-  double* thresh;              // [4] d_max, list radius, d_max pseudo, pseudo radius
+  double* thresh;              // [12] d_max, list radius, d_max pseudo, pseudo radius; 9 binary32
+                               // screen constants from byte 32; [10] R^2, [11] R_pseudo^2
   unsigned long long* E_fix;   // [E_NSLOTS]
   int* err;                    // [1]
   long long* step_ctr;         // [1] completed steps
@@ -241,6 +243,10 @@ __device__ __forceinline__ long long fixs(double v, int scale_log2, int* bad) {
 }
 
 __device__ __forceinline__ long long fix44(double v, int wshift, int* bad) { return fixs(v, 44 - wshift, bad); }
+
+// 2^-l (0 <= l <= 1022) assembled from its bits: the exact value of
+// 1.0 / (1 << l) without a division
+__device__ __forceinline__ double pow2_neg(int l) { return __hiloint2double((1023 - l) << 20, 0); }
 
 // Binary64 value of v * 2^-scale_log2 by integer instructions (normalise
 // with a leading-zero count, assemble exponent and mantissa); exact for
