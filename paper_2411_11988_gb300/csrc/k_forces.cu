@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(PAIR64_THREADS) k_pair64_b(const Dev* __restri
 // each lane walks the P* / P_i fine slices of its bead, s = b (P*/P_i) + k,
 // meeting partner bead s >> log2(P* / P_t). The displacement of a term is
 // the entry's bead-0 displacement plus the two beads' binary32 offsets from
-// their bead 0, so no large cancellation enters. Items hold ~2^10 terms
+// their bead 0, so no large cancellation enters. Items hold ~2^11 terms
 // whatever the bead counts and are handed out from a counter.
 //
 // The damped-shifted-force (or Ewald real-space) Coulomb comes from a

@@ -18,7 +18,7 @@ constexpr int BIG_CL_MAX = 16;  // CTAs per large-P tile (one thread-block clust
 constexpr int BIG_SMEM_TARGET = 100 * 1024;  // per-CTA shared memory of a large-P tile at most
 constexpr int PROP_SMEM_MAX = 200 * 1024;
 constexpr int P32_CH = 32;      // list entries per lane group of one FP64 pair item
-constexpr int LG_P32_TERMS = 10; // default log2 of the bead-pair terms of one FP32 pair item (Dev::p32_lgt)
+constexpr int LG_P32_TERMS = 11; // default log2 of the bead-pair terms of one FP32 pair item (Dev::p32_lgt)
 // shared memory of one CTA of a large-P propagation tile of na atoms split
 // over a cluster of cl CTAs: the twiddles, the bead-column and frequency
 // rows of the packed complex columns, and the owned q and p modes
