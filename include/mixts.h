@@ -19,8 +19,11 @@
  * atoms) bead b of the atom of within-type rank k is row off_t + b*N_t + k.
  *
  * Ownership: the caller owns q, p, f and the workspace (device memory,
- * e.g. torch tensors). The library owns only the host handle; it calls no
- * cudaMalloc. All device work is queued on the caller's stream.
+ * e.g. torch tensors). The library owns the host handle and, once a handle
+ * steps, one side stream and five events of its own; it calls no
+ * cudaMalloc. All device work is ordered on the caller's stream: work that
+ * runs beside other work goes to the side stream, forked from the caller's
+ * stream and joined back into it (with events) before the call returns.
  *
  * Errors: every entry point returns a mixts_status. Conditions detected on
  * the device (neighbour-list overflow, non-finite or out-of-range forces,
