@@ -1244,7 +1244,9 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
   const int cnt = min(d.pl_cnt[e], d.pl_cap);
   const int* lst = d.pl + (size_t)e * d.pl_cap;
   const double rc = d.rc, rc2 = d.rc2;
-  double fex = 0.0, fey = 0.0, fez = 0.0, ep = 0.0, vir = 0.0;
+  // the electron bead's sums in fixed point per term: the site list's order
+  // is set by the parallel list build, and integer sums do not depend on it
+  long long kx = 0, ky = 0, kz = 0, ke = 0, kv = 0;
   int nev = 0, bad = 0;
   const int ps_hi_min = __double2hiint(d.ps_smin);
   for (int k = chunk * 32 + lane; k < cnt; k += 32 * nch) {
@@ -1275,20 +1277,18 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo64(Dev d) {
         vsf = v - pp.vrc - (r - rc) * pp.dvrc;
         fru = -(dv - pp.dvrc) / r;
       }
-      ep += wgt * vsf;
       const double fr = wgt * fru;  // force on the site along d
       const double fx = fr * dx, fy = fr * dy, fz = fr * dz;
-      fex -= fx;
-      fey -= fy;
-      fez -= fz;
-      vir += fr * r2;
+      ke += fixs(wgt * vsf, 40, &bad);
+      kv += fixs(fr * r2, 40, &bad);
+      kx -= fix44(fx, 0, &bad);
+      ky -= fix44(fy, 0, &bad);
+      kz -= fix44(fz, 0, &bad);
       ++nev;
       fadd3w(d.F_fix, row_c, fx, fy, fz, &bad);
     }
   }
-  // lane partials to fixed point by bit assembly, then exact integer sums
-  long long kx = fix44(fex, 0, &bad), ky = fix44(fey, 0, &bad), kz = fix44(fez, 0, &bad);
-  long long ke = fixs(ep, 40, &bad), kv = fixs(vir, 40, &bad);
+  // exact integer sums over the lanes
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     kx += __shfl_xor_sync(0xffffffffu, kx, o);

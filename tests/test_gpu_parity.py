@@ -283,6 +283,32 @@ def test_nlist_overflow_reported(gpu):
     m.close()
 
 
+@pytest.mark.parametrize("case", ["water", "electron"])
+def test_side_stream_steps_equal_serial_order(gpu, case):
+    """The default step runs the bonded terms, the pseudopotential sweep, the
+    finalisation and the large-P clusters beside the other kernels on a side
+    stream; the per-phase timing mode runs everything in order on one
+    stream. Fixed-point accumulation makes the two bit-identical."""
+    if case == "water":
+        s = _c1(seed=9)
+    else:
+        s = synth.water_box(64, synth.density_box_length(64), 8, 2, seed=4, ion=dict(synth.systems.ION3),
+                            electron_P=1024)
+    a = gpu.MixTS(s, seed=5, dt=0.1)
+    a.step(13)
+    b = gpu.MixTS(s, seed=5, dt=0.1)
+    b.set_timing(True)
+    b.step(13)
+    assert np.array_equal(a.q.cpu().numpy(), b.q.cpu().numpy())
+    assert np.array_equal(a.p.cpu().numpy(), b.p.cpu().numpy())
+    assert np.array_equal(a.f.cpu().numpy(), b.f.cpu().numpy())
+    ea, eb = a.estimators(), b.estimators()
+    for k in ("V", "KE_beads", "E_spring", "H_conserved", "heat", "virial"):
+        assert ea[k] == eb[k], k
+    a.close()
+    b.close()
+
+
 def test_graph_steps_equal_plain_launches(gpu):
     """mixts_step by captured-graph replays (10 steps per launch) and by plain
     launches give the same state bit for bit."""
