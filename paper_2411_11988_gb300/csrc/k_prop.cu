@@ -950,7 +950,7 @@ size_t batch_prop_smem(const Dev& d) {
 
 // propagation (types with P <= SMALL_P) and step finalisation of every
 // member of a batch, one launch per kernel
-int launch_step_batched(const BatchGeom& g, cudaStream_t s, int mode) {
+int launch_step_batched(const BatchGeom& g, cudaStream_t s, int mode, int parts) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_prop_small_b, cudaFuncAttributeMaxDynamicSharedMemorySize, PROP_SMEM_MAX);
@@ -958,12 +958,15 @@ int launch_step_batched(const BatchGeom& g, cudaStream_t s, int mode) {
   }
   const int r = g.nm + 1;
   int n = 0;
-  if (g.blocks[BK_PROP] > 0) {
+  if ((parts & 1) && g.blocks[BK_PROP] > 0) {
     k_prop_small_b<<<g.blocks[BK_PROP], PROP_THREADS, g.prop_smem, s>>>(g.devs, g.pfx + BK_PROP * r, g.nm, mode);
     ++n;
   }
-  k_final_b<<<g.blocks[BK_FINAL], 1024, 0, s>>>(g.devs, g.pfx + BK_FINAL * r, g.nm, mode);
-  return n + 1;
+  if (parts & 2) {
+    k_final_b<<<g.blocks[BK_FINAL], 1024, 0, s>>>(g.devs, g.pfx + BK_FINAL * r, g.nm, mode);
+    ++n;
+  }
+  return n;
 }
 
 int launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type) {

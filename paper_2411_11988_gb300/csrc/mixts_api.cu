@@ -1706,13 +1706,45 @@ static mixts_status batch_capture_persistent(mixts_handle h) {
     st = cuda_check(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "capture stream");
     if (st != MIXTS_OK) return st;
   }
+  ensure_side(h);
   st = cuda_check(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
   if (st != MIXTS_OK) return st;
   const BatchGeom& g = h->geom;
-  long long nk = launch_step_batched(g, h->cap, PM_START);
-  for (int i = 0; i < K; ++i) {
-    nk += launch_forces_batched(g, h->cap);
-    nk += launch_step_batched(g, h->cap, i + 1 < K ? (PM_END | PM_EST | PM_START) : (PM_END | PM_EST | PM_PCART));
+  cudaStream_t s = h->cap;
+  long long nk = 0;
+  if (h->side) {
+    // as a single handle's step: each step's finalisation and the next
+    // step's bonded terms run on the side stream beside the neighbour
+    // search (and the bonded terms beside the pair sweep); the pair sweep
+    // waits for the finalisation (it clears the energy accumulators), the
+    // propagation for both
+    nk += launch_step_batched(g, s, PM_START, 1);
+    int fmode = PM_START;
+    for (int i = 0; i < K; ++i) {
+      cudaEventRecord(h->ev_post, s);
+      cudaStreamWaitEvent(h->side, h->ev_post, 0);
+      nk += launch_step_batched(g, h->side, fmode, 2);
+      cudaEventRecord(h->ev_fin, h->side);
+      nk += launch_forces_batched_part(g, h->side, 2);
+      cudaEventRecord(h->ev_join, h->side);
+      nk += launch_forces_batched_part(g, s, 0);
+      cudaStreamWaitEvent(s, h->ev_fin, 0);
+      nk += launch_forces_batched_part(g, s, 1);
+      cudaStreamWaitEvent(s, h->ev_join, 0);
+      fmode = i + 1 < K ? (PM_END | PM_EST | PM_START) : (PM_END | PM_EST | PM_PCART);
+      nk += launch_step_batched(g, s, fmode, 1);
+    }
+    cudaEventRecord(h->ev_post, s);
+    cudaStreamWaitEvent(h->side, h->ev_post, 0);
+    nk += launch_step_batched(g, h->side, fmode, 2);
+    cudaEventRecord(h->ev_fin, h->side);
+    cudaStreamWaitEvent(s, h->ev_fin, 0);
+  } else {
+    nk += launch_step_batched(g, s, PM_START);
+    for (int i = 0; i < K; ++i) {
+      nk += launch_forces_batched(g, s);
+      nk += launch_step_batched(g, s, i + 1 < K ? (PM_END | PM_EST | PM_START) : (PM_END | PM_EST | PM_PCART));
+    }
   }
   cudaGraph_t gr = nullptr;
   st = cuda_check(h, cudaStreamEndCapture(h->cap, &gr), "end capture");

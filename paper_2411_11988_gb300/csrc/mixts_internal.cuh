@@ -485,7 +485,8 @@ struct BatchGeom {
   int precision;
 };
 
-int launch_step_batched(const BatchGeom& g, cudaStream_t s, int mode);  // propagation + finalisation
+// propagation (parts bit 1) and finalisation (bit 2) of every member
+int launch_step_batched(const BatchGeom& g, cudaStream_t s, int mode, int parts = 3);
 int launch_forces_batched(const BatchGeom& g, cudaStream_t s);           // list, pair sweep, bonded
 int launch_forces_batched_part(const BatchGeom& g, cudaStream_t s, int part);  // 0 list, 1 pair, 2 bonded
 void batch_block_counts(const Dev& d, int* counts);                       // BK_KINDS blocks of one member
