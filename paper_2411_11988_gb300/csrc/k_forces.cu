@@ -498,7 +498,7 @@ __device__ __forceinline__ void dsf_direct(const Dev& d, double s, double* g, do
 // point; the partner's bead gets the reaction.
 // ---------------------------------------------------------------------------
 // Work items of the FP64 sweep for the current list: every owner row gets
-// (slice blocks) x (chunks of P32_CH entries per lane group) items, only as
+// (slice blocks) x (chunks of P64_CH entries per lane group) items, only as
 // many chunks as its row holds. One CTA per 1024 rows reserves a contiguous
 // range of the item array (the counter was cleared with the list) and writes
 // its rows' items in row order.
@@ -513,7 +513,7 @@ __device__ __forceinline__ void b_k_pair_items(const Dev& d, int bx) {
     const int cnt = min(d.nl_cnt[i], d.nl_cap);
     const int lgP = d.ainfo[i].log2P;
     const int lgPp = lgP < 5 ? lgP : 5;
-    const int per = P32_CH << (5 - lgPp);
+    const int per = P64_CH << (5 - lgPp);
     nch = (cnt + per - 1) / per;
     lgsb = lgP - lgPp;
     n = nch << lgsb;
@@ -617,8 +617,8 @@ __device__ __forceinline__ void b_k_pair64(const Dev& d, int bx) {
     const int lgPp = lgPi < 5 ? lgPi : 5;  // log2 of the lanes per group
     const int lgG = 5 - lgPp;
     const int cnt = min(d.nl_cnt[pos], d.nl_cap);
-    const int e0 = ch * (P32_CH << lgG);
-    const int e1 = min(cnt, e0 + (P32_CH << lgG));
+    const int e0 = ch * (P64_CH << lgG);
+    const int e1 = min(cnt, e0 + (P64_CH << lgG));
     const int sl = lane & ((1 << lgPp) - 1), grp = lane >> lgPp;
     const int b = (sb << lgPp) + sl;  // owner bead of this lane
     const int oi = tOff[ai.type];

@@ -713,7 +713,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   {  // FP64 pair items: at most every row's slice blocks times 32-entry chunks of a full row
     const int lgM = p.n_classes > 0 ? p.cls_log2P[0] : 0;
     const size_t nsbm = lgM > 5 ? (size_t)1 << (lgM - 5) : 1;
-    size_t nitems = (size_t)p.n_nonp * nsbm * ((p.nl_cap + P32_CH - 1) / P32_CH);
+    size_t nitems = (size_t)p.n_nonp * nsbm * ((p.nl_cap + P64_CH - 1) / P64_CH);
     if (prm->precision == MIXTS_FP32_FORCES) {
       // FP32 items: per row and partner type at most ceil(entries / 1) + 1 chunks of >= 1 entry per group...
       // bounded by one item per entry and slice block plus one partial item per type
@@ -1108,11 +1108,7 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.pseudo_chunks = prm->precision == MIXTS_FP32_FORCES ? 8 : 4;  // site-list slices per pseudo bead (measured)
   d.nl_cpl = 4;
   d.p32_lgt = LG_P32_TERMS;
-  d.p64_nch = (p.nl_cap + P32_CH - 1) / P32_CH;  // at most: one lane group, P32_CH entries per item
-  {  // FP32 pair items: P32_CH candidates for each of the 32 / min(P_max, 32) lane groups
-    const int lgG = 5 - std::min(d.lgPmax_nb, 5);
-    d.p32_nch = (p.nl_cap + (P32_CH << lgG) - 1) / (P32_CH << lgG);
-  }
+  d.p64_nch = (p.nl_cap + P64_CH - 1) / P64_CH;  // at most: one lane group, P64_CH entries per item
   d.nl = (int*)(w + p.o_nl);
   d.nl_cnt = (int*)(w + p.o_nlcnt);
   d.nc = p.nc;

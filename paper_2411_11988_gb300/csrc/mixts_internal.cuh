@@ -17,7 +17,7 @@ constexpr int NC_MAX = 16;      // cells per side of the neighbour search at mos
 constexpr int BIG_CL_MAX = 16;  // CTAs per large-P tile (one thread-block cluster) at most
 constexpr int BIG_SMEM_TARGET = 100 * 1024;  // per-CTA shared memory of a large-P tile at most
 constexpr int PROP_SMEM_MAX = 200 * 1024;
-constexpr int P32_CH = 32;      // list entries per lane group of one FP64 pair item
+constexpr int P64_CH = 16;      // list entries per lane group of one FP64 pair item (8: 0.3 %, 32: 3.5 %, 64: 19 % slower)
 constexpr int LG_P32_TERMS = 11; // default log2 of the bead-pair terms of one FP32 pair item (Dev::p32_lgt)
 // shared memory of one CTA of a large-P propagation tile of na atoms split
 // over a cluster of cl CTAs: the twiddles, the bead-column and frequency
@@ -129,7 +129,6 @@ struct Dev {
   int mc_off[MT];       // offset of the ModeCoef rows
   int pair_grid, pair32_grid, pseudo_chunks;  // persistent grid sizes, site-list split
   int nl_cpl;                                 // list candidates per lane of one list warp
-  int p32_nch;                                // FP32 pair items per owner row and slice block (list chunks)
   int p32_lgt;                                // log2 of the bead-pair terms of one FP32 pair item (tunable)
   int p64_nch;                                // FP64 slice-parallel items per owner row and slice block (bound)
   int2* pitems;                               // FP64 pair items of the current list: (owner pos, sb << 16 | chunk)
