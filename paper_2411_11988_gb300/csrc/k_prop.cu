@@ -16,7 +16,7 @@
 
 namespace mx {
 
-constexpr int PROP_THREADS = 384;  // one thread per element of a P x C tile (P C = 384)
+constexpr int PROP_THREADS = 3 * PROP_TILE_BEADS;  // one thread per element of a P x C tile
 constexpr int NPART = 6;  // KE, spring, CV, Rg, heat(end), heat(start)
 
 __device__ __forceinline__ void block_sum6(double* v, double* red) {
@@ -167,7 +167,7 @@ __device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
   extern __shared__ double sm[];
   __shared__ double red[(PROP_THREADS / 32) * NPART];
   __shared__ long long s_step;
-  __shared__ long long s_d2[128];
+  __shared__ long long s_d2[PROP_TILE_BEADS];
   const PropTile tl = d.tiles[bx];
   const int t = tl.type, P = d.P[t], N = d.N[t], k0 = tl.k0, na = tl.na;
   const int C = 3 * na;
@@ -853,7 +853,7 @@ __global__ void k_gauss(Dev d, uint32_t step, uint32_t stage, uint64_t dof0, lon
 // launchers
 // ---------------------------------------------------------------------------
 static size_t small_smem(int P) {
-  const int C = 3 * (128 / P);
+  const int C = 3 * (PROP_TILE_BEADS / P);
   return sizeof(double) * ((size_t)P * P + 5 * (size_t)P * C);
 }
 

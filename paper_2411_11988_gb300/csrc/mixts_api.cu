@@ -589,7 +589,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
   for (int t = 0; t < p.nt; ++t) {
     const int P = s->P_type[t];
     if (P > SMALL_P || p.N[t] == 0) continue;
-    const int apt = std::max(1, 128 / P);
+    const int apt = std::max(1, PROP_TILE_BEADS / P);
     for (int k0 = 0; k0 < p.N[t]; k0 += apt) {
       p.tiles.push_back(PropTile{t, k0, std::min(apt, p.N[t] - k0), (int)p.slot_type.size()});
       p.slot_type.push_back(t);

@@ -12,6 +12,7 @@ namespace mx {
 constexpr int MT = MIXTS_MAX_TYPES;
 constexpr int MAX_CLASSES = 12;
 constexpr int SMALL_P = 64;     // types with P <= SMALL_P propagate in one fused tile kernel
+constexpr int PROP_TILE_BEADS = 128;  // beads (P x atoms) of one small-P propagation tile
 constexpr int BIG_MAXA = 64;    // atoms per large-P propagation tile at most
 constexpr int NC_MAX = 16;      // cells per side of the neighbour search at most (NC_MAX^3 counted in shared memory)
 constexpr int BIG_CL_MAX = 16;  // CTAs per large-P tile (one thread-block cluster) at most
