@@ -113,7 +113,7 @@ def test_neighbour_lists_bit_exact(gpu, case):
     m.close()
 
 
-@pytest.mark.parametrize("P_e", [128, 256, 1024])
+@pytest.mark.parametrize("P_e", [128, 256, 512, 1024])
 def test_step_path_spread_and_lists(gpu, P_e):
     """After a step, the lists built from the propagation kernel's bead
     spreads (the large-P types' maximum gathered over a thread-block
@@ -186,7 +186,8 @@ def _run_both(s, nsteps, **kw):
     return m, run
 
 
-@pytest.mark.parametrize("case", ["c1", "mixed16", "mixed128", "h64", "h1_o4", "h4_o8", "electron1024", "h128_o256"])
+@pytest.mark.parametrize("case", ["c1", "mixed16", "mixed128", "mixed512", "h64", "h1_o4", "h4_o8", "electron1024",
+                                  "h128_o256"])
 def test_one_step_matches_oracle(gpu, case):
     if case == "c1":
         s = _c1(seed=1)
@@ -201,9 +202,9 @@ def test_one_step_matches_oracle(gpu, case):
         s = synth.water_box(256, 18.6, 8, 1, seed=2, ion=dict(synth.systems.ION3), electron_P=1024)
     elif case == "h64":  # the largest bead count of the fused small-P propagation tile
         s = synth.water_box(8, synth.density_box_length(8), 64, 16, seed=11)
-    else:
-        s = _mixed(16 if case == "mixed16" else 128, seed=9)
-    m, run = _run_both(s, 1, dt=0.1 if case in ("mixed16", "mixed128", "electron1024") else 0.25)
+    else:  # mixed512: the four-step split 16 x 32 over a 16-CTA cluster (one frequency row per CTA)
+        s = _mixed({"mixed16": 16, "mixed128": 128, "mixed512": 512}[case], seed=9)
+    m, run = _run_both(s, 1, dt=0.1 if case in ("mixed16", "mixed128", "mixed512", "electron1024") else 0.25)
     q, p, f = (x.cpu().numpy() for x in (m.q, m.p, m.f))
     assert np.abs(q - run.q).max() < 1e-11 * np.abs(run.q).max()
     assert np.abs(p - run.p).max() < FTOL * 10 * np.sqrt(np.mean(run.p ** 2))
