@@ -152,6 +152,86 @@ __device__ __forceinline__ void nm_inverse_parts(const double* Cm, int P, int C,
   }
 }
 
+// Second fold (P >= 4, h = P/2 even, q = h/2). The cosine-like modes are
+// even or odd under j -> h - j as k is even or odd, the sine-like ones odd
+// or even; after nm_fold, rows j and h - j of the s part (0 <= j < q) become
+// e_j = f_j + f_{h-j} and o_j = f_j - f_{h-j}, and rows P - j and P - h + j of
+// the d part (1 <= j < q) become d_j + d_{h-j} and d_j - d_{h-j}; the middle
+// rows q and P - q stay. Each mode's sum then runs over a quarter of the beads.
+__device__ __forceinline__ void nm_fold2(double* x, int P, int C, int tid, int nt) {
+  const int h = P / 2, q = h / 2;
+  const int n1 = q * C, n2 = (q - 1) * C;
+  for (int e = tid; e < n1 + n2; e += nt) {
+    if (e < n1) {
+      const int j = e / C, c = e - (e / C) * C;
+      const double a = x[j * C + c], b = x[(h - j) * C + c];
+      x[j * C + c] = a + b;
+      x[(h - j) * C + c] = a - b;
+    } else {
+      const int e2 = e - n1;
+      const int j = 1 + e2 / C, c = e2 - (e2 / C) * C;
+      const double a = x[(P - j) * C + c], b = x[(P - h + j) * C + c];
+      x[(P - j) * C + c] = a + b;
+      x[(P - h + j) * C + c] = a - b;
+    }
+  }
+}
+
+// out[k][c] = sum_j C[j][k] x_j from the twice-folded rows (nm_fold2); the
+// middle row enters only where its coefficient (cos or sin of a multiple of
+// pi/2) is not zero
+__device__ __forceinline__ void nm_forward_folded2(const double* Cm, int P, int C, const double* f, double* out,
+                                                   int tid, int nt) {
+  const int h = P / 2, q = h / 2;
+  for (int e = tid; e < P * C; e += nt) {
+    const int k = e / C, c = e - (e / C) * C;
+    double a = 0.0;
+    if (k <= h) {
+      if ((k & 1) == 0) {
+        for (int j = 0; j < q; ++j) a = fma(Cm[j * P + k], f[j * C + c], a);
+        a = fma(Cm[q * P + k], f[q * C + c], a);
+      } else {
+        for (int j = 0; j < q; ++j) a = fma(Cm[j * P + k], f[(h - j) * C + c], a);
+      }
+    } else {
+      if ((k & 1) == 0) {
+        for (int j = 1; j < q; ++j) a = fma(Cm[j * P + k], f[(P - h + j) * C + c], a);
+      } else {
+        for (int j = 1; j < q; ++j) a = fma(Cm[j * P + k], f[(P - j) * C + c], a);
+        a = fma(Cm[q * P + k], f[(P - q) * C + c], a);
+      }
+    }
+    out[e] = a;
+  }
+}
+
+// even and odd parts of the inverse from the even- and odd-k halves of each
+// sum: A_j, A_{h-j} = Ae_j +/- Ao_j (0 <= j <= q), B_j = Be_j + Bo_j and
+// B_{h-j} = Bo_j - Be_j (1 <= j <= q); same rows as nm_inverse_parts
+__device__ __forceinline__ void nm_inverse_parts2(const double* Cm, int P, int C, const double* qm, double* ev,
+                                                  double* od, int tid, int nt) {
+  const int h = P / 2, q = h / 2;
+  const int na = (q + 1) * C, nb = q * C;
+  for (int e = tid; e < na + nb; e += nt) {
+    if (e < na) {
+      const int j = e / C, c = e - (e / C) * C;
+      double ae = 0.0, ao = 0.0;
+      for (int k = 0; k <= h; k += 2) ae = fma(Cm[j * P + k], qm[k * C + c], ae);
+      for (int k = 1; k < h; k += 2) ao = fma(Cm[j * P + k], qm[k * C + c], ao);
+      ev[j * C + c] = ae + ao;
+      if (j != q) ev[(h - j) * C + c] = ae - ao;
+    } else {
+      const int e2 = e - na;
+      const int j = 1 + e2 / C, c = e2 - (e2 / C) * C;
+      double be = 0.0, bo = 0.0;
+      for (int k = h + 2; k < P; k += 2) be = fma(Cm[j * P + k], qm[k * C + c], be);
+      for (int k = h + 1; k < P; k += 2) bo = fma(Cm[j * P + k], qm[k * C + c], bo);
+      od[j * C + c] = be + bo;
+      if (j != q) od[(h - j) * C + c] = bo - be;
+    }
+  }
+}
+
 // value of bead j from the parts (after nm_inverse_parts and a barrier)
 __device__ __forceinline__ double nm_inverse_value(const double* ev, const double* od, int P, int C, int j, int c) {
   const int h = P / 2;
@@ -199,12 +279,21 @@ __device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
     }
   }
   __syncthreads();
+  const bool two_folds = P >= 4;
   if (mode & PM_IMPORT) {
     nm_fold(Xc, P, C, tid, nt);
     nm_fold(Fb, P, C, tid, nt);
     __syncthreads();
-    nm_forward_folded(Cm, P, C, Xc, Qn, tid, nt);
-    nm_forward_folded(Cm, P, C, Fb, Pn, tid, nt);
+    if (two_folds) {
+      nm_fold2(Xc, P, C, tid, nt);
+      nm_fold2(Fb, P, C, tid, nt);
+      __syncthreads();
+      nm_forward_folded2(Cm, P, C, Xc, Qn, tid, nt);
+      nm_forward_folded2(Cm, P, C, Fb, Pn, tid, nt);
+    } else {
+      nm_forward_folded(Cm, P, C, Xc, Qn, tid, nt);
+      nm_forward_folded(Cm, P, C, Fb, Pn, tid, nt);
+    }
     __syncthreads();
   }
   double part[NPART] = {0, 0, 0, 0, 0, 0};
@@ -225,7 +314,13 @@ __device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
     __syncthreads();
     nm_fold(Fb, P, C, tid, nt);
     __syncthreads();
-    nm_forward_folded(Cm, P, C, Fb, Fn, tid, nt);
+    if (two_folds) {
+      nm_fold2(Fb, P, C, tid, nt);
+      __syncthreads();
+      nm_forward_folded2(Cm, P, C, Fb, Fn, tid, nt);
+    } else {
+      nm_forward_folded(Cm, P, C, Fb, Fn, tid, nt);
+    }
     __syncthreads();
     const double hk = 0.5 * d.dt * d.kcal;  // F in kcal/mol/A -> amu A/fs^2
     const uint32_t s_end = (uint32_t)s_step;
@@ -277,7 +372,10 @@ __device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
   // Cartesian positions and mirrors
   if (mode & (PM_START | PM_QCART)) {
     // Fb and Fn are free here: they hold the even and odd parts
-    nm_inverse_parts(Cm, P, C, Qn, Fb, Fn, tid, nt);
+    if (two_folds)
+      nm_inverse_parts2(Cm, P, C, Qn, Fb, Fn, tid, nt);
+    else
+      nm_inverse_parts(Cm, P, C, Qn, Fb, Fn, tid, nt);
     __syncthreads();
     for (int e = tid; e < PC; e += nt) {
       const int j = e / C, c = e - (e / C) * C;
@@ -314,7 +412,10 @@ __device__ __forceinline__ void b_k_prop_small(const Dev& d, int bx, int mode) {
   }
   if (mode & PM_PCART) {
     __syncthreads();  // the position pass is done with Fb and Fn
-    nm_inverse_parts(Cm, P, C, Pn, Fb, Fn, tid, nt);
+    if (two_folds)
+      nm_inverse_parts2(Cm, P, C, Pn, Fb, Fn, tid, nt);
+    else
+      nm_inverse_parts(Cm, P, C, Pn, Fb, Fn, tid, nt);
     __syncthreads();
     for (int e = tid; e < PC; e += nt) {
       const int j = e / C, c = e - (e / C) * C;
