@@ -101,7 +101,8 @@ __device__ __forceinline__ double bead_dist(double dx, double dy, double dz) { r
 // folded beads s_j = x_j + x_{P-j} and d_j = x_j - x_{P-j} (0 < j < P/2) each
 // sum runs over half the beads; the inverse computes the even part A_j and
 // the odd part B_j for j <= P/2 and writes x_j = A_j + B_j, x_{P-j} = A_j - B_j.
-// Half the multiply-adds of the dense products, in another rounding order.
+// Half the multiply-adds of the dense products, in another rounding order
+// (nm_fold2 below halves them once more for P >= 4).
 // ---------------------------------------------------------------------------
 // in place: row j <- s_j, row P - j <- d_j (0 < j < P/2)
 __device__ __forceinline__ void nm_fold(double* x, int P, int C, int tid, int nt) {
