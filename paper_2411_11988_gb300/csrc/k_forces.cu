@@ -503,6 +503,61 @@ __device__ __forceinline__ void dsf_direct(const Dev& d, double s, double* g, do
 // range of the item array (the counter was cleared with the list) and writes
 // its rows' items in row order.
 constexpr int ITEM_THREADS = 1024;
+
+// chunks (per slice block) and slice blocks of owner row i's FP64 items
+__device__ __forceinline__ void p64_row_items(const Dev& d, int i, int* nch, int* lgsb) {
+  const int cnt = min(d.nl_cnt[i], d.nl_cap);
+  const int lgP = d.ainfo[i].log2P;
+  const int lgPp = lgP < 5 ? lgP : 5;
+  const int per = P64_CH << (5 - lgPp);
+  *nch = (cnt + per - 1) / per;
+  *lgsb = lgP - lgPp;
+}
+
+// exclusive prefix over the rows of the FP64 items per row, built by a
+// whole CTA in shared memory (rpfx[0..n_nonp]); returns the item count
+__device__ int p64_row_prefix(const Dev& d, int* rpfx, int* wtot) {
+  const int nr = d.n_nonp, nt = blockDim.x;
+  const int per_t = (nr + nt - 1) / nt;
+  const int r0 = min((int)threadIdx.x * per_t, nr), r1 = min(r0 + per_t, nr);
+  int run = 0;
+  for (int i = r0; i < r1; ++i) {
+    int nch, lgsb;
+    p64_row_items(d, i, &nch, &lgsb);
+    rpfx[i] = nch << lgsb;
+    run += nch << lgsb;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = nt >> 5;
+  int incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wtot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int v = lane < nw ? wtot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane < nw) wtot[lane] = v;
+  }
+  __syncthreads();
+  int start = (wid > 0 ? wtot[wid - 1] : 0) + incl - run;
+  for (int i = r0; i < r1; ++i) {
+    const int n = rpfx[i];
+    rpfx[i] = start;
+    start += n;
+  }
+  const int total = wtot[nw - 1];
+  if (threadIdx.x == 0) rpfx[nr] = total;
+  __syncthreads();
+  return total;
+}
+
 __device__ __forceinline__ void b_k_pair_items(const Dev& d, int bx) {
   __shared__ int wsum[ITEM_THREADS / 32];
   __shared__ int base;
@@ -510,12 +565,7 @@ __device__ __forceinline__ void b_k_pair_items(const Dev& d, int bx) {
   const int i = bx * ITEM_THREADS + tid;
   int n = 0, nch = 0, lgsb = 0;
   if (i < d.n_nonp) {
-    const int cnt = min(d.nl_cnt[i], d.nl_cap);
-    const int lgP = d.ainfo[i].log2P;
-    const int lgPp = lgP < 5 ? lgP : 5;
-    const int per = P64_CH << (5 - lgPp);
-    nch = (cnt + per - 1) / per;
-    lgsb = lgP - lgPp;
+    p64_row_items(d, i, &nch, &lgsb);
     n = nch << lgsb;
   }
   int incl = n;  // inclusive scan over the block
@@ -585,9 +635,13 @@ __device__ __forceinline__ void b_k_pair64(const Dev& d, int bx) {
     const int nx = e / 25 - 2, ny = (e / 5) % 5 - 2, nz = e % 5 - 2;
     shi[e] = make_longlong4_32a(nx * d.box_fix, ny * d.box_fix, nz * d.box_fix, 0);
   }
+  // the items: from the item array, or (p64_implicit) from a row prefix this
+  // CTA builds after the table in shared memory
+  int* rpfx = (int*)(ftab + 8 * d.dsf_nint);
+  __shared__ int wtot[32];
   __syncthreads();
+  const int n_items = d.p64_implicit ? p64_row_prefix(d, rpfx, wtot) : d.pctr[0];
   const int lane = threadIdx.x & 31;
-  const int n_items = d.pctr[0];
   const double rc = d.rc;
   // r_cut^2 in the 2^-96 A^2 units of the integer squared distances (exact)
   fm::u128 rc2q;
@@ -610,8 +664,28 @@ __device__ __forceinline__ void b_k_pair64(const Dev& d, int bx) {
     if (lane == 0) w = atomicAdd(d.pctr + 1, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_items) break;
-    const int2 it = d.pitems[w];
-    const int pos = it.x, sb = it.y >> 16, ch = it.y & 0xFFFF;
+    int pos, sb, ch;
+    if (d.p64_implicit) {  // the row holding item w: rpfx[pos] <= w < rpfx[pos + 1]
+      int lo = 0, hi = d.n_nonp;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (rpfx[mid] <= w)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      pos = lo;
+      int nch, lgsb;
+      p64_row_items(d, pos, &nch, &lgsb);
+      const int k = w - rpfx[pos];
+      sb = k / nch;
+      ch = k - sb * nch;
+    } else {
+      const int2 it = d.pitems[w];
+      pos = it.x;
+      sb = it.y >> 16;
+      ch = it.y & 0xFFFF;
+    }
     const AtomInfo ai = d.ainfo[pos];
     const int lgPi = ai.log2P;
     const int lgPp = lgPi < 5 ? lgPi : 5;  // log2 of the lanes per group
@@ -1442,13 +1516,19 @@ int launch_nlist(const Dev& d, cudaStream_t s, const int* atom_is_pseudo) {
 }
 
 // persistent grid sizes: resident CTAs per SM times SMs
-void pair_grids(int nt, int nint, int* g64, int* g32) {
+// dynamic shared memory of k_pair64: the interval table, and the row prefix
+// of implicit items
+size_t pair64_smem(const Dev& d) {
+  return PAIR64_SMEM_PER_INTERVAL * (size_t)d.dsf_nint + (d.p64_implicit ? sizeof(int) * ((size_t)d.n_nonp + 1) : 0);
+}
+
+void pair_grids(int nt, size_t smem64, int nint, int* g64, int* g32) {
   int dev = 0, sms = 0, b64 = 0, b32 = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   (void)nt;
   cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_pair64, PAIR64_THREADS, PAIR64_SMEM_PER_INTERVAL * (size_t)nint);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_pair64, PAIR64_THREADS, smem64);
   cudaFuncSetAttribute(k_pair32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_pair32, PAIR_THREADS, PAIR32_SMEM_PER_INTERVAL * (size_t)nint);
   *g64 = std::max(1, b64) * std::max(1, sms);
@@ -1469,7 +1549,7 @@ int launch_pair(const Dev& d, cudaStream_t s) {
     return 2;
   }
   if (d.n_pitems == 0) return 0;
-  const size_t smem = PAIR64_SMEM_PER_INTERVAL * (size_t)d.dsf_nint;
+  const size_t smem = pair64_smem(d);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -1477,10 +1557,14 @@ int launch_pair(const Dev& d, cudaStream_t s) {
   }
   const int nsbm = d.lgPmax_nb > 5 ? 1 << (d.lgPmax_nb - 5) : 1;
   const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;  // bound on the list's items
-  k_pair_items<<<(d.n_nonp + ITEM_THREADS - 1) / ITEM_THREADS, ITEM_THREADS, 0, s>>>(d);
+  int n = 0;
+  if (!d.p64_implicit) {
+    k_pair_items<<<(d.n_nonp + ITEM_THREADS - 1) / ITEM_THREADS, ITEM_THREADS, 0, s>>>(d);
+    ++n;
+  }
   const int wpb64 = PAIR64_THREADS / 32;
   k_pair64<<<(int)std::min<long long>((items + wpb64 - 1) / wpb64, d.pair_grid), PAIR64_THREADS, smem, s>>>(d);
-  return 2;
+  return n + 1;
 }
 
 int launch_bonded(const Dev& d, cudaStream_t s, const AtomInfo* ainfo_atom) {
@@ -1503,7 +1587,7 @@ void batch_block_counts(const Dev& d, int* c) {
     } else {
       const int nsbm = d.lgPmax_nb > 5 ? 1 << (d.lgPmax_nb - 5) : 1;
       const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;
-      c[BK_PAIRA] = (d.n_nonp + ITEM_THREADS - 1) / ITEM_THREADS;
+      c[BK_PAIRA] = d.p64_implicit ? 0 : (d.n_nonp + ITEM_THREADS - 1) / ITEM_THREADS;
       c[BK_PAIRB] = (int)std::min<long long>((items + PAIR64_THREADS / 32 - 1) / (PAIR64_THREADS / 32), d.pair_grid);
     }
   }
@@ -1532,15 +1616,22 @@ int launch_forces_batched_part(const BatchGeom& g, cudaStream_t s, int part) {
       ++n;
     }
   } else if (part == 1) {
-    if (g.blocks[BK_PAIRA] > 0) {
-      if (g.precision == MIXTS_FP32_FORCES) {
+    if (g.precision == MIXTS_FP32_FORCES) {
+      if (g.blocks[BK_PAIRA] > 0) {
         k_list_seg32_b<<<g.blocks[BK_PAIRA], NL_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
         k_pair32_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
-      } else {
-        k_pair_items_b<<<g.blocks[BK_PAIRA], ITEM_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
-        k_pair64_b<<<g.blocks[BK_PAIRB], PAIR64_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
+        n += 2;
       }
-      n += 2;
+    } else {
+      // item arrays only for members too large for the in-kernel row prefix
+      if (g.blocks[BK_PAIRA] > 0) {
+        k_pair_items_b<<<g.blocks[BK_PAIRA], ITEM_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
+        ++n;
+      }
+      if (g.blocks[BK_PAIRB] > 0) {
+        k_pair64_b<<<g.blocks[BK_PAIRB], PAIR64_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
+        ++n;
+      }
     }
   } else if (g.blocks[BK_BONDED] > 0) {
     k_bonded_b<<<g.blocks[BK_BONDED], 64, 0, s>>>(g.devs, pf(BK_BONDED), g.nm);

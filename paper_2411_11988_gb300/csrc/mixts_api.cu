@@ -1102,7 +1102,8 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   d.wrapn = (int4*)(w + p.o_wrapn);
   d.pos_of_atom = (const int*)(w + p.o_pos_of_atom);
   d.spread = (double*)(w + p.o_spread);
-  pair_grids(p.nt, p.dsf_nint, &d.pair_grid, &d.pair32_grid);
+  d.p64_implicit = p.n_nonp <= P64_IMPLICIT_ROWS ? 1 : 0;
+  pair_grids(p.nt, pair64_smem(d), p.dsf_nint, &d.pair_grid, &d.pair32_grid);
   h->full_grid64 = d.pair_grid;
   h->full_grid32 = d.pair32_grid;
   d.pseudo_chunks = prm->precision == MIXTS_FP32_FORCES ? 8 : 4;  // site-list slices per pseudo bead (measured)
@@ -1635,9 +1636,9 @@ static mixts_status batch_upload(mixts_handle h) {
     batch_block_counts(devs[m], c);
     for (int k = 0; k < BK_KINDS; ++k) pfx[(size_t)k * (nm + 1) + m + 1] = pfx[(size_t)k * (nm + 1) + m] + c[k];
     g.prop_smem = std::max(g.prop_smem, batch_prop_smem(devs[m]));
-    g.pair_smem = std::max(g.pair_smem, (devs[m].precision == MIXTS_FP32_FORCES ? (size_t)8 * sizeof(float)
-                                                                                 : (size_t)(6 * sizeof(double) + 8 * sizeof(float))) *
-                                             (size_t)devs[m].dsf_nint);
+    g.pair_smem = std::max(g.pair_smem, devs[m].precision == MIXTS_FP32_FORCES
+                                            ? (size_t)8 * sizeof(float) * (size_t)devs[m].dsf_nint
+                                            : pair64_smem(devs[m]));
   }
   for (int k = 0; k < BK_KINDS; ++k) g.blocks[k] = pfx[(size_t)k * (nm + 1) + nm];
   g.devs = (const Dev*)h->bdev;

@@ -18,6 +18,7 @@ constexpr int NC_MAX = 16;      // cells per side of the neighbour search at mos
 constexpr int BIG_CL_MAX = 16;  // CTAs per large-P tile (one thread-block cluster) at most
 constexpr int BIG_SMEM_TARGET = 100 * 1024;  // per-CTA shared memory of a large-P tile at most
 constexpr int PROP_SMEM_MAX = 200 * 1024;
+constexpr int P64_IMPLICIT_ROWS = 8192;  // FP64 item prefixes in shared memory up to this many rows
 constexpr int P64_CH = 16;      // list entries per lane group of one FP64 pair item (8: 0.3 %, 32: 3.5 %, 64: 19 % slower)
 constexpr int LG_P32_TERMS = 11; // default log2 of the bead-pair terms of one FP32 pair item (Dev::p32_lgt)
 // shared memory of one CTA of a large-P propagation tile of na atoms split
@@ -132,6 +133,7 @@ struct Dev {
   int nl_cpl;                                 // list candidates per lane of one list warp
   int p32_lgt;                                // log2 of the bead-pair terms of one FP32 pair item (tunable)
   int p64_nch;                                // FP64 slice-parallel items per owner row and slice block (bound)
+  int p64_implicit;                           // 1: FP64 items from a row prefix each CTA builds (no item array)
   int2* pitems;                               // FP64 pair items of the current list: (owner pos, sb << 16 | chunk)
   int* pctr;                                  // [0] item count of the current list, [1] next item to hand out
   float4* nlB;                 // FP32 path: list rows regrouped by partner type, (bead-0 displacement, tag)
@@ -433,7 +435,8 @@ int launch_prop(const Dev& d, cudaStream_t s, int mode, cudaStream_t side = null
                 cudaEvent_t ev_join = nullptr);
 int launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type);
 int launch_forces_out(const Dev& d, cudaStream_t s);
-void pair_grids(int nt, int nint, int* g64, int* g32);
+size_t pair64_smem(const Dev& d);  // dynamic shared memory of the FP64 pair sweep
+void pair_grids(int nt, size_t smem64, int nint, int* g64, int* g32);
 int launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out);
 int launch_ewald(const Dev& d, cudaStream_t s);
 
