@@ -78,6 +78,24 @@ def test_fp32_full_list_bit_exact(gpu):
     m.close()
 
 
+def test_fp32_cell_list_search(gpu):
+    """The FP32 path's full lists through the cell search (r_cut 6 A in the
+    24.83 A box: 3 cells per side) equal both orientations of the oracle's
+    canonical list, and the forces agree at 1e-5."""
+    rc = 6.0
+    s = synth.water_box(512, 24.83, 2, 1, seed=21)
+    m = gpu.MixTS(s, precision=gpu.FP32_FORCES, r_cut=rc)
+    m.forces()
+    tl, th = m.nlist(0)
+    ol, dmax, R = oracle.nlist(s, r_cut=rc)
+    assert th[0] == dmax and th[1] == R
+    assert np.array_equal(tl, both_ways(ol))
+    F_or = oracle.forces(s, r_cut=rc)[0]
+    f = m.f.cpu().numpy()
+    assert np.abs(f - F_or).max() / np.sqrt(np.mean(F_or ** 2)) < 1e-5
+    m.close()
+
+
 def test_fp32_step_tracks_fp64(gpu):
     s = _case("c1")
     a = gpu.MixTS(s, precision=gpu.FP32_FORCES, seed=4)
