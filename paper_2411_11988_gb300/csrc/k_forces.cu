@@ -726,10 +726,14 @@ __device__ __forceinline__ void b_k_pair64(const Dev& d, int bx) {
         const PairPar pp = tab[trow + tj];
         double fr = 0.0;
         if (fl & 1) {
-          double g, fg, x = 0.0;
-          const int key = pq >= 6 ? fm::dsf_key(q2, pq, &x) : 0;
+          // interval and offset from the binary64 r^2 (exponent and top six
+          // mantissa bits; the offset from the interval start is exact)
+          double g, fg;
+          const int hi = __double2hiint(r2);
+          const int key = hi >> 14;
           if (key >= base)
-            dsf_poly_split(dtab + 6 * (key - base), ftab + 8 * (key - base), x, &g, &fg);
+            dsf_poly_split(dtab + 6 * (key - base), ftab + 8 * (key - base),
+                           __dsub_rn(r2, __hiloint2double(key << 14, 0)), &g, &fg);
           else
             dsf_direct(d, r2, &g, &fg);
           ec = fma(pp.qq, g, ec);
