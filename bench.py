@@ -70,12 +70,13 @@ def measured_alu_peaks(torch, stream, clocks_idx):
             "method": "mixts_alu_probe: SM-filling grid of 16 independent FMA chains per thread, best of 3"}
 
 
-def ncu_pipe_pct(kernel):
-    """The pipe utilisation ncu recorded for `kernel` in its committed profile
-    summary (profiles/<kernel>_*.md), with the file it came from."""
+def ncu_pipe_pct(kernel, workload):
+    """The pipe utilisation ncu recorded for `kernel` on `workload` in its
+    committed profile summary (profiles/<kernel>_<workload>*.md), with the
+    file it came from; None when no capture of that workload is committed."""
     import glob
     import re
-    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_{workload}*.md"))):
         for line in open(f):
             m = re.match(r"\|\s*sm__(?:pipe_fp64_cycles_active|pipe_fma_cycles_active|inst_executed_pipe_fma)"
                          r"[^|]*\|\s*([\d.]+)\s*%", line)
@@ -85,13 +86,14 @@ def ncu_pipe_pct(kernel):
     return None
 
 
-def ncu_dram_bytes(kernel):
-    """DRAM bytes (read + write) per launch of `kernel` from the ncu capture in
-    its committed profile summary, with the file it came from."""
+def ncu_dram_bytes(kernel, workload):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
+    ncu capture in its committed profile summary, with the file it came from;
+    (None, None) when no capture of that workload is committed."""
     import glob
     import re
     units = {"B": 1.0, "KB": 1e3, "MB": 1e6, "GB": 1e9}
-    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md"))):
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_{workload}*.md"))):
         total, seen = 0.0, False
         for line in open(f):
             if not line.startswith("| dram__bytes_"):
@@ -221,7 +223,7 @@ def single_call_ms(m, torch, stream, steps, flush):
     return sum(a.elapsed_time(b) for a, b in ev) / steps
 
 
-def variant(torch, stream, flush, dev, sysm, dt, precision, steps, seed, peaks=None):
+def variant(torch, stream, flush, dev, sysm, dt, precision, steps, seed, peaks=None, workload="water512"):
     from paper_2411_11988_gb300 import MixTS
     m = MixTS(sysm, T=300.0, dt=dt, tau=100.0, seed=seed, device=str(dev), stream=stream, precision=precision)
     ms, ph, calls, _, _ = timed_run(m, torch, stream, steps, 3, flush)
@@ -237,7 +239,7 @@ def variant(torch, stream, flush, dev, sysm, dt, precision, steps, seed, peaks=N
         pk = peaks["fp32_tflops"] if peaks else FP32_PEAK_TFLOPS
         out["roofline_pair"] = {"bound": "alu", "kernel": "k_pair32", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                                 "frac": ach / pk, "peak_source": "measured FP32 FMA chains" if peaks else "nominal",
-                                "frac_of_nominal": ach / FP32_PEAK_TFLOPS, "ncu": ncu_pipe_pct("k_pair32"),
+                                "frac_of_nominal": ach / FP32_PEAK_TFLOPS, "ncu": ncu_pipe_pct("k_pair32", workload),
                                 "note": "algorithmic flops count each term once"}
     return out
 
@@ -646,7 +648,8 @@ def main():
         for prec, key in [(1, "fp32_forces_ion_electron"), (0, "fp64_ion_electron")]:
             sie = synth.water_box(ie["n_waters"], ie["box_A"], ie["P_H"], ie["P_O"], seed=rank,
                                   ion=dict(synth.systems.ION3), electron_P=ie["P_e"])
-            variants[key] = variant(torch, stream, flush, dev, sie, ie["dt_fs"], prec, vs, rank, peaks)
+            variants[key] = variant(torch, stream, flush, dev, sie, ie["dt_fs"], prec, vs, rank, peaks,
+                                    workload="ion_electron")
             variants[key]["workload"] = ie["workload"]
         variants["batched_64_fp32"] = batch_variant(torch, stream, flush, dev, vs, peaks)
         variants["grad_ion_electron512"] = grad_variant(torch, stream, dev, 100)
@@ -663,7 +666,7 @@ def main():
         per_phase = {k: ph_ms[k] / max(1, ph_calls[k]) for k in ph_ms if ph_calls[k]}
         # DRAM bytes per launch from the kernel's committed ncu summary
         # (L2-resident working set: far below the bytes the kernel touches)
-        traffic, traffic_src = ncu_dram_bytes(kname)
+        traffic, traffic_src = ncu_dram_bytes(kname, args.workload)
         line = {
             "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -683,7 +686,7 @@ def main():
                          "traffic_source": traffic_src,
                          "peak_source": peak_src, "peak_nominal": peak_nom,
                          "frac_of_nominal": achieved / peak_nom, "flops_per_launch": flops, "launch_ms": pair_ms,
-                         "ncu": ncu_pipe_pct(kname)},
+                         "ncu": ncu_pipe_pct(kname, args.workload)},
             "alu_peaks_measured": peaks,
             "phase_ms_per_call": per_phase,
             "cpu_baseline": cb,

@@ -5,8 +5,9 @@
 // rest in integer arithmetic, which is exact:
 //  * squared distances from the 2^-48 A fixed-point displacements, as 128-bit
 //    integers in units of 2^-96 A^2 (the cut-off test is then exact);
-//  * the interval key of the DSF table and the offset x = s - s0 inside the
-//    interval straight from the integer's leading bits;
+//  * the binary64 of r^2 rounded once from the integer, whose top bits give
+//    the interval key of the DSF table (the offset x = s - s0 inside the
+//    interval is then an exact subtraction);
 //  * force components f d rounded once to the fixed point of the
 //    accumulators from the 53-bit mantissa of f times the integer d.
 // The functions compile for the host as well, so that a CPU test can check
@@ -109,24 +110,19 @@ FM_HD double u128_to_dbl(u128 a, int p, int scale) {
   return bits_dbl((e << 52) | (m & 0xFFFFFFFFFFFFFull));
 }
 
-// The DSF interval of s = r2 * 2^-96 A^2 (64 sub-intervals per octave):
-// returns key = (biased binary64 exponent of s << 6) | (its top 6 mantissa
-// bits), the top bits of the binary64 s, and x = s - s0 in A^2, s0 the
-// interval start. Needs an msb p >= 6.
-FM_HD int dsf_key(u128 r2, int p, double* x) {
-  const int sh = p - 6;  // bits of the offset inside the interval
-  const unsigned key = (unsigned)((p - 96 + 1023) << 6) | (unsigned)(shr128(r2, sh).lo & 63ull);
-  u128 off;
-  if (sh >= 64) {
-    off.hi = r2.hi & ((1ull << (sh - 64)) - 1ull);
-    off.lo = r2.lo;
-  } else {
-    off.hi = 0ull;
-    off.lo = r2.lo & ((1ull << sh) - 1ull);
-  }
-  const int q = msb128(off);
-  *x = q < 0 ? 0.0 : u128_to_dbl(off, q, 96);
-  return (int)key;
+// The DSF interval of a positive normal binary64 s (in A^2; 64 sub-intervals
+// per octave): returns key = (biased exponent of s << 6) | (its top 6
+// mantissa bits), i.e. the top 18 bits of s, and x = s - s0, s0 the interval
+// start. s0 <= s < 2 s0 share the exponent, so the subtraction is exact.
+FM_HD int dsf_key(double s, double* x) {
+  const int key = (int)(dbl_bits(s) >> 46);
+  const double s0 = bits_dbl((unsigned long long)key << 46);
+#if defined(__CUDA_ARCH__)
+  *x = __dsub_rn(s, s0);
+#else
+  *x = s - s0;
+#endif
+  return key;
 }
 
 // round(f * d * 2^-k) for a normal or zero binary64 f and |d| < 2^62, with

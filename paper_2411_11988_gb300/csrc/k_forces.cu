@@ -728,12 +728,10 @@ __device__ __forceinline__ void b_k_pair64(const Dev& d, int bx) {
         if (fl & 1) {
           // interval and offset from the binary64 r^2 (exponent and top six
           // mantissa bits; the offset from the interval start is exact)
-          double g, fg;
-          const int hi = __double2hiint(r2);
-          const int key = hi >> 14;
+          double g, fg, x;
+          const int key = fm::dsf_key(r2, &x);
           if (key >= base)
-            dsf_poly_split(dtab + 6 * (key - base), ftab + 8 * (key - base),
-                           __dsub_rn(r2, __hiloint2double(key << 14, 0)), &g, &fg);
+            dsf_poly_split(dtab + 6 * (key - base), ftab + 8 * (key - base), x, &g, &fg);
           else
             dsf_direct(d, r2, &g, &fg);
           ec = fma(pp.qq, g, ec);

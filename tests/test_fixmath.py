@@ -1,7 +1,8 @@
 """The 128-bit integer helpers of the FP64 pair sweep (csrc/fixmath.cuh),
 compiled for the host and checked against exact Python integers: squared
-distances, the DSF interval key and offset, binary64 assembly from 128-bit
-integers, and force components rounded once into the fixed point."""
+distances, binary64 rounding of 128-bit integers, the DSF interval key and
+offset from that binary64, and force components rounded once into the
+fixed point."""
 import os
 import random
 import struct
@@ -20,14 +21,14 @@ DRIVER = r"""
 int main() {
   char op[8];
   while (scanf("%7s", op) == 1) {
-    if (op[0] == 'n') {  // norm2 dx dy dz -> hi lo key x_bits
+    if (op[0] == 'n') {  // norm2 dx dy dz -> hi lo key x_bits s_bits
       long long dx, dy, dz;
       scanf("%lld %lld %lld", &dx, &dy, &dz);
       fm::u128 r = fm::norm2(dx, dy, dz);
       int p = fm::msb128(r);
       double x = 0.0;
-      int key = p >= 6 ? fm::dsf_key(r, p, &x) : -1;
       double s = p >= 0 ? fm::u128_to_dbl(r, p, 96) : 0.0;
+      int key = p >= 0 ? fm::dsf_key(s, &x) : -1;
       printf("%llu %llu %d %llu %llu\n", r.hi, r.lo, key, fm::dbl_bits(x), fm::dbl_bits(s));
     } else {  // mulfix f_bits d k -> result bad
       unsigned long long fb;
@@ -93,18 +94,21 @@ def test_norm2_key_and_offset(driver):
         r2 = a * a + b * b + c * c
         assert (hi << 64) | lo == r2
         p = r2.bit_length() - 1
-        if p >= 6:
-            # key = top bits of the binary64 of s = r2 * 2^-96 (exponent, 6 mantissa bits)
-            assert key == ((p - 96 + 1023) << 6) | ((r2 >> (p - 6)) & 63)
-            off = r2 & ((1 << (p - 6)) - 1)
-            x = _dbl(xb)
-            if off == 0:
-                assert x == 0.0
-            else:
-                assert x == _round_half_up_dbl(off, 96)
-                assert abs(Fraction(x) - Fraction(off, 2 ** 96)) <= Fraction(off, 2 ** 96) * Fraction(1, 2 ** 53)
         if r2:
-            assert _dbl(sb) == _round_half_up_dbl(r2, 96)
+            sv = _dbl(sb)
+            assert sv == _round_half_up_dbl(r2, 96)
+            # key = top 18 bits of the binary64 s (exponent, 6 mantissa bits)
+            assert key == _bits(sv) >> 46
+            s0 = _dbl(key << 46)
+            x = _dbl(xb)
+            # the offset from the interval start is exact
+            assert Fraction(x) == Fraction(sv) - Fraction(s0)
+            assert 0 <= x < s0 / 64
+            if p >= 6:
+                # the interval of the exact integer, unless rounding s carried
+                # it onto the next interval's start
+                k_exact = ((p - 96 + 1023) << 6) | ((r2 >> (p - 6)) & 63)
+                assert key == k_exact or (key == k_exact + 1 and x == 0.0)
 
 
 def _exact_mulfix(f, d, k):
