@@ -159,4 +159,34 @@ FM_HD long long mulfix(double f, long long d, int k, int* bad) {
   return neg ? -(long long)r : (long long)r;
 }
 
+// round(f * 2^scale) for a binary32 f (halves away from zero; subnormal f
+// gives 0), by 32-bit integer instructions: f = m 2^(ex - 150) with a 24-bit
+// m. *bad is set when the result would reach 2^62 in magnitude, or f is not
+// finite. Equal to rounding the exact binary64 of f the same way.
+FM_HD long long fixf(float f, int scale, int* bad) {
+  unsigned u;
+#if defined(__CUDA_ARCH__)
+  u = __float_as_uint(f);
+#else
+  memcpy(&u, &f, 4);
+#endif
+  const int ex = (int)((u >> 23) & 0xFFu);
+  const int sh = ex - 150 + scale;
+  const unsigned m = (u & 0x7FFFFFu) | 0x800000u;
+  long long r;
+  if (ex == 0) {
+    r = 0;
+  } else if (sh > 38) {  // m 2^sh >= 2^62 (and inf, NaN)
+    *bad = 1;
+    r = 0;
+  } else if (sh >= 0) {
+    r = (long long)m << sh;
+  } else if (sh >= -24) {
+    r = (long long)((m + (1u << (-sh - 1))) >> (-sh));
+  } else {
+    r = 0;  // below one half
+  }
+  return (u >> 31) ? -r : r;
+}
+
 }  // namespace fm

@@ -158,7 +158,9 @@ __device__ __forceinline__ void b_k_list_prep(const Dev& d, int bx) {
   }
   for (int i = threadIdx.x; i < d.n_nonp; i += blockDim.x) d.nl_cnt[i] = 0;
   for (int i = threadIdx.x; i < d.n_pseudo; i += blockDim.x) d.pl_cnt[i] = 0;
-  if (threadIdx.x < 2) d.pctr[threadIdx.x] = 0;  // pair items of the new list, and their hand-out counter
+  // pair items of the new list and their hand-out counters (one per window
+  // of the FP32 window sweep)
+  if (threadIdx.x < 2 + (d.p32w ? 1 << d.p32w_lgnw : 0)) d.pctr[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     const double L = d.box;
     const double R = __dadd_rn(d.rc, __dmul_rn(2.0, ds));
@@ -860,6 +862,17 @@ __device__ __forceinline__ int p32_lg_entries(int lgPi, int lgPt, int lgt) {
   return lgE > 0 ? (lgE < cap ? lgE : cap) : 0;
 }
 
+// log2 of the entries of one window item (k_pair32w): 2^lgt terms = entries
+// x pair-grid slices per window (2^lgk, lanes per entry), at most 2^8 entries
+// (the item's count field); the sweep stages them P32W_BUF at a time
+__device__ __forceinline__ int p32w_lg_entries(int lgS, int lgnw, int lgt) {
+  const int lgk = lgS > lgnw ? lgS - lgnw : 0;
+  const int lgE = lgt - lgk;
+  return lgE > 0 ? (lgE < 8 ? lgE : 8) : 0;
+}
+
+constexpr int SEG32_AHEAD = 4;  // rounds of 32 list entries loaded together by k_list_seg32
+
 __device__ __forceinline__ void b_k_list_seg32(const Dev& d, int bx) {
   const int lane = threadIdx.x & 31;
   const int i = (bx * blockDim.x + threadIdx.x) >> 5;
@@ -867,15 +880,22 @@ __device__ __forceinline__ void b_k_list_seg32(const Dev& d, int bx) {
   const int nt = d.n_types;
   const int cnt = min(d.nl_cnt[i], d.nl_cap);
   const int* row = d.nl + (size_t)i * d.nl_cap;
-  // lane u counts the entries whose partner is of type u (n_types <= 16)
+  // lane u counts the entries whose partner is of type u (n_types <= 16);
+  // SEG32_AHEAD rounds of 32 entries are loaded before they are used
   int c_mine = 0;
-  for (int e0 = 0; e0 < cnt; e0 += 32) {
-    const int e = e0 + lane;
-    const int t = e < cnt ? (row[e] >> 7) & 15 : -1;
-    for (int u = 0; u < nt; ++u) {
-      const unsigned m = __ballot_sync(0xffffffffu, t == u);
-      if (lane == u) c_mine += __popc(m);
+  for (int e0 = 0; e0 < cnt; e0 += 32 * SEG32_AHEAD) {
+    int tq[SEG32_AHEAD];
+#pragma unroll
+    for (int q = 0; q < SEG32_AHEAD; ++q) {
+      const int e = e0 + 32 * q + lane;
+      tq[q] = e < cnt ? (row[e] >> 7) & 15 : -1;
     }
+#pragma unroll
+    for (int q = 0; q < SEG32_AHEAD; ++q)
+      for (int u = 0; u < nt; ++u) {
+        const unsigned m = __ballot_sync(0xffffffffu, tq[q] == u);
+        if (lane == u) c_mine += __popc(m);
+      }
   }
   int incl = c_mine;
 #pragma unroll
@@ -889,10 +909,15 @@ __device__ __forceinline__ void b_k_list_seg32(const Dev& d, int bx) {
   // terms each, in a range of the item array reserved with one atomic
   {
     const int lgP = d.ainfo[i].log2P;
-    const int lgsb = lgP > 5 ? lgP - 5 : 0;
-    const int nch = lane < nt ? (c_mine + (1 << p32_lg_entries(lgP, d.log2P[lane], d.p32_lgt)) - 1) >>
-                                    p32_lg_entries(lgP, d.log2P[lane], d.p32_lgt)
-                              : 0;
+    int lgsb, lgE;
+    if (d.p32w) {  // window sweep: slice blocks are the windows, one item array for all
+      lgsb = 0;
+      lgE = lane < nt ? p32w_lg_entries(lgP > d.log2P[lane] ? lgP : d.log2P[lane], d.p32w_lgnw, d.p32_lgt) : 0;
+    } else {
+      lgsb = lgP > 5 ? lgP - 5 : 0;
+      lgE = lane < nt ? p32_lg_entries(lgP, d.log2P[lane], d.p32_lgt) : 0;
+    }
+    const int nch = lane < nt ? (c_mine + (1 << lgE) - 1) >> lgE : 0;
     const int n = nch << lgsb;
     int ni = n;
 #pragma unroll
@@ -904,9 +929,16 @@ __device__ __forceinline__ void b_k_list_seg32(const Dev& d, int bx) {
     int base = 0;
     if (lane == 0 && total > 0) base = atomicAdd(d.pctr, total);
     base = __shfl_sync(0xffffffffu, base, 0) + ni - n;
-    for (int k = 0; k < n; ++k) {
-      const int sb = k / nch, ch = k - sb * nch;
-      d.pitems[base + k] = make_int2(i, (lane << 27) | (sb << 20) | ch);
+    if (d.p32w) {  // window items carry their entries: type << 27 | (count - 1) << 19 | first entry
+      for (int k = 0; k < n; ++k) {
+        const int e0 = next + (k << lgE), m = min(1 << lgE, c_mine - (k << lgE));
+        d.pitems[base + k] = make_int2(i, (lane << 27) | ((m - 1) << 19) | e0);
+      }
+    } else {
+      for (int k = 0; k < n; ++k) {
+        const int sb = k / nch, ch = k - sb * nch;
+        d.pitems[base + k] = make_int2(i, (lane << 27) | (sb << 20) | ch);
+      }
     }
   }
   const int r0i = d.ainfo[i].row0;
@@ -914,26 +946,48 @@ __device__ __forceinline__ void b_k_list_seg32(const Dev& d, int bx) {
   const float bh = d.box_hi, bl = d.box_lo;
   float4* out = d.nlB + (size_t)i * d.nl_cap;
   const unsigned lt_mask = (1u << lane) - 1u;
-  for (int e0 = 0; e0 < cnt; e0 += 32) {
-    const int e = e0 + lane;
-    const int ent = e < cnt ? row[e] : 0;
-    const int t = e < cnt ? (ent >> 7) & 15 : -1;
-    int dest = 0;
-    for (int u = 0; u < nt; ++u) {
-      const unsigned m = __ballot_sync(0xffffffffu, t == u);
-      const int bse = __shfl_sync(0xffffffffu, next, u);
-      if (t == u) dest = bse + __popc(m & lt_mask);
-      if (lane == u) next += __popc(m);
+  for (int e00 = 0; e00 < cnt; e00 += 32 * SEG32_AHEAD) {
+    // the rounds' entries and their partners' bead-0 positions, all loads in
+    // flight before the first is used
+    int entq[SEG32_AHEAD];
+    float4 hq[SEG32_AHEAD], lq[SEG32_AHEAD];
+#pragma unroll
+    for (int q = 0; q < SEG32_AHEAD; ++q) {
+      const int e = e00 + 32 * q + lane;
+      entq[q] = e < cnt ? row[e] : -1;
     }
-    if (e < cnt) {
-      const int row0j = ent >> 11, code = ent & 127;
-      const float nx = (float)(code / 25 - 2), ny = (float)((code / 5) % 5 - 2), nz = (float)(code % 5 - 2);
-      const float4 hj = d.Xf[row0j], lj = d.Xl[row0j];
-      const float bx = ((hj.x - hi.x) + nx * bh) + ((lj.x - lo.x) + nx * bl);
-      const float by = ((hj.y - hi.y) + ny * bh) + ((lj.y - lo.y) + ny * bl);
-      const float bz = ((hj.z - hi.z) + nz * bh) + ((lj.z - lo.z) + nz * bl);
-      const int abase = d.off[t] + ((row0j - d.off[t]) << d.log2P[t]);  // atom-major bead 0 of j
-      out[dest] = make_float4(bx, by, bz, __int_as_float((abase << 4) | t));
+#pragma unroll
+    for (int q = 0; q < SEG32_AHEAD; ++q) {
+      const int row0j = entq[q] >= 0 ? entq[q] >> 11 : r0i;
+      hq[q] = d.Xf[row0j];
+      lq[q] = d.Xl[row0j];
+    }
+#pragma unroll
+    for (int q = 0; q < SEG32_AHEAD; ++q) {
+      const int ent = entq[q];
+      const int t = ent >= 0 ? (ent >> 7) & 15 : -1;
+      int dest = 0;
+      for (int u = 0; u < nt; ++u) {
+        const unsigned m = __ballot_sync(0xffffffffu, t == u);
+        const int bse = __shfl_sync(0xffffffffu, next, u);
+        if (t == u) dest = bse + __popc(m & lt_mask);
+        if (lane == u) next += __popc(m);
+      }
+      if (ent >= 0) {
+        const int row0j = ent >> 11, code = ent & 127;
+        const float nx = (float)(code / 25 - 2), ny = (float)((code / 5) % 5 - 2), nz = (float)(code % 5 - 2);
+        const float4 hj = hq[q], lj = lq[q];
+        const float bx = ((hj.x - hi.x) + nx * bh) + ((lj.x - lo.x) + nx * bl);
+        const float by = ((hj.y - hi.y) + ny * bh) + ((lj.y - lo.y) + ny * bl);
+        const float bz = ((hj.z - hi.z) + nz * bh) + ((lj.z - lo.z) + nz * bl);
+        if (d.p32w) {  // j's first bead in a window stage
+          const int sbase = d.p32w_soff[t] + ((row0j - d.off[t]) << d.p32w_lgwt[t]);
+          out[dest] = make_float4(bx, by, bz, __int_as_float(sbase));
+        } else {  // atom-major bead 0 of j, and j's type
+          const int abase = d.off[t] + ((row0j - d.off[t]) << d.log2P[t]);
+          out[dest] = make_float4(bx, by, bz, __int_as_float((abase << 4) | t));
+        }
+      }
     }
   }
 }
@@ -1136,8 +1190,8 @@ __device__ __forceinline__ void b_k_pair32(const Dev& d, int bx) {
     // then exact integer sums over the groups, which hold the same owner beads
     const float fs = (c.e4 != 0.f ? 1.0f : c.qq) * wgt;
     int bad = 0;
-    long long kx = fixs(f2d_bits(fx * fs), 44, &bad), ky = fixs(f2d_bits(fy * fs), 44, &bad),
-              kz = fixs(f2d_bits(fz * fs), 44, &bad);
+    long long kx = fm::fixf(fx * fs, 44, &bad), ky = fm::fixf(fy * fs, 44, &bad),
+              kz = fm::fixf(fz * fs, 44, &bad);
     for (int o = 1 << lgPp; o < 32; o <<= 1) {
       kx += __shfl_xor_sync(0xffffffffu, kx, o);
       ky += __shfl_xor_sync(0xffffffffu, ky, o);
@@ -1150,8 +1204,8 @@ __device__ __forceinline__ void b_k_pair32(const Dev& d, int bx) {
       atomicAdd(fi + 2, (unsigned long long)kz);
     }
     // every term is seen from both of its atoms: energies carry a factor 1/2
-    long long kl = fixs(f2d_bits(elj * wgt), 39, &bad), kc = fixs(f2d_bits(ec * (c.qq * wgt)), 39, &bad),
-              kv = fixs(f2d_bits(vir * fs), 39, &bad);
+    long long kl = fm::fixf(elj * wgt, 39, &bad), kc = fm::fixf(ec * (c.qq * wgt), 39, &bad),
+              kv = fm::fixf(vir * fs, 39, &bad);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       kl += __shfl_xor_sync(0xffffffffu, kl, o);
@@ -1177,6 +1231,215 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32(const __grid_constant__
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair32_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
   MX_BATCH_ENTER();
   b_k_pair32(d, bx);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 pair sweep over imaginary-time windows (the same terms as k_pair32).
+//
+// A term of the mixTS sum couples bead s >> (log2 P* - log2 P_i) of i with
+// bead s >> (log2 P* - log2 P_j) of j on one slice s of their common grid P*
+// (Eq. (mts-hamiltonian), the coarse-to-fine map): the beads of one stretch of imaginary
+// time interact only with each other. The finest non-pseudo bead grid is cut
+// into 2^lgnw windows; every CTA owns one window and copies the binary32
+// bead offsets of all atoms inside it into shared memory once (for 512
+// waters at H32/O4 and four windows: 8 H beads and one O bead per atom,
+// 136 KB), so the partner beads of every term come from shared memory
+// instead of scattered L2 reads. The CTAs of a window take (owner, partner
+// type, chunk) items from that window's counter; lanes are (pair-grid slice
+// in the window) x (list entry), 2^lgk x 32 / 2^lgk. Each lane's owner-bead
+// partial goes to fixed point, lanes sharing an owner bead are summed
+// exactly, and one atomic per bead and component lands in F_fix.
+// ---------------------------------------------------------------------------
+template <bool LJ>
+__device__ __forceinline__ void pair32w_walk(const float4* buf, int nbuf, int grp, int G, const float4* stg, int pj,
+                                             float4 di, const P32Par& c, const float4* tab, float& fx, float& fy,
+                                             float& fz, float& ec, float& elj, float& vir, int& nev) {
+  for (int l = grp; l < nbuf; l += 2 * G) {
+    const float4 Ba = buf[l], Bb = buf[l + G];
+    const float4 da = stg[__float_as_int(Ba.w) + pj];
+    const float4 db = stg[__float_as_int(Bb.w) + pj];
+    pair32_term<LJ>(c, tab, (Ba.x - di.x) + da.x, (Ba.y - di.y) + da.y, (Ba.z - di.z) + da.z, fx, fy, fz, ec, elj,
+                    vir, nev);
+    pair32_term<LJ>(c, tab, (Bb.x - di.x) + db.x, (Bb.y - di.y) + db.y, (Bb.z - di.z) + db.z, fx, fy, fz, ec, elj,
+                    vir, nev);
+  }
+}
+
+__device__ __forceinline__ void b_k_pair32w(const Dev& d, int bx) {
+  extern __shared__ float4 sm32w[];
+  __shared__ float qqt[MT * MT], e4t[MT * MT], s2t[MT * MT], vrct[MT * MT], dvrct[MT * MT];
+  __shared__ int tLg[MT], tOff[MT], tSoff[MT], tLgw[MT], tB0[MT];
+  __shared__ unsigned long long eacc[5];  // the CTA's LJ, Coulomb, virial, term and LJ-term sums
+  __shared__ int ebad;
+  const int nt = d.n_types;
+  const int lgnw = d.p32w_lgnw;
+  const int g = bx & ((1 << lgnw) - 1);  // this CTA's window
+  float4* tab = sm32w;                   // the binary32 DSF table, 2 float4 per interval
+  float4* stg = tab + 2 * d.dsf_nint;    // the window's bead offsets, type blocks atom-major
+  float4* ebuf = stg + d.p32w_nstage;    // per-warp staged entries
+  for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
+    const PairPar pp = d.pairpar[(e / nt) * MT + (e % nt)];
+    qqt[e] = (float)pp.qq;
+    e4t[e] = (float)pp.e4;
+    s2t[e] = (float)pp.s2;
+    vrct[e] = (float)pp.vrc;
+    dvrct[e] = (float)pp.dvrc;
+  }
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const int lg = d.log2P[t];
+    tLg[t] = lg;
+    tOff[t] = d.off[t];
+    tSoff[t] = d.p32w_soff[t];
+    tLgw[t] = d.p32w_lgwt[t];
+    tB0[t] = lg >= lgnw ? g << (lg - lgnw) : g >> (lgnw - lg);  // first bead of type t in the window
+  }
+  if (threadIdx.x < 5) eacc[threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) ebad = 0;
+  for (int e = threadIdx.x; e < 2 * d.dsf_nint; e += blockDim.x) tab[e] = d.dsf32[e];
+  for (int t = 0; t < nt; ++t) {
+    if (d.pseudo[t]) continue;
+    const int lg = d.log2P[t], lgw = d.p32w_lgwt[t];
+    const int b0 = lg >= lgnw ? g << (lg - lgnw) : g >> (lgnw - lg);
+    const float4* src = d.Xd + d.off[t] + b0;
+    float4* dst = stg + d.p32w_soff[t];
+    const int cnt = d.N[t] << lgw;
+#pragma unroll 4
+    for (int x = threadIdx.x; x < cnt; x += blockDim.x)
+      dst[x] = __ldg(src + ((x >> lgw) << lg) + (x & ((1 << lgw) - 1)));
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int n_items = d.pctr[0];
+  const float rc = (float)d.rc, rc2 = (float)d.rc2, smin = (float)d.dsf_smin;
+  const int kbase = d.dsf_base - ((1023 - 127) << 6);
+  float4* buf = ebuf + (threadIdx.x >> 5) * P32W_BUF;
+  // the warp's energy sums over its items (exact, fixed point)
+  long long sl_lj = 0, sl_c = 0, sl_v = 0;
+  int s_nev = 0, s_nlj = 0, bad = 0;
+  // the next item is pulled and read while the current one is walked
+  int w = 0;
+  if (lane == 0) w = atomicAdd(d.pctr + 2 + g, 1);
+  w = __shfl_sync(0xffffffffu, w, 0);
+  int2 it = w < n_items ? d.pitems[w] : make_int2(0, 0);
+  while (w < n_items) {
+    const int i = it.x, t = it.y >> 27, n = ((it.y >> 19) & 255) + 1, e0 = it.y & 0x7FFFF;
+    int wn = 0;
+    if (lane == 0) wn = atomicAdd(d.pctr + 2 + g, 1);
+    const AtomInfo ai = d.ainfo[i];
+    const int ti = ai.type;
+    const int lgPi = ai.log2P, lgPt = tLg[t];
+    const int lgS = lgPi > lgPt ? lgPi : lgPt;
+    // the pair grid's slices in this window: 2^lgk from s0, or for a grid
+    // coarser than the windows one slice in every 2^(lgnw - lgS)-th window
+    int lgk = 0, s0 = 0;
+    bool none = false;
+    if (lgS >= lgnw) {
+      lgk = lgS - lgnw;
+      s0 = g << lgk;
+    } else {
+      none = (g & ((1 << (lgnw - lgS)) - 1)) != 0;
+      s0 = g >> (lgnw - lgS);
+    }
+    if (!none) {
+      const int G = 32 >> lgk;  // entry groups
+      const int sl = s0 + (lane & ((1 << lgk) - 1)), grp = lane >> lgk;
+      const int bi = sl >> (lgS - lgPi), bj = sl >> (lgS - lgPt);
+      const int pj = bj - tB0[t];
+      const float4 di = stg[tSoff[ti] + ((ai.row0 - tOff[ti]) << tLgw[ti]) + (bi - tB0[ti])];
+      const float4* lst = d.nlB + (size_t)i * d.nl_cap + e0;
+      const float4 far = make_float4(0.f, 0.f, 1e4f, __int_as_float(tSoff[t]));
+      const int k = ti * nt + t;
+      P32Par c;
+      c.rc = rc;
+      c.rc2 = rc2;
+      c.smin = smin;
+      c.kbase = kbase;
+      c.qq = qqt[k];
+      c.e4 = e4t[k];
+      c.s2 = s2t[k];
+      c.vrc = vrct[k];
+      c.dvrc = dvrct[k];
+      const float wgt = __int_as_float((127 - lgS) << 23);  // 1/P*
+      float fx = 0.f, fy = 0.f, fz = 0.f, ec = 0.f, elj = 0.f, vir = 0.f;
+      int nev = 0;
+      // the entries P32W_BUF at a time, each part padded to whole double
+      // rounds with far entries of type t (their stage reads stay inside type
+      // t's first atom)
+      for (int c0 = 0; c0 < n; c0 += P32W_BUF) {
+        const int m = min(P32W_BUF, n - c0);
+        const int nbuf = (m + 2 * G - 1) / (2 * G) * (2 * G);
+        const float4 v0 = lane < m ? __ldg(lst + c0 + lane) : far;  // both loads in flight
+        const float4 v1 = lane + 32 < m ? __ldg(lst + c0 + 32 + lane) : far;
+        if (lane < nbuf) buf[lane] = v0;
+        if (lane + 32 < nbuf) buf[lane + 32] = v1;
+        __syncwarp();
+        if (c.e4 != 0.f)
+          pair32w_walk<true>(buf, nbuf, grp, G, stg, pj, di, c, tab, fx, fy, fz, ec, elj, vir, nev);
+        else
+          pair32w_walk<false>(buf, nbuf, grp, G, stg, pj, di, c, tab, fx, fy, fz, ec, elj, vir, nev);
+        __syncwarp();  // the buffer is refilled next
+      }
+      const float fs = (c.e4 != 0.f ? 1.0f : c.qq) * wgt;
+      long long kx = fm::fixf(fx * fs, 44, &bad), ky = fm::fixf(fy * fs, 44, &bad),
+                kz = fm::fixf(fz * fs, 44, &bad);
+      // exact sums over the lanes of one owner bead: the other entry groups
+      // (lane bits >= lgk) and, for an owner coarser than the pair grid, the
+      // slices inside its bead (lane bits < lgS - lgPi)
+      const int lgc = lgS - lgPi < lgk ? lgS - lgPi : lgk;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        if (o < (1 << lgc) || o >= (1 << lgk)) {
+          kx += __shfl_xor_sync(0xffffffffu, kx, o);
+          ky += __shfl_xor_sync(0xffffffffu, ky, o);
+          kz += __shfl_xor_sync(0xffffffffu, kz, o);
+        }
+      }
+      const int wmask = ((1 << lgc) - 1) | (31 & ~((1 << lgk) - 1));
+      if ((lane & wmask) == 0 && (kx | ky | kz) != 0) {
+        unsigned long long* fi = d.F_fix + 3 * (size_t)(ai.row0 + bi * ai.stride);
+        atomicAdd(fi + 0, (unsigned long long)kx);
+        atomicAdd(fi + 1, (unsigned long long)ky);
+        atomicAdd(fi + 2, (unsigned long long)kz);
+      }
+      // every term is seen from both of its atoms: energies carry a factor 1/2
+      sl_lj += fm::fixf(elj * wgt, 39, &bad);
+      sl_c += fm::fixf(ec * (c.qq * wgt), 39, &bad);
+      sl_v += fm::fixf(vir * fs, 39, &bad);
+      s_nev += nev;  // the warp's count, the same on every lane
+      if (c.e4 != 0.f) s_nlj += nev;
+    }
+    w = __shfl_sync(0xffffffffu, wn, 0);
+    if (w < n_items) it = d.pitems[w];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sl_lj += __shfl_xor_sync(0xffffffffu, sl_lj, o);
+    sl_c += __shfl_xor_sync(0xffffffffu, sl_c, o);
+    sl_v += __shfl_xor_sync(0xffffffffu, sl_v, o);
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    if (sl_lj) atomicAdd(eacc + 0, (unsigned long long)sl_lj);
+    if (sl_c) atomicAdd(eacc + 1, (unsigned long long)sl_c);
+    if (sl_v) atomicAdd(eacc + 2, (unsigned long long)sl_v);
+    if (s_nev) atomicAdd(eacc + 3, (unsigned long long)s_nev);
+    if (s_nlj) atomicAdd(eacc + 4, (unsigned long long)s_nlj);
+    if (bad) ebad = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int slot[5] = {E_LJ, E_COUL, E_VIRIAL, E_NEVAL, E_NLJEVAL};
+    for (int k = 0; k < 5; ++k)
+      if (eacc[k]) atomicAdd(d.E_fix + slot[k], eacc[k]);
+    if (ebad) atomicOr(d.err, ERR_NONFINITE);
+  }
+}
+
+__global__ void __launch_bounds__(P32W_THREADS, 1) k_pair32w(const __grid_constant__ Dev d) { b_k_pair32w(d, blockIdx.x); }
+
+__global__ void __launch_bounds__(P32W_THREADS, 1) k_pair32w_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
+  MX_BATCH_ENTER();
+  b_k_pair32w(d, bx);
 }
 
 // ---------------------------------------------------------------------------
@@ -1468,12 +1731,12 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pseudo32(Dev d) {
     vir = fmaf(fr, r2, vir);
     ++nev;
     unsigned long long* fc = d.F_fix + 3 * (size_t)row_c;
-    atomicAdd(fc + 0, (unsigned long long)fixs(f2d_bits(fx), 44, &bad));
-    atomicAdd(fc + 1, (unsigned long long)fixs(f2d_bits(fy), 44, &bad));
-    atomicAdd(fc + 2, (unsigned long long)fixs(f2d_bits(fz), 44, &bad));
+    atomicAdd(fc + 0, (unsigned long long)fm::fixf(fx, 44, &bad));
+    atomicAdd(fc + 1, (unsigned long long)fm::fixf(fy, 44, &bad));
+    atomicAdd(fc + 2, (unsigned long long)fm::fixf(fz, 44, &bad));
   }
-  long long kx = fixs(f2d_bits(fex), 44, &bad), ky = fixs(f2d_bits(fey), 44, &bad), kz = fixs(f2d_bits(fez), 44, &bad);
-  long long ke = fixs(f2d_bits(ep), 40, &bad), kv = fixs(f2d_bits(vir), 40, &bad);
+  long long kx = fm::fixf(fex, 44, &bad), ky = fm::fixf(fey, 44, &bad), kz = fm::fixf(fez, 44, &bad);
+  long long ke = fm::fixf(ep, 40, &bad), kv = fm::fixf(vir, 40, &bad);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     kx += __shfl_xor_sync(0xffffffffu, kx, o);
@@ -1537,6 +1800,62 @@ void pair_grids(int nt, size_t smem64, int nint, int* g64, int* g32) {
   *g32 = std::max(1, b32) * std::max(1, sms);
 }
 
+// FP32 window sweep geometry: the widest window (at most 8 slices of the
+// finest non-pseudo bead grid) whose bead stage, DSF table and entry buffers
+// fit one CTA's shared memory, and whole multiples of the window count of
+// resident CTAs; p32w = 0 (the gather sweep k_pair32) when none fits
+void pair32w_plan(Dev& d) {
+  d.p32w = 0;
+  if (d.precision != MIXTS_FP32_FORCES || d.n_nonp == 0) return;
+  int dev = 0, sms = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // the single-system and batched kernels share the geometry: plan for the
+  // larger static shared memory of the two
+  cudaFuncAttributes fa, fb;
+  if (cudaFuncGetAttributes(&fa, k_pair32w) != cudaSuccess) return;
+  if (cudaFuncGetAttributes(&fb, k_pair32w_b) != cudaSuccess) return;
+  const size_t stat = std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
+  if (d.nl_cap >= (1 << 19)) return;  // entry offsets of window items have 19 bits
+  const int lgPm = d.lgPmax_nb;
+  for (int lgw = lgPm < 3 ? lgPm : 3; lgw >= 0; --lgw) {
+    const int lgnw = lgPm - lgw;
+    if ((1 << lgnw) > P32W_MAX_NW) break;
+    long long nst = 0;
+    int lgwt[MT] = {0}, soff[MT] = {0};
+    for (int t = 0; t < d.n_types; ++t) {
+      lgwt[t] = d.log2P[t] > lgnw ? d.log2P[t] - lgnw : 0;
+      soff[t] = (int)nst;
+      if (!d.pseudo[t]) nst += (long long)d.N[t] << lgwt[t];
+    }
+    const size_t smem = PAIR32_SMEM_PER_INTERVAL * (size_t)d.dsf_nint +
+                        sizeof(float4) * ((size_t)nst + (size_t)(P32W_THREADS / 32) * P32W_BUF);
+    if (smem + stat > (size_t)optin) continue;
+    // the attribute is the device's limit, so that handles of other sizes
+    // never lower it under one another
+    if (cudaFuncSetAttribute(k_pair32w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_pair32w_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fb.sharedSizeBytes) != cudaSuccess)
+      return;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair32w, P32W_THREADS, smem);
+    if (occ < 1) return;
+    const int nw = 1 << lgnw;
+    d.p32w = 1;
+    d.p32w_lgnw = lgnw;
+    d.p32w_nstage = (int)nst;
+    d.p32w_smem = (int)smem;
+    d.p32w_grid = nw * std::max(1, occ * std::max(1, sms) / nw);
+    for (int t = 0; t < MT; ++t) {
+      d.p32w_lgwt[t] = lgwt[t];
+      d.p32w_soff[t] = soff[t];
+    }
+    return;
+  }
+}
+
 int launch_pair(const Dev& d, cudaStream_t s) {
   const int wpb = PAIR_THREADS / 32;
   if (d.precision == MIXTS_FP32_FORCES) {
@@ -1547,7 +1866,10 @@ int launch_pair(const Dev& d, cudaStream_t s) {
       attr32 = true;
     }
     k_list_seg32<<<(d.n_nonp + wpb - 1) / wpb, NL_THREADS, 0, s>>>(d);
-    k_pair32<<<d.pair32_grid, PAIR_THREADS, PAIR32_SMEM_PER_INTERVAL * (size_t)d.dsf_nint, s>>>(d);
+    if (d.p32w)
+      k_pair32w<<<d.p32w_grid, P32W_THREADS, d.p32w_smem, s>>>(d);
+    else
+      k_pair32<<<d.pair32_grid, PAIR_THREADS, PAIR32_SMEM_PER_INTERVAL * (size_t)d.dsf_nint, s>>>(d);
     return 2;
   }
   if (d.n_pitems == 0) return 0;
@@ -1585,7 +1907,10 @@ void batch_block_counts(const Dev& d, int* c) {
     c[BK_NLIST] = (int)(((long long)d.n_nonp * nlist_parts(d) + NL_THREADS / 32 - 1) / (NL_THREADS / 32));
     if (d.precision == MIXTS_FP32_FORCES) {
       c[BK_PAIRA] = (d.n_nonp + wpb - 1) / wpb;
-      c[BK_PAIRB] = d.pair32_grid;
+      if (d.p32w)
+        c[BK_PAIRW] = d.p32w_grid;
+      else
+        c[BK_PAIRB] = d.pair32_grid;
     } else {
       const int nsbm = d.lgPmax_nb > 5 ? 1 << (d.lgPmax_nb - 5) : 1;
       const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;
@@ -1621,8 +1946,17 @@ int launch_forces_batched_part(const BatchGeom& g, cudaStream_t s, int part) {
     if (g.precision == MIXTS_FP32_FORCES) {
       if (g.blocks[BK_PAIRA] > 0) {
         k_list_seg32_b<<<g.blocks[BK_PAIRA], NL_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
+        ++n;
+      }
+      // members on the window sweep and on the gather sweep (too large for
+      // a window stage)
+      if (g.blocks[BK_PAIRW] > 0) {
+        k_pair32w_b<<<g.blocks[BK_PAIRW], P32W_THREADS, g.pairw_smem, s>>>(g.devs, pf(BK_PAIRW), g.nm);
+        ++n;
+      }
+      if (g.blocks[BK_PAIRB] > 0) {
         k_pair32_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
-        n += 2;
+        ++n;
       }
     } else {
       // item arrays only for members too large for the in-kernel row prefix

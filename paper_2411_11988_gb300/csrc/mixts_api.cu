@@ -722,7 +722,7 @@ Plan make_plan(const mixts_system* s, const mixts_params* prm) {
       p.o_nlseg = A.add(sizeof(int) * (size_t)std::max(1, p.n_nonp) * (p.nt + 1));
     }
     p.o_pitems = A.add(sizeof(int2) * std::max<size_t>(1, nitems));
-    p.o_pctr = A.add(sizeof(int) * 4);
+    p.o_pctr = A.add(sizeof(int) * (4 + P32W_MAX_NW));
   }
   p.o_pl = A.add(sizeof(int) * (size_t)std::max(1, p.n_pseudo) * p.pl_cap);
   p.o_plcnt = A.add(sizeof(int) * std::max(1, p.n_pseudo));
@@ -774,7 +774,7 @@ struct mixts_ctx {
   long long steps_done = 0;
   std::string err;
   int device = 0;
-  int full_grid64 = 0, full_grid32 = 0;  // SM-filling persistent grids
+  int full_grid64 = 0, full_grid32 = 0, full_grid32w = 0;  // SM-filling persistent grids
   // batched handle (n_sys > 1): one sub-context per system, advanced by one
   // captured graph whose branches run the systems concurrently
   std::vector<mixts_ctx*> kids;
@@ -1106,9 +1106,11 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   pair_grids(p.nt, pair64_smem(d), p.dsf_nint, &d.pair_grid, &d.pair32_grid);
   h->full_grid64 = d.pair_grid;
   h->full_grid32 = d.pair32_grid;
+  h->full_grid32w = d.p32w ? d.p32w_grid : 0;
   d.pseudo_chunks = prm->precision == MIXTS_FP32_FORCES ? 8 : 4;  // site-list slices per pseudo bead (measured)
   d.nl_cpl = 4;
   d.p32_lgt = LG_P32_TERMS;
+  pair32w_plan(d);
   d.p64_nch = (p.nl_cap + P64_CH - 1) / P64_CH;  // at most: one lane group, P64_CH entries per item
   d.nl = (int*)(w + p.o_nl);
   d.nl_cnt = (int*)(w + p.o_nlcnt);
@@ -1579,6 +1581,11 @@ void apply_tuning(mixts_handle h, const mixts_batch_tuning& t) {
     const int g32 = (int)ceil(t.grid_scale * k->full_grid32 * share);
     k->d.pair_grid = std::max(1, std::min(k->full_grid64, g64));
     k->d.pair32_grid = std::max(1, std::min(k->full_grid32, g32));
+    if (k->d.p32w) {  // whole multiples of the window count
+      const int nw = 1 << k->d.p32w_lgnw;
+      const int cpw = (int)ceil(t.grid_scale * k->full_grid32w * share / nw);
+      k->d.p32w_grid = nw * std::max(1, std::min(k->full_grid32w / nw, cpw));
+    }
     k->d.nl_cpl = t.nl_cpl;
     k->d.p32_lgt = t.item_lg_terms > 0 ? t.item_lg_terms : LG_P32_TERMS;
   }
@@ -1639,6 +1646,8 @@ static mixts_status batch_upload(mixts_handle h) {
     g.pair_smem = std::max(g.pair_smem, devs[m].precision == MIXTS_FP32_FORCES
                                             ? (size_t)8 * sizeof(float) * (size_t)devs[m].dsf_nint
                                             : pair64_smem(devs[m]));
+    if (devs[m].precision == MIXTS_FP32_FORCES && devs[m].p32w)
+      g.pairw_smem = std::max(g.pairw_smem, (size_t)devs[m].p32w_smem);
   }
   for (int k = 0; k < BK_KINDS; ++k) g.blocks[k] = pfx[(size_t)k * (nm + 1) + nm];
   g.devs = (const Dev*)h->bdev;
@@ -2208,6 +2217,7 @@ extern "C" MIXTS_API mixts_status mixts_potential_grad(mixts_handle h, int ta, i
   dd.pspar = (const PseudoPar*)(w + p.o_pspar_alt);
   dd.precision = MIXTS_FP64;
   dd.full_list = 0;
+  dd.p32w = 0;
   dd.ps_tab = nullptr;  // the tables hold the handle's parameters, not theta's
   unsigned long long* gacc = (unsigned long long*)(w + p.o_gacc);
   cudaMemcpyAsync(w + p.o_pairpar_alt, pairpar.data(), sizeof(PairPar) * MT * MT, cudaMemcpyHostToDevice, s);

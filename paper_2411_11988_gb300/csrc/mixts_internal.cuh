@@ -21,6 +21,12 @@ constexpr int PROP_SMEM_MAX = 200 * 1024;
 constexpr int P64_IMPLICIT_ROWS = 8192;  // FP64 item prefixes in shared memory up to this many rows
 constexpr int P64_CH = 16;      // list entries per lane group of one FP64 pair item (8: 0.3 %, 32: 3.5 %, 64: 19 % slower)
 constexpr int LG_P32_TERMS = 11; // default log2 of the bead-pair terms of one FP32 pair item (Dev::p32_lgt)
+// FP32 pair sweep over imaginary-time windows (k_pair32w): CTA threads,
+// staged list entries per warp (a multiple of 64, so that a padded part
+// stays within it), and the most windows a system may have
+constexpr int P32W_THREADS = 1024;
+constexpr int P32W_BUF = 64;
+constexpr int P32W_MAX_NW = 64;
 // shared memory of one CTA of a large-P propagation tile of na atoms split
 // over a cluster of cl CTAs: the twiddles, the bead-column and frequency
 // rows of the packed complex columns, and the owned q and p modes
@@ -135,7 +141,12 @@ struct Dev {
   int p64_nch;                                // FP64 slice-parallel items per owner row and slice block (bound)
   int p64_implicit;                           // 1: FP64 items from a row prefix each CTA builds (no item array)
   int2* pitems;                               // FP64 pair items of the current list: (owner pos, sb << 16 | chunk)
-  int* pctr;                                  // [0] item count of the current list, [1] next item to hand out
+  int* pctr;                                  // [0] item count of the current list, [1] next item to hand out,
+                                              // [2 + g] next item of window g (k_pair32w)
+  // FP32 window sweep: 1 when on; log2 of the windows; window beads and
+  // stage offset per type; staged beads of one window; dynamic shared memory
+  int p32w, p32w_lgnw, p32w_nstage, p32w_smem, p32w_grid;
+  int p32w_lgwt[MT], p32w_soff[MT];
   float4* nlB;                 // FP32 path: list rows regrouped by partner type, (bead-0 displacement, tag)
   int* nlseg;                  // FP32 path: [n_nonp][n_types + 1] first entry of each partner type in nlB
   float box_lo;                // box - box_hi (binary32)
@@ -437,6 +448,7 @@ int launch_final(const Dev& d, cudaStream_t s, int mode, const int* slot_type);
 int launch_forces_out(const Dev& d, cudaStream_t s);
 size_t pair64_smem(const Dev& d);  // dynamic shared memory of the FP64 pair sweep
 void pair_grids(int nt, size_t smem64, int nint, int* g64, int* g32);
+void pair32w_plan(Dev& d);  // FP32 window sweep geometry (sets d.p32w)
 int launch_gauss(const Dev& d, cudaStream_t s, uint32_t step, uint32_t stage, uint64_t dof0, long n, float* out);
 int launch_ewald(const Dev& d, cudaStream_t s);
 
@@ -477,14 +489,14 @@ __device__ __forceinline__ int batch_member(const int* pfx, int nm, int b) {
   const int bx = bdev_bx_
 
 // per-kernel block-count prefixes of a batched launch (rows of nm + 1 ints)
-enum : int { BK_PREP = 0, BK_NLIST, BK_PAIRA, BK_PAIRB, BK_BONDED, BK_PROP, BK_FINAL, BK_KINDS };
+enum : int { BK_PREP = 0, BK_NLIST, BK_PAIRA, BK_PAIRB, BK_BONDED, BK_PROP, BK_FINAL, BK_PAIRW, BK_KINDS };
 
 struct BatchGeom {
   const Dev* devs;   // device [nm]
   const int* pfx;    // device [BK_KINDS][nm + 1]
   int nm;
   int blocks[BK_KINDS];  // total blocks per kind
-  size_t prop_smem, pair_smem;
+  size_t prop_smem, pair_smem, pairw_smem;  // pairw: the FP32 window sweep's members
   int precision;
 };
 

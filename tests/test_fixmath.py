@@ -17,6 +17,7 @@ HDR = os.path.join(ROOT, "paper_2411_11988_gb300", "csrc", "fixmath.cuh")
 DRIVER = r"""
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include "fixmath.cuh"
 int main() {
   char op[8];
@@ -30,6 +31,15 @@ int main() {
       double s = p >= 0 ? fm::u128_to_dbl(r, p, 96) : 0.0;
       int key = p >= 0 ? fm::dsf_key(s, &x) : -1;
       printf("%llu %llu %d %llu %llu\n", r.hi, r.lo, key, fm::dbl_bits(x), fm::dbl_bits(s));
+    } else if (op[0] == 'f') {  // fixf f_bits scale -> result bad
+      unsigned fb;
+      int sc;
+      scanf("%u %d", &fb, &sc);
+      float f;
+      memcpy(&f, &fb, 4);
+      int bad = 0;
+      long long r = fm::fixf(f, sc, &bad);
+      printf("%lld %d\n", r, bad);
     } else {  // mulfix f_bits d k -> result bad
       unsigned long long fb;
       long long d;
@@ -138,3 +148,46 @@ def test_mulfix_rounds_once(driver):
     out = _run(driver, [f"m {_bits(2.0 ** 40)} {2 ** 52} 4", f"m {_bits(float('inf'))} 3 4"])
     assert [int(t) for t in out[0].split()][1] == 1
     assert [int(t) for t in out[1].split()][1] == 1
+
+
+def _fbits(v):
+    return struct.unpack("<I", struct.pack("<f", v))[0]
+
+
+def _fval(bits):
+    return struct.unpack("<f", struct.pack("<I", bits))[0]
+
+
+def test_fixf_rounds_once(driver):
+    """binary32 to fixed point: round half away from zero of the exact
+    product, 0 for subnormals, the flag at 2^62 and for inf/NaN."""
+    rng = random.Random(11)
+    cases = [(0.0, 44), (-0.0, 44), (1.0, 44), (-1.5, 1), (0.75, 1), (-0.25, 1), (2.0 ** -24, 0),
+             (1.5 * 2.0 ** -25, 0), (2.0 ** -25, 0), (1.0e-40, 44)]
+    for _ in range(4000):
+        f = _fval(_fbits(rng.uniform(-1, 1) * 2.0 ** rng.randint(-60, 30)))
+        cases.append((f, rng.choice([39, 44, rng.randint(0, 50)])))
+    # exact halves: integers + 1/2 scaled
+    for _ in range(500):
+        k = rng.randint(0, 2 ** 22)
+        sc = rng.randint(1, 20)
+        v = (2 * k + 1) / 2.0 ** (sc + 1)
+        cases.append((_fval(_fbits(v)) * rng.choice([1, -1]), sc))
+    out = _run(driver, [f"f {_fbits(f)} {sc}" for f, sc in cases])
+    for (f, sc), line in zip(cases, out):
+        r, bad = (int(t) for t in line.split())
+        if _fbits(abs(f)) < 0x800000:  # zero or subnormal
+            assert (r, bad) == (0, 0)
+            continue
+        v = Fraction(f) * 2 ** sc
+        a = abs(v)
+        want = int(a + Fraction(1, 2))
+        want = -want if v < 0 else want
+        if abs(want) >= 2 ** 62:
+            assert bad == 1
+        else:
+            assert bad == 0 and r == want, (f, sc, r, want)
+    out = _run(driver, [f"f {_fbits(2.0 ** 20)} 44", f"f {_fbits(float('inf'))} 4", f"f {0x7FC00000} 4"])
+    assert [int(t) for t in out[0].split()][1] == 1
+    assert [int(t) for t in out[1].split()][1] == 1
+    assert [int(t) for t in out[2].split()][1] == 1
