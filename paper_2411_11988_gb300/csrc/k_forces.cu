@@ -1013,16 +1013,21 @@ struct P32Par {
 // force stays per unit charge product (the item scales it once). Skipped as
 // a whole when no lane of the warp is inside the cut-off; otherwise
 // branch-free and masked at r_cut. nev counts the warp's in-cut-off terms
-// (the same on every lane).
-template <bool LJ>
+// (the same on every lane). WSKIP = false (lanes on different entries, so a
+// warp is rarely all outside): no skip, and nev counts the lane's own terms.
+template <bool LJ, bool WSKIP = true>
 __device__ __forceinline__ void pair32_term(const P32Par& c, const float4* tab, float dx, float dy, float dz,
                                             float& fx, float& fy, float& fz, float& ec, float& elj, float& vir,
                                             int& nev) {
   const float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
   const bool in = s < c.rc2;
-  const unsigned m = __ballot_sync(0xffffffffu, in);
-  if (m == 0u) return;
-  nev += __popc(m);
+  if (WSKIP) {
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (m == 0u) return;
+    nev += __popc(m);
+  } else {
+    nev += in ? 1 : 0;
+  }
   const float sc = fminf(fmaxf(s, c.smin), c.rc2);
   const int bits = __float_as_int(sc);
   const int key = (bits >> 17) - c.kbase;
@@ -1258,10 +1263,10 @@ __device__ __forceinline__ void pair32w_walk(const float4* buf, int nbuf, int gr
     const float4 Ba = buf[l], Bb = buf[l + G];
     const float4 da = stg[__float_as_int(Ba.w) + pj];
     const float4 db = stg[__float_as_int(Bb.w) + pj];
-    pair32_term<LJ>(c, tab, (Ba.x - di.x) + da.x, (Ba.y - di.y) + da.y, (Ba.z - di.z) + da.z, fx, fy, fz, ec, elj,
-                    vir, nev);
-    pair32_term<LJ>(c, tab, (Bb.x - di.x) + db.x, (Bb.y - di.y) + db.y, (Bb.z - di.z) + db.z, fx, fy, fz, ec, elj,
-                    vir, nev);
+    pair32_term<LJ, false>(c, tab, (Ba.x - di.x) + da.x, (Ba.y - di.y) + da.y, (Ba.z - di.z) + da.z, fx, fy, fz, ec,
+                           elj, vir, nev);
+    pair32_term<LJ, false>(c, tab, (Bb.x - di.x) + db.x, (Bb.y - di.y) + db.y, (Bb.z - di.z) + db.z, fx, fy, fz, ec,
+                           elj, vir, nev);
   }
 }
 
@@ -1405,7 +1410,7 @@ __device__ __forceinline__ void b_k_pair32w(const Dev& d, int bx) {
       sl_lj += fm::fixf(elj * wgt, 39, &bad);
       sl_c += fm::fixf(ec * (c.qq * wgt), 39, &bad);
       sl_v += fm::fixf(vir * fs, 39, &bad);
-      s_nev += nev;  // the warp's count, the same on every lane
+      s_nev += nev;  // this lane's in-cut-off terms
       if (c.e4 != 0.f) s_nlj += nev;
     }
     w = __shfl_sync(0xffffffffu, wn, 0);
@@ -1416,6 +1421,8 @@ __device__ __forceinline__ void b_k_pair32w(const Dev& d, int bx) {
     sl_lj += __shfl_xor_sync(0xffffffffu, sl_lj, o);
     sl_c += __shfl_xor_sync(0xffffffffu, sl_c, o);
     sl_v += __shfl_xor_sync(0xffffffffu, sl_v, o);
+    s_nev += __shfl_xor_sync(0xffffffffu, s_nev, o);
+    s_nlj += __shfl_xor_sync(0xffffffffu, s_nlj, o);
   }
   bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
