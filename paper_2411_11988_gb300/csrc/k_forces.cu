@@ -1444,11 +1444,6 @@ __device__ __forceinline__ void b_k_pair32w(const Dev& d, int bx) {
 
 __global__ void __launch_bounds__(P32W_THREADS, 1) k_pair32w(const __grid_constant__ Dev d) { b_k_pair32w(d, blockIdx.x); }
 
-__global__ void __launch_bounds__(P32W_THREADS, 1) k_pair32w_b(const Dev* __restrict__ devs, const int* __restrict__ pfx, int nm) {
-  MX_BATCH_ENTER();
-  b_k_pair32w(d, bx);
-}
-
 // ---------------------------------------------------------------------------
 // bonded terms: one thread per (term, fine slice)
 // ---------------------------------------------------------------------------
@@ -1813,17 +1808,16 @@ void pair_grids(int nt, size_t smem64, int nint, int* g64, int* g32) {
 // resident CTAs; p32w = 0 (the gather sweep k_pair32) when none fits
 void pair32w_plan(Dev& d) {
   d.p32w = 0;
-  if (d.precision != MIXTS_FP32_FORCES || d.n_nonp == 0) return;
+  // small systems give a 1024-thread CTA too few items per window: they keep
+  // the gather sweep (as do all members of a batched handle)
+  if (d.precision != MIXTS_FP32_FORCES || d.n_nonp < P32W_MIN_ATOMS) return;
   int dev = 0, sms = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  // the single-system and batched kernels share the geometry: plan for the
-  // larger static shared memory of the two
-  cudaFuncAttributes fa, fb;
+  cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, k_pair32w) != cudaSuccess) return;
-  if (cudaFuncGetAttributes(&fb, k_pair32w_b) != cudaSuccess) return;
-  const size_t stat = std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
+  const size_t stat = fa.sharedSizeBytes;
   if (d.nl_cap >= (1 << 19)) return;  // entry offsets of window items have 19 bits
   const int lgPm = d.lgPmax_nb;
   for (int lgw = lgPm < 3 ? lgPm : 3; lgw >= 0; --lgw) {
@@ -1842,9 +1836,7 @@ void pair32w_plan(Dev& d) {
     // the attribute is the device's limit, so that handles of other sizes
     // never lower it under one another
     if (cudaFuncSetAttribute(k_pair32w, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes) != cudaSuccess ||
-        cudaFuncSetAttribute(k_pair32w_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fb.sharedSizeBytes) != cudaSuccess)
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess)
       return;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair32w, P32W_THREADS, smem);
@@ -1912,12 +1904,9 @@ void batch_block_counts(const Dev& d, int* c) {
   c[BK_PREP] = 1;
   if (d.n_nonp > 0) {
     c[BK_NLIST] = (int)(((long long)d.n_nonp * nlist_parts(d) + NL_THREADS / 32 - 1) / (NL_THREADS / 32));
-    if (d.precision == MIXTS_FP32_FORCES) {
+    if (d.precision == MIXTS_FP32_FORCES) {  // members take the gather sweep (p32w = 0)
       c[BK_PAIRA] = (d.n_nonp + wpb - 1) / wpb;
-      if (d.p32w)
-        c[BK_PAIRW] = d.p32w_grid;
-      else
-        c[BK_PAIRB] = d.pair32_grid;
+      c[BK_PAIRB] = d.pair32_grid;
     } else {
       const int nsbm = d.lgPmax_nb > 5 ? 1 << (d.lgPmax_nb - 5) : 1;
       const long long items = (long long)d.n_nonp * nsbm * d.p64_nch;
@@ -1953,17 +1942,8 @@ int launch_forces_batched_part(const BatchGeom& g, cudaStream_t s, int part) {
     if (g.precision == MIXTS_FP32_FORCES) {
       if (g.blocks[BK_PAIRA] > 0) {
         k_list_seg32_b<<<g.blocks[BK_PAIRA], NL_THREADS, 0, s>>>(g.devs, pf(BK_PAIRA), g.nm);
-        ++n;
-      }
-      // members on the window sweep and on the gather sweep (too large for
-      // a window stage)
-      if (g.blocks[BK_PAIRW] > 0) {
-        k_pair32w_b<<<g.blocks[BK_PAIRW], P32W_THREADS, g.pairw_smem, s>>>(g.devs, pf(BK_PAIRW), g.nm);
-        ++n;
-      }
-      if (g.blocks[BK_PAIRB] > 0) {
         k_pair32_b<<<g.blocks[BK_PAIRB], PAIR_THREADS, g.pair_smem, s>>>(g.devs, pf(BK_PAIRB), g.nm);
-        ++n;
+        n += 2;
       }
     } else {
       // item arrays only for members too large for the in-kernel row prefix

@@ -774,7 +774,7 @@ struct mixts_ctx {
   long long steps_done = 0;
   std::string err;
   int device = 0;
-  int full_grid64 = 0, full_grid32 = 0, full_grid32w = 0;  // SM-filling persistent grids
+  int full_grid64 = 0, full_grid32 = 0;  // SM-filling persistent grids
   // batched handle (n_sys > 1): one sub-context per system, advanced by one
   // captured graph whose branches run the systems concurrently
   std::vector<mixts_ctx*> kids;
@@ -1106,7 +1106,6 @@ mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* 
   pair_grids(p.nt, pair64_smem(d), p.dsf_nint, &d.pair_grid, &d.pair32_grid);
   h->full_grid64 = d.pair_grid;
   h->full_grid32 = d.pair32_grid;
-  h->full_grid32w = d.p32w ? d.p32w_grid : 0;
   d.pseudo_chunks = prm->precision == MIXTS_FP32_FORCES ? 8 : 4;  // site-list slices per pseudo bead (measured)
   d.nl_cpl = 4;
   d.p32_lgt = LG_P32_TERMS;
@@ -1581,11 +1580,6 @@ void apply_tuning(mixts_handle h, const mixts_batch_tuning& t) {
     const int g32 = (int)ceil(t.grid_scale * k->full_grid32 * share);
     k->d.pair_grid = std::max(1, std::min(k->full_grid64, g64));
     k->d.pair32_grid = std::max(1, std::min(k->full_grid32, g32));
-    if (k->d.p32w) {  // whole multiples of the window count
-      const int nw = 1 << k->d.p32w_lgnw;
-      const int cpw = (int)ceil(t.grid_scale * k->full_grid32w * share / nw);
-      k->d.p32w_grid = nw * std::max(1, std::min(k->full_grid32w / nw, cpw));
-    }
     k->d.nl_cpl = t.nl_cpl;
     k->d.p32_lgt = t.item_lg_terms > 0 ? t.item_lg_terms : LG_P32_TERMS;
   }
@@ -1646,8 +1640,6 @@ static mixts_status batch_upload(mixts_handle h) {
     g.pair_smem = std::max(g.pair_smem, devs[m].precision == MIXTS_FP32_FORCES
                                             ? (size_t)8 * sizeof(float) * (size_t)devs[m].dsf_nint
                                             : pair64_smem(devs[m]));
-    if (devs[m].precision == MIXTS_FP32_FORCES && devs[m].p32w)
-      g.pairw_smem = std::max(g.pairw_smem, (size_t)devs[m].p32w_smem);
   }
   for (int k = 0; k < BK_KINDS; ++k) g.blocks[k] = pfx[(size_t)k * (nm + 1) + nm];
   g.devs = (const Dev*)h->bdev;
@@ -1681,6 +1673,10 @@ static mixts_status batch_init(const mixts_system* sys, int n_sys, const mixts_p
       return st;
     }
     k->graph_steps = 0;  // members are captured into the batch graph, never on their own
+    // FP32 members take the gather sweep: in one launch for the whole batch
+    // the window sweep's 1024-thread CTAs, sized by the largest member's
+    // stage, ran slower (2.36 against 1.54 ms per step for 64 members)
+    k->d.p32w = 0;
     h->kids.push_back(k);
     off += round_up(n, BATCH_ALIGN);
   }

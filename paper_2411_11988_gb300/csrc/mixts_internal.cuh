@@ -27,6 +27,7 @@ constexpr int LG_P32_TERMS = 11; // default log2 of the bead-pair terms of one F
 constexpr int P32W_THREADS = 1024;
 constexpr int P32W_BUF = 64;
 constexpr int P32W_MAX_NW = 64;
+constexpr int P32W_MIN_ATOMS = 768;  // fewer non-pseudo atoms: the gather sweep k_pair32
 // shared memory of one CTA of a large-P propagation tile of na atoms split
 // over a cluster of cl CTAs: the twiddles, the bead-column and frequency
 // rows of the packed complex columns, and the owned q and p modes
@@ -489,14 +490,14 @@ __device__ __forceinline__ int batch_member(const int* pfx, int nm, int b) {
   const int bx = bdev_bx_
 
 // per-kernel block-count prefixes of a batched launch (rows of nm + 1 ints)
-enum : int { BK_PREP = 0, BK_NLIST, BK_PAIRA, BK_PAIRB, BK_BONDED, BK_PROP, BK_FINAL, BK_PAIRW, BK_KINDS };
+enum : int { BK_PREP = 0, BK_NLIST, BK_PAIRA, BK_PAIRB, BK_BONDED, BK_PROP, BK_FINAL, BK_KINDS };
 
 struct BatchGeom {
   const Dev* devs;   // device [nm]
   const int* pfx;    // device [BK_KINDS][nm + 1]
   int nm;
   int blocks[BK_KINDS];  // total blocks per kind
-  size_t prop_smem, pair_smem, pairw_smem;  // pairw: the FP32 window sweep's members
+  size_t prop_smem, pair_smem;
   int precision;
 };
 

@@ -47,10 +47,18 @@ def _case(name):
         return synth.water_box(512, 24.83, 32, 4, seed=0)
     if name == "c3":
         return synth.water_box(256, 18.6, 8, 1, seed=0, ion=dict(synth.systems.ION3), electron_P=1024)
+    # 768 atoms and more take the window sweep: O-O terms on a grid coarser
+    # than the windows (H32/O1), and H coarser than O (H4/O32)
+    if name in ("w256_h32_o1", "w256_h4_o32"):
+        ph, po = (32, 1) if name == "w256_h32_o1" else (4, 32)
+        s = synth.water_box(256, 19.7, ph, po, seed=21)
+        s.q = s.q + np.random.default_rng(23).normal(0, 0.05, s.q.shape)
+        return s
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("name", ["c1", "c1_spread", "mixed", "h1_o4", "h4_o8", "c2", "c3"])
+@pytest.mark.parametrize("name", ["c1", "c1_spread", "mixed", "h1_o4", "h4_o8", "c2", "c3", "w256_h32_o1",
+                                  "w256_h4_o32"])
 def test_fp32_forces(gpu, name):
     s = _case(name)
     m = gpu.MixTS(s, precision=gpu.FP32_FORCES)
