@@ -1245,17 +1245,17 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair32_b(const Dev* __restrict
 //
 // A term of the mixTS sum couples bead s >> (log2 P* - log2 P_i) of i with
 // bead s >> (log2 P* - log2 P_j) of j on one slice s of their common grid P*
-// (Eq. (mts-hamiltonian), the coarse-to-fine map): the beads of one stretch of imaginary
-// time interact only with each other. The finest non-pseudo bead grid is cut
-// into 2^lgnw windows; every CTA owns one window and copies the binary32
-// bead offsets of all atoms inside it into shared memory once (for 512
-// waters at H32/O4 and four windows: 8 H beads and one O bead per atom,
-// 136 KB), so the partner beads of every term come from shared memory
+// (Eq. (mts-hamiltonian), the coarse-to-fine map): the beads of one stretch
+// of imaginary time interact only with each other. The finest non-pseudo
+// bead grid is cut into 2^lgnw windows; every CTA owns one window and copies
+// the binary32 bead offsets of all atoms inside it into shared memory once
+// (for 512 waters at H32/O4 and four windows: 8 H beads and one O bead per
+// atom, 136 KB), so the partner beads of every term come from shared memory
 // instead of scattered L2 reads. The CTAs of a window take (owner, partner
-// type, chunk) items from that window's counter; lanes are (pair-grid slice
-// in the window) x (list entry), 2^lgk x 32 / 2^lgk. Each lane's owner-bead
-// partial goes to fixed point, lanes sharing an owner bead are summed
-// exactly, and one atomic per bead and component lands in F_fix.
+// type, entry range) items from that window's counter; lanes are (pair-grid
+// slice in the window) x (list entry), 2^lgk x 32 / 2^lgk. Each lane's
+// owner-bead partial goes to fixed point, lanes sharing an owner bead are
+// summed exactly, and one atomic per bead and component lands in F_fix.
 // ---------------------------------------------------------------------------
 template <bool LJ>
 __device__ __forceinline__ void pair32w_walk(const float4* buf, int nbuf, int grp, int G, const float4* stg, int pj,
