@@ -176,9 +176,12 @@ MIXTS_API size_t mixts_workspace_size(const mixts_system* sys, int n_sys, const 
  * a step is launched once for all members (a block finds its member from a
  * prefix of the members' block counts); otherwise the members' own kernels
  * run on parallel graph branches. Trajectories are bit-identical to stepping
- * each system alone (with FP32 forces, while the work-item size is the
- * single-system default of 2^10 terms: another size regroups the binary32
- * partial sums). */
+ * each system alone, with two limits for FP32 forces: members take the
+ * gather sweep, which a standalone handle takes below 768 non-pseudo atoms
+ * only (from 768 atoms it takes the window sweep, which groups the binary32
+ * partial sums differently: agreement then within FP32 rounding), and the
+ * work-item size must be the single-system default of 2^11 terms (another
+ * size regroups the partial sums as well). */
 MIXTS_API mixts_status mixts_init(const mixts_system* sys, int n_sys, const mixts_params* prm, void* workspace,
                         size_t ws_bytes, void* stream, mixts_handle* out);
 
